@@ -1,0 +1,51 @@
+"""O0: Pauli decomposition by explicit Kronecker products (test infrastructure).
+
+Eq. 1 builds sigma^t = sigma^{t_1} (x) ... (x) sigma^{t_n} with numpy.kron, the
+first factor outermost (it indexes the most significant row/column bit, the
+block partition of Eq. 3).  Eq. 2 then gives w_t = 2^-n tr(sigma^t A) by a
+dense matrix product.  Exponential in memory and time: meant for n <= 4.
+"""
+import itertools
+
+import numpy as np
+
+# Sec. II.A: sigma^0..3 = I, X, Y, Z
+SIGMA = (
+    np.array([[1, 0], [0, 1]], dtype=np.complex128),
+    np.array([[0, 1], [1, 0]], dtype=np.complex128),
+    np.array([[0, -1j], [1j, 0]], dtype=np.complex128),
+    np.array([[1, 0], [0, -1]], dtype=np.complex128),
+)
+
+
+def pauli_string_matrix(t):
+    """sigma^t for a sequence t = (t_1, ..., t_n) (Eq. 1)."""
+    m = np.ones((1, 1), dtype=np.complex128)
+    for tj in t:
+        m = np.kron(m, SIGMA[tj])
+    return m
+
+
+def _strings(n):
+    # string order: base 4, t_1 most significant
+    return itertools.product(range(4), repeat=n)
+
+
+def coeffs_kron(A):
+    """All 4^n weights of Eq. 2, string order, by dense products."""
+    A = np.asarray(A, dtype=np.complex128)
+    N = A.shape[0]
+    n = N.bit_length() - 1
+    out = np.empty(4 ** n, dtype=np.complex128)
+    for s, t in enumerate(_strings(n)):
+        out[s] = np.trace(pauli_string_matrix(t) @ A) / N
+    return out
+
+
+def compose_kron(w, n):
+    """A = sum_t w_t sigma^t (Eq. 2, left side), w in string order."""
+    N = 2 ** n
+    A = np.zeros((N, N), dtype=np.complex128)
+    for s, t in enumerate(_strings(n)):
+        A += w[s] * pauli_string_matrix(t)
+    return A
