@@ -1,0 +1,387 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 tensorized Pauli decomposition (arXiv:2310.13421).
+
+Workload (the metric's configuration): one dense 16384 x 16384 complex128
+random Hermitian matrix (n = 14 qubits, 4.29 GB, above L2), decomposed in
+place into its 4^14 Pauli weights.  One step = one full decomposition (all
+passes) of the resident matrix; the pristine input is restored between steps
+outside the timed events.
+
+Prints ONE JSON line (rank 0).  `value` = Pauli coeffs/s over all ranks with
+inputs resident in HBM; `e2e` = the same metric through the C ABI with host
+buffers (pinned), host<->device copies inside the timed region; `roofline`
+= achieved HBM bandwidth of the pass kernel (algorithmic bytes: read + write
+of the matrix per pass launch) against the measured copy peak; `cpu_baseline`
+= the CPU oracle timed on a bounded sample; `extra` = the fp64 butterfly and
+the complex64 plain / compensated forms at n = 15.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Pauli coeffs/s & HBM GB/s (n=14 c128); fp32-compensated vs fp64 speedup"
+UNIT = "coeffs/s"
+N_QUBITS = 14
+SEED = 1002
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--no-extra", action="store_true", help="skip the fp64 / complex64 comparison runs")
+    p.add_argument("--e2e-steps", type=int, default=3)
+    return p.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return float("nan")
+        sm = [num(r[1]) for r in rows]
+        mx = [num(r[2]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        loaded = [s for s, p in zip(sm, (num(r[3]) for r in rows)) if p > 200] or sm
+        return {"sm_mhz": float(np.nanmedian(loaded)), "sm_max_mhz": float(np.nanmax(mx)),
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": float(np.nanmax([num(r[3]) for r in rows]))}
+
+
+# ------------------------------------------------------------------ oracle timing
+
+def oracle_rate(A, n, budget_s=12.0):
+    """CPU oracle (Walsh-Hadamard form, all host cores) on a bounded sample of
+    X-rows of the same matrix: returns (coeffs/s, cores, sample text)."""
+    import oracle
+    N = 2 ** n
+    rng = np.random.default_rng(0)
+    order = rng.permutation(N).astype(np.uint64)
+    done, t0, chunk = 0, time.perf_counter(), 256
+    while done < N and time.perf_counter() - t0 < budget_s:
+        xs = order[done:done + chunk]
+        oracle.coeffs_xrows(A, xs)
+        done += len(xs)
+        chunk = min(chunk * 2, 4096)
+    dt = time.perf_counter() - t0
+    return done * N / dt, oracle.num_threads(), "%d of %d X-rows (all %d Z-masks each) of the n=%d matrix, %.1f s" % (
+        done, N, N, n, dt)
+
+
+# ------------------------------------------------------------------ reference arm
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    from paper_2310_13421_gb300 import synth
+    import oracle
+    n = N_QUBITS
+    A = synth.hermitian(n, seed=SEED)
+    N = 2 ** n
+    rows_per_step = 512
+    rng = np.random.default_rng(1)
+    for _ in range(args.warmup):
+        oracle.coeffs_xrows(A, rng.integers(0, N, size=64).astype(np.uint64))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.coeffs_xrows(A, rng.integers(0, N, size=rows_per_step).astype(np.uint64))
+    dt = time.perf_counter() - t0
+    value = args.steps * rows_per_step * N / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "n=14 dense Hermitian complex128, 16384x16384 (CPU oracle, Walsh-Hadamard form)",
+                   "sample_per_step": "%d X-rows x %d Z-masks" % (rows_per_step, N)},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": "%d steps of %d random X-rows each" % (args.steps, rows_per_step)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------ our arm
+
+def kernel_digest():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2310_13421_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.startswith("tpd_") and f.endswith((".cu", ".cuh", ".h", ".cpp")):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic():
+    """Per-launch DRAM bytes of the pass kernel from the committed ncu summary,
+    if it was taken on the current kernel sources."""
+    p = os.path.join(ROOT, "profiles", "traffic_n14_c128.json")
+    try:
+        with open(p) as fh:
+            d = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    if d.get("kernel_digest") != kernel_digest():
+        return None
+    return d.get("bytes_per_launch")
+
+
+def time_decompose(tpd, L, torch, work, pristine, n, steps, warmup, precision, stream):
+    """Per-step and per-pass device times (ms) of in-place decompositions."""
+    code = L.TPD_C128 if work.dtype == torch.complex128 else L.TPD_C64
+    npass = L.tpd_plan_describe(n, code, L.options(precision=precision))[0]
+    nev = max(npass, 1) + 1
+    wsb = L.tpd_workspace_size(n, code, L.options(precision=precision))
+    ws = torch.empty(max(wsb, 16), dtype=torch.uint8, device=work.device)
+    for _ in range(warmup):
+        work.copy_(pristine)
+        st = L.tpd_decompose(work.data_ptr(), n, code, L.options(precision=precision), ws.data_ptr(), wsb,
+                             stream.cuda_stream)
+        assert st == 0, L.status_string(st)
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(nev)] for _ in range(steps)]
+    for row in evs:            # torch creates the CUDA event on first record
+        for e in row:
+            e.record(stream)
+    torch.cuda.synchronize()
+    for k in range(steps):
+        work.copy_(pristine)                       # restore, outside the events
+        opt = L.options(precision=precision, pass_events=[e.cuda_event for e in evs[k]])
+        st = L.tpd_decompose(work.data_ptr(), n, code, opt, ws.data_ptr(), wsb, stream.cuda_stream)
+        assert st == 0, L.status_string(st)
+    torch.cuda.synchronize()
+    step_ms = [evs[k][0].elapsed_time(evs[k][-1]) for k in range(steps)]
+    pass_ms = [[evs[k][p].elapsed_time(evs[k][p + 1]) for p in range(nev - 1)] for k in range(steps)]
+    return step_ms, pass_ms, npass
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    if not torch.cuda.is_available():
+        print(json.dumps({"metric": METRIC, "error": "no CUDA device"}))
+        return 1
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    import paper_2310_13421_gb300 as tpd
+    from paper_2310_13421_gb300 import _lib as L, synth
+    tpd.build()
+    L.load()
+    n = N_QUBITS
+    N = 2 ** n
+    coeffs = 4 ** n
+    elem = 16
+    A = synth.hermitian(n, seed=SEED + rank)
+    A_pin = torch.from_numpy(A).pin_memory()
+    pristine = A_pin.to("cuda", non_blocking=False)
+    work = torch.empty_like(pristine)
+    stream = torch.cuda.current_stream()
+
+    # ---- device-resident timed region
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    time.sleep(0.3)
+    step_ms, pass_ms, npass = time_decompose(tpd, L, torch, work, pristine, n, args.steps, args.warmup,
+                                             L.TPD_PREC_FIXED, stream)
+    barrier()
+    clk = clocks.stop()
+    total_ms = max_over_ranks(sum(step_ms))
+    ms_per_step = total_ms / args.steps
+    value = world * coeffs * args.steps / (total_ms * 1e-3)
+
+    # roofline of the pass kernel: algorithmic bytes per launch = read + write of the matrix
+    alg_bytes = 2 * coeffs * elem
+    launches = [ms for row in pass_ms for ms in row]
+    mean_launch_ms = float(np.mean(launches))
+    per_pass_ms = [float(np.mean([row[p] for row in pass_ms])) for p in range(npass)]
+    achieved = alg_bytes / (mean_launch_ms * 1e-3) / 1e9
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+    except (OSError, ValueError):
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": measured_traffic(),
+                "kernel": "k_pass<FixedArith,true> (one launch per pass, %d passes)" % npass,
+                "bytes_per_launch": alg_bytes, "per_pass_ms": per_pass_ms,
+                "per_pass_gbs": [alg_bytes / (m * 1e-3) / 1e9 for m in per_pass_ms],
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s"}
+
+    # ---- end to end through the C ABI with pinned host buffers
+    W_pin = torch.empty_like(A_pin).pin_memory()
+    wsb = L.tpd_workspace_size(n, L.TPD_C128, L.options())
+    ws = torch.empty(max(wsb, 16), dtype=torch.uint8, device="cuda")
+    e2e_ms = []
+    for k in range(args.e2e_steps + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        e0.record(stream)
+        st = L.tpd_decompose_host(A_pin.data_ptr(), W_pin.data_ptr(), work.data_ptr(), n, L.TPD_C128,
+                                  L.options(), ws.data_ptr(), wsb, stream.cuda_stream)
+        assert st == 0, L.status_string(st)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if k > 0:  # first call is warm-up
+            e2e_ms.append(e0.elapsed_time(e1))
+    e2e_total = max_over_ranks(sum(e2e_ms))
+    e2e = {"value": world * coeffs * len(e2e_ms) / (e2e_total * 1e-3), "unit": UNIT,
+           "h2d_bytes_per_step": coeffs * elem, "d2h_bytes_per_step": coeffs * elem,
+           "ms_per_step": e2e_total / len(e2e_ms)}
+    # sanity: the host result equals the device result of the same plan
+    ok = torch.equal(W_pin.to("cuda"), work)
+
+    extra = {}
+    if not args.no_extra:
+        # fp64 butterfly (IEEE double, rounded per level) on the same n=14 matrix
+        s64, p64, np64 = time_decompose(tpd, L, torch, work, pristine, n, 5, 2, L.TPD_PREC_PLAIN, stream)
+        f64_ms = float(np.mean(s64))
+        extra["c128_fp64_plain_n14"] = {"ms_per_step": f64_ms, "coeffs_per_s": coeffs / (f64_ms * 1e-3),
+                                        "passes": np64}
+        extra["c128_fixed_n14"] = {"ms_per_step": ms_per_step, "coeffs_per_s": coeffs / (ms_per_step * 1e-3)}
+        del work, pristine
+        torch.cuda.empty_cache()
+        # complex64 at n = 15: plain and compensated fp32 vs fp64 / fixed complex128 of the same matrix
+        n15 = 15
+        A64 = synth.hermitian(n15, seed=1003, dtype=np.complex64)
+        p15 = torch.from_numpy(A64).cuda()
+        w15 = torch.empty_like(p15)
+        res = {}
+        for name, prec in (("plain", L.TPD_PREC_PLAIN), ("compensated", L.TPD_PREC_COMPENSATED)):
+            s, _, npp = time_decompose(tpd, L, torch, w15, p15, n15, 5, 2, prec, stream)
+            res[name] = {"ms_per_step": float(np.mean(s)), "coeffs_per_s": 4 ** n15 / (np.mean(s) * 1e-3),
+                         "passes": npp, "hbm_gbs_per_pass": 2 * 4 ** n15 * 8 / (np.mean(s) / npp * 1e-3) / 1e9}
+            res[name]["_out"] = w15.clone()
+        ref = tpd.decompose(p15.to(torch.complex128), precision="fixed")
+        for name in ("plain", "compensated"):
+            out = res[name].pop("_out").to(torch.complex128)
+            res[name]["rel_err_vs_c128"] = float(torch.linalg.vector_norm(out - ref) / torch.linalg.vector_norm(ref))
+            del out
+        del ref
+        w128 = p15.to(torch.complex128)
+        p128 = w128.clone()
+        s, _, npp = time_decompose(tpd, L, torch, w128, p128, n15, 3, 1, L.TPD_PREC_PLAIN, stream)
+        res["c128_fp64_plain"] = {"ms_per_step": float(np.mean(s)), "passes": npp}
+        extra["n15"] = res
+        extra["speedup_c64_compensated_vs_c128_fp64_n15"] = res["c128_fp64_plain"]["ms_per_step"] / \
+            res["compensated"]["ms_per_step"]
+        del w128, p128, p15, w15
+
+    cpu = None
+    if rank == 0 and world == 1:
+        v, cores, sample = oracle_rate(A, n)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": "n=14 dense random Hermitian, 16384x16384 complex128 (4.29 GB) in place; "
+                               "Re,Im of B ~ N(0,1), A=(B+B^H)/2",
+                   "storage": "complex128", "precision": "fixed (exact int64 block fixed point per pass)",
+                   "passes": npass, "l2": "inputs larger than L2 (4.29 GB vs 126 MB); restored between steps",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+        "clocks": clk, "gpu_launches": args.steps * npass,
+        "e2e_matches_device": bool(ok), "extra": extra,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+    return run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

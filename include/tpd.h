@@ -1,0 +1,164 @@
+/*
+ * tpd.h -- C ABI of libtpd.so: the tensorized Pauli decomposition
+ * (Hantzko, Binkowski, Gupta, arXiv:2310.13421) on one GB300 GPU.
+ *
+ * What is computed.  For A in Mat(2^n), the Pauli weights (Sec. II.A, Eq. 2)
+ *
+ *     w_t = 2^-n tr(sigma^t A),     t in {0,1,2,3}^n = {I,X,Y,Z}^n,
+ *
+ * by the paper's cumulative matrix weights (Eq. 4): for every qubit the four
+ * blocks A11, A12, A21, A22 of a 2x2 block partition become
+ *     I: (A11 + A22)/2,  X: (A12 + A21)/2,  Y: i (A12 - A21)/2,  Z: (A11 - A22)/2,
+ * and by Eq. 5 applying this to all qubits yields the scalars w_t (Sec. III).
+ *
+ * Conventions used by every entry point.
+ *  - Matrices are dense, row-major, N x N with N = 2^n, complex interleaved
+ *    (re, im): complex128 = two doubles, complex64 = two floats.
+ *  - Qubit j = 1..n (tensor factor j of Eq. 1) is row/column index bit n-j:
+ *    the first factor picks the quadrant of Eq. 3.
+ *  - Results are written IN PLACE in "RC layout": the weight of string t sits
+ *    at the flat position r*N + c whose row bit r_{n-j} and column bit c_{n-j}
+ *    satisfy t_j = 2 r_{n-j} + c_{n-j}  (I at (0,0), X at (0,1), Y at (1,0),
+ *    Z at (1,1) of each qubit's 2x2 block, exactly where Eq. 4 puts them).
+ *  - All pointers passed as "device" must be device memory of the current
+ *    CUDA device, owned by the caller; the library never allocates, frees or
+ *    retains them.  All work is enqueued asynchronously on `stream`
+ *    (a cudaStream_t, NULL = legacy default stream).
+ *  - Every argument is checked before anything is enqueued; on error nothing
+ *    is launched and the buffer is untouched.  No entry point traps, asserts
+ *    on the device or waits without a bound.
+ *  - Status codes are returned; tpd_status_string() names them.
+ */
+#ifndef TPD_H_
+#define TPD_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TPD_OK = 0,
+  TPD_ERR_INVALID_ARG = 1,  /* bad n, dtype, precision, count, null pointer */
+  TPD_ERR_UNSUPPORTED = 2,  /* combination not implemented (e.g. COMPENSATED with C128) */
+  TPD_ERR_MISALIGNED = 3,   /* pointer not aligned to the element size */
+  TPD_ERR_WORKSPACE = 4,    /* workspace missing or smaller than *_workspace_size() */
+  TPD_ERR_CUDA = 5,         /* a CUDA call failed (launch error, no device, ...) */
+  TPD_ERR_TIMEOUT = 6       /* a bounded device-side wait gave up (batched path) */
+} tpd_status;
+
+typedef enum {
+  TPD_C128 = 0,             /* complex128 storage (16 bytes per element) */
+  TPD_C64 = 1               /* complex64 storage (8 bytes per element) */
+} tpd_dtype;
+
+/* Arithmetic of the butterfly.  Every mode applies Eq. 4 level by level; they
+ * differ only in how the sums are rounded. */
+typedef enum {
+  TPD_PREC_DEFAULT = 0,      /* C128 -> TPD_PREC_FIXED, C64 -> TPD_PREC_PLAIN */
+  TPD_PREC_PLAIN = 1,        /* IEEE adds in the storage precision (fp64 / fp32),
+                                rounded after every level as in the paper */
+  TPD_PREC_COMPENSATED = 2,  /* C64 only: fp32 sums carried with TwoSum error terms
+                                (Ogita-Rump-Oishi cascaded summation) across the
+                                levels of a pass, one rounding per pass */
+  TPD_PREC_FIXED = 3         /* C128 only: the levels of a pass are summed exactly
+                                in 64-bit integers on a per-tile binary point
+                                (block fixed point), one rounding per pass */
+} tpd_precision;
+
+typedef struct {
+  int precision;    /* tpd_precision */
+  int skip_zero;    /* 1: skip all-zero tiles exactly (the zero-CMW pruning of
+                       Alg. 1/2: Omega = 0 implies all its weights are 0).
+                       Needs a workspace of tpd_workspace_size() bytes. */
+  int tile_bits;    /* 0 = planner default; otherwise log2 of the elements in a
+                       tile (9..13), for tuning */
+  int max_levels;   /* 0 = planner default; otherwise the most qubit levels fused
+                       into one pass (1..6), for tuning */
+  void** pass_events; /* profiling, may be NULL: num_events cudaEvent_t handles
+                       (created by the caller); tpd_decompose / tpd_compose
+                       record event 0 before the first pass and event p+1 after
+                       pass p, on `stream`, for p < num_events - 1 */
+  int num_events;
+} tpd_options;
+
+/* Zero-initialised defaults (precision DEFAULT, no skip, planner tiles). */
+void tpd_options_init(tpd_options* opt);
+
+/* Bytes of device workspace tpd_decompose / tpd_compose need for (n, dtype,
+ * opt): 0 unless opt->skip_zero.  The workspace holds the per-tile nonzero
+ * flags a pass hands to the next.  Returns 0 for invalid arguments. */
+size_t tpd_workspace_size(int n, int dtype, const tpd_options* opt);
+
+/* Pauli decomposition in place (Eq. 2 via Eqs. 3-5).
+ *   A          device, N*N complex of `dtype`, 16-byte (C128) or 8-byte (C64)
+ *              aligned; on return holds 2^-n tr(sigma^t A) in RC layout.
+ *   n          qubits, 1 <= n <= 16 (n = 16 C128 is 64 GiB).
+ *   opt        may be NULL (defaults).
+ *   workspace  device, tpd_workspace_size() bytes, may be NULL when that is 0.
+ *   stream     cudaStream_t.
+ * Errors: INVALID_ARG, UNSUPPORTED, MISALIGNED, WORKSPACE, CUDA. */
+tpd_status tpd_decompose(void* A, int n, int dtype, const tpd_options* opt,
+                         void* workspace, size_t workspace_bytes, void* stream);
+
+/* Pauli composition in place: C holds weights w_t in RC layout, on return it
+ * holds  scale * sum_t w_t sigma^t  (Eq. 2, left side).  With scale = 2^-n
+ * this is the adjoint of tpd_decompose (the Pauli strings are Hermitian, so
+ * the decomposition's adjoint is 2^-n times composition).  Per qubit:
+ * a00 = I + Z, a01 = X - iY, a10 = X + iY, a11 = I - Z.
+ * Arguments as tpd_decompose; scale must be finite and nonzero.  A scale that
+ * is a power of two is applied exactly. */
+tpd_status tpd_compose(void* C, int n, int dtype, double scale, const tpd_options* opt,
+                       void* workspace, size_t workspace_bytes, void* stream);
+
+/* End to end from host memory: copy A_host (N*N complex of `dtype`, host,
+ * ideally pinned) into the caller's device buffer dev_A (device, N*N elements,
+ * aligned as for tpd_decompose), decompose it in place, and copy the weights
+ * (RC layout) back into W_host (host; may equal A_host).  All three steps are
+ * enqueued on `stream` and the call returns without waiting; the host buffers
+ * must stay valid until the stream reaches this point.
+ * Errors as tpd_decompose; host pointers must be non-NULL. */
+tpd_status tpd_decompose_host(const void* A_host, void* W_host, void* dev_A, int n, int dtype,
+                              const tpd_options* opt, void* workspace, size_t workspace_bytes,
+                              void* stream);
+
+/* Device workspace for the batched calls over `count` matrices with qubit
+ * counts ns[0..count) (host array). Returns 0 for invalid arguments. */
+size_t tpd_batched_workspace_size(const int* ns, int count, int dtype, const tpd_options* opt);
+
+/* Batched decomposition in place of `count` independent matrices.
+ *   ptrs_dev   device array of `count` device pointers (matrix i at ptrs_dev[i]).
+ *   ns_dev     device array of `count` ints, ns_dev[i] = n_i (same values as ns).
+ *   ns         host array of the same n_i, 1 <= n_i <= 12, used for planning.
+ *   workspace  device, tpd_batched_workspace_size() bytes (required).
+ * The matrices must not overlap.  The enqueued work depends only on the
+ * arguments (no host synchronisation), so it can be captured in a CUDA graph. */
+tpd_status tpd_decompose_batched(void* const* ptrs_dev, const int* ns_dev, const int* ns,
+                                 int count, int dtype, const tpd_options* opt,
+                                 void* workspace, size_t workspace_bytes, void* stream);
+
+/* Batched composition, scale_mode 0: scale 1, scale_mode 1: scale 2^-n_i
+ * (the adjoint of tpd_decompose_batched).  Arguments as above. */
+tpd_status tpd_compose_batched(void* const* ptrs_dev, const int* ns_dev, const int* ns,
+                               int count, int dtype, int scale_mode, const tpd_options* opt,
+                               void* workspace, size_t workspace_bytes, void* stream);
+
+/* Describe the pass plan the library uses for (n, dtype, opt) as a
+ * NUL-terminated text (one line per pass: levels, tile bits, stages) written
+ * to buf (at most len bytes).  Host only, no device call.  Returns the number
+ * of passes, or -1 on invalid arguments. */
+int tpd_plan_describe(int n, int dtype, const tpd_options* opt, char* buf, size_t len);
+
+/* Name of a status code (static string). */
+const char* tpd_status_string(int status);
+
+/* Library version: major*10000 + minor*100 + patch. */
+int tpd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TPD_H_ */

@@ -15,12 +15,12 @@ Coefficient layout everywhere in the oracle: STRING order, index
 s = sum_j t_j 4^(n-j) with t_1 (the first tensor factor) most significant and
 t in {0,1,2,3} = {I,X,Y,Z}.
 """
-from .core import (coeffs, coeffs_at, coeffs_fwht, coeffs_xrows, compose, grad_weighted_sq,
+from .core import (coeffs, coeffs_at, coeffs_fwht, coeffs_xrows, compose, compose_fwht, grad_weighted_sq,
                    num_threads, string_of_xz, build_library)
 from .kron import pauli_string_matrix, coeffs_kron, compose_kron
 
 __all__ = [
-    "coeffs", "coeffs_at", "coeffs_fwht", "coeffs_xrows", "compose", "grad_weighted_sq",
+    "coeffs", "coeffs_at", "coeffs_fwht", "coeffs_xrows", "compose", "compose_fwht", "grad_weighted_sq",
     "num_threads", "string_of_xz", "build_library",
     "pauli_string_matrix", "coeffs_kron", "compose_kron",
 ]

@@ -45,8 +45,9 @@ def _load():
             lib.oracle_coeffs_at.argtypes = [dp, ctypes.c_int, u64p, ctypes.c_int64, dp]
             lib.oracle_coeffs_xrows.argtypes = [dp, ctypes.c_int, u64p, ctypes.c_int64, dp]
             lib.oracle_compose.argtypes = [dp, ctypes.c_int, dp]
+            lib.oracle_compose_fwht.argtypes = [dp, ctypes.c_int, dp]
             for f in (lib.oracle_coeffs, lib.oracle_coeffs_fwht, lib.oracle_coeffs_at,
-                      lib.oracle_coeffs_xrows, lib.oracle_compose):
+                      lib.oracle_coeffs_xrows, lib.oracle_compose, lib.oracle_compose_fwht):
                 f.restype = ctypes.c_int
             lib.oracle_num_threads.argtypes = []
             lib.oracle_num_threads.restype = ctypes.c_int
@@ -126,14 +127,26 @@ def compose(w, n):
     return A
 
 
+def compose_fwht(w, n):
+    """A = sum_t w_t sigma^t, w in string order, with the inner sums over z
+    done by a Walsh-Hadamard transform per x-mask. O(n 4^n)."""
+    w = np.ascontiguousarray(w, dtype=np.complex128)
+    if w.shape != (4 ** n,):
+        raise ValueError("w must have 4^n entries")
+    A = np.empty((2 ** n, 2 ** n), dtype=np.complex128)
+    if _load().oracle_compose_fwht(_dptr(w), n, _dptr(A)):
+        raise RuntimeError("oracle_compose_fwht failed")
+    return A
+
+
 def grad_weighted_sq(A, weights):
     """Gradient of L(A) = sum_t w_t |c_t|^2, c = decomposition of A, in the
     convention dL/dRe + i dL/dIm.  c is linear in A with adjoint 2^-n times
     composition (the Pauli strings are Hermitian, Sec. II.A), and dL/dconj(c_t)
     = w_t c_t, so grad = 2 * 2^-n * sum_t w_t c_t sigma^t."""
     A, n = _square(A)
-    c = coeffs(A)
-    return compose(2.0 ** (1 - n) * np.asarray(weights, dtype=np.float64) * c, n)
+    c = coeffs_fwht(A)
+    return compose_fwht(2.0 ** (1 - n) * np.asarray(weights, dtype=np.float64) * c, n)
 
 
 def string_of_xz(x, z, n):

@@ -41,6 +41,8 @@
  *                                                                    O(count n 2^n)
  *   oracle_coeffs_fwht     the same for every x                      O(n 4^n)
  *   oracle_compose         A = sum_t w_t sigma^t (Eq. 2, left side)  O(8^n)
+ *   oracle_compose_fwht    the same, the sum over z per x-mask done by
+ *                          the Walsh-Hadamard transform              O(n 4^n)
  *   oracle_num_threads     OpenMP threads used
  */
 #include <stdint.h>
@@ -249,6 +251,36 @@ int oracle_compose(const double* w_, int n, double* A_) {
         for (uint64_t z = 0; z < N; ++z)
           u[z] = times_minus_i_pow(w[string_index(x, z, n)], popc64(x & z));
         for (uint64_t r = 0; r < N; ++r) A[r * N + (r ^ x)] = signed_sum(u, N, r);
+      }
+      free(u);
+    }
+  }
+  return bad;
+}
+
+/* A = sum_t w_t sigma^t, w in string order; for each x the entries
+ * A[r][r^x] = sum_z u[z] (-1)^{popc(z&r)} with u[z] = w_(x,z) (-i)^{popc(x&z)},
+ * i.e. a Walsh-Hadamard transform of u. */
+int oracle_compose_fwht(const double* w_, int n, double* A_) {
+  if (n < 0 || n > 15) return 1;
+  const cplx* w = (const cplx*)w_;
+  cplx* A = (cplx*)A_;
+  const uint64_t N = (uint64_t)1 << n;
+  int bad = 0;
+#pragma omp parallel
+  {
+    cplx* u = (cplx*)malloc(sizeof(cplx) * N);
+    if (!u) {
+#pragma omp atomic write
+      bad = 1;
+    } else {
+#pragma omp for schedule(dynamic, 1)
+      for (int64_t xi = 0; xi < (int64_t)N; ++xi) {
+        uint64_t x = (uint64_t)xi;
+        for (uint64_t z = 0; z < N; ++z)
+          u[z] = times_minus_i_pow(w[string_index(x, z, n)], popc64(x & z));
+        wht(u, N);
+        for (uint64_t r = 0; r < N; ++r) A[r * N + (r ^ x)] = u[r];
       }
       free(u);
     }

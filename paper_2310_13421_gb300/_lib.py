@@ -1,0 +1,159 @@
+"""ctypes binding of libtpd.so: the C ABI of include/tpd.h, same names, argument
+marshalling only.  Loading fails loudly when the library is missing; there is
+no fallback implementation."""
+import ctypes
+import os
+import threading
+
+from .buildlib import LIB
+
+TPD_OK = 0
+TPD_ERR_INVALID_ARG = 1
+TPD_ERR_UNSUPPORTED = 2
+TPD_ERR_MISALIGNED = 3
+TPD_ERR_WORKSPACE = 4
+TPD_ERR_CUDA = 5
+TPD_ERR_TIMEOUT = 6
+
+TPD_C128 = 0
+TPD_C64 = 1
+
+TPD_PREC_DEFAULT = 0
+TPD_PREC_PLAIN = 1
+TPD_PREC_COMPENSATED = 2
+TPD_PREC_FIXED = 3
+
+# every symbol include/tpd.h declares
+SYMBOLS = (
+    "tpd_options_init", "tpd_workspace_size", "tpd_decompose", "tpd_compose", "tpd_decompose_host",
+    "tpd_batched_workspace_size", "tpd_decompose_batched", "tpd_compose_batched",
+    "tpd_plan_describe", "tpd_status_string", "tpd_version",
+)
+
+
+class tpd_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("skip_zero", ctypes.c_int),
+                ("tile_bits", ctypes.c_int), ("max_levels", ctypes.c_int),
+                ("pass_events", ctypes.POINTER(ctypes.c_void_p)), ("num_events", ctypes.c_int)]
+
+
+class TPDError(RuntimeError):
+    def __init__(self, status, what):
+        super().__init__("%s: %s" % (what, status_string(status)))
+        self.status = status
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path=None):
+    """Load libtpd.so (built by paper_2310_13421_gb300.build.build())."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB
+        if not os.path.exists(p):
+            raise RuntimeError("libtpd.so not found at %s: run paper_2310_13421_gb300.build.build() "
+                               "(the CUDA library is required; there is no CPU fallback)" % p)
+        lib = ctypes.CDLL(p)
+        vp, i, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+        op = ctypes.POINTER(tpd_options)
+        ip = ctypes.POINTER(ctypes.c_int)
+        lib.tpd_options_init.argtypes = [op]
+        lib.tpd_options_init.restype = None
+        lib.tpd_workspace_size.argtypes = [i, i, op]
+        lib.tpd_workspace_size.restype = sz
+        lib.tpd_decompose.argtypes = [vp, i, i, op, vp, sz, vp]
+        lib.tpd_decompose.restype = i
+        lib.tpd_compose.argtypes = [vp, i, i, ctypes.c_double, op, vp, sz, vp]
+        lib.tpd_compose.restype = i
+        lib.tpd_decompose_host.argtypes = [vp, vp, vp, i, i, op, vp, sz, vp]
+        lib.tpd_decompose_host.restype = i
+        lib.tpd_batched_workspace_size.argtypes = [ip, i, i, op]
+        lib.tpd_batched_workspace_size.restype = sz
+        lib.tpd_decompose_batched.argtypes = [vp, vp, ip, i, i, op, vp, sz, vp]
+        lib.tpd_decompose_batched.restype = i
+        lib.tpd_compose_batched.argtypes = [vp, vp, ip, i, i, i, op, vp, sz, vp]
+        lib.tpd_compose_batched.restype = i
+        lib.tpd_plan_describe.argtypes = [i, i, op, ctypes.c_char_p, sz]
+        lib.tpd_plan_describe.restype = i
+        lib.tpd_status_string.argtypes = [i]
+        lib.tpd_status_string.restype = ctypes.c_char_p
+        lib.tpd_version.argtypes = []
+        lib.tpd_version.restype = i
+        _lib = lib
+        return lib
+
+
+def options(precision=TPD_PREC_DEFAULT, skip_zero=False, tile_bits=0, max_levels=0, pass_events=None):
+    """tpd_options; pass_events: sequence of cudaEvent_t handles (ints) for the profiling hook."""
+    o = tpd_options(int(precision), int(bool(skip_zero)), int(tile_bits), int(max_levels), None, 0)
+    if pass_events:
+        arr = (ctypes.c_void_p * len(pass_events))(*[int(e) for e in pass_events])
+        o.pass_events = ctypes.cast(arr, ctypes.POINTER(ctypes.c_void_p))
+        o.num_events = len(pass_events)
+        o._keep = arr  # keep the array alive with the struct
+    return o
+
+
+def _opt(opt):
+    return ctypes.byref(opt) if opt is not None else None
+
+
+def status_string(status):
+    return load().tpd_status_string(int(status)).decode()
+
+
+def tpd_workspace_size(n, dtype, opt=None):
+    return int(load().tpd_workspace_size(n, dtype, _opt(opt)))
+
+
+def tpd_decompose(A_ptr, n, dtype, opt=None, workspace=0, workspace_bytes=0, stream=0):
+    return int(load().tpd_decompose(A_ptr, n, dtype, _opt(opt), workspace or None, workspace_bytes,
+                                    stream or None))
+
+
+def tpd_compose(C_ptr, n, dtype, scale, opt=None, workspace=0, workspace_bytes=0, stream=0):
+    return int(load().tpd_compose(C_ptr, n, dtype, float(scale), _opt(opt), workspace or None,
+                                  workspace_bytes, stream or None))
+
+
+def tpd_decompose_host(A_host_ptr, W_host_ptr, dev_ptr, n, dtype, opt=None, workspace=0, workspace_bytes=0,
+                       stream=0):
+    return int(load().tpd_decompose_host(A_host_ptr, W_host_ptr, dev_ptr, n, dtype, _opt(opt), workspace or None,
+                                         workspace_bytes, stream or None))
+
+
+def _int_array(values):
+    arr = (ctypes.c_int * len(values))(*[int(v) for v in values])
+    return arr
+
+
+def tpd_batched_workspace_size(ns, dtype, opt=None):
+    arr = _int_array(ns)
+    return int(load().tpd_batched_workspace_size(arr, len(ns), dtype, _opt(opt)))
+
+
+def tpd_decompose_batched(ptrs_dev, ns_dev, ns, dtype, opt=None, workspace=0, workspace_bytes=0, stream=0):
+    arr = _int_array(ns)
+    return int(load().tpd_decompose_batched(ptrs_dev, ns_dev, arr, len(ns), dtype, _opt(opt),
+                                            workspace or None, workspace_bytes, stream or None))
+
+
+def tpd_compose_batched(ptrs_dev, ns_dev, ns, dtype, scale_mode, opt=None, workspace=0, workspace_bytes=0,
+                        stream=0):
+    arr = _int_array(ns)
+    return int(load().tpd_compose_batched(ptrs_dev, ns_dev, arr, len(ns), dtype, int(scale_mode), _opt(opt),
+                                          workspace or None, workspace_bytes, stream or None))
+
+
+def tpd_plan_describe(n, dtype, opt=None):
+    buf = ctypes.create_string_buffer(8192)
+    npass = load().tpd_plan_describe(n, dtype, _opt(opt), buf, len(buf))
+    return npass, buf.value.decode()
+
+
+def tpd_version():
+    return int(load().tpd_version())

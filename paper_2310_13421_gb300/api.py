@@ -1,0 +1,169 @@
+"""Torch-level front end: marshals tensors, streams and workspaces to the C ABI
+(_lib).  Every step of the decomposition runs in libtpd.so's kernels; there is
+no other code path.
+
+Layout reminder: results are IN the input's storage order ("RC layout"): the
+weight of string t sits at row r, column c with, for every qubit j, the row
+and column bits n-j equal to (t_j >> 1, t_j & 1) -- I (0,0), X (0,1), Y (1,0),
+Z (1,1).  ``string_order`` converts to base-4 string order.
+"""
+import numpy as np
+import torch
+
+from . import _lib as L
+
+_PREC = {
+    "default": L.TPD_PREC_DEFAULT, None: L.TPD_PREC_DEFAULT,
+    "plain": L.TPD_PREC_PLAIN, "fp64": L.TPD_PREC_PLAIN, "fp32": L.TPD_PREC_PLAIN,
+    "compensated": L.TPD_PREC_COMPENSATED,
+    "fixed": L.TPD_PREC_FIXED,
+}
+
+
+def _dtype_code(t):
+    if t.dtype == torch.complex128:
+        return L.TPD_C128
+    if t.dtype == torch.complex64:
+        return L.TPD_C64
+    raise TypeError("expected complex128 or complex64, got %s" % t.dtype)
+
+
+def _qubits(t):
+    if t.dim() != 2 or t.shape[0] != t.shape[1]:
+        raise ValueError("expected a square matrix, got shape %s" % (tuple(t.shape),))
+    N = int(t.shape[0])
+    if N < 2 or N & (N - 1):
+        raise ValueError("matrix side must be a power of two >= 2, got %d" % N)
+    return N.bit_length() - 1
+
+
+def _check_device(t):
+    if not t.is_cuda:
+        raise ValueError("tensor must be on a CUDA device (the decomposition runs only in libtpd.so)")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous (row-major)")
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _raise(st, what):
+    if st != L.TPD_OK:
+        raise L.TPDError(st, what)
+
+
+def make_options(precision=None, skip_zero=False, tile_bits=0, max_levels=0):
+    if isinstance(precision, str) or precision is None:
+        precision = _PREC[precision]
+    return L.options(precision, skip_zero, tile_bits, max_levels)
+
+
+def workspace_size(n, dtype, **kw):
+    code = L.TPD_C128 if dtype in (torch.complex128, L.TPD_C128) else L.TPD_C64
+    return L.tpd_workspace_size(n, code, make_options(**kw))
+
+
+def decompose(A, *, inplace=False, precision=None, skip_zero=False, tile_bits=0, max_levels=0,
+              workspace=None, stream=None):
+    """Pauli weights w_t = 2^-n tr(sigma^t A) of a 2^n x 2^n CUDA matrix, in RC layout."""
+    _check_device(A)
+    n = _qubits(A)
+    code = _dtype_code(A)
+    out = A if inplace else A.clone()
+    opt = make_options(precision, skip_zero, tile_bits, max_levels)
+    wsb = L.tpd_workspace_size(n, code, opt)
+    ws = workspace
+    if wsb and (ws is None or ws.numel() < wsb):
+        ws = torch.empty(wsb, dtype=torch.uint8, device=A.device)
+    with torch.cuda.device(A.device):
+        st = L.tpd_decompose(out.data_ptr(), n, code, opt, ws.data_ptr() if wsb else 0, wsb, _stream(stream))
+    _raise(st, "tpd_decompose")
+    return out
+
+
+def compose(C, *, scale=1.0, inplace=False, precision=None, skip_zero=False, tile_bits=0, max_levels=0,
+            workspace=None, stream=None):
+    """scale * sum_t w_t sigma^t from weights in RC layout (scale 2^-n: the adjoint of decompose)."""
+    _check_device(C)
+    n = _qubits(C)
+    code = _dtype_code(C)
+    out = C if inplace else C.clone()
+    opt = make_options(precision, skip_zero, tile_bits, max_levels)
+    wsb = L.tpd_workspace_size(n, code, opt)
+    ws = workspace
+    if wsb and (ws is None or ws.numel() < wsb):
+        ws = torch.empty(wsb, dtype=torch.uint8, device=C.device)
+    with torch.cuda.device(C.device):
+        st = L.tpd_compose(out.data_ptr(), n, code, float(scale), opt, ws.data_ptr() if wsb else 0, wsb,
+                           _stream(stream))
+    _raise(st, "tpd_compose")
+    return out
+
+
+class Batch:
+    """Device-side descriptor of a list of matrices for the batched calls
+    (pointer and qubit arrays plus workspace), reusable across calls and
+    CUDA-graph captures as long as the matrices stay in place."""
+
+    def __init__(self, mats, precision=None, tile_bits=0, max_levels=0):
+        if not mats:
+            raise ValueError("empty batch")
+        dev = mats[0].device
+        self.code = _dtype_code(mats[0])
+        self.ns = []
+        for m in mats:
+            _check_device(m)
+            if _dtype_code(m) != self.code or m.device != dev:
+                raise ValueError("batch matrices must share dtype and device")
+            self.ns.append(_qubits(m))
+        self.mats = list(mats)
+        self.opt = make_options(precision, False, tile_bits, max_levels)
+        self.ptrs = torch.tensor([m.data_ptr() for m in mats], dtype=torch.int64, device=dev)
+        self.ns_dev = torch.tensor(self.ns, dtype=torch.int32, device=dev)
+        wsb = L.tpd_batched_workspace_size(self.ns, self.code, self.opt)
+        if wsb == 0:
+            raise ValueError("invalid batch (qubit counts must be 1..12)")
+        self.ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+        self.device = dev
+
+    def decompose(self, stream=None):
+        with torch.cuda.device(self.device):
+            st = L.tpd_decompose_batched(self.ptrs.data_ptr(), self.ns_dev.data_ptr(), self.ns, self.code,
+                                         self.opt, self.ws.data_ptr(), self.ws.numel(), _stream(stream))
+        _raise(st, "tpd_decompose_batched")
+
+    def compose(self, adjoint=False, stream=None):
+        with torch.cuda.device(self.device):
+            st = L.tpd_compose_batched(self.ptrs.data_ptr(), self.ns_dev.data_ptr(), self.ns, self.code,
+                                       1 if adjoint else 0, self.opt, self.ws.data_ptr(), self.ws.numel(),
+                                       _stream(stream))
+        _raise(st, "tpd_compose_batched")
+
+
+def decompose_batched(mats, *, inplace=False, precision=None, stream=None):
+    """Decompose a list of CUDA matrices of (possibly different) sizes; one
+    call enqueues the whole batch."""
+    work = list(mats) if inplace else [m.clone() for m in mats]
+    Batch(work, precision=precision).decompose(stream)
+    return work
+
+
+def compose_batched(mats, *, adjoint=False, inplace=False, precision=None, stream=None):
+    work = list(mats) if inplace else [m.clone() for m in mats]
+    Batch(work, precision=precision).compose(adjoint=adjoint, stream=stream)
+    return work
+
+
+def string_order(n):
+    """Index array p with p[s] = flat RC position of string s (base-4 string
+    index, t_1 most significant): rc_tensor.flatten()[p] is in string order."""
+    s = np.arange(4 ** n, dtype=np.int64)
+    r = np.zeros_like(s)
+    c = np.zeros_like(s)
+    for beta in range(n):
+        t = (s >> (2 * beta)) & 3
+        r |= (t >> 1) << beta
+        c |= (t & 1) << beta
+    return r * (1 << n) + c

@@ -1,0 +1,378 @@
+// C ABI of libtpd.so (declared in include/tpd.h): argument checks, the plan
+// cache, workspace layout and the launch sequence of each call.  Host code
+// only; the kernels are behind the launchers of tpd_launch.h.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "tpd.h"
+#include "tpd_launch.h"
+#include "tpd_planner.h"
+
+namespace tpd {
+namespace {
+
+std::mutex g_plan_mu;
+std::map<std::tuple<int, int, int, int, int>, Plan> g_plans;
+
+int resolve_precision(int dtype, int precision) {
+  if (precision == TPD_PREC_DEFAULT) return dtype == TPD_C128 ? TPD_PREC_FIXED : TPD_PREC_PLAIN;
+  return precision;
+}
+
+int arith_of(int dtype, int prec) {
+  if (dtype == TPD_C128) return prec == TPD_PREC_FIXED ? kArithFixed : kArithF64;
+  return prec == TPD_PREC_COMPENSATED ? kArithF32C : kArithF32;
+}
+
+tpd_status check_options(int dtype, const tpd_options* opt, int* prec) {
+  if (dtype != TPD_C128 && dtype != TPD_C64) return TPD_ERR_INVALID_ARG;
+  const int p = resolve_precision(dtype, opt ? opt->precision : 0);
+  if (p < TPD_PREC_PLAIN || p > TPD_PREC_FIXED) return TPD_ERR_INVALID_ARG;
+  if (p == TPD_PREC_COMPENSATED && dtype != TPD_C64) return TPD_ERR_UNSUPPORTED;
+  if (p == TPD_PREC_FIXED && dtype != TPD_C128) return TPD_ERR_UNSUPPORTED;
+  if (opt && opt->tile_bits != 0 && (opt->tile_bits < kMinTileBits || opt->tile_bits > kMaxTileBits))
+    return TPD_ERR_INVALID_ARG;
+  if (opt && (opt->max_levels < 0 || opt->max_levels > kMaxLevels)) return TPD_ERR_INVALID_ARG;
+  *prec = p;
+  return TPD_OK;
+}
+
+tpd_status check_common(int n, int dtype, const tpd_options* opt, int* prec) {
+  if (n < 1 || n > kMaxQubits) return TPD_ERR_INVALID_ARG;
+  return check_options(dtype, opt, prec);
+}
+
+// Cached plan for (n, dtype, precision, tuning options); nullptr if impossible.
+const Plan* get_plan(int n, int dtype, int prec, const tpd_options* opt) {
+  const int tb = opt ? opt->tile_bits : 0, ml = opt ? opt->max_levels : 0;
+  const auto key = std::make_tuple(n, dtype, prec, tb, ml);
+  std::lock_guard<std::mutex> lk(g_plan_mu);
+  auto it = g_plans.find(key);
+  if (it != g_plans.end()) return &it->second;
+  Plan p;
+  std::string err;
+  if (!build_plan(n, dtype, prec, tb, ml, &p, &err)) return nullptr;
+  return &g_plans.emplace(key, p).first->second;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Workspace of one matrix's plan:
+//   zero-skip flags: one byte per tile of every pass after the first (skip only)
+//   binary points:   one int per tile of every pass but the last (fixed point only)
+struct Layout {
+  size_t flags_off[kMaxQubits];
+  size_t q_off[kMaxQubits];
+  size_t flags_bytes, q_bytes, total;
+};
+
+Layout layout_of(const Plan& p, int arith, int skip) {
+  Layout L;
+  std::memset(&L, 0, sizeof(L));
+  size_t off = 0;
+  if (skip)
+    for (int i = 1; i < p.npass; ++i) { L.flags_off[i] = off; off += (size_t)p.pass[i].ntiles; }
+  L.flags_bytes = align256(off);
+  off = L.flags_bytes;
+  if (arith == kArithFixed)
+    for (int i = 0; i + 1 < p.npass; ++i) { L.q_off[i] = off; off += (size_t)p.pass[i].ntiles * sizeof(int); }
+  L.q_bytes = align256(off) - L.flags_bytes;
+  L.total = L.flags_bytes + L.q_bytes;
+  return L;
+}
+
+// Composition scale = m * 2^e; exact power of two when m == 1/2 in frexp form.
+void split_scale(double scale, int* pow2, double* residual) {
+  int e = 0;
+  const double fr = std::frexp(scale, &e);
+  if (fr == 0.5) { *pow2 = e - 1; *residual = 1.0; }
+  else { *pow2 = 0; *residual = scale; }
+}
+
+void pass_scaling(bool dec, int arith, const PassDesc& pd, bool last, int spow, double sres, double scale,
+                  PassArgs* a) {
+  if (arith == kArithFixed) {
+    // the kernel folds the 1/2 of Eq. 4 into its binary point; only the
+    // composition's scale is applied here, on the last pass
+    a->out_pow2 = (!dec && last) ? spow : 0;
+    a->out_mul = (!dec && last) ? sres : 1.0;
+  } else if (dec) {
+    a->out_pow2 = -pd.K;                            // the 1/2 of Eq. 4, once per fused level
+    a->out_mul = std::ldexp(1.0, -pd.K);
+  } else {
+    a->out_pow2 = last ? spow : 0;
+    a->out_mul = last ? scale : 1.0;
+  }
+}
+
+// profiling hook: event k recorded before pass k (k = 0) / after pass k-1
+void record_event(const tpd_options* opt, int k, cudaStream_t s) {
+  if (opt && opt->pass_events && k < opt->num_events && opt->pass_events[k])
+    cudaEventRecord(static_cast<cudaEvent_t>(opt->pass_events[k]), s);
+}
+
+tpd_status run_single(bool dec, int arith, void* mat, const Plan& plan, int skip, double scale, void* ws,
+                      cudaStream_t s, const tpd_options* opt) {
+  record_event(opt, 0, s);
+  if (plan.npass == 0) {
+    SmallArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.mat = mat; a.n = plan.n; a.skip_zero = skip;
+    a.scale_mode = dec ? 0 : (scale == 1.0 ? 0 : 1);
+    if (launch_small(arith, dec, a, 1, plan.n, s) != cudaSuccess) return TPD_ERR_CUDA;
+    record_event(opt, 1, s);
+    return TPD_OK;
+  }
+  const Layout lay = layout_of(plan, arith, skip);
+  char* w = static_cast<char*>(ws);
+  if (skip && lay.flags_bytes && cudaMemsetAsync(w, 0, lay.flags_bytes, s) != cudaSuccess) return TPD_ERR_CUDA;
+  // with skipping, tiles a pass never visits keep the "zero tile" fill
+  if (skip && lay.q_bytes && cudaMemsetAsync(w + lay.flags_bytes, kQFillByte, lay.q_bytes, s) != cudaSuccess)
+    return TPD_ERR_CUDA;
+  int spow = 0;
+  double sres = 1.0;
+  if (!dec) split_scale(scale, &spow, &sres);
+  for (int p = 0; p < plan.npass; ++p) {
+    const PassDesc& pd = plan.pass[p];
+    const bool last = p + 1 == plan.npass;
+    PassArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.mat = mat;
+    a.skip_zero = skip;
+    if (skip && p > 0) a.flags_in = reinterpret_cast<uint8_t*>(w + lay.flags_off[p]);
+    if (skip && !last) a.flags_out = reinterpret_cast<uint8_t*>(w + lay.flags_off[p + 1]);
+    if (arith == kArithFixed) {
+      if (p > 0) a.q_in = reinterpret_cast<const int*>(w + lay.q_off[p - 1]);
+      if (!last) a.q_out = reinterpret_cast<int*>(w + lay.q_off[p]);
+    }
+    pass_scaling(dec, arith, pd, last, spow, sres, scale, &a);
+    if (launch_pass(arith, dec, pd, a, pd.ntiles, s) != cudaSuccess) return TPD_ERR_CUDA;
+    record_event(opt, p + 1, s);
+  }
+  return TPD_OK;
+}
+
+size_t single_ws(const Plan& plan, int arith, int skip) {
+  return plan.npass > 1 ? layout_of(plan, arith, skip).total : 0;
+}
+
+tpd_status single(bool dec, void* mat, int n, int dtype, double scale, const tpd_options* opt, void* ws,
+                  size_t ws_bytes, void* stream) {
+  int prec = 0;
+  tpd_status st = check_common(n, dtype, opt, &prec);
+  if (st != TPD_OK) return st;
+  if (mat == nullptr) return TPD_ERR_INVALID_ARG;
+  const size_t align = dtype == TPD_C128 ? 16 : 8;
+  if (reinterpret_cast<uintptr_t>(mat) % align) return TPD_ERR_MISALIGNED;
+  if (!dec && (!std::isfinite(scale) || scale == 0.0)) return TPD_ERR_INVALID_ARG;
+  const Plan* plan = get_plan(n, dtype, prec, opt);
+  if (!plan) return TPD_ERR_INVALID_ARG;
+  if (!dec && plan->npass == 0 && scale != 1.0 && scale != std::ldexp(1.0, -n))
+    return TPD_ERR_UNSUPPORTED;  // whole-matrix kernel: scale 1 or 2^-n
+  const int skip = opt ? (opt->skip_zero != 0) : 0;
+  const int arith = arith_of(dtype, prec);
+  const size_t need = single_ws(*plan, arith, skip);
+  if (need && (ws == nullptr || ws_bytes < need)) return TPD_ERR_WORKSPACE;
+  if (ws && reinterpret_cast<uintptr_t>(ws) % 16) return TPD_ERR_MISALIGNED;
+  return run_single(dec, arith, mat, *plan, skip, scale, ws, static_cast<cudaStream_t>(stream), opt);
+}
+
+// ------------------------------------------------------------------ batched
+constexpr int kBatchMaxQubits = 12;
+
+// workspace: items[count] | offsets[33] (device bucket lists) | per qubit
+// count n (ascending), for the fixed point: binary points of hist[n]
+// matrices for every pass but the last
+size_t batched_q_bytes(const Plan& plan, int arith, int count_n) {
+  if (arith != kArithFixed || plan.npass < 2) return 0;
+  size_t b = 0;
+  for (int i = 0; i + 1 < plan.npass; ++i) b += (size_t)plan.pass[i].ntiles * sizeof(int) * (size_t)count_n;
+  return align256(b);
+}
+size_t batched_head(int count) { return align256((size_t)count * sizeof(int)) + align256(64 * sizeof(int)); }
+
+tpd_status batched(bool dec, void* const* ptrs_dev, const int* ns_dev, const int* ns, int count, int dtype,
+                   int scale_mode, const tpd_options* opt, void* ws, size_t ws_bytes, void* stream) {
+  int prec = 0;
+  tpd_status st = check_options(dtype, opt, &prec);
+  if (st != TPD_OK) return st;
+  if (count < 0 || (count > 0 && (ptrs_dev == nullptr || ns_dev == nullptr || ns == nullptr)))
+    return TPD_ERR_INVALID_ARG;
+  if (scale_mode != 0 && scale_mode != 1) return TPD_ERR_INVALID_ARG;
+  if (opt && opt->skip_zero) return TPD_ERR_UNSUPPORTED;
+  if (count == 0) return TPD_OK;
+  int hist[kBatchMaxQubits + 1] = {0};
+  for (int i = 0; i < count; ++i) {
+    if (ns[i] < 1 || ns[i] > kBatchMaxQubits) return TPD_ERR_INVALID_ARG;
+    hist[ns[i]]++;
+  }
+  const int arith = arith_of(dtype, prec);
+  std::vector<const Plan*> plans(kBatchMaxQubits + 1, nullptr);
+  size_t need = batched_head(count);
+  for (int n = 1; n <= kBatchMaxQubits; ++n) {
+    if (hist[n] && !(plans[n] = get_plan(n, dtype, prec, opt))) return TPD_ERR_INVALID_ARG;
+    if (hist[n]) need += batched_q_bytes(*plans[n], arith, hist[n]);
+  }
+  if (ws == nullptr || ws_bytes < need) return TPD_ERR_WORKSPACE;
+  if (reinterpret_cast<uintptr_t>(ws) % 16) return TPD_ERR_MISALIGNED;
+  int* items = static_cast<int*>(ws);
+  int* offsets = reinterpret_cast<int*>(static_cast<char*>(ws) + align256((size_t)count * sizeof(int)));
+  char* qbase = static_cast<char*>(ws) + batched_head(count);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (launch_bucket(ns_dev, count, items, offsets, nullptr, s) != cudaSuccess) return TPD_ERR_CUDA;
+  int start = 0;  // host mirror of offsets[n]: buckets are in increasing n
+  for (int n = 1; n <= kBatchMaxQubits; ++n) {
+    if (!hist[n]) continue;
+    const Plan& plan = *plans[n];
+    const int* its = items + start;
+    if (plan.npass == 0) {
+      SmallArgs a;
+      std::memset(&a, 0, sizeof(a));
+      a.ptrs = ptrs_dev; a.ns = ns_dev; a.items = its;
+      a.scale_mode = dec ? 0 : scale_mode;
+      if (launch_small(arith, dec, a, hist[n], n, s) != cudaSuccess) return TPD_ERR_CUDA;
+    } else {
+      size_t qoff = 0;
+      const int* q_prev = nullptr;
+      long long q_prev_stride = 0;
+      for (int p = 0; p < plan.npass; ++p) {
+        const PassDesc& pd = plan.pass[p];
+        const bool last = p + 1 == plan.npass;
+        PassArgs a;
+        std::memset(&a, 0, sizeof(a));
+        a.ptrs = ptrs_dev; a.items = its; a.tiles_per_mat = pd.ntiles;
+        if (arith == kArithFixed) {
+          a.q_in = q_prev;
+          a.q_in_stride = q_prev_stride;
+          if (!last) {
+            a.q_out = reinterpret_cast<int*>(qbase + qoff);
+            a.q_out_stride = pd.ntiles;
+            qoff += (size_t)pd.ntiles * sizeof(int) * (size_t)hist[n];
+            q_prev = a.q_out;
+            q_prev_stride = pd.ntiles;
+          }
+        }
+        const double scale = scale_mode ? std::ldexp(1.0, -n) : 1.0;
+        pass_scaling(dec, arith, pd, last, scale_mode ? -n : 0, 1.0, scale, &a);
+        if (launch_pass(arith, dec, pd, a, pd.ntiles * hist[n], s) != cudaSuccess) return TPD_ERR_CUDA;
+      }
+      qbase += batched_q_bytes(plan, arith, hist[n]);
+    }
+    start += hist[n];
+  }
+  return TPD_OK;
+}
+
+}  // namespace
+}  // namespace tpd
+
+using namespace tpd;
+
+extern "C" {
+
+void tpd_options_init(tpd_options* opt) {
+  if (opt) std::memset(opt, 0, sizeof(*opt));
+}
+
+size_t tpd_workspace_size(int n, int dtype, const tpd_options* opt) {
+  int prec = 0;
+  if (check_common(n, dtype, opt, &prec) != TPD_OK) return 0;
+  const Plan* plan = get_plan(n, dtype, prec, opt);
+  if (!plan) return 0;
+  return single_ws(*plan, arith_of(dtype, prec), opt ? (opt->skip_zero != 0) : 0);
+}
+
+tpd_status tpd_decompose(void* A, int n, int dtype, const tpd_options* opt, void* workspace,
+                         size_t workspace_bytes, void* stream) {
+  return single(true, A, n, dtype, 1.0, opt, workspace, workspace_bytes, stream);
+}
+
+tpd_status tpd_compose(void* C, int n, int dtype, double scale, const tpd_options* opt, void* workspace,
+                       size_t workspace_bytes, void* stream) {
+  return single(false, C, n, dtype, scale, opt, workspace, workspace_bytes, stream);
+}
+
+tpd_status tpd_decompose_host(const void* A_host, void* W_host, void* dev_A, int n, int dtype,
+                              const tpd_options* opt, void* workspace, size_t workspace_bytes, void* stream) {
+  int prec = 0;
+  tpd_status st = check_common(n, dtype, opt, &prec);
+  if (st != TPD_OK) return st;
+  if (A_host == nullptr || W_host == nullptr || dev_A == nullptr) return TPD_ERR_INVALID_ARG;
+  const size_t align = dtype == TPD_C128 ? 16 : 8;
+  if (reinterpret_cast<uintptr_t>(dev_A) % align) return TPD_ERR_MISALIGNED;
+  const size_t bytes = ((size_t)1 << (2 * n)) * (dtype == TPD_C128 ? 16 : 8);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaMemcpyAsync(dev_A, A_host, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return TPD_ERR_CUDA;
+  st = single(true, dev_A, n, dtype, 1.0, opt, workspace, workspace_bytes, stream);
+  if (st != TPD_OK) return st;
+  if (cudaMemcpyAsync(W_host, dev_A, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return TPD_ERR_CUDA;
+  return TPD_OK;
+}
+
+size_t tpd_batched_workspace_size(const int* ns, int count, int dtype, const tpd_options* opt) {
+  int prec = 0;
+  if (check_options(dtype, opt, &prec) != TPD_OK || count < 0 || (count > 0 && ns == nullptr)) return 0;
+  int hist[kBatchMaxQubits + 1] = {0};
+  for (int i = 0; i < count; ++i) {
+    if (ns[i] < 1 || ns[i] > kBatchMaxQubits) return 0;
+    hist[ns[i]]++;
+  }
+  const int arith = arith_of(dtype, prec);
+  size_t need = batched_head(count);
+  for (int n = 1; n <= kBatchMaxQubits; ++n) {
+    if (!hist[n]) continue;
+    const Plan* plan = get_plan(n, dtype, prec, opt);
+    if (!plan) return 0;
+    need += batched_q_bytes(*plan, arith, hist[n]);
+  }
+  return need;
+}
+
+tpd_status tpd_decompose_batched(void* const* ptrs_dev, const int* ns_dev, const int* ns, int count, int dtype,
+                                 const tpd_options* opt, void* workspace, size_t workspace_bytes, void* stream) {
+  return batched(true, ptrs_dev, ns_dev, ns, count, dtype, 0, opt, workspace, workspace_bytes, stream);
+}
+
+tpd_status tpd_compose_batched(void* const* ptrs_dev, const int* ns_dev, const int* ns, int count, int dtype,
+                               int scale_mode, const tpd_options* opt, void* workspace, size_t workspace_bytes,
+                               void* stream) {
+  return batched(false, ptrs_dev, ns_dev, ns, count, dtype, scale_mode, opt, workspace, workspace_bytes, stream);
+}
+
+int tpd_plan_describe(int n, int dtype, const tpd_options* opt, char* buf, size_t len) {
+  int prec = 0;
+  if (check_common(n, dtype, opt, &prec) != TPD_OK) return -1;
+  const Plan* plan = get_plan(n, dtype, prec, opt);
+  if (!plan) return -1;
+  const std::string s = describe_plan(*plan);
+  if (buf && len) {
+    std::strncpy(buf, s.c_str(), len - 1);
+    buf[len - 1] = 0;
+  }
+  return plan->npass;
+}
+
+const char* tpd_status_string(int status) {
+  switch (status) {
+    case TPD_OK: return "TPD_OK";
+    case TPD_ERR_INVALID_ARG: return "TPD_ERR_INVALID_ARG";
+    case TPD_ERR_UNSUPPORTED: return "TPD_ERR_UNSUPPORTED";
+    case TPD_ERR_MISALIGNED: return "TPD_ERR_MISALIGNED";
+    case TPD_ERR_WORKSPACE: return "TPD_ERR_WORKSPACE";
+    case TPD_ERR_CUDA: return "TPD_ERR_CUDA";
+    case TPD_ERR_TIMEOUT: return "TPD_ERR_TIMEOUT";
+    default: return "TPD_ERR_UNKNOWN";
+  }
+}
+
+int tpd_version(void) { return 100; }
+
+}  // extern "C"

@@ -1,0 +1,236 @@
+// Element arithmetic for the Pauli butterfly (Eq. 4) and its inverse.
+//
+// Per qubit level the decomposition maps the quad (a00, a01, a10, a11) of a
+// 2x2 block (row bit, column bit) to
+//     I = a00 + a11,  X = a01 + a10,  Y = i (a01 - a10),  Z = a00 - a11
+// and leaves them at the same four positions; the factor 1/2 of Eq. 4 is
+// applied once per pass as 2^-K, which is exact.  The composition maps
+//     a00 = I + Z,  a01 = X - iY,  a10 = X + iY,  a11 = I - Z.
+//
+// Four arithmetics share this interface:
+//   FixedArith  complex128 storage; a pass loads each tile onto a common
+//               binary point in int64 (block fixed point), sums exactly, and
+//               rounds once to double (RNE) when it stores.  Only integer
+//               instructions: on GB300 the fp64 pipe issues ~2 ops/clk/SM,
+//               far below the HBM rate of this kernel.
+//   F64Arith    complex128, IEEE double adds (rounded every level).
+//   F32Arith    complex64, IEEE float adds.
+//   F32CArith   complex64, float sums with TwoSum error terms carried through
+//               the pass (cascaded summation, Ogita-Rump-Oishi 2005), one
+//               rounding fl(hi + lo) per pass.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tpd {
+
+// ---------------------------------------------------------------- per-tile output scaling
+struct OutScale {
+  int pow2;        // multiply by 2^pow2 (exact)
+  double extra;    // remaining non-power-of-two factor (1.0 normally)
+};
+
+__device__ __forceinline__ uint32_t shfl_x(uint32_t v, int mask) {
+  return __shfl_xor_sync(0xffffffffu, v, mask);
+}
+
+// ================================================================ fixed point
+struct FixedArith {
+  using Store = double2;
+  struct V { long long re, im; };
+  static constexpr bool kFixed = true;
+  static constexpr int kStoreBytes = 16;
+
+  __device__ static __forceinline__ V add(V a, V b) { return {a.re + b.re, a.im + b.im}; }
+  __device__ static __forceinline__ V sub(V a, V b) { return {a.re - b.re, a.im - b.im}; }
+  __device__ static __forceinline__ V mul_i(V d) { return {-d.im, d.re}; }       //  i d
+  __device__ static __forceinline__ V mul_mi(V d) { return {d.im, -d.re}; }      // -i d
+  __device__ static __forceinline__ V neg(V d) { return {-d.re, -d.im}; }
+  __device__ static __forceinline__ V shfl(V v, int mask) {
+    V o;
+    o.re = (long long)(((unsigned long long)shfl_x((uint32_t)(v.re >> 32), mask) << 32) |
+                       shfl_x((uint32_t)v.re, mask));
+    o.im = (long long)(((unsigned long long)shfl_x((uint32_t)(v.im >> 32), mask) << 32) |
+                       shfl_x((uint32_t)v.im, mask));
+    return o;
+  }
+
+  // x * 2^S truncated toward zero, S = 1084 - K - Emax_eff (see from_double).
+  // shift_base = 9 - K - Emax_eff, so that the element with the tile's
+  // largest exponent lands below 2^(62-K) and 2^K of them sum below 2^62.
+  __device__ static __forceinline__ long long to_fixed(double x, int shift_base) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)(bits >> 52) & 0x7FF;
+    const unsigned long long m =
+        (bits & 0x000FFFFFFFFFFFFFull) | ((unsigned long long)(e != 0) << 52);
+    const int sh = max(e, 1) + shift_base;   // <= 9 - K <= 8
+    const unsigned rs = (unsigned)(11 - sh); // >= 3
+    unsigned long long mag;
+    const unsigned long long ml = m << 11;   // m < 2^53
+    // PTX clamps shift amounts above 64 to 64 (result 0): no undefined shifts.
+    asm("shr.b64 %0, %1, %2;" : "=l"(mag) : "l"(ml), "r"(rs));
+    const unsigned long long s = (unsigned long long)((long long)bits >> 63);
+    return (long long)((mag ^ s) - s);
+  }
+
+  // Magnitude bits of a * 2^(be - 1086) (a has its leading one at bit 63)
+  // rounded to nearest even, when that falls outside the normal range:
+  // overflow to Inf or a subnormal result.  Out of line: never taken for
+  // data in the normal range.
+  __device__ static __noinline__ unsigned long long rare_bits(unsigned long long a, int be) {
+    if (be > 2046) return 0x7FF0000000000000ull;
+    const int rsh = 12 - be;                    // >= 12: subnormal, mantissa = a >> rsh
+    if (rsh > 64) return 0;
+    if (rsh == 64) return (a > 0x8000000000000000ull) ? 1ull : 0ull;
+    unsigned long long mant = a >> rsh;
+    const unsigned long long rem = a & ((1ull << rsh) - 1);
+    const unsigned long long half = 1ull << (rsh - 1);
+    mant += (unsigned long long)((rem > half) | ((rem == half) & (mant & 1ull)));
+    return mant;                                // reaching 2^52 gives the smallest normal
+  }
+
+  // v * 2^-T rounded to nearest even (integer instructions only).
+  __device__ static __forceinline__ double to_double_int(long long v, int T) {
+    if (v == 0) return 0.0;
+    const unsigned long long s = (unsigned long long)(v >> 63);
+    unsigned long long a = ((unsigned long long)v ^ s) - s;
+    const int lz = __clzll((long long)a);
+    a <<= lz;                                   // leading one at bit 63
+    const int be = 1086 - lz - T;               // biased exponent of that bit
+    unsigned long long bits;
+    if (be >= 1 && be <= 2046) {
+      unsigned long long mant = a >> 11;        // 53 bits
+      const unsigned rem = (unsigned)a & 0x7FFu;
+      mant += (unsigned long long)((rem > 0x400u) | ((rem == 0x400u) & (unsigned)mant));
+      bits = ((unsigned long long)(be - 1) << 52) + mant;   // a carry out of mant bumps the exponent
+      if ((bits >> 52) >= 2047) bits = 0x7FF0000000000000ull;
+    } else {
+      bits = rare_bits(a, be);
+    }
+    return __longlong_as_double((long long)(bits | (s & 0x8000000000000000ull)));
+  }
+
+  // v * 2^-T: the int64 -> double conversion (round to nearest even) followed
+  // by an exact exponent shift; out-of-range exponents take the integer path.
+  __device__ static __forceinline__ double to_double_cvt(long long v, int T) {
+    const double d = __ll2double_rn(v);
+    const long long b = __double_as_longlong(d);
+    const int e = (int)(b >> 52) & 0x7FF;       // >= 1023 for v != 0
+    if (v != 0 && e - T >= 1 && e - T <= 2046) return __longlong_as_double(b - ((long long)T << 52));
+    return to_double_int(v, T);
+  }
+
+  __device__ static __forceinline__ double to_double(long long v, int T) {
+#ifdef TPD_TO_DOUBLE_CVT
+    return to_double_cvt(v, T);
+#else
+    return to_double_int(v, T);
+#endif
+  }
+};
+
+// ================================================================ IEEE double
+struct F64Arith {
+  using Store = double2;
+  using V = double2;
+  static constexpr bool kFixed = false;
+  static constexpr int kStoreBytes = 16;
+  __device__ static __forceinline__ V add(V a, V b) { return make_double2(__dadd_rn(a.x, b.x), __dadd_rn(a.y, b.y)); }
+  __device__ static __forceinline__ V sub(V a, V b) { return make_double2(__dsub_rn(a.x, b.x), __dsub_rn(a.y, b.y)); }
+  __device__ static __forceinline__ V mul_i(V d) { return make_double2(-d.y, d.x); }
+  __device__ static __forceinline__ V mul_mi(V d) { return make_double2(d.y, -d.x); }
+  __device__ static __forceinline__ V neg(V d) { return make_double2(-d.x, -d.y); }
+  __device__ static __forceinline__ V shfl(V v, int mask) {
+    V o;
+    o.x = __hiloint2double((int)shfl_x((uint32_t)__double2hiint(v.x), mask),
+                           (int)shfl_x((uint32_t)__double2loint(v.x), mask));
+    o.y = __hiloint2double((int)shfl_x((uint32_t)__double2hiint(v.y), mask),
+                           (int)shfl_x((uint32_t)__double2loint(v.y), mask));
+    return o;
+  }
+  __device__ static __forceinline__ V load(Store s) { return s; }
+  __device__ static __forceinline__ Store store(V v, const OutScale& sc, double mul) {
+    if (mul == 1.0) return v;
+    return make_double2(__dmul_rn(v.x, mul), __dmul_rn(v.y, mul));
+  }
+  __device__ static __forceinline__ bool nonzero(Store o) {   // +-0 is zero, NaN is not
+    return (((uint32_t)__double2hiint(o.x) << 1) | (uint32_t)__double2loint(o.x) |
+            ((uint32_t)__double2hiint(o.y) << 1) | (uint32_t)__double2loint(o.y)) != 0;
+  }
+};
+
+// ================================================================ IEEE float
+struct F32Arith {
+  using Store = float2;
+  using V = float2;
+  static constexpr bool kFixed = false;
+  static constexpr int kStoreBytes = 8;
+  __device__ static __forceinline__ V add(V a, V b) { return make_float2(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y)); }
+  __device__ static __forceinline__ V sub(V a, V b) { return make_float2(__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y)); }
+  __device__ static __forceinline__ V mul_i(V d) { return make_float2(-d.y, d.x); }
+  __device__ static __forceinline__ V mul_mi(V d) { return make_float2(d.y, -d.x); }
+  __device__ static __forceinline__ V neg(V d) { return make_float2(-d.x, -d.y); }
+  __device__ static __forceinline__ V shfl(V v, int mask) {
+    return make_float2(__uint_as_float(shfl_x(__float_as_uint(v.x), mask)),
+                       __uint_as_float(shfl_x(__float_as_uint(v.y), mask)));
+  }
+  __device__ static __forceinline__ V load(Store s) { return s; }
+  __device__ static __forceinline__ Store store(V v, const OutScale& sc, double mul) {
+    const float m = (float)mul;
+    if (m == 1.0f) return v;
+    return make_float2(__fmul_rn(v.x, m), __fmul_rn(v.y, m));
+  }
+  __device__ static __forceinline__ bool nonzero(Store o) {
+    return ((__float_as_uint(o.x) | __float_as_uint(o.y)) << 1) != 0;
+  }
+};
+
+// ================================================================ compensated float
+struct F32CArith {
+  using Store = float2;
+  struct V { float re, im, rl, il; };   // value = (re + rl) + i (im + il)
+  static constexpr bool kFixed = false;
+  static constexpr int kStoreBytes = 8;
+
+  // Knuth's TwoSum: s + e == a + b exactly, s = fl(a + b).
+  __device__ static __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float aa = __fsub_rn(s, bb);
+    e = __fadd_rn(__fsub_rn(a, aa), __fsub_rn(b, bb));
+  }
+  __device__ static __forceinline__ V add(V a, V b) {
+    V o; float e;
+    two_sum(a.re, b.re, o.re, e); o.rl = __fadd_rn(__fadd_rn(a.rl, b.rl), e);
+    two_sum(a.im, b.im, o.im, e); o.il = __fadd_rn(__fadd_rn(a.il, b.il), e);
+    return o;
+  }
+  __device__ static __forceinline__ V sub(V a, V b) {
+    V o; float e;
+    two_sum(a.re, -b.re, o.re, e); o.rl = __fadd_rn(__fsub_rn(a.rl, b.rl), e);
+    two_sum(a.im, -b.im, o.im, e); o.il = __fadd_rn(__fsub_rn(a.il, b.il), e);
+    return o;
+  }
+  __device__ static __forceinline__ V mul_i(V d) { return {-d.im, d.re, -d.il, d.rl}; }
+  __device__ static __forceinline__ V mul_mi(V d) { return {d.im, -d.re, d.il, -d.rl}; }
+  __device__ static __forceinline__ V neg(V d) { return {-d.re, -d.im, -d.rl, -d.il}; }
+  __device__ static __forceinline__ V shfl(V v, int mask) {
+    return {__uint_as_float(shfl_x(__float_as_uint(v.re), mask)),
+            __uint_as_float(shfl_x(__float_as_uint(v.im), mask)),
+            __uint_as_float(shfl_x(__float_as_uint(v.rl), mask)),
+            __uint_as_float(shfl_x(__float_as_uint(v.il), mask))};
+  }
+  __device__ static __forceinline__ V load(Store s) { return {s.x, s.y, 0.0f, 0.0f}; }
+  __device__ static __forceinline__ Store store(V v, const OutScale& sc, double mul) {
+    float re = __fadd_rn(v.re, v.rl), im = __fadd_rn(v.im, v.il);
+    const float m = (float)mul;
+    if (m != 1.0f) { re = __fmul_rn(re, m); im = __fmul_rn(im, m); }
+    return make_float2(re, im);
+  }
+  __device__ static __forceinline__ bool nonzero(Store o) {
+    return ((__float_as_uint(o.x) | __float_as_uint(o.y)) << 1) != 0;
+  }
+};
+
+}  // namespace tpd

@@ -1,0 +1,36 @@
+// Launch helpers shared by the per-storage-type kernel translation units.
+#pragma once
+
+#include "tpd_launch.h"
+#include "tpd_pass.cuh"
+
+namespace tpd {
+
+template <class A, bool kDec>
+cudaError_t launch_pass_t(const PassDesc& pd, const PassArgs& args, long long ntiles_total, cudaStream_t s) {
+  const int threads = 1 << (pd.D - kRegBits);
+  const size_t vbytes = A::kFixed ? 16 : sizeof(typename A::V);
+  const size_t smem = ((size_t)1 << pd.D) * vbytes + 256;
+  auto kfn = threads <= 256 ? k_pass<A, kDec, 256> : k_pass<A, kDec, 512>;
+  cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (ntiles_total <= 0) return cudaSuccess;
+  if (ntiles_total > 0x7fffffffll) return cudaErrorInvalidValue;
+  kfn<<<(unsigned)ntiles_total, threads, smem, s>>>(pd, args);
+  return cudaGetLastError();
+}
+
+template <class A, bool kDec>
+cudaError_t launch_small_t(const SmallArgs& args, int blocks, int n_max, cudaStream_t s) {
+  const size_t vbytes = A::kFixed ? 16 : sizeof(typename A::V);
+  size_t smem = ((size_t)1 << (2 * n_max)) * vbytes;
+  if (smem < 256) smem = 256;
+  auto kfn = k_small<A, kDec>;
+  cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (blocks <= 0) return cudaSuccess;
+  kfn<<<blocks, 128, smem, s>>>(args);
+  return cudaGetLastError();
+}
+
+}  // namespace tpd

@@ -1,0 +1,594 @@
+// One pass of the Pauli butterfly over a group of qubit levels (Sec. III,
+// Eqs. 3-5), in place, one CTA per tile.  See tpd_plan.h for tiles and stages
+// and tpd_arith.cuh for the arithmetics.
+//
+// Flow of a CTA:
+//   1. skip the tile if the previous pass flagged it all-zero (zero-CMW
+//      pruning of Alg. 1/2: a zero block has only zero weights below it);
+//   2. load its 16 elements per thread from HBM with the stage-0 mapping
+//      (lanes on the lowest tile bits: 128-byte runs);
+//   3. fixed point: CTA-wide max exponent -> common binary point; optional
+//      all-zero test (then nothing is written);
+//   4. per stage: apply the stage's levels in registers / across lanes, then
+//      exchange through shared memory into the next stage's mapping;
+//   5. round back to the storage type, store in place with the last stage's
+//      mapping, and flag the next pass's tiles that received a nonzero.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tpd_arith.cuh"
+#include "tpd_launch.h"
+#include "tpd_plan.h"
+
+namespace tpd {
+
+
+constexpr uint32_t kFull = 0xffffffffu;
+
+// 2^e as a double, built from its bits (normal range only)
+__device__ __forceinline__ double pow2d(int e) {
+  return __longlong_as_double((long long)(1023 + e) << 52);
+}
+
+__device__ __forceinline__ long long thread_goff(const PassDesc& pd, const Stage& st, int lane, int warp) {
+  long long g = 0;
+#pragma unroll
+  for (int i = 0; i < kLaneBits; ++i)
+    if ((lane >> i) & 1) g += 1ll << pd.gbit[st.lane[i]];
+  for (int i = 0; i < pd.D - kMinTileBits; ++i)
+    if ((warp >> i) & 1) g += 1ll << pd.gbit[st.warp[i]];
+  return g;
+}
+
+__device__ __forceinline__ int thread_sidx(const PassDesc& pd, const Stage& st, int lane, int warp) {
+  int s = 0;
+#pragma unroll
+  for (int i = 0; i < kLaneBits; ++i) s |= ((lane >> i) & 1) << st.lane[i];
+  for (int i = 0; i < pd.D - kMinTileBits; ++i) s |= ((warp >> i) & 1) << st.warp[i];
+  return s;
+}
+
+__device__ __forceinline__ int thread_next(const PassDesc& pd, const Stage& st, int lane, int warp) {
+  int s = 0;
+#pragma unroll
+  for (int i = 0; i < kLaneBits; ++i)
+    if ((lane >> i) & 1) s += pd.next_w[st.lane[i]];
+  for (int i = 0; i < pd.D - kMinTileBits; ++i)
+    if ((warp >> i) & 1) s += pd.next_w[st.warp[i]];
+  return s;
+}
+
+// offset of register e from 4 per-bit weights (e is a compile-time constant after unrolling)
+template <class T>
+__device__ __forceinline__ T reg_off(int e, T w0, T w1, T w2, T w3) {
+  return ((e & 1) ? w0 : T(0)) + ((e & 2) ? w1 : T(0)) + ((e & 4) ? w2 : T(0)) + ((e & 8) ? w3 : T(0));
+}
+
+// -------------------------------------------------------------- levels
+
+// In-register level: register bits RC (column) and RR (row).
+template <class A, bool kDec, int RC, int RR>
+__device__ __forceinline__ void pair_level(typename A::V (&v)[kElems]) {
+#pragma unroll
+  for (int e = 0; e < kElems; ++e) {
+    if ((e >> RC) & 1) continue;
+    if ((e >> RR) & 1) continue;
+    const int e01 = e | (1 << RC), e10 = e | (1 << RR), e11 = e | (1 << RC) | (1 << RR);
+    const typename A::V a00 = v[e], a01 = v[e01], a10 = v[e10], a11 = v[e11];
+    if (kDec) {
+      v[e] = A::add(a00, a11);                  // I
+      v[e01] = A::add(a01, a10);                // X
+      v[e10] = A::mul_i(A::sub(a01, a10));      // Y
+      v[e11] = A::sub(a00, a11);                // Z
+    } else {
+      const typename A::V iy = A::mul_i(a10);   // positions hold I, X, Y, Z
+      v[e] = A::add(a00, a11);                  // I + Z
+      v[e01] = A::sub(a01, iy);                 // X - iY
+      v[e10] = A::add(a01, iy);                 // X + iY
+      v[e11] = A::sub(a00, a11);                // I - Z
+    }
+  }
+}
+
+// Cross-lane level: column bit on lane bit `lbit`, row bit on register bit RB.
+// Both lanes of a pair compute the same sums as pair_level, in the same order.
+template <class A, bool kDec, int RB>
+__device__ __forceinline__ void shfl_level(typename A::V (&v)[kElems], int lbit, int lane) {
+  const int mask = 1 << lbit;
+  const bool cb = (lane >> lbit) & 1;
+#pragma unroll
+  for (int e = 0; e < kElems; ++e) {
+    if ((e >> RB) & 1) continue;
+    const int e1i = e | (1 << RB);
+    const typename A::V e0 = v[e], e1 = v[e1i];
+    const typename A::V p0 = A::shfl(e0, mask), p1 = A::shfl(e1, mask);
+    if (kDec) {
+      // column 0 holds a00 (row 0), a10 (row 1); column 1 holds a01, a11
+      v[e] = A::add(e0, p1);                    // I at (0,0) / X at (0,1)
+      const typename A::V d = A::sub(p0, e1);   // a01 - a10 / a00 - a11
+      v[e1i] = cb ? d : A::mul_i(d);            // Y at (1,0) / Z at (1,1)
+    } else {
+      // column 0 holds I, Y; column 1 holds X, Z
+      const typename A::V t1 = cb ? A::mul_mi(p1) : p1;
+      const typename A::V t2 = cb ? A::neg(e1) : A::mul_i(e1);
+      v[e] = A::add(e0, t1);                    // I + Z / X - iY
+      v[e1i] = A::add(p0, t2);                  // X + iY / I - Z
+    }
+  }
+}
+
+template <class A, bool kDec>
+__device__ __forceinline__ void stage_levels(typename A::V (&v)[kElems], const Stage& st, int lane) {
+  if (st.npair >= 1) pair_level<A, kDec, 0, 1>(v);
+  if (st.npair >= 2) pair_level<A, kDec, 2, 3>(v);
+  const int r0 = 2 * st.npair;
+  for (int s = 0; s < st.nshfl; ++s) {
+    const int lb = st.shfl_lane[s];
+    switch (r0 + s) {
+      case 0: shfl_level<A, kDec, 0>(v, lb, lane); break;
+      case 1: shfl_level<A, kDec, 1>(v, lb, lane); break;
+      case 2: shfl_level<A, kDec, 2>(v, lb, lane); break;
+      default: shfl_level<A, kDec, 3>(v, lb, lane); break;
+    }
+  }
+}
+
+// Shared-memory exchange from stage `a`'s mapping to stage `b`'s.
+template <class V>
+__device__ __forceinline__ void exchange(V (&v)[kElems], const PassDesc& pd, const Stage& a,
+                                         const Stage& b, V* sm, int lane, int warp, bool sync_first) {
+  if (sync_first) __syncthreads();
+  {
+    const int t = thread_sidx(pd, a, lane, warp);
+    const int w0 = 1 << a.reg[0], w1 = 1 << a.reg[1], w2 = 1 << a.reg[2], w3 = 1 << a.reg[3];
+#pragma unroll
+    for (int e = 0; e < kElems; ++e) sm[t + reg_off(e, w0, w1, w2, w3)] = v[e];
+  }
+  __syncthreads();
+  {
+    const int t = thread_sidx(pd, b, lane, warp);
+    const int w0 = 1 << b.reg[0], w1 = 1 << b.reg[1], w2 = 1 << b.reg[2], w3 = 1 << b.reg[3];
+#pragma unroll
+    for (int e = 0; e < kElems; ++e) v[e] = sm[t + reg_off(e, w0, w1, w2, w3)];
+  }
+}
+
+// Stages, rounding and the in-place store, for arithmetic A on loaded data.
+template <class A, bool kDec, class Raw>
+__device__ __forceinline__ void finish_tile(const PassDesc& pd, const PassArgs& args, void* matp,
+                                            const Raw (&raw)[kElems], double mul, long long base,
+                                            int nbase, unsigned char* smem, int lane, int warp) {
+  using V = typename A::V;
+  using Store = typename A::Store;
+  V v[kElems];
+#pragma unroll
+  for (int e = 0; e < kElems; ++e) v[e] = A::load(raw[e]);
+  V* sm = reinterpret_cast<V*>(smem);
+  for (int s = 0; s < pd.nstage; ++s) {
+    if (s > 0) exchange(v, pd, pd.st[s - 1], pd.st[s], sm, lane, warp, s > 1);
+    stage_levels<A, kDec>(v, pd.st[s], lane);
+  }
+  const Stage& sl = pd.st[pd.nstage - 1];
+  Store* mat = reinterpret_cast<Store*>(matp);
+  const long long g = base + thread_goff(pd, sl, lane, warp);
+  const long long w0 = 1ll << pd.gbit[sl.reg[0]], w1 = 1ll << pd.gbit[sl.reg[1]];
+  const long long w2 = 1ll << pd.gbit[sl.reg[2]], w3 = 1ll << pd.gbit[sl.reg[3]];
+  const bool flags = args.flags_out != nullptr;
+  int nt = 0, n0 = 0, n1 = 0, n2 = 0, n3 = 0;
+  bool lanes_inside = true;
+  if (flags) {
+    nt = nbase + thread_next(pd, sl, lane, warp);
+    n0 = pd.next_w[sl.reg[0]]; n1 = pd.next_w[sl.reg[1]];
+    n2 = pd.next_w[sl.reg[2]]; n3 = pd.next_w[sl.reg[3]];
+#pragma unroll
+    for (int i = 0; i < kLaneBits; ++i) lanes_inside &= (pd.next_w[sl.lane[i]] == 0);
+  }
+#pragma unroll
+  for (int e = 0; e < kElems; ++e) {
+    const Store o = A::store(v[e], OutScale{0, 1.0}, mul);
+    const bool nz = flags && A::nonzero(o);
+    mat[g + reg_off(e, w0, w1, w2, w3)] = o;
+    if (flags) {
+      const int id = nt + reg_off(e, n0, n1, n2, n3);
+      if (lanes_inside) {
+        if (__any_sync(kFull, nz) && lane == 0) args.flags_out[id] = 1;
+      } else if (nz) {
+        args.flags_out[id] = 1;
+      }
+    }
+  }
+}
+
+template <class Store>
+__device__ __forceinline__ void load_tile(const PassDesc& pd, const void* matp, long long base, int lane, int warp,
+                                          Store (&raw)[kElems]) {
+  const Stage& s0 = pd.st[0];
+  const Store* mat = reinterpret_cast<const Store*>(matp);
+  const long long g = base + thread_goff(pd, s0, lane, warp);
+  const long long w0 = 1ll << pd.gbit[s0.reg[0]], w1 = 1ll << pd.gbit[s0.reg[1]];
+  const long long w2 = 1ll << pd.gbit[s0.reg[2]], w3 = 1ll << pd.gbit[s0.reg[3]];
+#pragma unroll
+  for (int e = 0; e < kElems; ++e) raw[e] = __ldg(mat + g + reg_off(e, w0, w1, w2, w3));
+}
+
+// ============================================================== fixed point
+//
+// A pass of the complex128 fixed-point path reads either IEEE doubles (the
+// first pass) or the int64 sums the previous pass stored in place together
+// with one binary point per previous tile (value = v * 2^q), and writes
+// either int64 sums plus its own tiles' binary points (a pass that does not
+// end the plan) or IEEE doubles rounded once (the last pass).  Between
+// passes the data stay 16-byte int64 pairs, so only the first pass converts
+// from double and only the last back to double.
+//
+// Headroom: every stored |v| < 2^62.  A reading pass of K levels aligns all
+// its elements to q_in = max(q_src) + K, i.e. shifts each right by at least
+// K bits (toward zero, so that conjugate inputs stay exactly conjugate),
+// after which 2^K-term sums stay below 2^62.
+
+__device__ __forceinline__ bool q_is_valid(int q) { return q > kQValidMin; }
+
+// v / 2^sh rounded toward zero (sh >= 0; 0 once sh >= 64)
+__device__ __forceinline__ long long shr_tz(long long v, unsigned sh) {
+  const unsigned long long s = (unsigned long long)(v >> 63);
+  unsigned long long a = ((unsigned long long)v ^ s) - s;
+  asm("shr.b64 %0, %0, %1;" : "+l"(a) : "r"(sh));   // PTX clamps the amount at 64
+  return (long long)((a ^ s) - s);
+}
+
+// Tiles meeting an Inf or NaN run the IEEE fp64 butterfly instead.  Out of
+// line (never taken for finite data) so the hot path stays small in the
+// instruction cache.  Elements are re-read: doubles as such, int64 sums of a
+// previous pass converted with their tile's binary point.
+template <bool kDec>
+__device__ __noinline__ void ieee_tile(const PassDesc& pd, const PassArgs& args, void* matp, const int* q_in,
+                                       int* q_out, long long tile, long long base, long long pbase, int nbase,
+                                       unsigned char* smem, int lane, int warp) {
+  double2 raw[kElems];
+  load_tile(pd, matp, base, lane, warp, raw);
+  if (q_in != nullptr) {
+    const Stage& s0 = pd.st[0];
+    long long pt = pbase;
+#pragma unroll
+    for (int i = 0; i < kLaneBits; ++i)
+      if ((lane >> i) & 1) pt += pd.prev_w[s0.lane[i]];
+    for (int i = 0; i < pd.D - kMinTileBits; ++i)
+      if ((warp >> i) & 1) pt += pd.prev_w[s0.warp[i]];
+    const int p0 = pd.prev_w[s0.reg[0]], p1 = pd.prev_w[s0.reg[1]], p2 = pd.prev_w[s0.reg[2]],
+              p3 = pd.prev_w[s0.reg[3]];
+    for (int e = 0; e < kElems; ++e) {
+      const int q = q_in[pt + reg_off(e, p0, p1, p2, p3)];
+      if (q == kQIeee) continue;
+      if (!q_is_valid(q)) { raw[e] = make_double2(0.0, 0.0); continue; }
+      raw[e].x = FixedArith::to_double_int(__double_as_longlong(raw[e].x), -q);
+      raw[e].y = FixedArith::to_double_int(__double_as_longlong(raw[e].y), -q);
+    }
+  }
+  const bool last = q_out == nullptr;
+  const double mul = kDec ? pow2d(-pd.K) : (last ? pow2d(args.out_pow2) * args.out_mul : 1.0);
+  finish_tile<F64Arith, kDec>(pd, args, matp, raw, mul, base, nbase, smem, lane, warp);
+  if (!last && threadIdx.x == 0) q_out[tile] = kQIeee;
+}
+
+template <bool kDec>
+__device__ __forceinline__ void fixed_tile(const PassDesc& pd, const PassArgs& args, void* matp, const int* q_in,
+                                           int* q_out, long long tile, long long base, long long pbase, int nbase,
+                                           unsigned char* smem, int lane, int warp) {
+  using V = FixedArith::V;
+  const int nwarps = 1 << (pd.D - kMinTileBits);
+  int* red = reinterpret_cast<int*>(smem + ((size_t)16 << pd.D));   // 64 ints after the tile
+  V v[kElems];
+  int qin;
+  if (q_in == nullptr) {
+    // ---- first pass: IEEE doubles onto the tile's binary point
+    double2 raw[kElems];
+    load_tile(pd, matp, base, lane, warp, raw);
+    uint32_t hmax = 0, nzw = 0;
+#pragma unroll
+    for (int e = 0; e < kElems; ++e) {
+      const uint32_t hx = (uint32_t)__double2hiint(raw[e].x) & 0x7fffffffu;
+      const uint32_t hy = (uint32_t)__double2hiint(raw[e].y) & 0x7fffffffu;
+      hmax = max(hmax, max(hx, hy));
+    }
+    if (args.skip_zero) {
+#pragma unroll
+      for (int e = 0; e < kElems; ++e)
+        nzw |= (uint32_t)__double2hiint(raw[e].x) << 1 | (uint32_t)__double2loint(raw[e].x) |
+               (uint32_t)__double2hiint(raw[e].y) << 1 | (uint32_t)__double2loint(raw[e].y);
+      nzw = __reduce_or_sync(kFull, nzw);
+    }
+    const uint32_t wmax = __reduce_max_sync(kFull, hmax >> 20);
+    if (lane == 0) { red[warp] = (int)wmax; red[16 + warp] = (int)nzw; }
+    __syncthreads();
+    int emax = 0, nz = 0;
+    for (int w = 0; w < nwarps; ++w) { emax = max(emax, red[w]); nz |= red[16 + w]; }
+    if (args.skip_zero && nz == 0) return;                // all +-0: outputs are zero already
+    if (emax == 2047) {                                   // Inf/NaN in the tile
+      ieee_tile<kDec>(pd, args, matp, nullptr, q_out, tile, base, pbase, nbase, smem, lane, warp);
+      return;
+    }
+    // x * 2^S with S = 1084 - K - emax_eff puts the largest element below 2^(62-K)
+    const int emax_eff = max(emax, 1);
+    const int shift_base = 9 - pd.K - emax_eff;
+#pragma unroll
+    for (int e = 0; e < kElems; ++e) {
+      v[e].re = FixedArith::to_fixed(raw[e].x, shift_base);
+      v[e].im = FixedArith::to_fixed(raw[e].y, shift_base);
+    }
+    qin = emax_eff + pd.K - 1084;                          // = -S
+  } else {
+    // ---- later pass: int64 sums with their previous tile's binary point
+    longlong2 raw[kElems];
+    load_tile(pd, matp, base, lane, warp, raw);
+    const Stage& s0 = pd.st[0];
+    long long pt = pbase;
+#pragma unroll
+    for (int i = 0; i < kLaneBits; ++i)
+      if ((lane >> i) & 1) pt += pd.prev_w[s0.lane[i]];
+    for (int i = 0; i < pd.D - kMinTileBits; ++i)
+      if ((warp >> i) & 1) pt += pd.prev_w[s0.warp[i]];
+    const int p0 = pd.prev_w[s0.reg[0]], p1 = pd.prev_w[s0.reg[1]], p2 = pd.prev_w[s0.reg[2]],
+              p3 = pd.prev_w[s0.reg[3]];
+    int q[kElems];
+#pragma unroll
+    for (int e = 0; e < kElems; ++e) q[e] = __ldg(q_in + pt + reg_off(e, p0, p1, p2, p3));
+    int qmax = kQValidMin, ieee = 0;
+#pragma unroll
+    for (int e = 0; e < kElems; ++e) { qmax = max(qmax, q[e]); ieee |= (q[e] == kQIeee); }
+    // kQIeee sits below kQValidMin, so it never wins the max
+    qmax = __reduce_max_sync(kFull, qmax);
+    ieee = __reduce_or_sync(kFull, ieee);
+    if (lane == 0) { red[warp] = qmax; red[16 + warp] = ieee; }
+    __syncthreads();
+    qmax = kQValidMin; ieee = 0;
+    for (int w = 0; w < nwarps; ++w) { qmax = max(qmax, red[w]); ieee |= red[16 + w]; }
+    if (ieee) {
+      ieee_tile<kDec>(pd, args, matp, q_in, q_out, tile, base, pbase, nbase, smem, lane, warp);
+      return;
+    }
+    if (qmax == kQValidMin) {                              // every source tile was zero
+      if (args.skip_zero) return;
+      qmax = 0;
+    }
+    qin = qmax + pd.K;
+#pragma unroll
+    for (int e = 0; e < kElems; ++e) {
+      if (q_is_valid(q[e])) {
+        const unsigned sh = (unsigned)(qin - q[e]);
+        v[e].re = shr_tz(raw[e].x, sh);
+        v[e].im = shr_tz(raw[e].y, sh);
+      } else {
+        v[e].re = 0; v[e].im = 0;
+      }
+    }
+  }
+
+  // ---- the pass's levels
+  V* sm = reinterpret_cast<V*>(smem);
+  for (int s = 0; s < pd.nstage; ++s) {
+    if (s > 0) exchange(v, pd, pd.st[s - 1], pd.st[s], sm, lane, warp, s > 1);
+    stage_levels<FixedArith, kDec>(v, pd.st[s], lane);
+  }
+  const int qout = qin - (kDec ? pd.K : 0);                // the 1/2 of Eq. 4 per level
+
+  // ---- store in place
+  const Stage& sl = pd.st[pd.nstage - 1];
+  const long long g = base + thread_goff(pd, sl, lane, warp);
+  const long long w0 = 1ll << pd.gbit[sl.reg[0]], w1 = 1ll << pd.gbit[sl.reg[1]];
+  const long long w2 = 1ll << pd.gbit[sl.reg[2]], w3 = 1ll << pd.gbit[sl.reg[3]];
+  const bool flags = args.flags_out != nullptr;
+  int nt = 0, n0 = 0, n1 = 0, n2 = 0, n3 = 0;
+  bool lanes_inside = true;
+  if (flags) {
+    nt = nbase + thread_next(pd, sl, lane, warp);
+    n0 = pd.next_w[sl.reg[0]]; n1 = pd.next_w[sl.reg[1]];
+    n2 = pd.next_w[sl.reg[2]]; n3 = pd.next_w[sl.reg[3]];
+#pragma unroll
+    for (int i = 0; i < kLaneBits; ++i) lanes_inside &= (pd.next_w[sl.lane[i]] == 0);
+  }
+  if (q_out != nullptr) {
+    longlong2* mat = reinterpret_cast<longlong2*>(matp);
+#pragma unroll
+    for (int e = 0; e < kElems; ++e) mat[g + reg_off(e, w0, w1, w2, w3)] = make_longlong2(v[e].re, v[e].im);
+    if (threadIdx.x == 0) q_out[tile] = qout;
+  } else {
+    double2* mat = reinterpret_cast<double2*>(matp);
+    const int T = -(qout + args.out_pow2);
+    const bool resid = args.out_mul != 1.0;                // non-power-of-two composition scale (rare)
+#pragma unroll
+    for (int e = 0; e < kElems; ++e) {
+      double2 o;
+      o.x = FixedArith::to_double(v[e].re, T);
+      o.y = FixedArith::to_double(v[e].im, T);
+      if (resid) { o.x *= args.out_mul; o.y *= args.out_mul; }
+      mat[g + reg_off(e, w0, w1, w2, w3)] = o;
+    }
+  }
+  if (flags) {
+#pragma unroll
+    for (int e = 0; e < kElems; ++e) {
+      const bool nz = (v[e].re | v[e].im) != 0;
+      const int id = nt + reg_off(e, n0, n1, n2, n3);
+      if (lanes_inside) {
+        if (__any_sync(kFull, nz) && lane == 0) args.flags_out[id] = 1;
+      } else if (nz) {
+        args.flags_out[id] = 1;
+      }
+    }
+  }
+}
+
+// Tiles of up to 2^12 elements run 256-thread CTAs, several per SM; 2^13
+// element tiles run 512-thread CTAs.
+#ifndef TPD_MIN_BLOCKS_256
+#define TPD_MIN_BLOCKS_256 2
+#endif
+
+template <class A, bool kDec, int kThreads>
+__global__ void __launch_bounds__(kThreads, kThreads == 256 ? TPD_MIN_BLOCKS_256 : 1)
+    k_pass(const __grid_constant__ PassDesc pd, const __grid_constant__ PassArgs args) {
+  using Store = typename A::Store;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  long long tile = (long long)blockIdx.x + (long long)blockIdx.y * gridDim.x;
+  void* matp = args.mat;
+  const int* q_in = args.q_in;
+  int* q_out = args.q_out;
+  if (args.ptrs != nullptr) {              // batched: tiles of matrix items[m] are contiguous in the grid
+    const long long m = tile / args.tiles_per_mat;
+    tile -= m * args.tiles_per_mat;
+    matp = args.ptrs[args.items[m]];
+    if (q_in) q_in += m * args.q_in_stride;
+    if (q_out) q_out += m * args.q_out_stride;
+  }
+  if (tile >= pd.ntiles) return;
+  if (args.flags_in != nullptr && args.flags_in[tile] == 0) return;
+
+  long long base = 0, pbase = 0;
+  int nbase = 0;
+  for (int j = 0; j < pd.nrest; ++j)
+    if ((tile >> j) & 1) {
+      base += 1ll << pd.rest_gbit[j];
+      nbase += (int)pd.next_rest_w[j];
+      pbase += pd.prev_rest_w[j];
+    }
+
+  if constexpr (A::kFixed) {
+    fixed_tile<kDec>(pd, args, matp, q_in, q_out, tile, base, pbase, nbase, smem, lane, warp);
+  } else {
+    Store raw[kElems];
+    load_tile(pd, matp, base, lane, warp, raw);
+    if (args.skip_zero) {
+      int nz = 0;
+#pragma unroll
+      for (int e = 0; e < kElems; ++e) nz |= A::nonzero(raw[e]);
+      if (!__syncthreads_or(nz)) return;
+    }
+    finish_tile<A, kDec>(pd, args, matp, raw, args.out_mul, base, nbase, smem, lane, warp);
+  }
+}
+
+// -------------------------------------------------------------- whole small matrices
+// One CTA per matrix of n <= 6 qubits held entirely in shared memory; every
+// level is a sweep over the 4^(n-1) quads.  Used for n <= 4 and in batches.
+
+template <class A, bool kDec>
+__device__ __forceinline__ void small_levels(typename A::V* sm, int n, int tid, int nthr) {
+  const int quads = 1 << (2 * n - 2);
+  for (int beta = 0; beta < n; ++beta) {
+    const int rbit = n + beta;
+    for (int q = tid; q < quads; q += nthr) {
+      // insert zero bits at beta and n+beta
+      const int lo = q & ((1 << beta) - 1);
+      const int q1 = q >> beta;
+      const int mid = q1 & ((1 << (n - 1)) - 1);
+      const int hi = q1 >> (n - 1);
+      const int i00 = lo | (mid << (beta + 1)) | (hi << (rbit + 1));
+      const int i01 = i00 | (1 << beta), i10 = i00 | (1 << rbit), i11 = i01 | (1 << rbit);
+      const typename A::V a00 = sm[i00], a01 = sm[i01], a10 = sm[i10], a11 = sm[i11];
+      if (kDec) {
+        sm[i00] = A::add(a00, a11);
+        sm[i01] = A::add(a01, a10);
+        sm[i10] = A::mul_i(A::sub(a01, a10));
+        sm[i11] = A::sub(a00, a11);
+      } else {
+        const typename A::V iy = A::mul_i(a10);
+        sm[i00] = A::add(a00, a11);
+        sm[i01] = A::sub(a01, iy);
+        sm[i10] = A::add(a01, iy);
+        sm[i11] = A::sub(a00, a11);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <class A, bool kDec>
+__device__ __forceinline__ void small_run(typename A::Store* mat, int n, int skip, int scale_mode,
+                                          unsigned char* smem, int tid, int nthr, int emax_in) {
+  using V = typename A::V;
+  V* sm = reinterpret_cast<V*>(smem);
+  const int count = 1 << (2 * n);
+  int shift_base = 0, outT = 0;
+  if constexpr (A::kFixed) {
+    const int emax_eff = max(emax_in, 1);
+    shift_base = 9 - n - emax_eff;
+    // fixed = x * 2^S with headroom for n levels; the output is sum * 2^-S,
+    // times 2^-n for the decomposition (the 1/2 of Eq. 4 per level) or for a
+    // composition scaled to the adjoint.
+    const int S = 1084 - n - emax_eff;
+    outT = (kDec || scale_mode) ? S + n : S;
+  }
+  for (int i = tid; i < count; i += nthr) {
+    const typename A::Store x = mat[i];
+    if constexpr (A::kFixed) {
+      V t; t.re = A::to_fixed(x.x, shift_base); t.im = A::to_fixed(x.y, shift_base);
+      sm[i] = t;
+    } else {
+      sm[i] = A::load(x);
+    }
+  }
+  __syncthreads();
+  small_levels<A, kDec>(sm, n, tid, nthr);
+  const double mul = (kDec || scale_mode) ? pow2d(-n) : 1.0;
+  for (int i = tid; i < count; i += nthr) {
+    typename A::Store o;
+    if constexpr (A::kFixed) {
+      o.x = A::to_double(sm[i].re, outT);
+      o.y = A::to_double(sm[i].im, outT);
+    } else {
+      o = A::store(sm[i], OutScale{0, 1.0}, mul);
+    }
+    mat[i] = o;
+  }
+}
+
+template <class A, bool kDec>
+__global__ void __launch_bounds__(256) k_small(const SmallArgs args) {
+  using Store = typename A::Store;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  int idx = blockIdx.x;
+  if (args.items) idx = args.items[idx];
+  Store* mat = reinterpret_cast<Store*>(args.ptrs ? args.ptrs[idx] : args.mat);
+  const int n = args.ptrs ? args.ns[idx] : args.n;
+  const int count = 1 << (2 * n);
+  // max exponent / nonzero over the whole matrix
+  uint32_t emax = 0, nzw = 0;
+  for (int i = tid; i < count; i += nthr) {
+    const Store x = mat[i];
+    uint32_t hx, hy, lx, ly;
+    if constexpr (sizeof(Store) == 16) {
+      hx = (uint32_t)__double2hiint(((const double2&)x).x) & 0x7fffffffu;
+      hy = (uint32_t)__double2hiint(((const double2&)x).y) & 0x7fffffffu;
+      lx = (uint32_t)__double2loint(((const double2&)x).x);
+      ly = (uint32_t)__double2loint(((const double2&)x).y);
+      emax = max(emax, max(hx >> 20, hy >> 20));
+    } else {
+      hx = __float_as_uint(((const float2&)x).x) & 0x7fffffffu;
+      hy = __float_as_uint(((const float2&)x).y) & 0x7fffffffu;
+      lx = ly = 0;
+    }
+    nzw |= hx | hy | lx | ly;
+  }
+  const int nz = __syncthreads_or((int)(nzw != 0));
+  if (args.skip_zero && !nz) return;
+  uint32_t* red = reinterpret_cast<uint32_t*>(smem);
+  emax = __reduce_max_sync(kFull, emax);
+  if ((tid & 31) == 0) red[tid >> 5] = emax;
+  __syncthreads();
+  uint32_t em = 0;
+  for (int w = 0; w < (nthr + 31) / 32; ++w) em = max(em, red[w]);
+  __syncthreads();
+  if constexpr (A::kFixed) {
+    if (em == 2047) {
+      small_run<F64Arith, kDec>(mat, n, args.skip_zero, args.scale_mode, smem, tid, nthr, 0);
+      return;
+    }
+  }
+  small_run<A, kDec>(mat, n, args.skip_zero, args.scale_mode, smem, tid, nthr, (int)em);
+}
+
+}  // namespace tpd

@@ -1,0 +1,82 @@
+// Pass plans for the in-place Pauli decomposition butterfly.
+//
+// The element at flat index r*N + c of an N x N matrix (N = 2^n) has 2n index
+// bits: column bits c_0..c_{n-1} are global bits 0..n-1, row bits r_0..r_{n-1}
+// are global bits n..2n-1.  One qubit level beta applies Eq. 4 to every 2x2
+// quad over (r_beta, c_beta), i.e. it couples global bits beta and n+beta.
+// Eq. 5 makes the levels commute, so a pass may apply any group of levels.
+//
+// A pass applies the levels [b, b+K).  Its work unit, a *tile*, is the set of
+// 2^D elements that agree on all global bits outside a D-bit tile mask; the
+// mask holds the 2K bits of the levels plus D-2K "passenger" bits, the lowest
+// column bits, so that every thread's memory runs are at least 128 bytes.
+// Tile bit i is the i-th lowest global bit of the mask.
+//
+// Inside a CTA of 2^(D-4) threads each thread holds E = 16 elements in
+// registers.  A *stage* fixes which tile bits are register bits, lane bits and
+// warp bits.  A level is applied in a stage either in registers (its column
+// and row bit are both register bits) or across lanes with shuffles (column
+// bit a lane bit, row bit a register bit).  Consecutive stages exchange the
+// tile through shared memory.  Lanes always cover tile bits 0..2 (0..3 for
+// 8-byte elements), so shared-memory accesses are conflict-free and global
+// accesses cover whole 128-byte lines.
+#pragma once
+
+#include <stdint.h>
+
+namespace tpd {
+
+constexpr int kRegBits = 4;                 // E = 16 elements per thread
+constexpr int kElems = 1 << kRegBits;
+constexpr int kLaneBits = 5;
+constexpr int kMinTileBits = kRegBits + kLaneBits;   // one warp
+constexpr int kMaxTileBits = 13;                      // 512 threads
+constexpr int kMaxWarpBits = kMaxTileBits - kMinTileBits;
+constexpr int kMaxStages = 4;
+constexpr int kMaxQubits = 16;
+constexpr int kMaxRuns = 2 * kMaxQubits;
+constexpr int kMaxLevels = 6;
+
+struct Stage {
+  int8_t reg[kRegBits];      // tile bit of register-index bit i
+  int8_t lane[kLaneBits];    // tile bit of lane bit i
+  int8_t warp[kMaxWarpBits]; // tile bit of warp bit i (D-9 of them)
+  int8_t npair;              // in-register levels: reg bits (2p, 2p+1) = (column, row)
+  int8_t nshfl;              // shuffle levels: reg bit 2*npair+s is the row bit ...
+  int8_t shfl_lane[4];       // ... and lane bit shfl_lane[s] the column bit
+};
+
+struct PassDesc {
+  int32_t n;                 // qubits of the matrix
+  int32_t D;                 // tile bits
+  int32_t K;                 // levels applied by this pass
+  int32_t b;                 // first level
+  int32_t nstage;
+  int32_t nrest;             // tile-id bits = 2n - D
+  int64_t ntiles;            // 2^(2n - D)
+  Stage st[kMaxStages];
+  int8_t gbit[kMaxTileBits];            // global bit of tile bit i
+  int8_t rest_gbit[2 * kMaxQubits];     // global bit of tile-id bit j (ascending)
+  // Zero-skip bookkeeping.  The tile id, in the NEXT pass, of an element is
+  // linear in the element's global bits: next_w[i] per tile bit i and
+  // next_rest_w[j] per tile-id bit j (0 where the bit lies inside the next
+  // pass's tile).
+  int32_t has_next;
+  int32_t next_w[kMaxTileBits];
+  int64_t next_rest_w[2 * kMaxQubits];
+  // Fixed point between passes: an element's tile id in the PREVIOUS pass
+  // (whose per-tile binary point it was stored with), by the same linear rule.
+  int32_t has_prev;
+  int32_t prev_w[kMaxTileBits];
+  int64_t prev_rest_w[2 * kMaxQubits];
+};
+
+// A whole-matrix plan: one pass per group of levels.
+struct Plan {
+  int32_t n;
+  int32_t npass;
+  int32_t elem_bytes;        // 16 (c128, compensated c64 in registers) or 8
+  PassDesc pass[kMaxQubits];  // one level per pass at worst
+};
+
+}  // namespace tpd

@@ -1,0 +1,308 @@
+// Host planner: splits the n qubit levels into passes and lays out each pass's
+// tile and stages (see tpd_plan.h).
+#include "tpd_planner.h"
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <memory>
+#include <vector>
+
+namespace tpd {
+
+namespace {
+
+struct Level { int c, r; };  // tile bit positions of a level's column and row bit
+
+struct StageChoice {
+  std::vector<int> pairs, shfls;  // level indices
+};
+
+struct SearchCtx {
+  int D, lf, K;
+  std::vector<Level> lev;
+  double cx, cs;
+  // memo over (stage index, remaining-level mask): best cost and choice
+  double memo_cost[kMaxStages + 1][1 << kMaxLevels];
+  int memo_nst[kMaxStages + 1][1 << kMaxLevels];
+  bool memo_done[kMaxStages + 1][1 << kMaxLevels];
+  StageChoice memo_choice[kMaxStages + 1][1 << kMaxLevels];
+};
+
+bool in(const std::vector<int>& v, int x) { return std::find(v.begin(), v.end(), x) != v.end(); }
+
+// Lanes of stage `si` for a choice: stage 0 uses tile bits 0..4; later stages
+// the forced low bits, the shuffles' column bits, then the lowest free bits.
+bool stage_lanes(const SearchCtx& c, int si, const StageChoice& ch, std::vector<int>& lanes,
+                 std::vector<int>& regs) {
+  regs.clear();
+  for (int j : ch.pairs) { regs.push_back(c.lev[j].c); regs.push_back(c.lev[j].r); }
+  for (int j : ch.shfls) regs.push_back(c.lev[j].r);
+  lanes.clear();
+  if (si == 0) {
+    for (int i = 0; i < kLaneBits; ++i) lanes.push_back(i);
+  } else {
+    for (int i = 0; i < c.lf; ++i) lanes.push_back(i);
+    for (int j : ch.shfls)
+      if (!in(lanes, c.lev[j].c)) lanes.push_back(c.lev[j].c);
+    for (int b = 0; b < c.D && (int)lanes.size() < kLaneBits; ++b)
+      if (!in(lanes, b) && !in(regs, b)) lanes.push_back(b);
+  }
+  if ((int)lanes.size() != kLaneBits) return false;
+  for (int x : regs)
+    if (in(lanes, x)) return false;
+  for (int j : ch.shfls)
+    if (!in(lanes, c.lev[j].c)) return false;
+  return (int)regs.size() <= kRegBits;
+}
+
+// Cheapest way to finish the levels in `remaining` starting at stage si:
+// each stage after the first costs an exchange, each shuffle level its cost.
+double search(SearchCtx& c, int si, unsigned remaining, int* nst) {
+  if (remaining == 0) { *nst = 0; return 0.0; }
+  if (si >= kMaxStages) { *nst = 99; return 1e30; }
+  if (c.memo_done[si][remaining]) { *nst = c.memo_nst[si][remaining]; return c.memo_cost[si][remaining]; }
+  std::vector<int> rem;
+  for (int j = 0; j < c.K; ++j)
+    if (remaining & (1u << j)) rem.push_back(j);
+  const int R = (int)rem.size();
+  int total = 1;
+  for (int i = 0; i < R; ++i) total *= 3;
+  double best = 1e30;
+  int best_nst = 99;
+  StageChoice best_ch;
+  std::vector<int> lanes, regs;
+  for (int code = 1; code < total; ++code) {  // per level: 0 later, 1 pair, 2 shuffle
+    StageChoice ch;
+    int x = code;
+    for (int i = 0; i < R; ++i, x /= 3) {
+      if (x % 3 == 1) ch.pairs.push_back(rem[i]);
+      else if (x % 3 == 2) ch.shfls.push_back(rem[i]);
+    }
+    if ((int)ch.pairs.size() > 2) continue;
+    if (2 * (int)ch.pairs.size() + (int)ch.shfls.size() > kRegBits) continue;
+    if (!stage_lanes(c, si, ch, lanes, regs)) continue;
+    unsigned done = 0;
+    for (int j : ch.pairs) done |= 1u << j;
+    for (int j : ch.shfls) done |= 1u << j;
+    int sub_nst = 0;
+    const double sub = search(c, si + 1, remaining & ~done, &sub_nst);
+    const double cost = (si > 0 ? c.cx : 0.0) + c.cs * (double)ch.shfls.size() + sub;
+    if (cost < best - 1e-9 || (cost < best + 1e-9 && sub_nst + 1 < best_nst)) {
+      best = cost; best_nst = sub_nst + 1; best_ch = ch;
+    }
+  }
+  c.memo_done[si][remaining] = true;
+  c.memo_cost[si][remaining] = best;
+  c.memo_nst[si][remaining] = best_nst;
+  c.memo_choice[si][remaining] = best_ch;
+  *nst = best_nst;
+  return best;
+}
+
+// Tile mask of a pass: the 2K level bits plus the D-2K lowest column bits
+// outside the group, then the lowest row bits.
+std::vector<int> tile_bits(int n, int b, int K, int D) {
+  std::vector<int> t;
+  for (int j = 0; j < K; ++j) { t.push_back(b + j); t.push_back(n + b + j); }
+  for (int g = 0; g < 2 * n && (int)t.size() < D; ++g)
+    if (!in(t, g)) t.push_back(g);
+  std::sort(t.begin(), t.end());
+  return t;
+}
+
+bool build_pass(int n, int b, int K, int D, int lf, double cs, PassDesc* pd, std::string* err) {
+  std::memset(pd, 0, sizeof(*pd));
+  if (K < 1 || K > kMaxLevels || D < kMinTileBits || D > kMaxTileBits || 2 * K > D || D > 2 * n ||
+      b < 0 || b + K > n) {
+    if (err) *err = "invalid pass shape";
+    return false;
+  }
+  std::vector<int> t = tile_bits(n, b, K, D);
+  pd->n = n; pd->D = D; pd->K = K; pd->b = b;
+  for (int i = 0; i < D; ++i) pd->gbit[i] = (int8_t)t[i];
+  std::vector<int> rest;
+  for (int g = 0; g < 2 * n; ++g)
+    if (!in(t, g)) rest.push_back(g);
+  pd->nrest = (int)rest.size();
+  for (int j = 0; j < pd->nrest; ++j) pd->rest_gbit[j] = (int8_t)rest[j];
+  pd->ntiles = 1ll << pd->nrest;
+
+  std::unique_ptr<SearchCtx> cp(new SearchCtx());
+  SearchCtx& c = *cp;
+  for (int si = 0; si <= kMaxStages; ++si)
+    for (int m = 0; m < (1 << kMaxLevels); ++m) c.memo_done[si][m] = false;
+  c.D = D; c.lf = lf; c.K = K;
+  for (int j = 0; j < K; ++j) {
+    Level L;
+    L.c = (int)(std::find(t.begin(), t.end(), b + j) - t.begin());
+    L.r = (int)(std::find(t.begin(), t.end(), n + b + j) - t.begin());
+    c.lev.push_back(L);
+  }
+  c.cx = 2.0; c.cs = cs;
+  int nst = 0;
+  if (search(c, 0, (1u << K) - 1, &nst) >= 1e29) {
+    if (err) *err = "no stage plan";
+    return false;
+  }
+  std::vector<StageChoice> chosen;
+  unsigned remaining = (1u << K) - 1;
+  for (int si = 0; remaining; ++si) {
+    const StageChoice& ch = c.memo_choice[si][remaining];
+    chosen.push_back(ch);
+    for (int j : ch.pairs) remaining &= ~(1u << j);
+    for (int j : ch.shfls) remaining &= ~(1u << j);
+  }
+  pd->nstage = (int)chosen.size();
+  std::vector<int> lanes, regs;
+  for (int si = 0; si < pd->nstage; ++si) {
+    const StageChoice& ch = chosen[si];
+    stage_lanes(c, si, ch, lanes, regs);
+    Stage& st = pd->st[si];
+    std::vector<bool> used(D, false);
+    for (int x : lanes) used[x] = true;
+    for (int x : regs) used[x] = true;
+    // fillers: the highest unused bits
+    for (int bit = D - 1; bit >= 0 && (int)regs.size() < kRegBits; --bit)
+      if (!used[bit]) { regs.push_back(bit); used[bit] = true; }
+    std::vector<int> warps;
+    for (int bit = 0; bit < D; ++bit)
+      if (!used[bit]) warps.push_back(bit);
+    std::sort(lanes.begin(), lanes.end());
+    for (int i = 0; i < kRegBits; ++i) st.reg[i] = (int8_t)regs[i];
+    for (int i = 0; i < kLaneBits; ++i) st.lane[i] = (int8_t)lanes[i];
+    for (int i = 0; i < (int)warps.size(); ++i) st.warp[i] = (int8_t)warps[i];
+    st.npair = (int8_t)ch.pairs.size();
+    st.nshfl = (int8_t)ch.shfls.size();
+    for (int s = 0; s < st.nshfl; ++s) {
+      const int cb = c.lev[ch.shfls[s]].c;
+      st.shfl_lane[s] = (int8_t)(std::find(lanes.begin(), lanes.end(), cb) - lanes.begin());
+    }
+  }
+  return true;
+}
+
+void set_next(PassDesc* cur, const PassDesc& nxt) {
+  std::vector<int> rest_next(nxt.rest_gbit, nxt.rest_gbit + nxt.nrest);
+  auto w = [&](int g) -> long long {
+    auto it = std::find(rest_next.begin(), rest_next.end(), g);
+    if (it == rest_next.end()) return 0;
+    return 1ll << (int)(it - rest_next.begin());
+  };
+  cur->has_next = 1;
+  for (int i = 0; i < cur->D; ++i) cur->next_w[i] = (int32_t)w(cur->gbit[i]);
+  for (int j = 0; j < cur->nrest; ++j) cur->next_rest_w[j] = w(cur->rest_gbit[j]);
+}
+
+// Tile id in the previous pass of an element of `cur`, as linear weights.
+void set_prev(PassDesc* cur, const PassDesc& prv) {
+  std::vector<int> rest_prev(prv.rest_gbit, prv.rest_gbit + prv.nrest);
+  auto w = [&](int g) -> long long {
+    auto it = std::find(rest_prev.begin(), rest_prev.end(), g);
+    if (it == rest_prev.end()) return 0;
+    return 1ll << (int)(it - rest_prev.begin());
+  };
+  cur->has_prev = 1;
+  for (int i = 0; i < cur->D; ++i) cur->prev_w[i] = (int32_t)w(cur->gbit[i]);
+  for (int j = 0; j < cur->nrest; ++j) cur->prev_rest_w[j] = w(cur->rest_gbit[j]);
+}
+
+}  // namespace
+
+int arith_elem_bytes(int dtype, int precision) {
+  if (dtype == 0) return 16;               // fixed int64 pair or double2
+  return precision == 2 ? 16 : 8;          // compensated: hi/lo pairs in registers
+}
+
+bool build_plan(int n, int dtype, int precision, int tile_bits_opt, int max_levels_opt, Plan* plan,
+                std::string* err) {
+  std::memset(plan, 0, sizeof(*plan));
+  plan->n = n;
+  plan->elem_bytes = arith_elem_bytes(dtype, precision);
+  if (n < 1 || n > kMaxQubits) {
+    if (err) *err = "n out of range";
+    return false;
+  }
+  if (2 * n < kMinTileBits) {  // whole matrix in one CTA
+    plan->npass = 0;
+    return true;
+  }
+  const int lf = dtype == 1 ? 4 : 3;                       // low tile bits always on lanes
+  const double cs = plan->elem_bytes == 16 ? 1.0 : 0.5;    // shuffle cost per level
+  int dmax = tile_bits_opt ? tile_bits_opt : (dtype == 1 && precision != 2 ? 13 : 12);
+  dmax = std::min(dmax, 2 * n);
+  int kcap = max_levels_opt ? max_levels_opt : kMaxLevels;
+  const int k0 = std::min({n, dmax / 2, kcap});
+  const int rem = n - k0;
+  std::vector<std::pair<int, int>> groups;  // (K, D)
+  groups.push_back({k0, dmax});
+  if (rem > 0) {
+    auto kmax_for = [&](int D) { return std::max(1, std::min({(D - lf) / 2, kcap, kMaxLevels})); };
+    int D1 = dmax;
+    int m = (rem + kmax_for(D1) - 1) / kmax_for(D1);
+    if (!tile_bits_opt && D1 < kMaxTileBits && 2 * n >= D1 + 1) {
+      const int m13 = (rem + kmax_for(D1 + 1) - 1) / kmax_for(D1 + 1);
+      if (m13 < m) { D1 = D1 + 1; m = m13; }
+    }
+    const int base = rem / m, extra = rem % m;
+    for (int i = 0; i < m; ++i) groups.push_back({base + (i < extra ? 1 : 0), D1});
+  }
+  if ((int)groups.size() > kMaxQubits) {
+    if (err) *err = "too many passes";
+    return false;
+  }
+  plan->npass = (int)groups.size();
+  int b = 0;
+  for (int p = 0; p < plan->npass; ++p) {
+    const int K = groups[p].first;
+    int D = std::min(groups[p].second, 2 * n);
+    if (D < 2 * K) D = 2 * K;
+    if (!build_pass(n, b, K, D, lf, cs, &plan->pass[p], err)) return false;
+    b += K;
+  }
+  for (int p = 0; p + 1 < plan->npass; ++p) set_next(&plan->pass[p], plan->pass[p + 1]);
+  for (int p = 1; p < plan->npass; ++p) set_prev(&plan->pass[p], plan->pass[p - 1]);
+  return true;
+}
+
+std::string describe_plan(const Plan& plan) {
+  std::string s;
+  char buf[512];
+  if (plan.npass == 0) {
+    std::snprintf(buf, sizeof(buf), "n=%d whole-matrix kernel (%d elements in shared memory)\n", plan.n,
+                  1 << (2 * plan.n));
+    return buf;
+  }
+  for (int p = 0; p < plan.npass; ++p) {
+    const PassDesc& pd = plan.pass[p];
+    std::snprintf(buf, sizeof(buf), "pass %d: levels [%d,%d) D=%d tiles=%lld gbits=", p, pd.b, pd.b + pd.K,
+                  pd.D, (long long)pd.ntiles);
+    s += buf;
+    for (int i = 0; i < pd.D; ++i) {
+      std::snprintf(buf, sizeof(buf), "%s%d", i ? "," : "", pd.gbit[i]);
+      s += buf;
+    }
+    for (int si = 0; si < pd.nstage; ++si) {
+      const Stage& st = pd.st[si];
+      std::snprintf(buf, sizeof(buf), " | stage %d: pairs=%d shfl=%d reg=%d,%d,%d,%d lane=%d,%d,%d,%d,%d", si,
+                    st.npair, st.nshfl, st.reg[0], st.reg[1], st.reg[2], st.reg[3], st.lane[0], st.lane[1],
+                    st.lane[2], st.lane[3], st.lane[4]);
+      s += buf;
+      s += " warp=";
+      for (int i = 0; i < pd.D - kMinTileBits; ++i) {
+        std::snprintf(buf, sizeof(buf), "%s%d", i ? "," : "", st.warp[i]);
+        s += buf;
+      }
+      s += " shfl_lane=";
+      for (int i = 0; i < st.nshfl; ++i) {
+        std::snprintf(buf, sizeof(buf), "%s%d", i ? "," : "", st.shfl_lane[i]);
+        s += buf;
+      }
+    }
+    s += "\n";
+  }
+  return s;
+}
+
+}  // namespace tpd

@@ -10,6 +10,9 @@ Conventions: A is row-major N x N, N = 2^n; qubit j = 1..n is row/column bit
 n-j (qubit 1 most significant, the block partition of Eq. 3); a bit value s
 gives the Z eigenvalue 1 - 2s.
 """
+import concurrent.futures
+import os
+
 import numpy as np
 
 DYADIC_BITS = 20  # couplings rounded to multiples of 2^-20 keep planted sums exact in fp64
@@ -19,25 +22,41 @@ def _rng(seed, *stream):
     return np.random.Generator(np.random.PCG64(np.random.SeedSequence([int(seed), *map(int, stream)])))
 
 
+def _threads():
+    return max(1, min(32, os.cpu_count() or 1))
+
+
 def hermitian(n, seed, dtype=np.complex128):
     """A = (B + B^H)/2 with Re B, Im B i.i.d. N(0,1).  Exactly Hermitian in
     floating point: entry (i,j) and (j,i) are conjugate sums of the same pair.
-    B is drawn in row blocks with one stream per block, so the result does not
-    depend on how the work is split."""
+    B is drawn in fixed row blocks, one stream per block, and symmetrised in
+    place tile by tile, so the bits do not depend on the thread count."""
     N = 1 << n
-    blk = max(1, min(N, (1 << 24) // N))  # ~16M entries per block
-    B = np.empty((N, N), dtype=np.complex128)
-    for r0 in range(0, N, blk):
-        g = _rng(seed, 1, r0)
-        rows = min(blk, N - r0)
-        B.real[r0:r0 + rows] = g.standard_normal((rows, N))
-        B.imag[r0:r0 + rows] = g.standard_normal((rows, N))
+    rows_per = max(1, min(N, (1 << 22) // N))  # ~4M entries per stream
     A = np.empty((N, N), dtype=np.complex128)
-    for r0 in range(0, N, blk):
-        rows = min(blk, N - r0)
-        A[r0:r0 + rows] = B[r0:r0 + rows] + B[:, r0:r0 + rows].T.conj()
-    A *= 0.5
-    del B
+
+    def draw(r0):
+        g = _rng(seed, 1, r0)
+        rows = min(rows_per, N - r0)
+        A.real[r0:r0 + rows] = g.standard_normal((rows, N))
+        A.imag[r0:r0 + rows] = g.standard_normal((rows, N))
+
+    T = min(N, 512)  # symmetrisation tile
+
+    def sym(ij):
+        i, j = ij
+        X = A[i:i + T, j:j + T]
+        if i == j:
+            X[...] = (X + X.T.conj()) * 0.5
+        else:
+            Y = A[j:j + T, i:i + T]
+            S = (X + Y.T.conj()) * 0.5
+            X[...] = S
+            Y[...] = S.T.conj()
+
+    with concurrent.futures.ThreadPoolExecutor(_threads()) as ex:
+        list(ex.map(draw, range(0, N, rows_per)))
+        list(ex.map(sym, [(i, j) for i in range(0, N, T) for j in range(i, N, T)]))
     if dtype == np.complex64:
         return A.astype(np.complex64)
     return A

@@ -1,0 +1,200 @@
+"""Host-side tests of libtpd.so (no GPU needed): the library loads, exports
+every symbol include/tpd.h declares, rejects bad arguments before touching the
+device, and its pass plans are valid -- checked by emulating each plan's data
+movement on the CPU and comparing with the oracle."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2310_13421_gb300 import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2310_13421_gb300 import buildlib, _lib
+    buildlib.build()
+    _lib.load()
+    return _lib
+
+
+def _declared_symbols():
+    with open(os.path.join(ROOT, "include", "tpd.h")) as fh:
+        text = fh.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(tpd_[a-z_]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(L):
+    lib = ctypes.CDLL(L.LIB)
+    declared = _declared_symbols()
+    assert len(declared) >= 10
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert set(declared) == set(L.SYMBOLS)
+
+
+def test_status_strings_and_version(L):
+    assert L.status_string(0) == "TPD_OK"
+    assert L.status_string(6) == "TPD_ERR_TIMEOUT"
+    assert L.tpd_version() >= 100
+
+
+def test_argument_errors_return_before_any_launch(L):
+    # none of these reaches the CUDA runtime
+    assert L.tpd_decompose(0, 4, L.TPD_C128) == L.TPD_ERR_INVALID_ARG          # null
+    assert L.tpd_decompose(4096, 0, L.TPD_C128) == L.TPD_ERR_INVALID_ARG       # n = 0
+    assert L.tpd_decompose(4096, 17, L.TPD_C128) == L.TPD_ERR_INVALID_ARG      # n too big
+    assert L.tpd_decompose(4096, 4, 7) == L.TPD_ERR_INVALID_ARG                # dtype
+    assert L.tpd_decompose(4104, 4, L.TPD_C128) == L.TPD_ERR_MISALIGNED        # 8 mod 16
+    assert L.tpd_decompose(4100, 4, L.TPD_C64) == L.TPD_ERR_MISALIGNED         # 4 mod 8
+    assert L.tpd_decompose(4096, 4, L.TPD_C128, L.options(precision=2)) == L.TPD_ERR_UNSUPPORTED
+    assert L.tpd_decompose(4096, 4, L.TPD_C64, L.options(precision=3)) == L.TPD_ERR_UNSUPPORTED
+    assert L.tpd_decompose(4096, 4, L.TPD_C128, L.options(precision=9)) == L.TPD_ERR_INVALID_ARG
+    assert L.tpd_decompose(4096, 4, L.TPD_C128, L.options(tile_bits=20)) == L.TPD_ERR_INVALID_ARG
+    assert L.tpd_compose(4096, 8, L.TPD_C128, 0.0) == L.TPD_ERR_INVALID_ARG
+    assert L.tpd_compose(4096, 8, L.TPD_C128, float("inf")) == L.TPD_ERR_INVALID_ARG
+    assert L.tpd_compose(4096, 3, L.TPD_C128, 3.0) == L.TPD_ERR_UNSUPPORTED   # whole-matrix: 1 or 2^-n
+    # zero skip on a multi-pass plan needs the workspace
+    assert L.tpd_workspace_size(10, L.TPD_C128, L.options(precision=1, skip_zero=True)) > 0
+    assert L.tpd_workspace_size(10, L.TPD_C128, L.options(precision=1)) == 0
+    assert L.tpd_decompose(4096, 10, L.TPD_C128, L.options(precision=1, skip_zero=True)) == L.TPD_ERR_WORKSPACE
+    # the fixed point keeps one binary point per tile between passes
+    ws = L.tpd_workspace_size(14, L.TPD_C128, L.options())
+    assert ws >= 4 * (2 ** 16 + 2 ** 16)
+    assert L.tpd_workspace_size(14, L.TPD_C128, L.options(skip_zero=True)) > ws
+    assert L.tpd_workspace_size(6, L.TPD_C128, L.options()) == 0      # one pass: nothing between passes
+    assert L.tpd_decompose(4096, 10, L.TPD_C128) == L.TPD_ERR_WORKSPACE
+    assert L.tpd_decompose(4096, 10, L.TPD_C128, None, 4104, 1 << 20) == L.TPD_ERR_MISALIGNED
+    # batched
+    assert L.tpd_batched_workspace_size([3, 4, 13], L.TPD_C128) == 0
+    assert L.tpd_batched_workspace_size([3, 4, 10], L.TPD_C128) > 0
+    assert L.tpd_decompose_batched(0, 0, [3, 4], L.TPD_C128) == L.TPD_ERR_INVALID_ARG
+    assert L.tpd_decompose_batched(4096, 4096, [3, 0], L.TPD_C128, None, 4096, 1 << 20) == L.TPD_ERR_INVALID_ARG
+    assert L.tpd_decompose_batched(4096, 4096, [3, 4], L.TPD_C128, None, 0, 0) == L.TPD_ERR_WORKSPACE
+    assert L.tpd_decompose_batched(4096, 4096, [3, 4], L.TPD_C128, L.options(skip_zero=True), 4096,
+                                   1 << 20) == L.TPD_ERR_UNSUPPORTED
+
+
+# ------------------------------------------------------------------ plan emulation
+
+def _parse(desc):
+    passes = []
+    for line in desc.strip().splitlines():
+        head, *stages = line.split(" | ")
+        m = re.match(r"pass \d+: levels \[(\d+),(\d+)\) D=(\d+) tiles=(\d+) gbits=([\d,]+)", head)
+        b, e, D, ntiles, gbits = m.groups()
+        p = dict(b=int(b), K=int(e) - int(b), D=int(D), ntiles=int(ntiles),
+                 gbits=[int(x) for x in gbits.split(",")], stages=[])
+        for st in stages:
+            kv = dict(re.findall(r"(\w+)=([\d,]*)", st))
+            ints = lambda k: [int(x) for x in kv[k].split(",")] if kv.get(k) else []
+            p["stages"].append(dict(npair=int(kv["pairs"]), nshfl=int(kv["shfl"]), reg=ints("reg"),
+                                    lane=ints("lane"), warp=ints("warp"), shfl_lane=ints("shfl_lane")))
+        passes.append(p)
+    return passes
+
+
+def _level_on(x, cpos, rpos, dec=True):
+    """Eq. 4 applied to tile axis pair (column bit cpos, row bit rpos) of x[..., 2^D]."""
+    D = x.shape[-1].bit_length() - 1
+    shp = [2] * D
+    y = x.reshape(shp[::-1])  # numpy axis k <-> tile bit D-1-k
+    ac, ar = D - 1 - cpos, D - 1 - rpos
+
+    def sl(r, c):
+        idx = [slice(None)] * D
+        idx[ar], idx[ac] = r, c
+        return tuple(idx)
+
+    a00, a01, a10, a11 = (y[sl(0, 0)].copy(), y[sl(0, 1)].copy(), y[sl(1, 0)].copy(), y[sl(1, 1)].copy())
+    y[sl(0, 0)] = (a00 + a11) / 2
+    y[sl(0, 1)] = (a01 + a10) / 2
+    y[sl(1, 0)] = 1j * (a01 - a10) / 2
+    y[sl(1, 1)] = (a00 - a11) / 2
+    return y.reshape(-1)
+
+
+def _emulate(A, passes, n):
+    flat = A.reshape(-1).copy()
+    for p in passes:
+        D, gb = p["D"], p["gbits"]
+        rest = [g for g in range(2 * n) if g not in gb]
+        tidx = np.arange(1 << D)
+        off_in = np.zeros(1 << D, dtype=np.int64)
+        for i, g in enumerate(gb):
+            off_in += ((tidx >> i) & 1) << g
+        for tile in range(p["ntiles"]):
+            base = sum(((tile >> j) & 1) << g for j, g in enumerate(rest))
+            x = flat[base + off_in]
+            done = []
+            for st in p["stages"]:
+                # every stage mapping must be a bijection of the D tile bits
+                assert sorted(st["reg"] + st["lane"] + st["warp"]) == list(range(D))
+                assert set(range(3)) <= set(st["lane"])
+                lv = []
+                for q in range(st["npair"]):
+                    lv.append((st["reg"][2 * q], st["reg"][2 * q + 1]))
+                for s in range(st["nshfl"]):
+                    lv.append((st["lane"][st["shfl_lane"][s]], st["reg"][2 * st["npair"] + s]))
+                for cpos, rpos in lv:
+                    # the pair must be one level's column and row bit
+                    c, r = gb[cpos], gb[rpos]
+                    assert r == c + n and p["b"] <= c < p["b"] + p["K"]
+                    x = _level_on(x, cpos, rpos)
+                    done.append(c)
+            assert sorted(done) == list(range(p["b"], p["b"] + p["K"]))
+            flat[base + off_in] = x
+    return flat
+
+
+def _to_string_order(flat, n):
+    # independent of the package helper: walk strings, place t_j = 2 r + c
+    out = np.empty(4 ** n, dtype=flat.dtype)
+    N = 1 << n
+    for s in range(4 ** n):
+        r = c = 0
+        for beta in range(n):
+            t = (s >> (2 * beta)) & 3
+            r |= (t >> 1) << beta
+            c |= (t & 1) << beta
+        out[s] = flat[r * N + c]
+    return out
+
+
+@pytest.mark.parametrize("n,dtype,prec", [(5, 0, 0), (6, 0, 0), (7, 0, 0), (8, 0, 0), (7, 1, 0), (8, 1, 2),
+                                          (9, 0, 0)])
+def test_plans_emulated_on_cpu_match_oracle(L, n, dtype, prec):
+    npass, desc = L.tpd_plan_describe(n, dtype, L.options(precision=prec))
+    passes = _parse(desc)
+    assert len(passes) == npass
+    assert sum(p["K"] for p in passes) == n
+    A = synth.general(n, seed=77 + n)
+    got = _to_string_order(_emulate(A, passes, n), n)
+    want = oracle.coeffs_fwht(A)
+    assert np.linalg.norm(got - want) <= 1e-13 * np.linalg.norm(want)
+
+
+@pytest.mark.parametrize("n", list(range(1, 17)))
+def test_plans_exist_for_every_size(L, n):
+    for dtype, prec in ((0, 0), (0, 1), (1, 0), (1, 2)):
+        npass, desc = L.tpd_plan_describe(n, dtype, L.options(precision=prec))
+        if 2 * n < 9:
+            assert npass == 0
+            continue
+        passes = _parse(desc)
+        assert 1 <= npass <= n and len(passes) == npass
+        assert [p["b"] for p in passes] == list(np.cumsum([0] + [p["K"] for p in passes])[:-1])
+        for p in passes:
+            assert len(p["gbits"]) == p["D"] and p["ntiles"] == 2 ** (2 * n - p["D"])
+            # lanes of every stage cover the three lowest tile bits, which are the
+            # lowest column bits (128-byte runs of 16-byte elements)
+            assert p["gbits"][:3] == [0, 1, 2]
+    if n == 14:
+        npass, _ = L.tpd_plan_describe(14, 0, L.options())
+        assert npass == 3

@@ -1,0 +1,328 @@
+"""GPU parity: libtpd.so (through the C ABI) against the CPU oracle.
+
+Tolerances (derivation in the design doc): complex128 1e-12 relative, normwise and
+elementwise against max|w|; integer and dyadic inputs bit-exact; complex64
+against the oracle run on the same c64-rounded input, plain fp32 within
+gamma_n = n u32 / (1 - n u32), compensated within (P+1) u32 for P passes.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2310_13421_gb300 import synth
+from _helpers import U32, assert_close, assert_exact, rc_index_of_xz, rel_err, to_string_order
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL128 = 1e-12
+
+
+@pytest.fixture(scope="module")
+def tpd():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2310_13421_gb300 as pkg
+    pkg.build()
+    return pkg
+
+
+def gpu(a, dtype=torch.complex128):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def npass(n, dtype=0, prec=0, **kw):
+    from paper_2310_13421_gb300 import _lib as L
+    return L.tpd_plan_describe(n, dtype, L.options(precision=prec, **kw))[0]
+
+
+# ------------------------------------------------------------------ complex128
+
+@pytest.mark.parametrize("precision", ["fixed", "plain"])
+@pytest.mark.parametrize("n", list(range(1, 11)))
+def test_c128_random_general(tpd, n, precision):
+    A = synth.general(n, seed=2000 + n)
+    got = to_string_order(host(tpd.decompose(gpu(A), precision=precision)), n)
+    assert_close(got, oracle.coeffs_fwht(A), TOL128, "n=%d %s" % (n, precision))
+
+
+@pytest.mark.parametrize("precision", ["fixed", "plain"])
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 6, 7, 9, 10, 11])
+def test_c128_integer_bit_exact(tpd, n, precision):
+    A = synth.int_general(n, seed=2100 + n)
+    got = to_string_order(host(tpd.decompose(gpu(A), precision=precision)), n)
+    assert_exact(got, oracle.coeffs_fwht(A), "n=%d %s" % (n, precision))
+
+
+def test_n1_unit_matrices_golden(tpd):
+    import os
+    rows = np.loadtxt(os.path.join(os.path.dirname(__file__), "golden", "n1_unit_matrices.txt"))
+    for prec in ("fixed", "plain"):
+        for row in rows:
+            E = np.zeros((2, 2), dtype=np.complex128)
+            E[int(row[0]), int(row[1])] = 1.0
+            want = row[2::2] + 1j * row[3::2]
+            assert_exact(to_string_order(host(tpd.decompose(gpu(E), precision=prec)), 1), want)
+
+
+@pytest.mark.parametrize("precision", ["fixed", "plain"])
+def test_c128_config_n12_integer_symmetric_bit_exact(tpd, precision):
+    # real symmetric, entries uniform integers in [-8, 8], n = 12
+    n = 12
+    A = synth.int_symmetric(n, seed=3003)
+    got = to_string_order(host(tpd.decompose(gpu(A), precision=precision)), n)
+    want = oracle.coeffs_fwht(A)
+    assert_exact(got, want, "n=12 int symmetric")
+    # odd number of Y factors: exactly zero (footnote of Sec. II.B)
+    s = np.arange(4 ** n)
+    ny = np.zeros_like(s)
+    for b in range(n):
+        ny += ((s >> (2 * b)) & 3) == 2
+    assert np.all(got[ny % 2 == 1] == 0)
+
+
+@pytest.mark.parametrize("precision", ["fixed", "plain"])
+def test_c128_n12_hermitian_full(tpd, precision):
+    n = 12
+    A = synth.hermitian(n, seed=3012)
+    got = to_string_order(host(tpd.decompose(gpu(A), precision=precision)), n)
+    assert_close(got, oracle.coeffs_fwht(A), TOL128, "n=12")
+    assert np.all(got.imag == 0)  # Hermitian: exactly real in the butterfly
+
+
+def test_c128_config_n6(tpd):
+    # 64x64 Hermitian, N(0,1) parts: all 4096 weights
+    n = 6
+    A = synth.hermitian(n, seed=1001)
+    for prec in ("fixed", "plain"):
+        got = to_string_order(host(tpd.decompose(gpu(A), precision=prec)), n)
+        assert_close(got, oracle.coeffs(A), TOL128, "n=6 " + prec)
+
+
+@pytest.mark.parametrize("opt", [dict(tile_bits=9), dict(tile_bits=10), dict(tile_bits=11), dict(tile_bits=13),
+                                 dict(max_levels=1), dict(max_levels=2), dict(max_levels=3),
+                                 dict(max_levels=5), dict(tile_bits=12, max_levels=4)])
+def test_c128_plan_variants(tpd, opt):
+    n = 10
+    A = synth.general(n, seed=4000)
+    want = oracle.coeffs_fwht(A)
+    for prec in ("fixed", "plain"):
+        got = to_string_order(host(tpd.decompose(gpu(A), precision=prec, **opt)), n)
+        assert_close(got, want, TOL128, str(opt))
+    Ai = synth.int_general(n, seed=4001)
+    assert_exact(to_string_order(host(tpd.decompose(gpu(Ai), **opt)), n), oracle.coeffs_fwht(Ai))
+
+
+def test_c128_magnitude_extremes(tpd):
+    # tiny (subnormal-range products) and huge entries go through the fixed
+    # point's exponent handling; compare with the oracle on the same input
+    n = 8
+    base = synth.general(n, seed=4100)
+    for scale in (1e-300, 1e-310, 1e300, 2.0 ** -1070):
+        A = base * scale
+        want = oracle.coeffs_fwht(A)
+        got = to_string_order(host(tpd.decompose(gpu(A), precision="fixed")), n)
+        if scale < 1e-305:
+            # results sit in the subnormal range: absolute error half an ulp of the smallest normal
+            assert np.max(np.abs(got - want)) <= 2.0 ** -1074 * 2 ** n
+        else:
+            # compare rescaled copies (norms of 1e300-sized vectors overflow)
+            assert_close(got / scale, want / scale, TOL128, "scale %g" % scale)
+    # wide dynamic range inside one tile
+    A = base.copy()
+    A[::3, ::5] *= 1e12
+    assert_close(to_string_order(host(tpd.decompose(gpu(A))), n), oracle.coeffs_fwht(A), TOL128, "mixed")
+
+
+def test_c128_nonfinite_tiles_follow_ieee(tpd):
+    n = 8
+    A = synth.general(n, seed=4200)
+    A[3, 7] = np.inf
+    A[100, 5] = np.nan
+    fixed = host(tpd.decompose(gpu(A), precision="fixed"))
+    plain = host(tpd.decompose(gpu(A), precision="plain"))
+    assert np.array_equal(np.isnan(fixed), np.isnan(plain))
+    assert np.array_equal(np.isinf(fixed), np.isinf(plain))
+    fin = np.isfinite(fixed) & np.isfinite(plain)
+    assert fin.any() and np.allclose(fixed[fin], plain[fin], rtol=1e-12, atol=1e-12)
+
+
+def test_c128_zero_matrix_and_skip(tpd):
+    for n in (3, 7, 10):
+        Z = torch.zeros((2 ** n, 2 ** n), dtype=torch.complex128, device="cuda")
+        for skip in (False, True):
+            out = tpd.decompose(Z, skip_zero=skip)
+            assert torch.count_nonzero(out).item() == 0
+
+
+@pytest.mark.parametrize("n", [6, 9, 10])
+def test_skip_zero_identical_results(tpd, n):
+    for A in (synth.general(n, seed=4300 + n), synth.heisenberg(n, *synth.heisenberg_params(n, seed=n))):
+        a = host(tpd.decompose(gpu(A), skip_zero=False))
+        b = host(tpd.decompose(gpu(A), skip_zero=True))
+        assert_exact(b, a)
+
+
+@pytest.mark.parametrize("n", [5, 8, 10, 12])
+def test_planted_heisenberg_exact(tpd, n):
+    J, h = synth.heisenberg_params(n, seed=5000 + n)
+    H = synth.heisenberg(n, J, h)
+    terms = synth.heisenberg_terms(n, J, h)
+    for prec in ("fixed", "plain"):
+        got = to_string_order(host(tpd.decompose(gpu(H), precision=prec, skip_zero=True)), n)
+        want = np.zeros(4 ** n, dtype=np.complex128)
+        for t, v in terms.items():
+            want[synth.string_index(t)] = v
+        assert_exact(got, want, "heisenberg n=%d" % n)
+
+
+def test_tfim_eq7_first_level_and_terms(tpd):
+    # Eq. 8: after the first qubit level (the top one), the CMWs are H_{n-1}, -J g I,
+    # 0 and -J Z; the full decomposition has the 2n-1 terms of Eq. 7
+    n, J, g = 8, 0.75, -1.25
+    H = synth.tfim(n, J, g)
+    got = to_string_order(host(tpd.decompose(gpu(H), skip_zero=True)), n)
+    want = np.zeros(4 ** n, dtype=np.complex128)
+    for t, v in synth.tfim_terms(n, J, g).items():
+        want[synth.string_index(t)] = v
+    assert_exact(got, want)
+
+
+# ------------------------------------------------------------------ complex64
+
+@pytest.mark.parametrize("n", [3, 5, 8, 10, 11])
+def test_c64_plain_and_compensated(tpd, n):
+    A64 = synth.hermitian(n, seed=6000 + n, dtype=np.complex64)
+    want = oracle.coeffs_fwht(A64.astype(np.complex128))
+    plain = to_string_order(host(tpd.decompose(gpu(A64, torch.complex64), precision="plain")), n)
+    comp = to_string_order(host(tpd.decompose(gpu(A64, torch.complex64), precision="compensated")), n)
+    P = max(npass(n, 1, 2), 1)
+    g_plain = n * U32 / (1 - n * U32)
+    g_comp = (P + 1) * U32 / (1 - (P + 1) * U32)
+    e_plain, e_comp = rel_err(plain, want), rel_err(comp, want)
+    assert e_plain <= g_plain, e_plain
+    assert e_comp <= g_comp, e_comp
+    if n >= 8:
+        assert e_comp < e_plain
+
+
+@pytest.mark.parametrize("n", [4, 9, 10])
+def test_c64_integer_bit_exact(tpd, n):
+    A = synth.int_general(n, seed=6100 + n)
+    want = oracle.coeffs_fwht(A)
+    for prec in ("plain", "compensated"):
+        got = to_string_order(host(tpd.decompose(gpu(A, torch.complex64), precision=prec)), n)
+        assert_exact(got.astype(np.complex128), want, prec)
+
+
+# ------------------------------------------------------------------ composition
+
+@pytest.mark.parametrize("precision", ["fixed", "plain"])
+@pytest.mark.parametrize("n", [1, 3, 6, 9, 10])
+def test_compose_matches_oracle(tpd, n, precision):
+    W = synth.general(n, seed=7000 + n)  # weights in RC layout
+    want = oracle.compose_fwht(to_string_order(W, n), n)
+    got = host(tpd.compose(gpu(W), precision=precision))
+    assert_close(got, want, TOL128, "compose n=%d" % n)
+    adj = host(tpd.compose(gpu(W), scale=2.0 ** -n, precision=precision))
+    assert_close(adj, want * 2.0 ** -n, TOL128, "adjoint n=%d" % n)
+
+
+@pytest.mark.parametrize("n", [2, 7, 10, 12])
+def test_roundtrip_exact_on_integers(tpd, n):
+    A = synth.int_general(n, seed=7100 + n)
+    c = tpd.decompose(gpu(A))
+    assert_exact(host(tpd.compose(c)), A)
+    c64 = tpd.decompose(gpu(A, torch.complex64), precision="compensated")
+    assert_exact(host(tpd.compose(c64, precision="compensated")).astype(np.complex128), A)
+
+
+def test_compose_non_power_of_two_scale(tpd):
+    n = 9
+    W = synth.general(n, seed=7200)
+    want = 0.3 * oracle.compose_fwht(to_string_order(W, n), n)
+    for prec in ("fixed", "plain"):
+        assert_close(host(tpd.compose(gpu(W), scale=0.3, precision=prec)), want, TOL128)
+
+
+def test_adjoint_dot_product(tpd):
+    n = 10
+    A = gpu(synth.general(n, seed=7300))
+    G = gpu(synth.general(n, seed=7301))
+    lhs = torch.vdot(tpd.decompose(A).reshape(-1), G.reshape(-1)).item()
+    rhs = torch.vdot(A.reshape(-1), tpd.compose(G, scale=2.0 ** -n).reshape(-1)).item()
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+# ------------------------------------------------------------------ batched
+
+def test_batched_mixed_sizes(tpd):
+    rng = np.random.default_rng(8000)
+    ns = [1, 2, 3, 4, 5, 6, 7, 8, 9, 10] + list(rng.integers(1, 11, size=22))
+    mats = [synth.general(int(n), seed=8000 + i) for i, n in enumerate(ns)]
+    for prec in ("fixed", "plain"):
+        outs = tpd.decompose_batched([gpu(m) for m in mats], precision=prec)
+        for m, o, n in zip(mats, outs, ns):
+            assert_close(to_string_order(host(o), int(n)), oracle.coeffs_fwht(m), TOL128, "batched n=%d" % n)
+    ints = [synth.int_general(int(n), seed=8100 + i) for i, n in enumerate(ns)]
+    outs = tpd.decompose_batched([gpu(m) for m in ints])
+    for m, o, n in zip(ints, outs, ns):
+        assert_exact(to_string_order(host(o), int(n)), oracle.coeffs_fwht(m))
+    # batched composition with the adjoint scaling inverts up to 2^-n: C(D(A)) = A
+    back = tpd.compose_batched(outs)
+    for m, b in zip(ints, back):
+        assert_exact(host(b), m)
+
+
+def test_batched_c64(tpd):
+    ns = [3, 5, 8, 10, 4, 9]
+    mats = [synth.hermitian(n, seed=8200 + n, dtype=np.complex64) for n in ns]
+    outs = tpd.decompose_batched([gpu(m, torch.complex64) for m in mats], precision="compensated")
+    for m, o, n in zip(mats, outs, ns):
+        P = max(npass(n, 1, 2), 1)
+        assert rel_err(to_string_order(host(o), n), oracle.coeffs_fwht(m.astype(np.complex128))) <= (P + 1) * U32 * 1.01
+
+
+def test_batched_cuda_graph_replay(tpd):
+    ns = [3, 6, 8, 10]
+    mats = [synth.general(n, seed=8300 + n) for n in ns]
+    work = [gpu(m) for m in mats]
+    pristine = [w.clone() for w in work]
+    batch = tpd.Batch(work)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        batch.decompose(stream=s)   # warm-up (plans, attributes) outside capture
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        batch.decompose()
+    for rep in range(3):
+        for w, p in zip(work, pristine):
+            w.copy_(p)
+        g.replay()
+        torch.cuda.synchronize()
+        for m, w, n in zip(mats, work, ns):
+            assert_close(to_string_order(host(w), n), oracle.coeffs_fwht(m), TOL128, "graph n=%d" % n)
+
+
+# ------------------------------------------------------------------ autograd
+
+def test_autograd_matches_oracle_gradient(tpd):
+    n = 8
+    A = synth.hermitian(n, seed=9000)
+    w = synth.loss_weights(n, seed=9001)
+    wt_rc = np.empty(4 ** n)
+    from _helpers import rc_positions
+    wt_rc[rc_positions(n)] = w
+    At = gpu(A).requires_grad_(True)
+    c = tpd.tpd(At)
+    loss = (torch.from_numpy(wt_rc).cuda().reshape(c.shape) * c.abs() ** 2).sum()
+    loss.backward()
+    assert_close(host(At.grad), oracle.grad_weighted_sq(A, w), TOL128, "grad")

@@ -152,6 +152,15 @@ def test_compose_matches_kronecker_sum(n):
     assert np.max(np.abs(oracle.compose(w, n) - kron.compose_kron(w, n))) <= 1e-14 * np.max(np.abs(w)) * 4 ** n
 
 
+@pytest.mark.parametrize("n", [1, 3, 6])
+def test_compose_forms_agree(n):
+    wi = synth.int_general(n + n, seed=750 + n).reshape(-1)[: 4 ** n] / 4.0
+    assert np.array_equal(oracle.compose(wi, n), oracle.compose_fwht(wi, n))
+    w = synth.general(n + n, seed=760 + n).reshape(-1)[: 4 ** n]
+    a, b = oracle.compose(w, n), oracle.compose_fwht(w, n)
+    assert np.linalg.norm(a - b) <= 1e-14 * np.linalg.norm(a)
+
+
 @pytest.mark.parametrize("n", [3, 6])
 def test_reconstruction(n):
     # Eq. 2: A = sum_t w_t sigma^t; exact on integer inputs (dyadic weights)
