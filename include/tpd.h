@@ -124,6 +124,29 @@ tpd_status tpd_decompose_host(const void* A_host, void* W_host, void* dev_A, int
                               const tpd_options* opt, void* workspace, size_t workspace_bytes,
                               void* stream);
 
+/* Decomposition for callers that cannot allocate device memory.
+ *
+ * The paper has no counterpart: this entry point exists for callers that may
+ * not call cudaMalloc or an allocating library -- for instance code running
+ * where a custom allocator owns all device memory, or a real-time path that
+ * must not allocate or synchronise.  It behaves like tpd_decompose, but its
+ * workspace (the per-tile binary points and zero-skip flags passes hand to
+ * one another) is a fixed array of TPD_NOALLOC_SCRATCH_BYTES in the library's
+ * own device memory, present on every GPU that loads the library until the
+ * process exits.  The caller still passes the matrix A (device, in place).
+ *   - Plans whose workspace (tpd_workspace_size) exceeds the array are
+ *     rejected with TPD_ERR_WORKSPACE before anything is enqueued; use
+ *     tpd_decompose with a caller buffer for those.
+ *   - The first call on a device looks up the array's device address with
+ *     that device current; make that first call before any stream capture.
+ *   - All calls on a device share the one array, and a call leaves its
+ *     contents behind (each call clears what it needs cleared).  Calls whose
+ *     work overlaps on the GPU (different streams, no ordering) race on it.
+ *   - Nothing is allocated or freed, by the library or by a library it calls.
+ * Arguments and other errors as tpd_decompose. */
+#define TPD_NOALLOC_SCRATCH_BYTES ((size_t)8 << 20)
+tpd_status tpd_decompose_noalloc(void* A, int n, int dtype, const tpd_options* opt, void* stream);
+
 /* Device workspace for the batched calls over `count` matrices with qubit
  * counts ns[0..count) (host array). Returns 0 for invalid arguments. */
 size_t tpd_batched_workspace_size(const int* ns, int count, int dtype, const tpd_options* opt);

@@ -27,8 +27,11 @@ TPD_PREC_FIXED = 3
 SYMBOLS = (
     "tpd_options_init", "tpd_workspace_size", "tpd_decompose", "tpd_compose", "tpd_decompose_host",
     "tpd_batched_workspace_size", "tpd_decompose_batched", "tpd_compose_batched",
-    "tpd_plan_describe", "tpd_status_string", "tpd_version",
+    "tpd_plan_describe", "tpd_status_string", "tpd_version", "tpd_decompose_noalloc",
 )
+
+# size of the library's own scratch array used by tpd_decompose_noalloc
+TPD_NOALLOC_SCRATCH_BYTES = 8 << 20
 
 
 class tpd_options(ctypes.Structure):
@@ -69,6 +72,8 @@ def load(path=None):
         lib.tpd_decompose.restype = i
         lib.tpd_compose.argtypes = [vp, i, i, ctypes.c_double, op, vp, sz, vp]
         lib.tpd_compose.restype = i
+        lib.tpd_decompose_noalloc.argtypes = [vp, i, i, op, vp]
+        lib.tpd_decompose_noalloc.restype = i
         lib.tpd_decompose_host.argtypes = [vp, vp, vp, i, i, op, vp, sz, vp]
         lib.tpd_decompose_host.restype = i
         lib.tpd_batched_workspace_size.argtypes = [ip, i, i, op]
@@ -118,6 +123,11 @@ def tpd_decompose(A_ptr, n, dtype, opt=None, workspace=0, workspace_bytes=0, str
 def tpd_compose(C_ptr, n, dtype, scale, opt=None, workspace=0, workspace_bytes=0, stream=0):
     return int(load().tpd_compose(C_ptr, n, dtype, float(scale), _opt(opt), workspace or None,
                                   workspace_bytes, stream or None))
+
+
+def tpd_decompose_noalloc(A_ptr, n, dtype, opt=None, stream=0):
+    """Decomposition with the library's own fixed scratch array (no allocation)."""
+    return int(load().tpd_decompose_noalloc(A_ptr, n, dtype, _opt(opt), stream or None))
 
 
 def tpd_decompose_host(A_host_ptr, W_host_ptr, dev_ptr, n, dtype, opt=None, workspace=0, workspace_bytes=0,
