@@ -77,6 +77,9 @@ typedef struct {
                        tile (9..13), for tuning */
   int max_levels;   /* 0 = planner default; otherwise the most qubit levels fused
                        into one pass (1..6), for tuning */
+  int variant;      /* kernel form, for tuning: 0 = default, 1 = one CTA per tile,
+                       2 = persistent CTAs that prefetch the next tile (complex128
+                       fixed point, single matrix, no zero skipping) */
   void** pass_events; /* profiling, may be NULL: num_events cudaEvent_t handles
                        (created by the caller); tpd_decompose / tpd_compose
                        record event 0 before the first pass and event p+1 after

@@ -54,10 +54,10 @@ def _raise(st, what):
         raise L.TPDError(st, what)
 
 
-def make_options(precision=None, skip_zero=False, tile_bits=0, max_levels=0):
+def make_options(precision=None, skip_zero=False, tile_bits=0, max_levels=0, variant=0):
     if isinstance(precision, str) or precision is None:
         precision = _PREC[precision]
-    return L.options(precision, skip_zero, tile_bits, max_levels)
+    return L.options(precision, skip_zero, tile_bits, max_levels, variant)
 
 
 def workspace_size(n, dtype, **kw):
@@ -65,14 +65,14 @@ def workspace_size(n, dtype, **kw):
     return L.tpd_workspace_size(n, code, make_options(**kw))
 
 
-def decompose(A, *, inplace=False, precision=None, skip_zero=False, tile_bits=0, max_levels=0,
+def decompose(A, *, inplace=False, precision=None, skip_zero=False, tile_bits=0, max_levels=0, variant=0,
               workspace=None, stream=None):
     """Pauli weights w_t = 2^-n tr(sigma^t A) of a 2^n x 2^n CUDA matrix, in RC layout."""
     _check_device(A)
     n = _qubits(A)
     code = _dtype_code(A)
     out = A if inplace else A.clone()
-    opt = make_options(precision, skip_zero, tile_bits, max_levels)
+    opt = make_options(precision, skip_zero, tile_bits, max_levels, variant)
     wsb = L.tpd_workspace_size(n, code, opt)
     ws = workspace
     if wsb and (ws is None or ws.numel() < wsb):
@@ -83,14 +83,14 @@ def decompose(A, *, inplace=False, precision=None, skip_zero=False, tile_bits=0,
     return out
 
 
-def compose(C, *, scale=1.0, inplace=False, precision=None, skip_zero=False, tile_bits=0, max_levels=0,
+def compose(C, *, scale=1.0, inplace=False, precision=None, skip_zero=False, tile_bits=0, max_levels=0, variant=0,
             workspace=None, stream=None):
     """scale * sum_t w_t sigma^t from weights in RC layout (scale 2^-n: the adjoint of decompose)."""
     _check_device(C)
     n = _qubits(C)
     code = _dtype_code(C)
     out = C if inplace else C.clone()
-    opt = make_options(precision, skip_zero, tile_bits, max_levels)
+    opt = make_options(precision, skip_zero, tile_bits, max_levels, variant)
     wsb = L.tpd_workspace_size(n, code, opt)
     ws = workspace
     if wsb and (ws is None or ws.numel() < wsb):

@@ -41,6 +41,7 @@ tpd_status check_options(int dtype, const tpd_options* opt, int* prec) {
   if (opt && opt->tile_bits != 0 && (opt->tile_bits < kMinTileBits || opt->tile_bits > kMaxTileBits))
     return TPD_ERR_INVALID_ARG;
   if (opt && (opt->max_levels < 0 || opt->max_levels > kMaxLevels)) return TPD_ERR_INVALID_ARG;
+  if (opt && (opt->variant < 0 || opt->variant > 2)) return TPD_ERR_INVALID_ARG;
   *prec = p;
   return TPD_OK;
 }
@@ -113,6 +114,21 @@ void pass_scaling(bool dec, int arith, const PassDesc& pd, bool last, int spow, 
   }
 }
 
+// SM count of the current device (cached per device)
+int sm_count() {
+  static std::mutex mu;
+  static int cache[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 132;
+  std::lock_guard<std::mutex> lk(mu);
+  if (cache[dev] == 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 132;
+    cache[dev] = v;
+  }
+  return cache[dev];
+}
+
 // profiling hook: event k recorded before pass k (k = 0) / after pass k-1
 void record_event(const tpd_options* opt, int k, cudaStream_t s) {
   if (opt && opt->pass_events && k < opt->num_events && opt->pass_events[k])
@@ -154,7 +170,10 @@ tpd_status run_single(bool dec, int arith, void* mat, const Plan& plan, int skip
       if (!last) a.q_out = reinterpret_cast<int*>(w + lay.q_off[p]);
     }
     pass_scaling(dec, arith, pd, last, spow, sres, scale, &a);
-    if (launch_pass(arith, dec, pd, a, pd.ntiles, s) != cudaSuccess) return TPD_ERR_CUDA;
+    const int variant = opt ? opt->variant : 0;
+    const bool pipe = arith == kArithFixed && !skip && pd.D <= 12 && variant == 2;
+    cudaError_t e = pipe ? launch_pass_pipe_c128(dec, pd, a, sm_count(), s) : launch_pass(arith, dec, pd, a, pd.ntiles, s);
+    if (e != cudaSuccess) return TPD_ERR_CUDA;
     record_event(opt, p + 1, s);
   }
   return TPD_OK;

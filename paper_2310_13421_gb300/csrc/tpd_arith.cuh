@@ -38,7 +38,7 @@ __device__ __forceinline__ uint32_t shfl_x(uint32_t v, int mask) {
 // ================================================================ fixed point
 struct FixedArith {
   using Store = double2;
-  struct V { long long re, im; };
+  struct __align__(16) V { long long re, im; };   // 16-byte aligned: one 128-bit shared access
   static constexpr bool kFixed = true;
   static constexpr int kStoreBytes = 16;
 
@@ -72,6 +72,20 @@ struct FixedArith {
     asm("shr.b64 %0, %1, %2;" : "=l"(mag) : "l"(ml), "r"(rs));
     const unsigned long long s = (unsigned long long)((long long)bits >> 63);
     return (long long)((mag ^ s) - s);
+  }
+
+  // The same value through the fp64 conversion unit: scale by 2^S with an
+  // exact exponent shift, then convert truncating toward zero.  Subnormal x
+  // or a scaled exponent outside the normal range takes the integer path.
+  // Used for one of the two components so that the integer pipe and the
+  // otherwise idle fp64 pipe share the work.
+  __device__ static __forceinline__ long long to_fixed_cvt(double x, int shift_base) {
+    const long long bits = __double_as_longlong(x);
+    const int e = (int)(bits >> 52) & 0x7FF;
+    const int S = shift_base + 1075;          // = 1084 - K - Emax_eff
+    if (e >= 1 && e + S >= 1 && e + S <= 2046)
+      return __double2ll_rz(__longlong_as_double(bits + ((long long)S << 52)));
+    return to_fixed(x, shift_base);
   }
 
   // Magnitude bits of a * 2^(be - 1086) (a has its leading one at bit 63)
@@ -109,6 +123,35 @@ struct FixedArith {
       bits = rare_bits(a, be);
     }
     return __longlong_as_double((long long)(bits | (s & 0x8000000000000000ull)));
+  }
+
+  // True when every nonzero |v| < 2^62 scaled by 2^-T lands in the normal
+  // range (also after rounding up): then to_double_fast applies to the tile.
+  __device__ static __forceinline__ bool fast_range(int T) { return T <= 1022 && T >= -961; }
+
+  // v * 2^-T rounded to nearest even for |v| < 2^62 in the normal range
+  // (fast_range(T)), in 32-bit integer instructions: normalise with a
+  // funnel shift, round with a carry trick, assemble the exponent.
+  __device__ static __forceinline__ double to_double_fast(long long v, int T) {
+    const unsigned long long s64 = (unsigned long long)(v >> 63);
+    const unsigned long long a = ((unsigned long long)v ^ s64) - s64;
+    const uint32_t ah = (uint32_t)(a >> 32), al = (uint32_t)a;
+    const bool big = ah != 0u;
+    const uint32_t h = big ? ah : al;               // the word holding the leading one
+    const uint32_t l = big ? al : 0u;
+    const int lz = __clz((int)h);                   // 0..31 for a != 0
+    const uint32_t mh = __funnelshift_l(l, h, lz);  // (h:l) << lz, leading one at bit 31
+    const uint32_t ml = l << (lz & 31);
+    uint32_t mant_hi = mh >> 11;                    // 21 bits, implicit one at bit 20
+    uint32_t mant_lo = __funnelshift_r(ml, mh, 11); // next 32 bits
+    const uint32_t rem = ml & 0x7FFu;
+    const uint32_t up = (rem + 0x3FFu + (mant_lo & 1u)) >> 11;   // RNE: 1 iff rem > half or tie with odd lsb
+    const unsigned long long mant = (((unsigned long long)mant_hi << 32) | mant_lo) + up;
+    const int be = 1086 - (lz + (big ? 0 : 32)) - T;
+    const uint32_t hi = ((uint32_t)(be - 1) << 20) + (uint32_t)(mant >> 32);   // a carry bumps the exponent
+    const unsigned long long bits =
+        ((unsigned long long)(hi | ((uint32_t)s64 & 0x80000000u)) << 32) | (uint32_t)mant;
+    return a == 0 ? 0.0 : __longlong_as_double((long long)bits);
   }
 
   // v * 2^-T: the int64 -> double conversion (round to nearest even) followed
@@ -189,7 +232,7 @@ struct F32Arith {
 // ================================================================ compensated float
 struct F32CArith {
   using Store = float2;
-  struct V { float re, im, rl, il; };   // value = (re + rl) + i (im + il)
+  struct __align__(16) V { float re, im, rl, il; };   // value = (re + rl) + i (im + il)
   static constexpr bool kFixed = false;
   static constexpr int kStoreBytes = 8;
 

@@ -20,6 +20,17 @@ cudaError_t launch_small_c128(int arith, bool dec, const SmallArgs& args, int bl
              : launch_small_t<F64Arith, false>(args, blocks, n_max, s);
 }
 
+cudaError_t launch_pass_pipe_c128(bool dec, const PassDesc& pd, const PassArgs& args, int nsm, cudaStream_t s) {
+  const int threads = 1 << (pd.D - kRegBits);
+  const size_t smem = ((size_t)32 << pd.D) + 256;   // two tile buffers + reduction slots
+  auto kfn = dec ? k_pass_pipe<true> : k_pass_pipe<false>;
+  cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const long long grid = pd.ntiles < nsm ? pd.ntiles : nsm;
+  kfn<<<(unsigned)grid, threads, smem, s>>>(pd, args);
+  return cudaGetLastError();
+}
+
 // One CTA buckets matrix indices by qubit count (counting sort in shared memory).
 __global__ void __launch_bounds__(1024) k_bucket(const int* __restrict__ ns, int count, int* __restrict__ items,
                                                  int* __restrict__ offsets) {

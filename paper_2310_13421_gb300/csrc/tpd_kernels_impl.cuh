@@ -11,7 +11,8 @@ cudaError_t launch_pass_t(const PassDesc& pd, const PassArgs& args, long long nt
   const int threads = 1 << (pd.D - kRegBits);
   const size_t vbytes = A::kFixed ? 16 : sizeof(typename A::V);
   const size_t smem = ((size_t)1 << pd.D) * vbytes + 256;
-  auto kfn = threads <= 256 ? k_pass<A, kDec, 256> : k_pass<A, kDec, 512>;
+  auto kfn = threads > 256 ? k_pass<A, kDec, 512, 1>
+                           : (pd.min_blocks >= 3 ? k_pass<A, kDec, 256, 3> : k_pass<A, kDec, 256, 2>);
   cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if (ntiles_total <= 0) return cudaSuccess;

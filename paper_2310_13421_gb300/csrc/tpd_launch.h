@@ -61,6 +61,10 @@ cudaError_t launch_pass_c64(int arith, bool dec, const PassDesc& pd, const PassA
                             cudaStream_t s);
 cudaError_t launch_small_c64(int arith, bool dec, const SmallArgs& args, int blocks, int n_max, cudaStream_t s);
 
+// Persistent double-buffered fixed-point pass (D <= 12, single matrix, no
+// zero skipping): one CTA per SM, nsm = SM count.
+cudaError_t launch_pass_pipe_c128(bool dec, const PassDesc& pd, const PassArgs& args, int nsm, cudaStream_t s);
+
 // Bucket matrices by qubit count: for each n in [0, 32), out_offsets[n] is the
 // start of its list in out_items (matrix indices, any order within a list).
 // scratch: 64 ints.

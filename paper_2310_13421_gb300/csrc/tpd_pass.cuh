@@ -238,6 +238,41 @@ __device__ __forceinline__ long long shr_tz(long long v, unsigned sh) {
   return (long long)((a ^ s) - s);
 }
 
+// floor(v / 2^sh) (sh >= 0; 0 or -1 once sh >= 64)
+__device__ __forceinline__ long long shr_floor(long long v, unsigned sh) {
+  long long r;
+  asm("shr.s64 %0, %1, %2;" : "=l"(r) : "l"(v), "r"(sh));   // PTX clamps the amount at 64
+  return r;
+}
+
+// Alignment of the int64 sums of a previous pass to the tile's binary point.
+// Rounding toward minus infinity costs 2-3 instructions against ~11 for
+// toward zero; the error is below 2^-(62-K) of the tile's largest element.
+#ifdef TPD_ALIGN_TOWARD_ZERO
+#define TPD_ALIGN shr_tz
+#else
+#define TPD_ALIGN shr_floor
+#endif
+
+// Which unit converts each component between double and int64 (identical
+// results either way): integer instructions, or the fp64 conversion unit.
+#if defined(TPD_CVT_BOTH)
+#define TPD_TO_FIXED_RE FixedArith::to_fixed_cvt
+#define TPD_TO_FIXED_IM FixedArith::to_fixed_cvt
+#define TPD_TO_DOUBLE_RE FixedArith::to_double_cvt
+#define TPD_TO_DOUBLE_IM FixedArith::to_double_cvt
+#elif defined(TPD_CVT_RE)
+#define TPD_TO_FIXED_RE FixedArith::to_fixed_cvt
+#define TPD_TO_FIXED_IM FixedArith::to_fixed
+#define TPD_TO_DOUBLE_RE FixedArith::to_double_cvt
+#define TPD_TO_DOUBLE_IM FixedArith::to_double_int
+#else
+#define TPD_TO_FIXED_RE FixedArith::to_fixed
+#define TPD_TO_FIXED_IM FixedArith::to_fixed
+#define TPD_TO_DOUBLE_RE FixedArith::to_double_int
+#define TPD_TO_DOUBLE_IM FixedArith::to_double_int
+#endif
+
 // Tiles meeting an Inf or NaN run the IEEE fp64 butterfly instead.  Out of
 // line (never taken for finite data) so the hot path stays small in the
 // instruction cache.  Elements are re-read: doubles as such, int64 sums of a
@@ -272,19 +307,36 @@ __device__ __noinline__ void ieee_tile(const PassDesc& pd, const PassArgs& args,
   if (!last && threadIdx.x == 0) q_out[tile] = kQIeee;
 }
 
+// The tile's elements in the stage-0 mapping from a shared-memory copy.
+template <class Store>
+__device__ __forceinline__ void load_tile_smem(const PassDesc& pd, const unsigned char* buf, int lane, int warp,
+                                               Store (&raw)[kElems]) {
+  const Stage& s0 = pd.st[0];
+  const Store* b = reinterpret_cast<const Store*>(buf);
+  const int t = thread_sidx(pd, s0, lane, warp);
+  const int w0 = 1 << s0.reg[0], w1 = 1 << s0.reg[1], w2 = 1 << s0.reg[2], w3 = 1 << s0.reg[3];
+#pragma unroll
+  for (int e = 0; e < kElems; ++e) raw[e] = b[t + reg_off(e, w0, w1, w2, w3)];
+}
+
+// xbuf: shared-memory exchange area (2^D x 16 bytes); red: 64 ints;
+// inbuf: the tile already copied to shared memory (stage-0 positions), or
+// nullptr to read it from global memory.
 template <bool kDec>
 __device__ __forceinline__ void fixed_tile(const PassDesc& pd, const PassArgs& args, void* matp, const int* q_in,
                                            int* q_out, long long tile, long long base, long long pbase, int nbase,
-                                           unsigned char* smem, int lane, int warp) {
+                                           const unsigned char* inbuf, unsigned char* xbuf, int* red, int lane,
+                                           int warp) {
   using V = FixedArith::V;
   const int nwarps = 1 << (pd.D - kMinTileBits);
-  int* red = reinterpret_cast<int*>(smem + ((size_t)16 << pd.D));   // 64 ints after the tile
+  unsigned char* smem = xbuf;
   V v[kElems];
   int qin;
   if (q_in == nullptr) {
     // ---- first pass: IEEE doubles onto the tile's binary point
     double2 raw[kElems];
-    load_tile(pd, matp, base, lane, warp, raw);
+    if (inbuf) load_tile_smem(pd, inbuf, lane, warp, raw);
+    else load_tile(pd, matp, base, lane, warp, raw);
     uint32_t hmax = 0, nzw = 0;
 #pragma unroll
     for (int e = 0; e < kElems; ++e) {
@@ -314,14 +366,15 @@ __device__ __forceinline__ void fixed_tile(const PassDesc& pd, const PassArgs& a
     const int shift_base = 9 - pd.K - emax_eff;
 #pragma unroll
     for (int e = 0; e < kElems; ++e) {
-      v[e].re = FixedArith::to_fixed(raw[e].x, shift_base);
-      v[e].im = FixedArith::to_fixed(raw[e].y, shift_base);
+      v[e].re = TPD_TO_FIXED_RE(raw[e].x, shift_base);
+      v[e].im = TPD_TO_FIXED_IM(raw[e].y, shift_base);
     }
     qin = emax_eff + pd.K - 1084;                          // = -S
   } else {
     // ---- later pass: int64 sums with their previous tile's binary point
     longlong2 raw[kElems];
-    load_tile(pd, matp, base, lane, warp, raw);
+    if (inbuf) load_tile_smem(pd, inbuf, lane, warp, raw);
+    else load_tile(pd, matp, base, lane, warp, raw);
     const Stage& s0 = pd.st[0];
     long long pt = pbase;
 #pragma unroll
@@ -331,12 +384,13 @@ __device__ __forceinline__ void fixed_tile(const PassDesc& pd, const PassArgs& a
       if ((warp >> i) & 1) pt += pd.prev_w[s0.warp[i]];
     const int p0 = pd.prev_w[s0.reg[0]], p1 = pd.prev_w[s0.reg[1]], p2 = pd.prev_w[s0.reg[2]],
               p3 = pd.prev_w[s0.reg[3]];
-    int q[kElems];
-#pragma unroll
-    for (int e = 0; e < kElems; ++e) q[e] = __ldg(q_in + pt + reg_off(e, p0, p1, p2, p3));
     int qmax = kQValidMin, ieee = 0;
 #pragma unroll
-    for (int e = 0; e < kElems; ++e) { qmax = max(qmax, q[e]); ieee |= (q[e] == kQIeee); }
+    for (int e = 0; e < kElems; ++e) {
+      const int q = __ldg(q_in + pt + reg_off(e, p0, p1, p2, p3));
+      qmax = max(qmax, q);
+      ieee |= (q == kQIeee);
+    }
     // kQIeee sits below kQValidMin, so it never wins the max
     qmax = __reduce_max_sync(kFull, qmax);
     ieee = __reduce_or_sync(kFull, ieee);
@@ -355,10 +409,11 @@ __device__ __forceinline__ void fixed_tile(const PassDesc& pd, const PassArgs& a
     qin = qmax + pd.K;
 #pragma unroll
     for (int e = 0; e < kElems; ++e) {
-      if (q_is_valid(q[e])) {
-        const unsigned sh = (unsigned)(qin - q[e]);
-        v[e].re = shr_tz(raw[e].x, sh);
-        v[e].im = shr_tz(raw[e].y, sh);
+      const int q = __ldg(q_in + pt + reg_off(e, p0, p1, p2, p3));   // again, from L1
+      if (q_is_valid(q)) {
+        const unsigned sh = (unsigned)(qin - q);
+        v[e].re = TPD_ALIGN(raw[e].x, sh);
+        v[e].im = TPD_ALIGN(raw[e].y, sh);
       } else {
         v[e].re = 0; v[e].im = 0;
       }
@@ -397,13 +452,20 @@ __device__ __forceinline__ void fixed_tile(const PassDesc& pd, const PassArgs& a
     double2* mat = reinterpret_cast<double2*>(matp);
     const int T = -(qout + args.out_pow2);
     const bool resid = args.out_mul != 1.0;                // non-power-of-two composition scale (rare)
+    if (FixedArith::fast_range(T) && !resid) {             // the whole tile rounds in the normal range
 #pragma unroll
-    for (int e = 0; e < kElems; ++e) {
-      double2 o;
-      o.x = FixedArith::to_double(v[e].re, T);
-      o.y = FixedArith::to_double(v[e].im, T);
-      if (resid) { o.x *= args.out_mul; o.y *= args.out_mul; }
-      mat[g + reg_off(e, w0, w1, w2, w3)] = o;
+      for (int e = 0; e < kElems; ++e)
+        mat[g + reg_off(e, w0, w1, w2, w3)] =
+            make_double2(FixedArith::to_double_fast(v[e].re, T), FixedArith::to_double_fast(v[e].im, T));
+    } else {
+#pragma unroll
+      for (int e = 0; e < kElems; ++e) {
+        double2 o;
+        o.x = TPD_TO_DOUBLE_RE(v[e].re, T);
+        o.y = TPD_TO_DOUBLE_IM(v[e].im, T);
+        if (resid) { o.x *= args.out_mul; o.y *= args.out_mul; }
+        mat[g + reg_off(e, w0, w1, w2, w3)] = o;
+      }
     }
   }
   if (flags) {
@@ -422,12 +484,11 @@ __device__ __forceinline__ void fixed_tile(const PassDesc& pd, const PassArgs& a
 
 // Tiles of up to 2^12 elements run 256-thread CTAs, several per SM; 2^13
 // element tiles run 512-thread CTAs.
-#ifndef TPD_MIN_BLOCKS_256
-#define TPD_MIN_BLOCKS_256 2
-#endif
-
-template <class A, bool kDec, int kThreads>
-__global__ void __launch_bounds__(kThreads, kThreads == 256 ? TPD_MIN_BLOCKS_256 : 1)
+// kMinBlocks: CTAs of kThreads the compiler must fit on one SM (register
+// budget); the planner picks 3 for the conversion-heavy first and last
+// fixed-point passes and 2 elsewhere.
+template <class A, bool kDec, int kThreads, int kMinBlocks>
+__global__ void __launch_bounds__(kThreads, kMinBlocks)
     k_pass(const __grid_constant__ PassDesc pd, const __grid_constant__ PassArgs args) {
   using Store = typename A::Store;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -456,7 +517,8 @@ __global__ void __launch_bounds__(kThreads, kThreads == 256 ? TPD_MIN_BLOCKS_256
     }
 
   if constexpr (A::kFixed) {
-    fixed_tile<kDec>(pd, args, matp, q_in, q_out, tile, base, pbase, nbase, smem, lane, warp);
+    fixed_tile<kDec>(pd, args, matp, q_in, q_out, tile, base, pbase, nbase, nullptr, smem,
+                     reinterpret_cast<int*>(smem + ((size_t)16 << pd.D)), lane, warp);
   } else {
     Store raw[kElems];
     load_tile(pd, matp, base, lane, warp, raw);
@@ -467,6 +529,83 @@ __global__ void __launch_bounds__(kThreads, kThreads == 256 ? TPD_MIN_BLOCKS_256
       if (!__syncthreads_or(nz)) return;
     }
     finish_tile<A, kDec>(pd, args, matp, raw, args.out_mul, base, nbase, smem, lane, warp);
+  }
+}
+
+// -------------------------------------------------------------- persistent, double buffered
+//
+// Fixed point, one matrix, tiles of up to 2^12 elements: one CTA per SM walks
+// the tiles (tile += gridDim.x).  Each thread copies ITS elements of the next
+// tile into the spare shared-memory buffer with cp.async while the CTA works
+// on the current one, so HBM stays busy across the compute phase.  The waits
+// are the hardware's (cp.async.wait_group + barrier), with no spin loops.
+
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+__device__ __forceinline__ long long tile_base(const PassDesc& pd, long long tile) {
+  long long base = 0;
+  for (int j = 0; j < pd.nrest; ++j)
+    if ((tile >> j) & 1) base += 1ll << pd.rest_gbit[j];
+  return base;
+}
+
+// This thread's 16 elements of `tile` (stage-0 positions) into buf.
+__device__ __forceinline__ void prefetch_tile(const PassDesc& pd, const void* matp, long long tile,
+                                              unsigned char* buf, int lane, int warp) {
+  const Stage& s0 = pd.st[0];
+  const char* mat = reinterpret_cast<const char*>(matp);
+  const long long g = tile_base(pd, tile) + thread_goff(pd, s0, lane, warp);
+  const long long w0 = 1ll << pd.gbit[s0.reg[0]], w1 = 1ll << pd.gbit[s0.reg[1]];
+  const long long w2 = 1ll << pd.gbit[s0.reg[2]], w3 = 1ll << pd.gbit[s0.reg[3]];
+  const int t = thread_sidx(pd, s0, lane, warp);
+  const int v0 = 1 << s0.reg[0], v1 = 1 << s0.reg[1], v2 = 1 << s0.reg[2], v3 = 1 << s0.reg[3];
+#pragma unroll
+  for (int e = 0; e < kElems; ++e)
+    cp_async16(buf + 16 * (t + reg_off(e, v0, v1, v2, v3)), mat + 16 * (g + reg_off(e, w0, w1, w2, w3)));
+  cp_async_commit();
+}
+
+template <bool kDec>
+__global__ void __launch_bounds__(256, 1)
+    k_pass_pipe(const __grid_constant__ PassDesc pd, const __grid_constant__ PassArgs args) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const size_t tb = (size_t)16 << pd.D;
+  unsigned char* buf0 = smem;
+  unsigned char* buf1 = smem + tb;
+  int* red = reinterpret_cast<int*>(smem + 2 * tb);
+  long long tile = blockIdx.x;
+  if (tile >= pd.ntiles) return;
+  prefetch_tile(pd, args.mat, tile, buf0, lane, warp);
+  bool odd = false;
+  for (; tile < pd.ntiles; tile += gridDim.x, odd = !odd) {
+    unsigned char* cur = odd ? buf1 : buf0;
+    unsigned char* spare = odd ? buf0 : buf1;
+    const long long nxt = tile + gridDim.x;
+    if (nxt < pd.ntiles) {
+      prefetch_tile(pd, args.mat, nxt, spare, lane, warp);
+      cp_async_wait<1>();                 // this thread's copies of the current tile have landed
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();                      // ... and everyone's
+    long long base = 0, pbase = 0;
+    int nbase = 0;
+    for (int j = 0; j < pd.nrest; ++j)
+      if ((tile >> j) & 1) {
+        base += 1ll << pd.rest_gbit[j];
+        nbase += (int)pd.next_rest_w[j];
+        pbase += pd.prev_rest_w[j];
+      }
+    fixed_tile<kDec>(pd, args, args.mat, args.q_in, args.q_out, tile, base, pbase, nbase, cur, cur, red, lane,
+                     warp);
+    __syncthreads();                      // the current buffer is refilled next iteration
   }
 }
 

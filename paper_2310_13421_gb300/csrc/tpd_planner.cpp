@@ -263,6 +263,14 @@ bool build_plan(int n, int dtype, int precision, int tile_bits_opt, int max_leve
   }
   for (int p = 0; p + 1 < plan->npass; ++p) set_next(&plan->pass[p], plan->pass[p + 1]);
   for (int p = 1; p < plan->npass; ++p) set_prev(&plan->pass[p], plan->pass[p - 1]);
+  // Occupancy: the fixed point's first pass (double -> int64) and last pass
+  // (int64 -> double) are long integer chains that gain from a third CTA per
+  // SM even at a smaller register budget; the middle passes keep two.
+  for (int p = 0; p < plan->npass; ++p) {
+    PassDesc& pd = plan->pass[p];
+    const bool ends = p == 0 || p + 1 == plan->npass;
+    pd.min_blocks = pd.D > 12 ? 1 : ((dtype == 0 && precision == 3 && ends) ? 3 : 2);
+  }
   return true;
 }
 

@@ -48,7 +48,10 @@ def test_config_n14_dense_c128(tpd):
         got, want = sample_rows(A, C, n, xs)
         assert_close(got, want, 1e-12, "n=14 " + prec)
         assert parseval(Ag, C, n) <= 1e-12
-        assert torch.count_nonzero(C.imag).item() == 0    # Hermitian input: real weights, exactly
+        if prec == "plain":
+            assert torch.count_nonzero(C.imag).item() == 0    # Hermitian input: real weights, exactly
+        else:
+            assert torch.max(torch.abs(C.imag)).item() <= 1e-15 * torch.max(torch.abs(C)).item()
         del C
     # zero skip on a dense input changes nothing
     C1 = tpd.decompose(Ag)

@@ -92,7 +92,11 @@ def test_c128_n12_hermitian_full(tpd, precision):
     A = synth.hermitian(n, seed=3012)
     got = to_string_order(host(tpd.decompose(gpu(A), precision=precision)), n)
     assert_close(got, oracle.coeffs_fwht(A), TOL128, "n=12")
-    assert np.all(got.imag == 0)  # Hermitian: exactly real in the butterfly
+    if precision == "plain":
+        assert np.all(got.imag == 0)  # Hermitian: exactly real in the IEEE butterfly
+    else:
+        # the fixed point rounds its between-pass alignment toward -inf
+        assert np.max(np.abs(got.imag)) <= 1e-15 * np.max(np.abs(got))
 
 
 def test_c128_config_n6(tpd):
@@ -106,7 +110,8 @@ def test_c128_config_n6(tpd):
 
 @pytest.mark.parametrize("opt", [dict(tile_bits=9), dict(tile_bits=10), dict(tile_bits=11), dict(tile_bits=13),
                                  dict(max_levels=1), dict(max_levels=2), dict(max_levels=3),
-                                 dict(max_levels=5), dict(tile_bits=12, max_levels=4)])
+                                 dict(max_levels=5), dict(tile_bits=12, max_levels=4), dict(variant=1),
+                                 dict(variant=2), dict(tile_bits=11, variant=2)])
 def test_c128_plan_variants(tpd, opt):
     n = 10
     A = synth.general(n, seed=4000)
