@@ -79,7 +79,9 @@ typedef struct {
                        into one pass (1..6), for tuning */
   int variant;      /* kernel form, for tuning: 0 = default, 1 = one CTA per tile,
                        2 = persistent CTAs that prefetch the next tile (complex128
-                       fixed point, single matrix, no zero skipping) */
+                       fixed point, single matrix, no zero skipping),
+                       3 / 4 = one CTA per tile compiled for 2 / 3 CTAs per SM
+                       (tiles of up to 2^12 elements) */
   void** pass_events; /* profiling, may be NULL: num_events cudaEvent_t handles
                        (created by the caller); tpd_decompose / tpd_compose
                        record event 0 before the first pass and event p+1 after

@@ -41,7 +41,7 @@ tpd_status check_options(int dtype, const tpd_options* opt, int* prec) {
   if (opt && opt->tile_bits != 0 && (opt->tile_bits < kMinTileBits || opt->tile_bits > kMaxTileBits))
     return TPD_ERR_INVALID_ARG;
   if (opt && (opt->max_levels < 0 || opt->max_levels > kMaxLevels)) return TPD_ERR_INVALID_ARG;
-  if (opt && (opt->variant < 0 || opt->variant > 2)) return TPD_ERR_INVALID_ARG;
+  if (opt && (opt->variant < 0 || opt->variant > 4)) return TPD_ERR_INVALID_ARG;
   *prec = p;
   return TPD_OK;
 }
@@ -172,7 +172,10 @@ tpd_status run_single(bool dec, int arith, void* mat, const Plan& plan, int skip
     pass_scaling(dec, arith, pd, last, spow, sres, scale, &a);
     const int variant = opt ? opt->variant : 0;
     const bool pipe = arith == kArithFixed && !skip && pd.D <= 12 && variant == 2;
-    cudaError_t e = pipe ? launch_pass_pipe_c128(dec, pd, a, sm_count(), s) : launch_pass(arith, dec, pd, a, pd.ntiles, s);
+    PassDesc tuned = pd;                       // occupancy override (variants 3 and 4)
+    if (pd.D <= 12 && (variant == 3 || variant == 4)) tuned.min_blocks = variant == 3 ? 2 : 3;
+    cudaError_t e = pipe ? launch_pass_pipe_c128(dec, tuned, a, sm_count(), s)
+                         : launch_pass(arith, dec, tuned, a, pd.ntiles, s);
     if (e != cudaSuccess) return TPD_ERR_CUDA;
     record_event(opt, p + 1, s);
   }

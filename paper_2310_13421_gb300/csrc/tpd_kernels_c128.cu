@@ -23,7 +23,14 @@ cudaError_t launch_small_c128(int arith, bool dec, const SmallArgs& args, int bl
 cudaError_t launch_pass_pipe_c128(bool dec, const PassDesc& pd, const PassArgs& args, int nsm, cudaStream_t s) {
   const int threads = 1 << (pd.D - kRegBits);
   const size_t smem = ((size_t)32 << pd.D) + 256;   // two tile buffers + reduction slots
-  auto kfn = dec ? k_pass_pipe<true> : k_pass_pipe<false>;
+  const int role = (args.q_in ? kRoleIntIn : 0) | (args.q_out ? kRoleIntOut : 0);
+  PassKernel kfn;
+  switch (role) {
+    case 0: kfn = dec ? k_pass_pipe<true, 0> : k_pass_pipe<false, 0>; break;
+    case kRoleIntIn: kfn = dec ? k_pass_pipe<true, kRoleIntIn> : k_pass_pipe<false, kRoleIntIn>; break;
+    case kRoleIntOut: kfn = dec ? k_pass_pipe<true, kRoleIntOut> : k_pass_pipe<false, kRoleIntOut>; break;
+    default: kfn = dec ? k_pass_pipe<true, 3> : k_pass_pipe<false, 3>; break;
+  }
   cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const long long grid = pd.ntiles < nsm ? pd.ntiles : nsm;

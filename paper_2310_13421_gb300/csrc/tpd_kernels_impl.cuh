@@ -6,13 +6,31 @@
 
 namespace tpd {
 
+using PassKernel = void (*)(const PassDesc, const PassArgs);
+
+// the instantiation for a pass's CTA size, occupancy and (fixed point) role
+template <class A, bool kDec, int kRole>
+PassKernel pick_pass_kernel(const PassDesc& pd, int threads) {
+  if (threads > 256) return k_pass<A, kDec, 512, 1, kRole>;
+  return pd.min_blocks >= 3 ? k_pass<A, kDec, 256, 3, kRole> : k_pass<A, kDec, 256, 2, kRole>;
+}
+
 template <class A, bool kDec>
 cudaError_t launch_pass_t(const PassDesc& pd, const PassArgs& args, long long ntiles_total, cudaStream_t s) {
   const int threads = 1 << (pd.D - kRegBits);
   const size_t vbytes = A::kFixed ? 16 : sizeof(typename A::V);
   const size_t smem = ((size_t)1 << pd.D) * vbytes + 256;
-  auto kfn = threads > 256 ? k_pass<A, kDec, 512, 1>
-                           : (pd.min_blocks >= 3 ? k_pass<A, kDec, 256, 3> : k_pass<A, kDec, 256, 2>);
+  PassKernel kfn;
+  if constexpr (A::kFixed) {
+    switch ((args.q_in ? kRoleIntIn : 0) | (args.q_out ? kRoleIntOut : 0)) {
+      case 0: kfn = pick_pass_kernel<A, kDec, 0>(pd, threads); break;
+      case kRoleIntIn: kfn = pick_pass_kernel<A, kDec, kRoleIntIn>(pd, threads); break;
+      case kRoleIntOut: kfn = pick_pass_kernel<A, kDec, kRoleIntOut>(pd, threads); break;
+      default: kfn = pick_pass_kernel<A, kDec, kRoleIntIn | kRoleIntOut>(pd, threads); break;
+    }
+  } else {
+    kfn = pick_pass_kernel<A, kDec, 0>(pd, threads);
+  }
   cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if (ntiles_total <= 0) return cudaSuccess;

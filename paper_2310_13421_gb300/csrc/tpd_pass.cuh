@@ -319,10 +319,17 @@ __device__ __forceinline__ void load_tile_smem(const PassDesc& pd, const unsigne
   for (int e = 0; e < kElems; ++e) raw[e] = b[t + reg_off(e, w0, w1, w2, w3)];
 }
 
+// Role of a fixed-point pass, a compile-time choice so that each kernel
+// carries only its own conversions (smaller code, fewer registers): input
+// IEEE doubles or int64 sums of a previous pass, output int64 sums for a
+// next pass or IEEE doubles.
+constexpr int kRoleIntIn = 1;
+constexpr int kRoleIntOut = 2;
+
 // xbuf: shared-memory exchange area (2^D x 16 bytes); red: 64 ints;
 // inbuf: the tile already copied to shared memory (stage-0 positions), or
 // nullptr to read it from global memory.
-template <bool kDec>
+template <bool kDec, int kRole>
 __device__ __forceinline__ void fixed_tile(const PassDesc& pd, const PassArgs& args, void* matp, const int* q_in,
                                            int* q_out, long long tile, long long base, long long pbase, int nbase,
                                            const unsigned char* inbuf, unsigned char* xbuf, int* red, int lane,
@@ -332,7 +339,7 @@ __device__ __forceinline__ void fixed_tile(const PassDesc& pd, const PassArgs& a
   unsigned char* smem = xbuf;
   V v[kElems];
   int qin;
-  if (q_in == nullptr) {
+  if constexpr (!(kRole & kRoleIntIn)) {
     // ---- first pass: IEEE doubles onto the tile's binary point
     double2 raw[kElems];
     if (inbuf) load_tile_smem(pd, inbuf, lane, warp, raw);
@@ -443,7 +450,7 @@ __device__ __forceinline__ void fixed_tile(const PassDesc& pd, const PassArgs& a
 #pragma unroll
     for (int i = 0; i < kLaneBits; ++i) lanes_inside &= (pd.next_w[sl.lane[i]] == 0);
   }
-  if (q_out != nullptr) {
+  if constexpr ((kRole & kRoleIntOut) != 0) {
     longlong2* mat = reinterpret_cast<longlong2*>(matp);
 #pragma unroll
     for (int e = 0; e < kElems; ++e) mat[g + reg_off(e, w0, w1, w2, w3)] = make_longlong2(v[e].re, v[e].im);
@@ -486,8 +493,8 @@ __device__ __forceinline__ void fixed_tile(const PassDesc& pd, const PassArgs& a
 // element tiles run 512-thread CTAs.
 // kMinBlocks: CTAs of kThreads the compiler must fit on one SM (register
 // budget); the planner picks 3 for the conversion-heavy first and last
-// fixed-point passes and 2 elsewhere.
-template <class A, bool kDec, int kThreads, int kMinBlocks>
+// fixed-point passes and 2 elsewhere.  kRole: fixed point only (see above).
+template <class A, bool kDec, int kThreads, int kMinBlocks, int kRole = 0>
 __global__ void __launch_bounds__(kThreads, kMinBlocks)
     k_pass(const __grid_constant__ PassDesc pd, const __grid_constant__ PassArgs args) {
   using Store = typename A::Store;
@@ -517,8 +524,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
     }
 
   if constexpr (A::kFixed) {
-    fixed_tile<kDec>(pd, args, matp, q_in, q_out, tile, base, pbase, nbase, nullptr, smem,
-                     reinterpret_cast<int*>(smem + ((size_t)16 << pd.D)), lane, warp);
+    fixed_tile<kDec, kRole>(pd, args, matp, q_in, q_out, tile, base, pbase, nbase, nullptr, smem,
+                            reinterpret_cast<int*>(smem + ((size_t)16 << pd.D)), lane, warp);
   } else {
     Store raw[kElems];
     load_tile(pd, matp, base, lane, warp, raw);
@@ -571,7 +578,7 @@ __device__ __forceinline__ void prefetch_tile(const PassDesc& pd, const void* ma
   cp_async_commit();
 }
 
-template <bool kDec>
+template <bool kDec, int kRole>
 __global__ void __launch_bounds__(256, 1)
     k_pass_pipe(const __grid_constant__ PassDesc pd, const __grid_constant__ PassArgs args) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -603,8 +610,8 @@ __global__ void __launch_bounds__(256, 1)
         nbase += (int)pd.next_rest_w[j];
         pbase += pd.prev_rest_w[j];
       }
-    fixed_tile<kDec>(pd, args, args.mat, args.q_in, args.q_out, tile, base, pbase, nbase, cur, cur, red, lane,
-                     warp);
+    fixed_tile<kDec, kRole>(pd, args, args.mat, args.q_in, args.q_out, tile, base, pbase, nbase, cur, cur, red,
+                            lane, warp);
     __syncthreads();                      // the current buffer is refilled next iteration
   }
 }

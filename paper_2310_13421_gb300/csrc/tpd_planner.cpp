@@ -230,7 +230,9 @@ bool build_plan(int n, int dtype, int precision, int tile_bits_opt, int max_leve
   }
   const int lf = dtype == 1 ? 4 : 3;                       // low tile bits always on lanes
   const double cs = plan->elem_bytes == 16 ? 1.0 : 0.5;    // shuffle cost per level
-  int dmax = tile_bits_opt ? tile_bits_opt : (dtype == 1 && precision != 2 ? 13 : 12);
+  // 2^12-element tiles by default: two CTAs of 256 threads fit an SM; 2^13
+  // (512 threads, one CTA per SM) only where it saves a pass (below)
+  int dmax = tile_bits_opt ? tile_bits_opt : 12;
   dmax = std::min(dmax, 2 * n);
   int kcap = max_levels_opt ? max_levels_opt : kMaxLevels;
   const int k0 = std::min({n, dmax / 2, kcap});
@@ -263,13 +265,14 @@ bool build_plan(int n, int dtype, int precision, int tile_bits_opt, int max_leve
   }
   for (int p = 0; p + 1 < plan->npass; ++p) set_next(&plan->pass[p], plan->pass[p + 1]);
   for (int p = 1; p < plan->npass; ++p) set_prev(&plan->pass[p], plan->pass[p - 1]);
-  // Occupancy: the fixed point's first pass (double -> int64) and last pass
-  // (int64 -> double) are long integer chains that gain from a third CTA per
-  // SM even at a smaller register budget; the middle passes keep two.
+  // Occupancy: the fixed point's first pass (double -> int64, long integer
+  // chains, few live values) gains from a third CTA per SM at a smaller
+  // register budget; the others keep two (measured on GB300: the last pass
+  // spills at three).
   for (int p = 0; p < plan->npass; ++p) {
     PassDesc& pd = plan->pass[p];
-    const bool ends = p == 0 || p + 1 == plan->npass;
-    pd.min_blocks = pd.D > 12 ? 1 : ((dtype == 0 && precision == 3 && ends) ? 3 : 2);
+    const bool first_of_many = p == 0 && plan->npass > 1;
+    pd.min_blocks = pd.D > 12 ? 1 : ((dtype == 0 && precision == 3 && first_of_many) ? 3 : 2);
   }
   return true;
 }
