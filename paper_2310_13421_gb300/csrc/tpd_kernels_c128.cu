@@ -1,13 +1,18 @@
-// complex128 kernels: exact block fixed point and IEEE fp64 arithmetic.
+// complex128 kernels: IEEE fp64 passes, whole small matrices, batching
+// helpers; the block-fixed-point passes sit in tpd_kernels_fixed_{dec,com}.cu.
 #include "tpd_kernels_impl.cuh"
 
 namespace tpd {
 
+cudaError_t launch_pass_fixed_dec(const PassDesc& pd, const PassArgs& args, long long ntiles_total, cudaStream_t s);
+cudaError_t launch_pass_fixed_com(const PassDesc& pd, const PassArgs& args, long long ntiles_total, cudaStream_t s);
+cudaError_t launch_pass_pipe_fixed_dec(const PassDesc& pd, const PassArgs& args, int nsm, cudaStream_t s);
+cudaError_t launch_pass_pipe_fixed_com(const PassDesc& pd, const PassArgs& args, int nsm, cudaStream_t s);
+
 cudaError_t launch_pass_c128(int arith, bool dec, const PassDesc& pd, const PassArgs& args,
                              long long ntiles_total, cudaStream_t s) {
   if (arith == kArithFixed)
-    return dec ? launch_pass_t<FixedArith, true>(pd, args, ntiles_total, s)
-               : launch_pass_t<FixedArith, false>(pd, args, ntiles_total, s);
+    return dec ? launch_pass_fixed_dec(pd, args, ntiles_total, s) : launch_pass_fixed_com(pd, args, ntiles_total, s);
   return dec ? launch_pass_t<F64Arith, true>(pd, args, ntiles_total, s)
              : launch_pass_t<F64Arith, false>(pd, args, ntiles_total, s);
 }
@@ -21,21 +26,7 @@ cudaError_t launch_small_c128(int arith, bool dec, const SmallArgs& args, int bl
 }
 
 cudaError_t launch_pass_pipe_c128(bool dec, const PassDesc& pd, const PassArgs& args, int nsm, cudaStream_t s) {
-  const int threads = 1 << (pd.D - kRegBits);
-  const size_t smem = ((size_t)32 << pd.D) + 256;   // two tile buffers + reduction slots
-  const int role = (args.q_in ? kRoleIntIn : 0) | (args.q_out ? kRoleIntOut : 0);
-  PassKernel kfn;
-  switch (role) {
-    case 0: kfn = dec ? k_pass_pipe<true, 0> : k_pass_pipe<false, 0>; break;
-    case kRoleIntIn: kfn = dec ? k_pass_pipe<true, kRoleIntIn> : k_pass_pipe<false, kRoleIntIn>; break;
-    case kRoleIntOut: kfn = dec ? k_pass_pipe<true, kRoleIntOut> : k_pass_pipe<false, kRoleIntOut>; break;
-    default: kfn = dec ? k_pass_pipe<true, 3> : k_pass_pipe<false, 3>; break;
-  }
-  cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  const long long grid = pd.ntiles < nsm ? pd.ntiles : nsm;
-  kfn<<<(unsigned)grid, threads, smem, s>>>(pd, args);
-  return cudaGetLastError();
+  return dec ? launch_pass_pipe_fixed_dec(pd, args, nsm, s) : launch_pass_pipe_fixed_com(pd, args, nsm, s);
 }
 
 // One CTA buckets matrix indices by qubit count (counting sort in shared memory).

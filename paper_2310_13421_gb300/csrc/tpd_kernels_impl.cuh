@@ -52,4 +52,22 @@ cudaError_t launch_small_t(const SmallArgs& args, int blocks, int n_max, cudaStr
   return cudaGetLastError();
 }
 
+template <bool kDec>
+cudaError_t launch_pass_pipe_t(const PassDesc& pd, const PassArgs& args, int nsm, cudaStream_t s) {
+  const int threads = 1 << (pd.D - kRegBits);
+  const size_t smem = ((size_t)32 << pd.D) + 256;   // two tile buffers + reduction slots
+  PassKernel kfn;
+  switch ((args.q_in ? kRoleIntIn : 0) | (args.q_out ? kRoleIntOut : 0)) {
+    case 0: kfn = k_pass_pipe<kDec, 0>; break;
+    case kRoleIntIn: kfn = k_pass_pipe<kDec, kRoleIntIn>; break;
+    case kRoleIntOut: kfn = k_pass_pipe<kDec, kRoleIntOut>; break;
+    default: kfn = k_pass_pipe<kDec, kRoleIntIn | kRoleIntOut>; break;
+  }
+  cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const long long grid = pd.ntiles < nsm ? pd.ntiles : nsm;
+  kfn<<<(unsigned)grid, threads, smem, s>>>(pd, args);
+  return cudaGetLastError();
+}
+
 }  // namespace tpd
