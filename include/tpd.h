@@ -173,6 +173,18 @@ tpd_status tpd_compose_batched(void* const* ptrs_dev, const int* ns_dev, const i
                                int count, int dtype, int scale_mode, const tpd_options* opt,
                                void* workspace, size_t workspace_bytes, void* stream);
 
+/* Tuned defaults.  Registers tile_bits, max_levels and variant of `tuned`
+ * for (n, dtype, precision); every later call for that key whose options
+ * leave all three at 0 (or pass opt == NULL) uses them instead of the
+ * planner's defaults -- the batched calls per qubit count.  The project's
+ * autotuner (paper_2310_13421_gb300/autotune.py) times candidates and sets
+ * them.  tuned == NULL removes the entry.  Host only, thread-safe.
+ * Errors: INVALID_ARG (bad key or values). */
+tpd_status tpd_tune_set(int n, int dtype, int precision, const tpd_options* tuned);
+
+/* Forget every tuned default. */
+void tpd_tune_clear(void);
+
 /* Describe the pass plan the library uses for (n, dtype, opt) as a
  * NUL-terminated text (one line per pass: levels, tile bits, stages) written
  * to buf (at most len bytes).  Host only, no device call.  Returns the number

@@ -28,6 +28,7 @@ SYMBOLS = (
     "tpd_options_init", "tpd_workspace_size", "tpd_decompose", "tpd_compose", "tpd_decompose_host",
     "tpd_batched_workspace_size", "tpd_decompose_batched", "tpd_compose_batched",
     "tpd_plan_describe", "tpd_status_string", "tpd_version", "tpd_decompose_noalloc",
+    "tpd_tune_set", "tpd_tune_clear",
 )
 
 # size of the library's own scratch array used by tpd_decompose_noalloc
@@ -72,6 +73,10 @@ def load(path=None):
         lib.tpd_decompose.restype = i
         lib.tpd_compose.argtypes = [vp, i, i, ctypes.c_double, op, vp, sz, vp]
         lib.tpd_compose.restype = i
+        lib.tpd_tune_set.argtypes = [i, i, i, op]
+        lib.tpd_tune_set.restype = i
+        lib.tpd_tune_clear.argtypes = []
+        lib.tpd_tune_clear.restype = None
         lib.tpd_decompose_noalloc.argtypes = [vp, i, i, op, vp]
         lib.tpd_decompose_noalloc.restype = i
         lib.tpd_decompose_host.argtypes = [vp, vp, vp, i, i, op, vp, sz, vp]
@@ -123,6 +128,14 @@ def tpd_decompose(A_ptr, n, dtype, opt=None, workspace=0, workspace_bytes=0, str
 def tpd_compose(C_ptr, n, dtype, scale, opt=None, workspace=0, workspace_bytes=0, stream=0):
     return int(load().tpd_compose(C_ptr, n, dtype, float(scale), _opt(opt), workspace or None,
                                   workspace_bytes, stream or None))
+
+
+def tpd_tune_set(n, dtype, precision, tuned=None):
+    return int(load().tpd_tune_set(n, dtype, precision, _opt(tuned)))
+
+
+def tpd_tune_clear():
+    load().tpd_tune_clear()
 
 
 def tpd_decompose_noalloc(A_ptr, n, dtype, opt=None, stream=0):

@@ -51,6 +51,28 @@ tpd_status check_common(int n, int dtype, const tpd_options* opt, int* prec) {
   return check_options(dtype, opt, prec);
 }
 
+// Tuned defaults (tpd_tune_set): (n, dtype, precision) -> tile_bits, max_levels, variant.
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int>, std::tuple<int, int, int>> g_tuned;
+
+// The caller's options, with the tuned defaults filled in when it left all
+// three tuning fields at 0.
+tpd_options effective_options(int n, int dtype, int prec, const tpd_options* opt) {
+  tpd_options e;
+  if (opt) e = *opt;
+  else std::memset(&e, 0, sizeof(e));
+  if (e.tile_bits == 0 && e.max_levels == 0 && e.variant == 0) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(std::make_tuple(n, dtype, prec));
+    if (it != g_tuned.end()) {
+      e.tile_bits = std::get<0>(it->second);
+      e.max_levels = std::get<1>(it->second);
+      e.variant = std::get<2>(it->second);
+    }
+  }
+  return e;
+}
+
 // Cached plan for (n, dtype, precision, tuning options); nullptr if impossible.
 const Plan* get_plan(int n, int dtype, int prec, const tpd_options* opt) {
   const int tb = opt ? opt->tile_bits : 0, ml = opt ? opt->max_levels : 0;
@@ -186,11 +208,13 @@ size_t single_ws(const Plan& plan, int arith, int skip) {
   return plan.npass > 1 ? layout_of(plan, arith, skip).total : 0;
 }
 
-tpd_status single(bool dec, void* mat, int n, int dtype, double scale, const tpd_options* opt, void* ws,
+tpd_status single(bool dec, void* mat, int n, int dtype, double scale, const tpd_options* opt_in, void* ws,
                   size_t ws_bytes, void* stream) {
   int prec = 0;
-  tpd_status st = check_common(n, dtype, opt, &prec);
+  tpd_status st = check_common(n, dtype, opt_in, &prec);
   if (st != TPD_OK) return st;
+  const tpd_options eff = effective_options(n, dtype, prec, opt_in);
+  const tpd_options* opt = &eff;
   if (mat == nullptr) return TPD_ERR_INVALID_ARG;
   const size_t align = dtype == TPD_C128 ? 16 : 8;
   if (reinterpret_cast<uintptr_t>(mat) % align) return TPD_ERR_MISALIGNED;
@@ -238,10 +262,14 @@ tpd_status batched(bool dec, void* const* ptrs_dev, const int* ns_dev, const int
   }
   const int arith = arith_of(dtype, prec);
   std::vector<const Plan*> plans(kBatchMaxQubits + 1, nullptr);
+  std::vector<int> variants(kBatchMaxQubits + 1, 0);
   size_t need = batched_head(count);
   for (int n = 1; n <= kBatchMaxQubits; ++n) {
-    if (hist[n] && !(plans[n] = get_plan(n, dtype, prec, opt))) return TPD_ERR_INVALID_ARG;
-    if (hist[n]) need += batched_q_bytes(*plans[n], arith, hist[n]);
+    if (!hist[n]) continue;
+    const tpd_options eff = effective_options(n, dtype, prec, opt);   // tuned per qubit count
+    if (!(plans[n] = get_plan(n, dtype, prec, &eff))) return TPD_ERR_INVALID_ARG;
+    variants[n] = eff.variant;
+    need += batched_q_bytes(*plans[n], arith, hist[n]);
   }
   if (ws == nullptr || ws_bytes < need) return TPD_ERR_WORKSPACE;
   if (reinterpret_cast<uintptr_t>(ws) % 16) return TPD_ERR_MISALIGNED;
@@ -284,7 +312,9 @@ tpd_status batched(bool dec, void* const* ptrs_dev, const int* ns_dev, const int
         }
         const double scale = scale_mode ? std::ldexp(1.0, -n) : 1.0;
         pass_scaling(dec, arith, pd, last, scale_mode ? -n : 0, 1.0, scale, &a);
-        if (launch_pass(arith, dec, pd, a, pd.ntiles * hist[n], s) != cudaSuccess) return TPD_ERR_CUDA;
+        PassDesc tuned = pd;                   // occupancy override (variants 3 and 4)
+        if (pd.D <= 12 && (variants[n] == 3 || variants[n] == 4)) tuned.min_blocks = variants[n] == 3 ? 2 : 3;
+        if (launch_pass(arith, dec, tuned, a, pd.ntiles * hist[n], s) != cudaSuccess) return TPD_ERR_CUDA;
       }
       qbase += batched_q_bytes(plan, arith, hist[n]);
     }
@@ -304,9 +334,11 @@ void tpd_options_init(tpd_options* opt) {
   if (opt) std::memset(opt, 0, sizeof(*opt));
 }
 
-size_t tpd_workspace_size(int n, int dtype, const tpd_options* opt) {
+size_t tpd_workspace_size(int n, int dtype, const tpd_options* opt_in) {
   int prec = 0;
-  if (check_common(n, dtype, opt, &prec) != TPD_OK) return 0;
+  if (check_common(n, dtype, opt_in, &prec) != TPD_OK) return 0;
+  const tpd_options eff = effective_options(n, dtype, prec, opt_in);
+  const tpd_options* opt = &eff;
   const Plan* plan = get_plan(n, dtype, prec, opt);
   if (!plan) return 0;
   return single_ws(*plan, arith_of(dtype, prec), opt ? (opt->skip_zero != 0) : 0);
@@ -351,7 +383,8 @@ size_t tpd_batched_workspace_size(const int* ns, int count, int dtype, const tpd
   size_t need = batched_head(count);
   for (int n = 1; n <= kBatchMaxQubits; ++n) {
     if (!hist[n]) continue;
-    const Plan* plan = get_plan(n, dtype, prec, opt);
+    const tpd_options eff = effective_options(n, dtype, prec, opt);
+    const Plan* plan = get_plan(n, dtype, prec, &eff);
     if (!plan) return 0;
     need += batched_q_bytes(*plan, arith, hist[n]);
   }
@@ -369,10 +402,38 @@ tpd_status tpd_compose_batched(void* const* ptrs_dev, const int* ns_dev, const i
   return batched(false, ptrs_dev, ns_dev, ns, count, dtype, scale_mode, opt, workspace, workspace_bytes, stream);
 }
 
-int tpd_plan_describe(int n, int dtype, const tpd_options* opt, char* buf, size_t len) {
+tpd_status tpd_tune_set(int n, int dtype, int precision, const tpd_options* tuned) {
   int prec = 0;
-  if (check_common(n, dtype, opt, &prec) != TPD_OK) return -1;
-  const Plan* plan = get_plan(n, dtype, prec, opt);
+  tpd_options probe;
+  std::memset(&probe, 0, sizeof(probe));
+  probe.precision = precision;
+  if (check_common(n, dtype, &probe, &prec) != TPD_OK) return TPD_ERR_INVALID_ARG;
+  const auto key = std::make_tuple(n, dtype, prec);
+  if (tuned == nullptr) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned.erase(key);
+    return TPD_OK;
+  }
+  tpd_options t = *tuned;
+  t.precision = precision;
+  int p2 = 0;
+  if (check_common(n, dtype, &t, &p2) != TPD_OK) return TPD_ERR_INVALID_ARG;
+  if (!get_plan(n, dtype, prec, &t)) return TPD_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tuned[key] = std::make_tuple(t.tile_bits, t.max_levels, t.variant);
+  return TPD_OK;
+}
+
+void tpd_tune_clear(void) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tuned.clear();
+}
+
+int tpd_plan_describe(int n, int dtype, const tpd_options* opt_in, char* buf, size_t len) {
+  int prec = 0;
+  if (check_common(n, dtype, opt_in, &prec) != TPD_OK) return -1;
+  const tpd_options eff = effective_options(n, dtype, prec, opt_in);
+  const Plan* plan = get_plan(n, dtype, prec, &eff);
   if (!plan) return -1;
   const std::string s = describe_plan(*plan);
   if (buf && len) {

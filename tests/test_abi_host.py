@@ -198,3 +198,48 @@ def test_plans_exist_for_every_size(L, n):
     if n == 14:
         npass, _ = L.tpd_plan_describe(14, 0, L.options())
         assert npass == 3
+
+
+def test_tuned_defaults_apply_only_when_fields_are_zero(L):
+    base = L.tpd_plan_describe(14, 0, L.options())
+    small = L.tpd_plan_describe(14, 0, L.options(tile_bits=11))
+    assert base != small
+    try:
+        assert L.tpd_tune_set(14, 0, 0, L.options(tile_bits=11)) == L.TPD_OK
+        # a call that leaves the tuning fields at 0 (or passes no options) gets the tuned plan
+        assert L.tpd_plan_describe(14, 0, L.options()) == small
+        assert L.tpd_plan_describe(14, 0, None) == small
+        # an explicit choice wins over the table; other keys are untouched
+        assert L.tpd_plan_describe(14, 0, L.options(tile_bits=12)) == L.tpd_plan_describe(14, 0, L.options(
+            tile_bits=12, max_levels=0))
+        assert L.tpd_plan_describe(14, 0, L.options(max_levels=4))[1] != small[1]
+        assert L.tpd_plan_describe(13, 0, L.options()) == L.tpd_plan_describe(13, 0, L.options(tile_bits=12))
+        assert L.tpd_plan_describe(14, 0, L.options(precision=1)) == L.tpd_plan_describe(14, 0, L.options(
+            precision=1, tile_bits=12))
+        # removing the entry restores the planner
+        assert L.tpd_tune_set(14, 0, 0, None) == L.TPD_OK
+        assert L.tpd_plan_describe(14, 0, L.options()) == base
+        # bad keys and values are rejected
+        assert L.tpd_tune_set(0, 0, 0, L.options()) == L.TPD_ERR_INVALID_ARG
+        assert L.tpd_tune_set(14, 5, 0, L.options()) == L.TPD_ERR_INVALID_ARG
+        assert L.tpd_tune_set(14, 0, 9, L.options()) == L.TPD_ERR_INVALID_ARG
+        assert L.tpd_tune_set(14, 0, 0, L.options(tile_bits=5)) == L.TPD_ERR_INVALID_ARG
+        assert L.tpd_tune_set(14, 0, 0, L.options(variant=9)) == L.TPD_ERR_INVALID_ARG
+    finally:
+        L.tpd_tune_clear()
+    assert L.tpd_plan_describe(14, 0, L.options()) == base
+
+
+def test_autotune_candidates_are_distinct_valid_plans(L):
+    from paper_2310_13421_gb300 import autotune
+    for n, dt, prec in ((14, "c128", 0), (8, "c128", 0), (15, "c64", 2), (4, "c64", 1)):
+        cands = autotune.candidates(n, dt, prec)
+        assert cands and cands[0] == dict(tile_bits=0, max_levels=0, variant=0, passes=cands[0]["passes"])
+        keys = set()
+        for c in cands:
+            opt = L.options(precision=prec, tile_bits=c["tile_bits"], max_levels=c["max_levels"],
+                            variant=c["variant"])
+            npass, desc = L.tpd_plan_describe(n, autotune._DT[dt][0], opt)
+            assert npass == c["passes"] >= 0
+            keys.add((desc, c["variant"]))
+        assert len(keys) == len(cands)

@@ -331,3 +331,32 @@ def test_autograd_matches_oracle_gradient(tpd):
     loss = (torch.from_numpy(wt_rc).cuda().reshape(c.shape) * c.abs() ** 2).sum()
     loss.backward()
     assert_close(host(At.grad), oracle.grad_weighted_sq(A, w), TOL128, "grad")
+
+
+# ------------------------------------------------------------------ autotuner
+
+def test_autotune_registers_a_plan_that_matches_oracle(tpd, tmp_path):
+    from paper_2310_13421_gb300 import autotune, _lib as L
+    cache = str(tmp_path / "tune.json")
+    try:
+        res = autotune.tune(9, "c128", "default", reps=2, batch_bytes=8 << 20, cache=cache)
+        assert res["best"] and res["ms"] > 0 and len(res["tried"]) >= 2
+        res64 = autotune.tune(11, "c64", "compensated", reps=2, cache=cache)
+        L.tpd_tune_clear()
+        assert autotune.load(cache) == 2
+        # calls that leave the tuning fields at 0 now run the tuned plans
+        A = synth.general(9, seed=9100)
+        out = tpd.decompose(gpu(A))
+        assert_close(to_string_order(host(out), 9), oracle.coeffs_fwht(A), TOL128, "tuned n=9")
+        ns = [9, 9, 9]
+        mats = [synth.int_general(9, seed=9110 + i) for i in range(3)]
+        outs = tpd.decompose_batched([gpu(m) for m in mats])
+        for m, o in zip(mats, outs):
+            assert_exact(to_string_order(host(o), 9), oracle.coeffs_fwht(m))
+        B = synth.hermitian(11, seed=9120, dtype=np.complex64)
+        o = tpd.decompose(gpu(B, torch.complex64), precision="compensated")
+        P = max(npass(11, 1, 2, **res64["best"]), 1)
+        assert rel_err(to_string_order(host(o), 11), oracle.coeffs_fwht(B.astype(np.complex128))) <= \
+            (P + 1) * U32 * 1.01
+    finally:
+        L.tpd_tune_clear()
