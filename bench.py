@@ -45,6 +45,9 @@ def parse():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-extra", action="store_true", help="skip the fp64 / complex64 comparison runs")
     p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--qubits", type=int, default=N_QUBITS,
+                   help="matrix size of the timed workload (14 = the metric's workload; smaller for profiling)")
+    p.add_argument("--no-batch", action="store_true", help="skip the batch-of-4096 comparison run")
     return p.parse_args()
 
 
@@ -167,11 +170,16 @@ def run_reference(args, world, rank):
 
 # ------------------------------------------------------------------ our arm
 
+KERNEL_SOURCES = ("tpd_pass.cuh", "tpd_arith.cuh", "tpd_plan.h", "tpd_launch.h", "tpd_planner.cpp",
+                  "tpd_kernels_impl.cuh", "tpd_kernels_fixed_dec.cu", "tpd_kernels_fixed_com.cu")
+
+
 def kernel_digest():
+    """Hash of the sources that decide the complex128 pass kernels and their plans."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2310_13421_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
-        if f.startswith("tpd_") and f.endswith((".cu", ".cuh", ".h", ".cpp")):
+        if f in KERNEL_SOURCES:
             with open(os.path.join(csrc, f), "rb") as fh:
                 h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]
@@ -220,6 +228,69 @@ def time_decompose(tpd, L, torch, work, pristine, n, steps, warmup, precision, s
     return step_ms, pass_ms, npass
 
 
+def time_batch(tpd, L, torch, stream, count=4096, seed=1004, reps=5):
+    """Batch of `count` random Hermitian complex128 matrices, n_i ~ U{3..10}:
+    the batched call (every pass of every matrix, captured in one CUDA graph)
+    against one tpd_decompose call per matrix on the same stream.  All
+    matrices live in one buffer, restored from a pristine copy between
+    repetitions outside the timed events."""
+    from paper_2310_13421_gb300 import synth
+    ns = [int(x) for x in synth.batch_sizes(count, seed=seed)]
+    offs = np.concatenate([[0], np.cumsum([4 ** n for n in ns])]).astype(np.int64)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    buf = torch.randn(int(offs[-1]), dtype=torch.complex128, device="cuda", generator=g) * np.sqrt(2.0)
+    mats = [buf[offs[i]:offs[i + 1]].view(2 ** n, 2 ** n) for i, n in enumerate(ns)]
+    for m in mats:                           # A = (B + B^H) / 2
+        m.copy_((m + m.mH) * 0.5)
+    pristine = buf.clone()
+    passes = {n: max(L.tpd_plan_describe(n, L.TPD_C128, L.options())[0], 1) for n in set(ns)}
+    alg_bytes = sum(32 * passes[n] * 4 ** n for n in ns)
+    batch = tpd.Batch(mats)
+    batch.decompose()                        # plans and kernel attributes, outside the capture
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        batch.decompose()
+    wsb = max(L.tpd_workspace_size(n, L.TPD_C128, L.options()) for n in set(ns))
+    ws = torch.empty(max(wsb, 16), dtype=torch.uint8, device="cuda")
+
+    def loop():
+        for m, n in zip(mats, ns):
+            st = L.tpd_decompose(m.data_ptr(), n, L.TPD_C128, None, ws.data_ptr(), wsb, stream.cuda_stream)
+            assert st == 0, L.status_string(st)
+
+    res = {}
+    for name, fn in (("graph", graph.replay), ("per_matrix_loop", loop)):
+        times = []
+        for k in range(reps + 2):
+            buf.copy_(pristine)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if k >= 2:
+                times.append(e0.elapsed_time(e1))
+        res[name] = float(np.median(times))
+    # the two forms agree exactly (same plans, same kernels)
+    buf.copy_(pristine)
+    graph.replay()
+    out_graph = buf.clone()
+    buf.copy_(pristine)
+    loop()
+    same = bool(torch.equal(out_graph, buf))
+    del buf, pristine, out_graph, mats, batch, graph
+    torch.cuda.empty_cache()
+    ms = res["graph"]
+    return {"matrices": count, "n_range": [3, 10], "data_bytes": int(offs[-1]) * 16,
+            "algorithmic_bytes": alg_bytes, "graph_ms": ms, "matrices_per_s": count / (ms * 1e-3),
+            "coeffs_per_s": int(offs[-1]) / (ms * 1e-3), "hbm_gbs": alg_bytes / (ms * 1e-3) / 1e9,
+            "per_matrix_loop_ms": res["per_matrix_loop"],
+            "speedup_vs_loop": res["per_matrix_loop"] / ms, "identical_results": same}
+
+
 def run_ours(args, world, rank, local):
     import torch
     if not torch.cuda.is_available():
@@ -247,7 +318,7 @@ def run_ours(args, world, rank, local):
     from paper_2310_13421_gb300 import _lib as L, synth
     tpd.build()
     L.load()
-    n = N_QUBITS
+    n = args.qubits
     N = 2 ** n
     coeffs = 4 ** n
     elem = 16
@@ -315,12 +386,12 @@ def run_ours(args, world, rank, local):
 
     extra = {}
     if not args.no_extra:
-        # fp64 butterfly (IEEE double, rounded per level) on the same n=14 matrix
+        # fp64 butterfly (IEEE double, rounded per level) on the same matrix
         s64, p64, np64 = time_decompose(tpd, L, torch, work, pristine, n, 5, 2, L.TPD_PREC_PLAIN, stream)
         f64_ms = float(np.mean(s64))
-        extra["c128_fp64_plain_n14"] = {"ms_per_step": f64_ms, "coeffs_per_s": coeffs / (f64_ms * 1e-3),
+        extra["c128_fp64_plain_n%d" % n] = {"ms_per_step": f64_ms, "coeffs_per_s": coeffs / (f64_ms * 1e-3),
                                         "passes": np64}
-        extra["c128_fixed_n14"] = {"ms_per_step": ms_per_step, "coeffs_per_s": coeffs / (ms_per_step * 1e-3)}
+        extra["c128_fixed_n%d" % n] = {"ms_per_step": ms_per_step, "coeffs_per_s": coeffs / (ms_per_step * 1e-3)}
         del work, pristine
         torch.cuda.empty_cache()
         # complex64 at n = 15: plain and compensated fp32 vs fp64 / fixed complex128 of the same matrix
@@ -348,6 +419,9 @@ def run_ours(args, world, rank, local):
         extra["speedup_c64_compensated_vs_c128_fp64_n15"] = res["c128_fp64_plain"]["ms_per_step"] / \
             res["compensated"]["ms_per_step"]
         del w128, p128, p15, w15
+        torch.cuda.empty_cache()
+    if not args.no_extra and not args.no_batch:
+        extra["batch_4096_n3_10"] = time_batch(tpd, L, torch, stream)
 
     cpu = None
     if rank == 0 and world == 1:
@@ -358,10 +432,11 @@ def run_ours(args, world, rank, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": "n=14 dense random Hermitian, 16384x16384 complex128 (4.29 GB) in place; "
-                               "Re,Im of B ~ N(0,1), A=(B+B^H)/2",
+        "config": {"workload": "n=%d dense random Hermitian, %dx%d complex128 (%.2f GB) in place; "
+                               "Re,Im of B ~ N(0,1), A=(B+B^H)/2" % (n, N, N, coeffs * elem / 1e9),
                    "storage": "complex128", "precision": "fixed (exact int64 block fixed point per pass)",
-                   "passes": npass, "l2": "inputs larger than L2 (4.29 GB vs 126 MB); restored between steps",
+                   "passes": npass,
+                   "l2": "inputs larger than L2 (%.2f GB vs 126 MB); restored between steps" % (coeffs * elem / 1e9),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
         "clocks": clk, "gpu_launches": args.steps * npass,
