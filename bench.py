@@ -185,16 +185,16 @@ def kernel_digest():
     return h.hexdigest()[:16]
 
 
-def measured_traffic():
+def measured_traffic(n):
     """Per-launch DRAM bytes of the pass kernel from the committed ncu summary,
-    if it was taken on the current kernel sources."""
+    if it was taken on the current kernel sources and the same matrix size."""
     p = os.path.join(ROOT, "profiles", "traffic_n14_c128.json")
     try:
         with open(p) as fh:
             d = json.load(fh)
     except (OSError, ValueError):
         return None
-    if d.get("kernel_digest") != kernel_digest():
+    if d.get("kernel_digest") != kernel_digest() or d.get("qubits") != n:
         return None
     return d.get("bytes_per_launch")
 
@@ -230,10 +230,11 @@ def time_decompose(tpd, L, torch, work, pristine, n, steps, warmup, precision, s
 
 def time_batch(tpd, L, torch, stream, count=4096, seed=1004, reps=5):
     """Batch of `count` random Hermitian complex128 matrices, n_i ~ U{3..10}:
-    the batched call (every pass of every matrix, captured in one CUDA graph)
-    against one tpd_decompose call per matrix on the same stream.  All
-    matrices live in one buffer, restored from a pristine copy between
-    repetitions outside the timed events."""
+    the batched call in its two forms, each captured in a CUDA graph -- one
+    persistent kernel launch for the whole batch (default) and one launch per
+    (qubit count, pass) -- against one tpd_decompose call per matrix on the
+    same stream.  All matrices live in one buffer, restored from a pristine
+    copy between repetitions outside the timed events."""
     from paper_2310_13421_gb300 import synth
     ns = [int(x) for x in synth.batch_sizes(count, seed=seed)]
     offs = np.concatenate([[0], np.cumsum([4 ** n for n in ns])]).astype(np.int64)
@@ -246,12 +247,16 @@ def time_batch(tpd, L, torch, stream, count=4096, seed=1004, reps=5):
     pristine = buf.clone()
     passes = {n: max(L.tpd_plan_describe(n, L.TPD_C128, L.options())[0], 1) for n in set(ns)}
     alg_bytes = sum(32 * passes[n] * 4 ** n for n in ns)
-    batch = tpd.Batch(mats)
-    batch.decompose()                        # plans and kernel attributes, outside the capture
-    torch.cuda.synchronize()
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph):
-        batch.decompose()
+    graphs = {}
+    batches = {}
+    for name, variant in (("persistent", 0), ("per_pass", 1)):
+        batch = tpd.Batch(mats, variant=variant)
+        batch.decompose()                    # plans and kernel attributes, outside the capture
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            batch.decompose()
+        graphs[name], batches[name] = graph, batch
     wsb = max(L.tpd_workspace_size(n, L.TPD_C128, L.options()) for n in set(ns))
     ws = torch.empty(max(wsb, 16), dtype=torch.uint8, device="cuda")
 
@@ -261,7 +266,8 @@ def time_batch(tpd, L, torch, stream, count=4096, seed=1004, reps=5):
             assert st == 0, L.status_string(st)
 
     res = {}
-    for name, fn in (("graph", graph.replay), ("per_matrix_loop", loop)):
+    for name, fn in (("persistent", graphs["persistent"].replay), ("per_pass", graphs["per_pass"].replay),
+                     ("per_matrix_loop", loop)):
         times = []
         for k in range(reps + 2):
             buf.copy_(pristine)
@@ -274,21 +280,23 @@ def time_batch(tpd, L, torch, stream, count=4096, seed=1004, reps=5):
             if k >= 2:
                 times.append(e0.elapsed_time(e1))
         res[name] = float(np.median(times))
-    # the two forms agree exactly (same plans, same kernels)
-    buf.copy_(pristine)
-    graph.replay()
-    out_graph = buf.clone()
-    buf.copy_(pristine)
-    loop()
-    same = bool(torch.equal(out_graph, buf))
-    del buf, pristine, out_graph, mats, batch, graph
+    # the three forms agree exactly (same exact sums, one rounding per output)
+    outs = []
+    for fn in (graphs["persistent"].replay, graphs["per_pass"].replay, loop):
+        buf.copy_(pristine)
+        fn()
+        outs.append(buf.clone())
+    same = bool(torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2]))
+    status = batches["persistent"].status()
+    del buf, pristine, outs, mats, batches, graphs
     torch.cuda.empty_cache()
-    ms = res["graph"]
+    ms = res["persistent"]
     return {"matrices": count, "n_range": [3, 10], "data_bytes": int(offs[-1]) * 16,
-            "algorithmic_bytes": alg_bytes, "graph_ms": ms, "matrices_per_s": count / (ms * 1e-3),
+            "algorithmic_bytes": alg_bytes, "persistent_graph_ms": ms, "matrices_per_s": count / (ms * 1e-3),
             "coeffs_per_s": int(offs[-1]) / (ms * 1e-3), "hbm_gbs": alg_bytes / (ms * 1e-3) / 1e9,
+            "per_pass_graph_ms": res["per_pass"], "per_pass_hbm_gbs": alg_bytes / (res["per_pass"] * 1e-3) / 1e9,
             "per_matrix_loop_ms": res["per_matrix_loop"],
-            "speedup_vs_loop": res["per_matrix_loop"] / ms, "identical_results": same}
+            "speedup_vs_loop": res["per_matrix_loop"] / ms, "identical_results": same, "status": status}
 
 
 def run_ours(args, world, rank, local):
@@ -355,7 +363,7 @@ def run_ours(args, world, rank, local):
         pass
     peak = float(peaks.get("hbm_gbs", 6800.0))
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": measured_traffic(),
+                "traffic": measured_traffic(n),
                 "kernel": "k_pass<FixedArith,true> (one launch per pass, %d passes)" % npass,
                 "bytes_per_launch": alg_bytes, "per_pass_ms": per_pass_ms,
                 "per_pass_gbs": [alg_bytes / (m * 1e-3) / 1e9 for m in per_pass_ms],

@@ -81,7 +81,11 @@ typedef struct {
                        2 = persistent CTAs that prefetch the next tile (complex128
                        fixed point, single matrix, no zero skipping),
                        3 / 4 = one CTA per tile compiled for 2 / 3 CTAs per SM
-                       (tiles of up to 2^12 elements) */
+                       (tiles of up to 2^12 elements).
+                       Batched calls: 0 or 2 = the whole batch in one persistent
+                       kernel launch when every matrix has n <= 6 or a plan of
+                       2^12-element tiles (else as 1); 1, 3, 4 = one launch per
+                       (qubit count, pass) */
   void** pass_events; /* profiling, may be NULL: num_events cudaEvent_t handles
                        (created by the caller); tpd_decompose / tpd_compose
                        record event 0 before the first pass and event p+1 after
@@ -160,9 +164,16 @@ size_t tpd_batched_workspace_size(const int* ns, int count, int dtype, const tpd
  *   ptrs_dev   device array of `count` device pointers (matrix i at ptrs_dev[i]).
  *   ns_dev     device array of `count` ints, ns_dev[i] = n_i (same values as ns).
  *   ns         host array of the same n_i, 1 <= n_i <= 12, used for planning.
- *   workspace  device, tpd_batched_workspace_size() bytes (required).
- * The matrices must not overlap.  The enqueued work depends only on the
- * arguments (no host synchronisation), so it can be captured in a CUDA graph. */
+ *   workspace  device, tpd_batched_workspace_size() bytes (required).  Its
+ *              first bytes hold the status word read by tpd_batch_status.
+ * The matrices must not overlap.  The enqueued work (a memset of the control
+ * words and the kernel launches) depends only on the arguments (no host
+ * synchronisation), so it can be captured in a CUDA graph.  By default the
+ * whole batch runs in ONE persistent kernel launch (see tpd_options.variant):
+ * CTAs claim tiles in order, and a tile of a later pass waits, with a bound,
+ * for the tiles of its own matrix's previous pass; a wait that gives up, or
+ * ns_dev disagreeing with ns, is reported by tpd_batch_status (the results
+ * are then invalid).  No device-side wait is unbounded. */
 tpd_status tpd_decompose_batched(void* const* ptrs_dev, const int* ns_dev, const int* ns,
                                  int count, int dtype, const tpd_options* opt,
                                  void* workspace, size_t workspace_bytes, void* stream);
@@ -172,6 +183,20 @@ tpd_status tpd_decompose_batched(void* const* ptrs_dev, const int* ns_dev, const
 tpd_status tpd_compose_batched(void* const* ptrs_dev, const int* ns_dev, const int* ns,
                                int count, int dtype, int scale_mode, const tpd_options* opt,
                                void* workspace, size_t workspace_bytes, void* stream);
+
+/* Status of the last batched call that used `workspace` (device): TPD_OK,
+ * TPD_ERR_TIMEOUT (a bounded device-side wait gave up), TPD_ERR_INVALID_ARG
+ * (ns_dev disagreed with ns), or TPD_ERR_CUDA if the status cannot be read.
+ * Waits for `stream` to reach this point (host synchronisation: call it
+ * outside stream capture). */
+tpd_status tpd_batch_status(const void* workspace, void* stream);
+
+/* Test hook, host only: while `on` is nonzero, batched calls that take the
+ * persistent form make every tile of a pass after the first wait for one more
+ * completed tile of the previous pass than there are, so each such wait runs
+ * into its bound and tpd_batch_status reports TPD_ERR_TIMEOUT.  It exercises
+ * the timeout path without any fault; the results of such calls are invalid. */
+void tpd_test_hold_batch_waits(int on);
 
 /* Tuned defaults.  Registers tile_bits, max_levels and variant of `tuned`
  * for (n, dtype, precision); every later call for that key whose options

@@ -28,7 +28,7 @@ SYMBOLS = (
     "tpd_options_init", "tpd_workspace_size", "tpd_decompose", "tpd_compose", "tpd_decompose_host",
     "tpd_batched_workspace_size", "tpd_decompose_batched", "tpd_compose_batched",
     "tpd_plan_describe", "tpd_status_string", "tpd_version", "tpd_decompose_noalloc",
-    "tpd_tune_set", "tpd_tune_clear",
+    "tpd_tune_set", "tpd_tune_clear", "tpd_batch_status", "tpd_test_hold_batch_waits",
 )
 
 # size of the library's own scratch array used by tpd_decompose_noalloc
@@ -77,6 +77,10 @@ def load(path=None):
         lib.tpd_tune_set.restype = i
         lib.tpd_tune_clear.argtypes = []
         lib.tpd_tune_clear.restype = None
+        lib.tpd_batch_status.argtypes = [vp, vp]
+        lib.tpd_batch_status.restype = i
+        lib.tpd_test_hold_batch_waits.argtypes = [i]
+        lib.tpd_test_hold_batch_waits.restype = None
         lib.tpd_decompose_noalloc.argtypes = [vp, i, i, op, vp]
         lib.tpd_decompose_noalloc.restype = i
         lib.tpd_decompose_host.argtypes = [vp, vp, vp, i, i, op, vp, sz, vp]
@@ -136,6 +140,14 @@ def tpd_tune_set(n, dtype, precision, tuned=None):
 
 def tpd_tune_clear():
     load().tpd_tune_clear()
+
+
+def tpd_batch_status(workspace, stream=0):
+    return int(load().tpd_batch_status(workspace, stream or None))
+
+
+def tpd_test_hold_batch_waits(on):
+    load().tpd_test_hold_batch_waits(int(bool(on)))
 
 
 def tpd_decompose_noalloc(A_ptr, n, dtype, opt=None, stream=0):

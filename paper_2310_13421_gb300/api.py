@@ -107,7 +107,7 @@ class Batch:
     (pointer and qubit arrays plus workspace), reusable across calls and
     CUDA-graph captures as long as the matrices stay in place."""
 
-    def __init__(self, mats, precision=None, tile_bits=0, max_levels=0):
+    def __init__(self, mats, precision=None, tile_bits=0, max_levels=0, variant=0):
         if not mats:
             raise ValueError("empty batch")
         dev = mats[0].device
@@ -119,7 +119,7 @@ class Batch:
                 raise ValueError("batch matrices must share dtype and device")
             self.ns.append(_qubits(m))
         self.mats = list(mats)
-        self.opt = make_options(precision, False, tile_bits, max_levels)
+        self.opt = make_options(precision, False, tile_bits, max_levels, variant)
         self.ptrs = torch.tensor([m.data_ptr() for m in mats], dtype=torch.int64, device=dev)
         self.ns_dev = torch.tensor(self.ns, dtype=torch.int32, device=dev)
         wsb = L.tpd_batched_workspace_size(self.ns, self.code, self.opt)
@@ -134,6 +134,11 @@ class Batch:
                                          self.opt, self.ws.data_ptr(), self.ws.numel(), _stream(stream))
         _raise(st, "tpd_decompose_batched")
 
+    def status(self, stream=None):
+        """Status word of the last call (waits for the stream): 0 = OK; see tpd_batch_status."""
+        with torch.cuda.device(self.device):
+            return L.tpd_batch_status(self.ws.data_ptr(), _stream(stream))
+
     def compose(self, adjoint=False, stream=None):
         with torch.cuda.device(self.device):
             st = L.tpd_compose_batched(self.ptrs.data_ptr(), self.ns_dev.data_ptr(), self.ns, self.code,
@@ -142,17 +147,17 @@ class Batch:
         _raise(st, "tpd_compose_batched")
 
 
-def decompose_batched(mats, *, inplace=False, precision=None, stream=None):
+def decompose_batched(mats, *, inplace=False, precision=None, variant=0, stream=None):
     """Decompose a list of CUDA matrices of (possibly different) sizes; one
-    call enqueues the whole batch."""
+    call enqueues the whole batch (by default one persistent kernel launch)."""
     work = list(mats) if inplace else [m.clone() for m in mats]
-    Batch(work, precision=precision).decompose(stream)
+    Batch(work, precision=precision, variant=variant).decompose(stream)
     return work
 
 
-def compose_batched(mats, *, adjoint=False, inplace=False, precision=None, stream=None):
+def compose_batched(mats, *, adjoint=False, inplace=False, precision=None, variant=0, stream=None):
     work = list(mats) if inplace else [m.clone() for m in mats]
-    Batch(work, precision=precision).compose(adjoint=adjoint, stream=stream)
+    Batch(work, precision=precision, variant=variant).compose(adjoint=adjoint, stream=stream)
     return work
 
 

@@ -31,12 +31,15 @@ def _gpu_key():
     return "%s/%d" % (p.name, p.multi_processor_count)
 
 
-def candidates(n, dtype, precision):
-    """Distinct valid tunings for the key (same plan text and variant = same candidate)."""
+def candidates(n, dtype, precision, batched=False):
+    """Distinct valid tunings for the key (same plan text and variant = same
+    candidate).  For batches, variant 1 (one launch per qubit count and pass)
+    competes with the default single persistent launch."""
     code = _DT[dtype][0]
     prec = _PREC[precision] if isinstance(precision, str) else precision
     seen, out = set(), []
-    for tb, ml, var in itertools.product((0, 11, 12, 13), (0, 3, 4, 5, 6), (0, 2, 3, 4)):
+    variants = (0, 1, 3, 4) if batched else (0, 2, 3, 4)
+    for tb, ml, var in itertools.product((0, 11, 12, 13), (0, 3, 4, 5, 6), variants):
         opt = L.options(precision=prec, tile_bits=tb, max_levels=ml, variant=var)
         npass, desc = L.tpd_plan_describe(n, code, opt)
         if npass < 0:
@@ -133,7 +136,7 @@ def tune(n, dtype="c128", precision="default", reps=5, batch_bytes=64 << 20, reg
     elem = 16 if dtype == "c128" else 8
     count = max(1, batch_bytes // (4 ** n * elem)) if n <= 10 else 1
     tried = []
-    for cand in candidates(n, dtype, prec):
+    for cand in candidates(n, dtype, prec, batched=count > 1):
         if not _agrees_with_default(n, code, tdt, prec, cand):
             continue
         t = _time_batch(n, code, tdt, prec, cand, reps, count) if count > 1 else \

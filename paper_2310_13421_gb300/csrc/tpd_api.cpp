@@ -232,18 +232,132 @@ tpd_status single(bool dec, void* mat, int n, int dtype, double scale, const tpd
 }
 
 // ------------------------------------------------------------------ batched
-constexpr int kBatchMaxQubits = 12;
+constexpr int kBatchMaxQubits = kBatchMaxN;
+static_assert(kBatchStatusTimeout == TPD_ERR_TIMEOUT && kBatchStatusBadSizes == TPD_ERR_INVALID_ARG,
+              "device status codes are tpd_status values");
+static_assert(sizeof(BatchParams) <= 32000, "kernel parameter space");
 
-// workspace: items[count] | offsets[33] (device bucket lists) | per qubit
-// count n (ascending), for the fixed point: binary points of hist[n]
-// matrices for every pass but the last
+bool g_hold_batch_waits = false;   // test hook (tpd_test_hold_batch_waits)
+
+// workspace: control words (status, work counter, per-matrix pass completion
+// counters of the persistent kernel) | items[count] (matrix indices bucketed
+// by qubit count, on the device) | per qubit count n (ascending), for the fixed point: binary
+// points of hist[n] matrices for every pass but the last
 size_t batched_q_bytes(const Plan& plan, int arith, int count_n) {
   if (arith != kArithFixed || plan.npass < 2) return 0;
   size_t b = 0;
   for (int i = 0; i + 1 < plan.npass; ++i) b += (size_t)plan.pass[i].ntiles * sizeof(int) * (size_t)count_n;
   return align256(b);
 }
-size_t batched_head(int count) { return align256((size_t)count * sizeof(int)) + align256(64 * sizeof(int)); }
+size_t batched_ctrl(const int* hist, const std::vector<const Plan*>& plans) {
+  size_t words = kCtrlDone;
+  for (int n = 1; n <= kBatchMaxQubits; ++n)
+    if (hist[n] && plans[n]->npass > 1) words += (size_t)hist[n] * (plans[n]->npass - 1);
+  return align256(words * sizeof(unsigned));
+}
+size_t batched_head(int count) { return align256((size_t)count * sizeof(int)); }
+
+// The persistent form applies when every matrix is either small (n <= 6: one
+// work item, whole matrix in shared memory) or planned with 2^12-element
+// tiles (256-thread CTAs), and the work list fits the kernel's parameters.
+bool persistent_fits(const int* hist, const std::vector<const Plan*>& plans, long long* total) {
+  int ndesc = 0, nseg = 0;
+  long long items = 1;
+  for (int n = 1; n <= kBatchMaxQubits; ++n) {
+    if (!hist[n]) continue;
+    const Plan& p = *plans[n];
+    if (n <= 6) { ++nseg; items += hist[n]; continue; }
+    for (int i = 0; i < p.npass; ++i) {
+      if (p.pass[i].D != 12) return false;
+      ++ndesc; ++nseg;
+      items += (long long)hist[n] * p.pass[i].ntiles;
+    }
+  }
+  *total = items;
+  return ndesc <= kBatchMaxDescs && nseg <= kBatchMaxSegs && items < 0x7fffffffll;
+}
+
+// Work list of the persistent kernel (see tpd_launch.h): bucketing, the first
+// pass of every qubit count n >= 7 (largest first), the small matrices, then
+// the later passes.
+tpd_status run_persistent(bool dec, int arith, void* const* ptrs_dev, const int* ns_dev, int count, const int* hist,
+                          const std::vector<const Plan*>& plans, int scale_mode, unsigned* ctrl, int* items,
+                          char* qbase0, size_t ctrl_bytes, cudaStream_t s) {
+  static BatchParams bp;               // large: built under the lock, copied into the launch
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lk(mu);
+  std::memset(&bp, 0, sizeof(bp));
+  bp.count = count;
+  for (int n = 0; n <= kBatchMaxQubits; ++n) bp.hist[n] = hist[n];
+  bp.scale_mode = dec ? 0 : scale_mode;
+  bp.ptrs = ptrs_dev; bp.ns = ns_dev; bp.items = items; bp.ctrl = ctrl;
+  int item_start[kBatchMaxQubits + 2] = {0};
+  for (int n = 1; n <= kBatchMaxQubits + 1; ++n) item_start[n] = item_start[n - 1] + hist[n - 1];
+  // per n: q area and done-counter bases per pass
+  size_t qoff[kBatchMaxQubits + 1][kMaxQubits];
+  int dbase[kBatchMaxQubits + 1][kMaxQubits];
+  {
+    size_t q = 0;
+    int d = 0;
+    for (int n = 1; n <= kBatchMaxQubits; ++n) {
+      if (!hist[n]) continue;
+      const Plan& p = *plans[n];
+      size_t qn = q;
+      for (int i = 0; i < p.npass; ++i) {
+        qoff[n][i] = qn;
+        if (i + 1 < p.npass && arith == kArithFixed) qn += (size_t)p.pass[i].ntiles * sizeof(int) * hist[n];
+        dbase[n][i] = -1;
+        if (i + 1 < p.npass) { dbase[n][i] = d; d += hist[n]; }
+      }
+      q += batched_q_bytes(p, arith, hist[n]);
+    }
+  }
+  long long first = 1;
+  int nseg = 0, ndesc = 0;
+  auto add_pass = [&](int n, int i) {
+    const Plan& p = *plans[n];
+    const PassDesc& pd = p.pass[i];
+    const bool last = i + 1 == p.npass;
+    BatchSeg& sg = bp.seg[nseg++];
+    bp.desc[ndesc] = pd;
+    sg.kind = kSegPass; sg.n = n; sg.desc = ndesc++;
+    sg.role = (i > 0 ? kRoleIntIn : 0) | (!last ? kRoleIntOut : 0);
+    sg.item_start = item_start[n]; sg.nmat = hist[n];
+    sg.first = first; sg.tiles = pd.ntiles;
+    sg.wait_ctr = i > 0 ? dbase[n][i - 1] : -1;
+    sg.wait_need = i > 0 ? p.pass[i - 1].ntiles + (g_hold_batch_waits ? 1 : 0) : 0;
+    sg.post_ctr = dbase[n][i];
+    PassArgs& a = sg.args;
+    if (arith == kArithFixed) {
+      if (i > 0) { a.q_in = reinterpret_cast<const int*>(qbase0 + qoff[n][i - 1]); a.q_in_stride = p.pass[i - 1].ntiles; }
+      if (!last) { a.q_out = reinterpret_cast<int*>(qbase0 + qoff[n][i]); a.q_out_stride = pd.ntiles; }
+    } else {
+      sg.role = 0;
+    }
+    const double scale = scale_mode ? std::ldexp(1.0, -n) : 1.0;
+    pass_scaling(dec, arith, pd, last, scale_mode ? -n : 0, 1.0, scale, &a);
+    first += (long long)hist[n] * pd.ntiles;
+  };
+  for (int n = kBatchMaxQubits; n >= 7; --n)
+    if (hist[n]) add_pass(n, 0);
+  for (int n = 6; n >= 1; --n) {
+    if (!hist[n]) continue;
+    BatchSeg& sg = bp.seg[nseg++];
+    sg.kind = kSegSmall; sg.n = n; sg.desc = -1; sg.role = 0;
+    sg.item_start = item_start[n]; sg.nmat = hist[n];
+    sg.first = first; sg.tiles = 1; sg.wait_ctr = -1; sg.post_ctr = -1;
+    sg.args.out_mul = 1.0;
+    first += hist[n];
+  }
+  for (int i = 1; i < kMaxQubits; ++i)
+    for (int n = kBatchMaxQubits; n >= 7; --n)
+      if (hist[n] && plans[n]->npass > i) add_pass(n, i);
+  bp.nseg = nseg;
+  bp.total = first;
+  if (cudaMemsetAsync(ctrl, 0, ctrl_bytes, s) != cudaSuccess) return TPD_ERR_CUDA;
+  if (launch_batch(arith, dec, bp, nullptr, s) != cudaSuccess) return TPD_ERR_CUDA;
+  return TPD_OK;
+}
 
 tpd_status batched(bool dec, void* const* ptrs_dev, const int* ns_dev, const int* ns, int count, int dtype,
                    int scale_mode, const tpd_options* opt, void* ws, size_t ws_bytes, void* stream) {
@@ -271,14 +385,24 @@ tpd_status batched(bool dec, void* const* ptrs_dev, const int* ns_dev, const int
     variants[n] = eff.variant;
     need += batched_q_bytes(*plans[n], arith, hist[n]);
   }
+  const size_t ctrl_bytes = batched_ctrl(hist, plans);
+  need += ctrl_bytes;
   if (ws == nullptr || ws_bytes < need) return TPD_ERR_WORKSPACE;
   if (reinterpret_cast<uintptr_t>(ws) % 16) return TPD_ERR_MISALIGNED;
-  int* items = static_cast<int*>(ws);
-  int* offsets = reinterpret_cast<int*>(static_cast<char*>(ws) + align256((size_t)count * sizeof(int)));
-  char* qbase = static_cast<char*>(ws) + batched_head(count);
+  unsigned* ctrl = static_cast<unsigned*>(ws);
+  int* items = reinterpret_cast<int*>(static_cast<char*>(ws) + ctrl_bytes);
+  char* qbase = reinterpret_cast<char*>(items) + batched_head(count);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (launch_bucket(ns_dev, count, items, offsets, nullptr, s) != cudaSuccess) return TPD_ERR_CUDA;
-  int start = 0;  // host mirror of offsets[n]: buckets are in increasing n
+  const int caller_variant = opt ? opt->variant : 0;
+  long long total = 0;
+  if ((caller_variant == 0 || caller_variant == 2) && persistent_fits(hist, plans, &total))
+    return run_persistent(dec, arith, ptrs_dev, ns_dev, count, hist, plans, scale_mode, ctrl, items, qbase,
+                          ctrl_bytes, s);
+  if (cudaMemsetAsync(ctrl, 0, ctrl_bytes, s) != cudaSuccess) return TPD_ERR_CUDA;   // status word: OK
+  BucketHist bh;
+  for (int n = 0; n <= kBatchMaxQubits; ++n) bh.h[n] = hist[n];
+  if (launch_bucket(ns_dev, count, bh, items, ctrl + kCtrlStatus, s) != cudaSuccess) return TPD_ERR_CUDA;
+  int start = 0;  // first bucket position of qubit count n: buckets are in increasing n
   for (int n = 1; n <= kBatchMaxQubits; ++n) {
     if (!hist[n]) continue;
     const Plan& plan = *plans[n];
@@ -371,6 +495,19 @@ tpd_status tpd_decompose_host(const void* A_host, void* W_host, void* dev_A, int
   return TPD_OK;
 }
 
+tpd_status tpd_batch_status(const void* workspace, void* stream) {
+  if (workspace == nullptr) return TPD_ERR_INVALID_ARG;
+  unsigned st = 0;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaMemcpyAsync(&st, static_cast<const unsigned*>(workspace) + kCtrlStatus, sizeof(st), cudaMemcpyDeviceToHost,
+                      s) != cudaSuccess)
+    return TPD_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return TPD_ERR_CUDA;
+  return static_cast<tpd_status>(st);
+}
+
+void tpd_test_hold_batch_waits(int on) { g_hold_batch_waits = on != 0; }
+
 size_t tpd_batched_workspace_size(const int* ns, int count, int dtype, const tpd_options* opt) {
   int prec = 0;
   if (check_options(dtype, opt, &prec) != TPD_OK || count < 0 || (count > 0 && ns == nullptr)) return 0;
@@ -381,14 +518,16 @@ size_t tpd_batched_workspace_size(const int* ns, int count, int dtype, const tpd
   }
   const int arith = arith_of(dtype, prec);
   size_t need = batched_head(count);
+  std::vector<const Plan*> plans(kBatchMaxQubits + 1, nullptr);
   for (int n = 1; n <= kBatchMaxQubits; ++n) {
     if (!hist[n]) continue;
     const tpd_options eff = effective_options(n, dtype, prec, opt);
     const Plan* plan = get_plan(n, dtype, prec, &eff);
     if (!plan) return 0;
+    plans[n] = plan;
     need += batched_q_bytes(*plan, arith, hist[n]);
   }
-  return need;
+  return need + batched_ctrl(hist, plans);
 }
 
 tpd_status tpd_decompose_batched(void* const* ptrs_dev, const int* ns_dev, const int* ns, int count, int dtype,

@@ -1,0 +1,191 @@
+// Persistent batched Pauli decomposition / composition: a whole batch of
+// matrices of mixed qubit counts in ONE kernel launch (the batch form of
+// Sec. III's algorithm: every matrix independently, Eqs. 3-5).
+//
+// CTAs claim work items in order from a device counter (the work list is
+// described in tpd_launch.h: bucketing, then per segment the tiles of one pass
+// of all matrices of one qubit count, or whole small matrices).  A tile of
+// pass p > 0 of matrix m reads what the tiles of pass p-1 of m wrote, so it
+// waits until m's per-matrix completion counter of pass p-1 is full.  All
+// those tiles were claimed earlier by CTAs that are running and never wait on
+// later items, so the wait ends; it is nonetheless bounded: after
+// kSpinLimit polls the CTA records TPD_ERR_TIMEOUT in the status word and
+// skips the item, and every later item is skipped as soon as the status word
+// is set, so the launch always finishes and the context stays usable.
+//
+// Publication: the CTA finishes a tile's stores, barriers, and one thread
+// issues a gpu-scope fence and increments the counter; the waiting thread
+// polls with ld.acquire.gpu and the CTA barriers before loading, and the
+// loads of data written in this launch go through L2 (ld.global.cg).
+#pragma once
+
+#include "tpd_pass.cuh"
+
+namespace tpd {
+
+constexpr unsigned kSpinLimit = 1u << 21;       // polls, with back-off up to 0.5 us: ~1-3 s
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned ld_volatile(const unsigned* p) {
+  return *reinterpret_cast<const volatile unsigned*>(p);
+}
+
+// Wait until *p >= need.  false when the status word is (or becomes) set, or
+// when the poll limit runs out (the status word is then set to TIMEOUT).
+static __device__ __noinline__ bool wait_count(const unsigned* p, unsigned need, unsigned* status) {
+  unsigned sleep_ns = 32;
+  for (unsigned it = 0;; ++it) {
+    if (ld_acquire_gpu(p) >= need) return true;
+    if (ld_volatile(status) != 0) return false;
+    if (it >= kSpinLimit) {
+      atomicCAS(status, 0u, kBatchStatusTimeout);
+      return false;
+    }
+    __nanosleep(sleep_ns);
+    if (sleep_ns < 512) sleep_ns *= 2;
+  }
+}
+
+// Work item 0: counting sort of the matrix indices by qubit count into
+// bp.items (ascending n, as the host laid out the segments), checking the
+// counts against the host's histogram.
+static __device__ __noinline__ void bucket_item(const BatchParams& bp, int tid, int nthr) {
+  __shared__ int cnt[kBatchMaxN + 1];
+  __shared__ int cur[kBatchMaxN + 1];
+  __shared__ int bad;
+  if (tid <= kBatchMaxN) cnt[tid] = 0;
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  for (int i = tid; i < bp.count; i += nthr) {
+    const int n = __ldg(bp.ns + i);
+    if (n >= 1 && n <= kBatchMaxN) atomicAdd(&cnt[n], 1);
+    else bad = 1;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int acc = 0;
+    for (int n = 0; n <= kBatchMaxN; ++n) {
+      if (cnt[n] != bp.hist[n]) bad = 1;
+      cur[n] = acc;
+      acc += cnt[n];
+    }
+  }
+  __syncthreads();
+  if (!bad)
+    for (int i = tid; i < bp.count; i += nthr) {
+      const int n = __ldg(bp.ns + i);
+      bp.items[atomicAdd(&cur[n], 1)] = i;
+    }
+  __syncthreads();
+  if (tid == 0) {
+    if (bad) atomicCAS(bp.ctrl + kCtrlStatus, 0u, kBatchStatusBadSizes);
+    __threadfence();
+    atomicExch(bp.ctrl + kCtrlBucket, 1u);
+  }
+}
+
+template <class A, bool kDec>
+__device__ __forceinline__ void batch_pass_tile(const BatchSeg& sg, const PassDesc& pd, void* matp,
+                                                long long j, long long tile, unsigned char* smem, int lane,
+                                                int warp) {
+  const int* q_in = sg.args.q_in ? sg.args.q_in + j * sg.args.q_in_stride : nullptr;
+  int* q_out = sg.args.q_out ? sg.args.q_out + j * sg.args.q_out_stride : nullptr;
+  if constexpr (A::kFixed) {
+    switch (sg.role) {
+      case 0: pass_tile<A, kDec, 0, true>(pd, sg.args, matp, q_in, q_out, tile, smem, lane, warp); break;
+      case kRoleIntIn:
+        pass_tile<A, kDec, kRoleIntIn, true>(pd, sg.args, matp, q_in, q_out, tile, smem, lane, warp);
+        break;
+      case kRoleIntOut:
+        pass_tile<A, kDec, kRoleIntOut, true>(pd, sg.args, matp, q_in, q_out, tile, smem, lane, warp);
+        break;
+      default:
+        pass_tile<A, kDec, kRoleIntIn | kRoleIntOut, true>(pd, sg.args, matp, q_in, q_out, tile, smem, lane,
+                                                           warp);
+        break;
+    }
+  } else {
+    pass_tile<A, kDec, 0, true>(pd, sg.args, matp, q_in, q_out, tile, smem, lane, warp);
+  }
+}
+
+// 256 threads; dynamic shared memory: 2^12 x 16 bytes + 256 (a D = 12 tile or
+// a whole n <= 6 matrix, plus reduction slots).
+template <class A, bool kDec>
+__global__ void __launch_bounds__(256, 2) k_batch(const __grid_constant__ BatchParams bp) {
+  using Store = typename A::Store;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ unsigned s_work;
+  __shared__ int s_ok;
+  __shared__ void* s_mat;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  unsigned* status = bp.ctrl + kCtrlStatus;
+  unsigned* done = bp.ctrl + kCtrlDone;
+  bool seen_bucket = false;
+  for (;;) {
+    if (tid == 0) s_work = atomicAdd(bp.ctrl + kCtrlWork, 1u);
+    __syncthreads();
+    const long long w = s_work;
+    if (w >= bp.total) break;
+    if (w == 0) {
+      bucket_item(bp, tid, blockDim.x);       // ends with barriers: s_work may be rewritten after it
+      seen_bucket = true;
+      continue;
+    }
+    int si = 0;
+    while (si + 1 < bp.nseg && w >= bp.seg[si + 1].first) ++si;
+    const BatchSeg& sg = bp.seg[si];
+    const long long rel = w - sg.first;
+    const long long j = rel / sg.tiles;       // matrix within the segment
+    const long long tile = rel - j * sg.tiles;
+    if (tid == 0) {
+      bool ok = seen_bucket || wait_count(bp.ctrl + kCtrlBucket, 1u, status);
+      if (ok && sg.wait_ctr >= 0) ok = wait_count(done + sg.wait_ctr + j, (unsigned)sg.wait_need, status);
+      ok = ok && ld_volatile(status) == 0;
+      if (ok) {
+        const int m = __ldcg(bp.items + sg.item_start + j);
+        s_mat = bp.ptrs[m];
+      }
+      s_ok = ok;
+    }
+    __syncthreads();
+    seen_bucket = true;
+    if (s_ok) {
+      void* matp = s_mat;
+      if (sg.kind == kSegSmall) {
+        small_matrix<A, kDec>(reinterpret_cast<Store*>(matp), sg.n, 0, bp.scale_mode, smem, tid, blockDim.x);
+      } else {
+        batch_pass_tile<A, kDec>(sg, bp.desc[sg.desc], matp, j, tile, smem, lane, warp);
+      }
+    }
+    __syncthreads();                          // the tile's stores are done (and smem is free)
+    if (tid == 0 && sg.post_ctr >= 0) {
+      __threadfence();
+      atomicAdd(done + sg.post_ctr + j, 1u);
+    }
+  }
+}
+
+template <class A, bool kDec>
+cudaError_t launch_batch_t(const BatchParams& bp, int* grid_out, cudaStream_t s) {
+  const size_t smem = ((size_t)16 << 12) + 256;
+  auto kfn = k_batch<A, kDec>;
+  cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, nsm = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, 256, smem)) != cudaSuccess) return e;
+  long long grid = (long long)nsm * (per_sm > 0 ? per_sm : 1);
+  if (grid > bp.total) grid = bp.total;
+  if (grid_out) *grid_out = (int)grid;
+  kfn<<<(unsigned)grid, 256, smem, s>>>(bp);
+  return cudaGetLastError();
+}
+
+}  // namespace tpd

@@ -30,33 +30,40 @@ cudaError_t launch_pass_pipe_c128(bool dec, const PassDesc& pd, const PassArgs& 
 }
 
 // One CTA buckets matrix indices by qubit count (counting sort in shared memory).
-__global__ void __launch_bounds__(1024) k_bucket(const int* __restrict__ ns, int count, int* __restrict__ items,
-                                                 int* __restrict__ offsets) {
-  __shared__ int cnt[32];
-  __shared__ int cur[32];
+__global__ void __launch_bounds__(1024) k_bucket(const int* __restrict__ ns, int count, const BucketHist hist,
+                                                 int* __restrict__ items, unsigned* __restrict__ status) {
+  __shared__ int cnt[kBatchMaxN + 1];
+  __shared__ int cur[kBatchMaxN + 1];
+  __shared__ int bad;
   const int tid = threadIdx.x;
-  if (tid < 32) cnt[tid] = 0;
+  if (tid <= kBatchMaxN) cnt[tid] = 0;
+  if (tid == 0) bad = 0;
   __syncthreads();
   for (int i = tid; i < count; i += blockDim.x) {
     const int n = ns[i];
-    if (n >= 0 && n < 32) atomicAdd(&cnt[n], 1);
+    if (n >= 1 && n <= kBatchMaxN) atomicAdd(&cnt[n], 1);
+    else bad = 1;
   }
   __syncthreads();
   if (tid == 0) {
     int acc = 0;
-    for (int n = 0; n < 32; ++n) { offsets[n] = acc; cur[n] = acc; acc += cnt[n]; }
-    offsets[32] = acc;
+    for (int n = 0; n <= kBatchMaxN; ++n) {
+      if (cnt[n] != hist.h[n]) bad = 1;
+      cur[n] = acc;
+      acc += cnt[n];
+    }
+    if (bad) atomicCAS(status, 0u, kBatchStatusBadSizes);
   }
   __syncthreads();
   for (int i = tid; i < count; i += blockDim.x) {
-    const int n = ns[i];
-    if (n >= 0 && n < 32) items[atomicAdd(&cur[n], 1)] = i;
+    if (bad) items[i] = -1;
+    else items[atomicAdd(&cur[ns[i]], 1)] = i;
   }
 }
 
-cudaError_t launch_bucket(const int* ns_dev, int count, int* out_items, int* out_offsets, int* /*scratch*/,
+cudaError_t launch_bucket(const int* ns_dev, int count, const BucketHist& hist, int* out_items, unsigned* status,
                           cudaStream_t s) {
-  k_bucket<<<1, 1024, 0, s>>>(ns_dev, count, out_items, out_offsets);
+  k_bucket<<<1, 1024, 0, s>>>(ns_dev, count, hist, out_items, status);
   return cudaGetLastError();
 }
 

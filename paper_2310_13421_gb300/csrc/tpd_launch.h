@@ -35,6 +35,12 @@ struct PassArgs {
   long long q_out_stride;     // batched: q entries per matrix (this pass's tile count)
 };
 
+// Role of a fixed-point pass: input IEEE doubles (0) or int64 sums of a
+// previous pass (kRoleIntIn); output IEEE doubles (0) or int64 sums for a next
+// pass (kRoleIntOut).
+constexpr int kRoleIntIn = 1;
+constexpr int kRoleIntOut = 2;
+
 // q values above kQValidMin are binary points; kQIeee marks an IEEE tile; any
 // other value (e.g. the 0xC0 byte fill of a cleared array) a zero tile.
 constexpr int kQValidMin = -0x20000000;
@@ -51,6 +57,63 @@ struct SmallArgs {
   int scale_mode;             // compose: 0 scale 1, 1 scale 2^-n; decompose ignores
 };
 
+// ---------------------------------------------------------------- batched, one launch
+//
+// The persistent batched kernel walks one global list of work items, claimed
+// in order from a device counter: item 0 buckets the matrices by qubit count;
+// then, per *segment*, the tiles of one pass over every matrix of one qubit
+// count (tile-major within a matrix), or whole small matrices (n <= 6, one
+// item each).  Segments are ordered so that every pass comes after the pass
+// it depends on; a tile of pass p > 0 waits (bounded) until all tiles of pass
+// p-1 of ITS matrix are done, counted per matrix in `done`.
+constexpr int kBatchMaxDescs = 16;
+constexpr int kBatchMaxSegs = 32;
+constexpr int kBatchMaxN = 12;
+constexpr int kSegSmall = 0;
+constexpr int kSegPass = 1;
+
+struct BatchSeg {
+  PassArgs args;              // per-pass arguments (q arrays: pass-level bases, per matrix + j * stride)
+  int32_t kind;               // kSegSmall / kSegPass
+  int32_t n;                  // qubits of the segment's matrices
+  int32_t desc;               // kSegPass: index into BatchParams::desc
+  int32_t role;               // fixed point: kRoleIntIn / kRoleIntOut bits of the pass
+  int32_t item_start;         // first bucket position of the segment's matrices
+  int32_t nmat;               // matrices in the segment
+  int32_t wait_ctr;           // done-counter base of the pass this one depends on (-1: none)
+  int32_t post_ctr;           // done-counter base this pass increments (-1: none)
+  int64_t first;              // first work index of the segment
+  int64_t tiles;              // tiles per matrix (1 for kSegSmall)
+  int64_t wait_need;          // tiles per matrix of the pass waited for
+};
+
+struct BatchParams {
+  PassDesc desc[kBatchMaxDescs];
+  BatchSeg seg[kBatchMaxSegs];
+  int32_t nseg;
+  int32_t count;              // matrices
+  int32_t hist[kBatchMaxN + 1];  // host's count per qubit number (checked by the bucket item)
+  int32_t scale_mode;         // compose: 0 scale 1, 1 scale 2^-n (small matrices)
+  int64_t total;              // work items
+  void* const* ptrs;          // device array of matrix pointers
+  const int* ns;              // device array of n_i
+  int* items;                 // bucketed matrix indices (written by item 0)
+  unsigned* ctrl;             // [0] next work item, [1] status, [2] bucket done, [3] -, then done counters
+};
+
+// status codes the kernel writes to ctrl[kCtrlStatus] (tpd_status values)
+constexpr unsigned kBatchStatusBadSizes = 1;    // TPD_ERR_INVALID_ARG: ns_dev disagrees with ns
+constexpr unsigned kBatchStatusTimeout = 6;     // TPD_ERR_TIMEOUT: a bounded wait gave up
+
+// control words (unsigned) at the head of BatchParams::ctrl; cleared before each launch
+constexpr int kCtrlWork = 0;
+constexpr int kCtrlStatus = 1;
+constexpr int kCtrlBucket = 2;
+constexpr int kCtrlDone = 4;
+
+// Persistent batched kernel for an arithmetic: `grid` CTAs of 256 threads.
+cudaError_t launch_batch(int arith, bool dec, const BatchParams& bp, int* grid_out, cudaStream_t s);
+
 // Bytes per element in registers / shared memory for an arithmetic.
 inline int arith_vbytes(int arith) { return arith == kArithF32 ? 8 : 16; }
 
@@ -65,10 +128,13 @@ cudaError_t launch_small_c64(int arith, bool dec, const SmallArgs& args, int blo
 // zero skipping): one CTA per SM, nsm = SM count.
 cudaError_t launch_pass_pipe_c128(bool dec, const PassDesc& pd, const PassArgs& args, int nsm, cudaStream_t s);
 
-// Bucket matrices by qubit count: for each n in [0, 32), out_offsets[n] is the
-// start of its list in out_items (matrix indices, any order within a list).
-// scratch: 64 ints.
-cudaError_t launch_bucket(const int* ns_dev, int count, int* out_items, int* out_offsets, int* scratch,
+// Bucket matrices by qubit count: out_items lists the matrix indices of each
+// n in turn (ascending n).  The device counts are checked against the host's
+// histogram hist[0..12]; on a mismatch (ns_dev disagreeing with the host's ns)
+// the kernel sets *status to kBatchStatusBadSizes and fills out_items with -1,
+// which every batched kernel treats as "no matrix" (nothing is touched).
+struct BucketHist { int h[13]; };
+cudaError_t launch_bucket(const int* ns_dev, int count, const BucketHist& hist, int* out_items, unsigned* status,
                           cudaStream_t s);
 
 inline cudaError_t launch_pass(int arith, bool dec, const PassDesc& pd, const PassArgs& args,

@@ -27,6 +27,17 @@ namespace tpd {
 
 constexpr uint32_t kFull = 0xffffffffu;
 
+// Loads of data a pass reads.  kCg = false: the read-only path (ld.global.nc),
+// valid when nothing in the same launch writes the data; kCg = true: loads
+// cached in L2 only (ld.global.cg), for the persistent batched kernel whose
+// later passes read what other CTAs of the same launch wrote (after an
+// acquire on their completion counters).
+template <bool kCg, class T>
+__device__ __forceinline__ T ld_in(const T* p) {
+  if constexpr (kCg) return __ldcg(p);
+  else return __ldg(p);
+}
+
 // 2^e as a double, built from its bits (normal range only)
 __device__ __forceinline__ double pow2d(int e) {
   return __longlong_as_double((long long)(1023 + e) << 52);
@@ -201,7 +212,7 @@ __device__ __forceinline__ void finish_tile(const PassDesc& pd, const PassArgs& 
   }
 }
 
-template <class Store>
+template <bool kCg = false, class Store>
 __device__ __forceinline__ void load_tile(const PassDesc& pd, const void* matp, long long base, int lane, int warp,
                                           Store (&raw)[kElems]) {
   const Stage& s0 = pd.st[0];
@@ -210,7 +221,7 @@ __device__ __forceinline__ void load_tile(const PassDesc& pd, const void* matp, 
   const long long w0 = 1ll << pd.gbit[s0.reg[0]], w1 = 1ll << pd.gbit[s0.reg[1]];
   const long long w2 = 1ll << pd.gbit[s0.reg[2]], w3 = 1ll << pd.gbit[s0.reg[3]];
 #pragma unroll
-  for (int e = 0; e < kElems; ++e) raw[e] = __ldg(mat + g + reg_off(e, w0, w1, w2, w3));
+  for (int e = 0; e < kElems; ++e) raw[e] = ld_in<kCg>(mat + g + reg_off(e, w0, w1, w2, w3));
 }
 
 // ============================================================== fixed point
@@ -277,12 +288,12 @@ __device__ __forceinline__ long long shr_floor(long long v, unsigned sh) {
 // line (never taken for finite data) so the hot path stays small in the
 // instruction cache.  Elements are re-read: doubles as such, int64 sums of a
 // previous pass converted with their tile's binary point.
-template <bool kDec>
+template <bool kDec, bool kCg = false>
 __device__ __noinline__ void ieee_tile(const PassDesc& pd, const PassArgs& args, void* matp, const int* q_in,
                                        int* q_out, long long tile, long long base, long long pbase, int nbase,
                                        unsigned char* smem, int lane, int warp) {
   double2 raw[kElems];
-  load_tile(pd, matp, base, lane, warp, raw);
+  load_tile<kCg>(pd, matp, base, lane, warp, raw);
   if (q_in != nullptr) {
     const Stage& s0 = pd.st[0];
     long long pt = pbase;
@@ -294,7 +305,7 @@ __device__ __noinline__ void ieee_tile(const PassDesc& pd, const PassArgs& args,
     const int p0 = pd.prev_w[s0.reg[0]], p1 = pd.prev_w[s0.reg[1]], p2 = pd.prev_w[s0.reg[2]],
               p3 = pd.prev_w[s0.reg[3]];
     for (int e = 0; e < kElems; ++e) {
-      const int q = q_in[pt + reg_off(e, p0, p1, p2, p3)];
+      const int q = ld_in<kCg>(q_in + pt + reg_off(e, p0, p1, p2, p3));
       if (q == kQIeee) continue;
       if (!q_is_valid(q)) { raw[e] = make_double2(0.0, 0.0); continue; }
       raw[e].x = FixedArith::to_double_int(__double_as_longlong(raw[e].x), -q);
@@ -319,17 +330,14 @@ __device__ __forceinline__ void load_tile_smem(const PassDesc& pd, const unsigne
   for (int e = 0; e < kElems; ++e) raw[e] = b[t + reg_off(e, w0, w1, w2, w3)];
 }
 
-// Role of a fixed-point pass, a compile-time choice so that each kernel
-// carries only its own conversions (smaller code, fewer registers): input
-// IEEE doubles or int64 sums of a previous pass, output int64 sums for a
-// next pass or IEEE doubles.
-constexpr int kRoleIntIn = 1;
-constexpr int kRoleIntOut = 2;
+// Role of a fixed-point pass (kRoleIntIn / kRoleIntOut of tpd_launch.h), a
+// compile-time choice so that each kernel carries only its own conversions
+// (smaller code, fewer registers).
 
 // xbuf: shared-memory exchange area (2^D x 16 bytes); red: 64 ints;
 // inbuf: the tile already copied to shared memory (stage-0 positions), or
 // nullptr to read it from global memory.
-template <bool kDec, int kRole>
+template <bool kDec, int kRole, bool kCg = false>
 __device__ __forceinline__ void fixed_tile(const PassDesc& pd, const PassArgs& args, void* matp, const int* q_in,
                                            int* q_out, long long tile, long long base, long long pbase, int nbase,
                                            const unsigned char* inbuf, unsigned char* xbuf, int* red, int lane,
@@ -343,7 +351,7 @@ __device__ __forceinline__ void fixed_tile(const PassDesc& pd, const PassArgs& a
     // ---- first pass: IEEE doubles onto the tile's binary point
     double2 raw[kElems];
     if (inbuf) load_tile_smem(pd, inbuf, lane, warp, raw);
-    else load_tile(pd, matp, base, lane, warp, raw);
+    else load_tile<kCg>(pd, matp, base, lane, warp, raw);
     uint32_t hmax = 0, nzw = 0;
 #pragma unroll
     for (int e = 0; e < kElems; ++e) {
@@ -365,7 +373,7 @@ __device__ __forceinline__ void fixed_tile(const PassDesc& pd, const PassArgs& a
     for (int w = 0; w < nwarps; ++w) { emax = max(emax, red[w]); nz |= red[16 + w]; }
     if (args.skip_zero && nz == 0) return;                // all +-0: outputs are zero already
     if (emax == 2047) {                                   // Inf/NaN in the tile
-      ieee_tile<kDec>(pd, args, matp, nullptr, q_out, tile, base, pbase, nbase, smem, lane, warp);
+      ieee_tile<kDec, kCg>(pd, args, matp, nullptr, q_out, tile, base, pbase, nbase, smem, lane, warp);
       return;
     }
     // x * 2^S with S = 1084 - K - emax_eff puts the largest element below 2^(62-K)
@@ -381,7 +389,7 @@ __device__ __forceinline__ void fixed_tile(const PassDesc& pd, const PassArgs& a
     // ---- later pass: int64 sums with their previous tile's binary point
     longlong2 raw[kElems];
     if (inbuf) load_tile_smem(pd, inbuf, lane, warp, raw);
-    else load_tile(pd, matp, base, lane, warp, raw);
+    else load_tile<kCg>(pd, matp, base, lane, warp, raw);
     const Stage& s0 = pd.st[0];
     long long pt = pbase;
 #pragma unroll
@@ -394,7 +402,7 @@ __device__ __forceinline__ void fixed_tile(const PassDesc& pd, const PassArgs& a
     int qmax = kQValidMin, ieee = 0;
 #pragma unroll
     for (int e = 0; e < kElems; ++e) {
-      const int q = __ldg(q_in + pt + reg_off(e, p0, p1, p2, p3));
+      const int q = ld_in<kCg>(q_in + pt + reg_off(e, p0, p1, p2, p3));
       qmax = max(qmax, q);
       ieee |= (q == kQIeee);
     }
@@ -406,7 +414,7 @@ __device__ __forceinline__ void fixed_tile(const PassDesc& pd, const PassArgs& a
     qmax = kQValidMin; ieee = 0;
     for (int w = 0; w < nwarps; ++w) { qmax = max(qmax, red[w]); ieee |= red[16 + w]; }
     if (ieee) {
-      ieee_tile<kDec>(pd, args, matp, q_in, q_out, tile, base, pbase, nbase, smem, lane, warp);
+      ieee_tile<kDec, kCg>(pd, args, matp, q_in, q_out, tile, base, pbase, nbase, smem, lane, warp);
       return;
     }
     if (qmax == kQValidMin) {                              // every source tile was zero
@@ -416,7 +424,7 @@ __device__ __forceinline__ void fixed_tile(const PassDesc& pd, const PassArgs& a
     qin = qmax + pd.K;
 #pragma unroll
     for (int e = 0; e < kElems; ++e) {
-      const int q = __ldg(q_in + pt + reg_off(e, p0, p1, p2, p3));   // again, from L1
+      const int q = ld_in<kCg>(q_in + pt + reg_off(e, p0, p1, p2, p3));   // again, from L1 / L2
       if (q_is_valid(q)) {
         const unsigned sh = (unsigned)(qin - q);
         v[e].re = TPD_ALIGN(raw[e].x, sh);
@@ -489,31 +497,13 @@ __device__ __forceinline__ void fixed_tile(const PassDesc& pd, const PassArgs& a
   }
 }
 
-// Tiles of up to 2^12 elements run 256-thread CTAs, several per SM; 2^13
-// element tiles run 512-thread CTAs.
-// kMinBlocks: CTAs of kThreads the compiler must fit on one SM (register
-// budget); the planner picks 3 for the conversion-heavy first and last
-// fixed-point passes and 2 elsewhere.  kRole: fixed point only (see above).
-template <class A, bool kDec, int kThreads, int kMinBlocks, int kRole = 0>
-__global__ void __launch_bounds__(kThreads, kMinBlocks)
-    k_pass(const __grid_constant__ PassDesc pd, const __grid_constant__ PassArgs args) {
+// One tile of a pass: its position from the tile id, then the arithmetic's
+// load / levels / store.  smem: the exchange area (2^D x 16 bytes) followed by
+// 64 ints of reduction slots.
+template <class A, bool kDec, int kRole, bool kCg>
+__device__ __forceinline__ void pass_tile(const PassDesc& pd, const PassArgs& args, void* matp, const int* q_in,
+                                          int* q_out, long long tile, unsigned char* smem, int lane, int warp) {
   using Store = typename A::Store;
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  long long tile = (long long)blockIdx.x + (long long)blockIdx.y * gridDim.x;
-  void* matp = args.mat;
-  const int* q_in = args.q_in;
-  int* q_out = args.q_out;
-  if (args.ptrs != nullptr) {              // batched: tiles of matrix items[m] are contiguous in the grid
-    const long long m = tile / args.tiles_per_mat;
-    tile -= m * args.tiles_per_mat;
-    matp = args.ptrs[args.items[m]];
-    if (q_in) q_in += m * args.q_in_stride;
-    if (q_out) q_out += m * args.q_out_stride;
-  }
-  if (tile >= pd.ntiles) return;
-  if (args.flags_in != nullptr && args.flags_in[tile] == 0) return;
-
   long long base = 0, pbase = 0;
   int nbase = 0;
   for (int j = 0; j < pd.nrest; ++j)
@@ -524,11 +514,11 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
     }
 
   if constexpr (A::kFixed) {
-    fixed_tile<kDec, kRole>(pd, args, matp, q_in, q_out, tile, base, pbase, nbase, nullptr, smem,
-                            reinterpret_cast<int*>(smem + ((size_t)16 << pd.D)), lane, warp);
+    fixed_tile<kDec, kRole, kCg>(pd, args, matp, q_in, q_out, tile, base, pbase, nbase, nullptr, smem,
+                                 reinterpret_cast<int*>(smem + ((size_t)16 << pd.D)), lane, warp);
   } else {
     Store raw[kElems];
-    load_tile(pd, matp, base, lane, warp, raw);
+    load_tile<kCg>(pd, matp, base, lane, warp, raw);
     if (args.skip_zero) {
       int nz = 0;
 #pragma unroll
@@ -537,6 +527,34 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
     }
     finish_tile<A, kDec>(pd, args, matp, raw, args.out_mul, base, nbase, smem, lane, warp);
   }
+}
+
+// Tiles of up to 2^12 elements run 256-thread CTAs, several per SM; 2^13
+// element tiles run 512-thread CTAs.
+// kMinBlocks: CTAs of kThreads the compiler must fit on one SM (register
+// budget); the planner picks 3 for the conversion-heavy first and last
+// fixed-point passes and 2 elsewhere.  kRole: fixed point only (see above).
+template <class A, bool kDec, int kThreads, int kMinBlocks, int kRole = 0>
+__global__ void __launch_bounds__(kThreads, kMinBlocks)
+    k_pass(const __grid_constant__ PassDesc pd, const __grid_constant__ PassArgs args) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  long long tile = (long long)blockIdx.x + (long long)blockIdx.y * gridDim.x;
+  void* matp = args.mat;
+  const int* q_in = args.q_in;
+  int* q_out = args.q_out;
+  if (args.ptrs != nullptr) {              // batched: tiles of matrix items[m] are contiguous in the grid
+    const long long m = tile / args.tiles_per_mat;
+    tile -= m * args.tiles_per_mat;
+    const int idx = args.items[m];
+    if (idx < 0) return;                   // bucketing found ns_dev inconsistent: touch nothing
+    matp = args.ptrs[idx];
+    if (q_in) q_in += m * args.q_in_stride;
+    if (q_out) q_out += m * args.q_out_stride;
+  }
+  if (tile >= pd.ntiles) return;
+  if (args.flags_in != nullptr && args.flags_in[tile] == 0) return;
+  pass_tile<A, kDec, kRole, false>(pd, args, matp, q_in, q_out, tile, smem, lane, warp);
 }
 
 // -------------------------------------------------------------- persistent, double buffered
@@ -691,15 +709,12 @@ __device__ __forceinline__ void small_run(typename A::Store* mat, int n, int ski
   }
 }
 
+// A whole matrix of n <= 6 qubits by the CTA's nthr threads (all of them call
+// it): max exponent / nonzero test, then small_run (IEEE fallback for Inf/NaN).
 template <class A, bool kDec>
-__global__ void __launch_bounds__(256) k_small(const SmallArgs args) {
+__device__ __forceinline__ void small_matrix(typename A::Store* mat, int n, int skip_zero, int scale_mode,
+                                             unsigned char* smem, int tid, int nthr) {
   using Store = typename A::Store;
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  int idx = blockIdx.x;
-  if (args.items) idx = args.items[idx];
-  Store* mat = reinterpret_cast<Store*>(args.ptrs ? args.ptrs[idx] : args.mat);
-  const int n = args.ptrs ? args.ns[idx] : args.n;
   const int count = 1 << (2 * n);
   // max exponent / nonzero over the whole matrix
   uint32_t emax = 0, nzw = 0;
@@ -720,7 +735,7 @@ __global__ void __launch_bounds__(256) k_small(const SmallArgs args) {
     nzw |= hx | hy | lx | ly;
   }
   const int nz = __syncthreads_or((int)(nzw != 0));
-  if (args.skip_zero && !nz) return;
+  if (skip_zero && !nz) return;
   uint32_t* red = reinterpret_cast<uint32_t*>(smem);
   emax = __reduce_max_sync(kFull, emax);
   if ((tid & 31) == 0) red[tid >> 5] = emax;
@@ -730,11 +745,24 @@ __global__ void __launch_bounds__(256) k_small(const SmallArgs args) {
   __syncthreads();
   if constexpr (A::kFixed) {
     if (em == 2047) {
-      small_run<F64Arith, kDec>(mat, n, args.skip_zero, args.scale_mode, smem, tid, nthr, 0);
+      small_run<F64Arith, kDec>(mat, n, skip_zero, scale_mode, smem, tid, nthr, 0);
       return;
     }
   }
-  small_run<A, kDec>(mat, n, args.skip_zero, args.scale_mode, smem, tid, nthr, (int)em);
+  small_run<A, kDec>(mat, n, skip_zero, scale_mode, smem, tid, nthr, (int)em);
+}
+
+template <class A, bool kDec>
+__global__ void __launch_bounds__(256) k_small(const SmallArgs args) {
+  using Store = typename A::Store;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  int idx = blockIdx.x;
+  if (args.items) idx = args.items[idx];
+  if (idx < 0) return;                     // bucketing found ns_dev inconsistent: touch nothing
+  Store* mat = reinterpret_cast<Store*>(args.ptrs ? args.ptrs[idx] : args.mat);
+  const int n = args.ptrs ? args.ns[idx] : args.n;
+  small_matrix<A, kDec>(mat, n, args.skip_zero, args.scale_mode, smem, tid, nthr);
 }
 
 }  // namespace tpd

@@ -79,6 +79,13 @@ def test_argument_errors_return_before_any_launch(L):
     assert L.tpd_decompose_batched(4096, 4096, [3, 4], L.TPD_C128, None, 0, 0) == L.TPD_ERR_WORKSPACE
     assert L.tpd_decompose_batched(4096, 4096, [3, 4], L.TPD_C128, L.options(skip_zero=True), 4096,
                                    1 << 20) == L.TPD_ERR_UNSUPPORTED
+    assert L.tpd_batch_status(0) == L.TPD_ERR_INVALID_ARG
+    # workspace: control words (status, work counter, one completion counter per
+    # matrix and pass but the last) + bucket list + binary points
+    base = L.tpd_batched_workspace_size([3, 5], L.TPD_C128)
+    assert base % 256 == 0 and base >= 256 + 256
+    two_pass = L.tpd_batched_workspace_size([10] * 100, L.TPD_C128)
+    assert two_pass >= 4 * (4 + 100) + 4 * 100 + 4 * 100 * 256
 
 
 # ------------------------------------------------------------------ plan emulation
