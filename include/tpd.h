@@ -82,10 +82,11 @@ typedef struct {
                        fixed point, single matrix, no zero skipping),
                        3 / 4 = one CTA per tile compiled for 2 / 3 CTAs per SM
                        (tiles of up to 2^12 elements).
-                       Batched calls: 0 or 2 = the whole batch in one persistent
-                       kernel launch when every matrix has n <= 6 or a plan of
-                       2^12-element tiles (else as 1); 1, 3, 4 = one launch per
-                       (qubit count, pass) */
+                       Batched calls: 0, 1, 3, 4 = one launch per (qubit count,
+                       pass) over all matrices of that qubit count (the fastest
+                       form measured on GB300); 2 = the whole batch in ONE
+                       persistent kernel launch when every matrix has n <= 6 or
+                       a plan of 2^12-element tiles (else as 0) */
   void** pass_events; /* profiling, may be NULL: num_events cudaEvent_t handles
                        (created by the caller); tpd_decompose / tpd_compose
                        record event 0 before the first pass and event p+1 after
@@ -168,12 +169,14 @@ size_t tpd_batched_workspace_size(const int* ns, int count, int dtype, const tpd
  *              first bytes hold the status word read by tpd_batch_status.
  * The matrices must not overlap.  The enqueued work (a memset of the control
  * words and the kernel launches) depends only on the arguments (no host
- * synchronisation), so it can be captured in a CUDA graph.  By default the
- * whole batch runs in ONE persistent kernel launch (see tpd_options.variant):
- * CTAs claim tiles in order, and a tile of a later pass waits, with a bound,
- * for the tiles of its own matrix's previous pass; a wait that gives up, or
- * ns_dev disagreeing with ns, is reported by tpd_batch_status (the results
- * are then invalid).  No device-side wait is unbounded. */
+ * synchronisation), so it can be captured in a CUDA graph.  By default one
+ * kernel launch per (qubit count, pass) covers all matrices of that qubit
+ * count; with tpd_options.variant = 2 the whole batch runs in ONE persistent
+ * kernel launch: CTAs claim tiles in order, and a tile of a later pass waits,
+ * with a bound, for the tiles of its own matrix's previous pass.  A wait that
+ * gives up, or ns_dev disagreeing with ns, is reported by tpd_batch_status
+ * (the results are then invalid; with ns_dev inconsistent nothing is
+ * touched).  No device-side wait is unbounded. */
 tpd_status tpd_decompose_batched(void* const* ptrs_dev, const int* ns_dev, const int* ns,
                                  int count, int dtype, const tpd_options* opt,
                                  void* workspace, size_t workspace_bytes, void* stream);
@@ -184,6 +187,59 @@ tpd_status tpd_compose_batched(void* const* ptrs_dev, const int* ns_dev, const i
                                int count, int dtype, int scale_mode, const tpd_options* opt,
                                void* workspace, size_t workspace_bytes, void* stream);
 
+/* Partial decomposition (Alg. 3, Sec. III): only the weights of a given list
+ * of strings -- the paper's quaternary subtree T of the strings of interest.
+ * Two steps, because the first is host work:
+ *
+ * tpd_partial_prepare  computes, on the host, which tiles of which pass the
+ *   requested weights depend on and uploads that, with the strings' RC
+ *   positions, into `workspace` (device, tpd_partial_workspace_size() bytes).
+ *   strings: host array of `count` base-4 string indices
+ *   s = sum_j t_j 4^(n-j) (t_1 most significant, I=0 X=1 Y=2 Z=3), each
+ *   < 4^n; duplicates allowed.  Synchronises `stream` (the host arrays are
+ *   temporary), so call it outside stream capture.
+ * tpd_decompose_partial  runs the passes on A in place, each skipping the
+ *   tiles no requested weight depends on, and gathers the requested weights,
+ *   in request order, into `weights` (device, count elements of `dtype`).
+ *   Afterwards A holds the requested weights at their RC positions; its other
+ *   elements are unspecified.  The same (n, dtype, opt, count) as the prepare
+ *   call, and the workspace it filled; the call enqueues only, so it can be
+ *   captured in a CUDA graph and repeated.
+ * The requested weights are bit-identical to those of tpd_decompose with the
+ * same options (the needed tiles are computed the same way).  The first pass
+ * reads every element (dense input); later passes shrink with the subtree.
+ * opt->skip_zero is not supported (TPD_ERR_UNSUPPORTED).
+ * Errors: as tpd_decompose; INVALID_ARG also for a string index >= 4^n. */
+size_t tpd_partial_workspace_size(int n, int dtype, const tpd_options* opt, size_t count);
+tpd_status tpd_partial_prepare(int n, int dtype, const tpd_options* opt, const unsigned long long* strings,
+                               size_t count, void* workspace, size_t workspace_bytes, void* stream);
+tpd_status tpd_decompose_partial(void* A, int n, int dtype, const tpd_options* opt, size_t count, void* workspace,
+                                 size_t workspace_bytes, void* weights, void* stream);
+
+/* Layout conversion, out of place.  RC is the layout every decomposition
+ * leaves (see the conventions above); STRING puts the weight of
+ * t = (t_1, ..., t_n) at the base-4 index s = sum_j t_j 4^(n-j) (t_1 most
+ * significant; the labelling of Sec. II, Eq. 2), so bit 2b+1 of s is row bit
+ * r_b and bit 2b is column bit c_b.
+ *   src, dst   device, N*N elements of `dtype` each, aligned as for
+ *              tpd_decompose; they must not overlap.
+ *   to_string  1: RC -> STRING, 0: STRING -> RC.
+ * Errors: INVALID_ARG (n outside 1..16, null, overlap), MISALIGNED, CUDA. */
+tpd_status tpd_convert_layout(const void* src, void* dst, int n, int dtype, int to_string, void* stream);
+
+/* Sum of squared magnitudes: *result = sum_i |x_i|^2 over `count` complex
+ * elements of `dtype`, accumulated in fp64 in a fixed order (the same bits on
+ * every call).  With w the weights of A, Parseval's identity for the
+ * orthogonal Pauli basis (tr(sigma^s sigma^t) = 2^n delta_st, Sec. II) gives
+ * ||A||_F^2 = 2^n sum_t |w_t|^2: the pair of sums checks a decomposition.
+ *   x          device, count elements.  count >= 0 (0 gives 0).
+ *   result     device, one double.
+ *   workspace  device, TPD_SUMSQ_WORKSPACE_BYTES bytes.
+ * Errors: INVALID_ARG, MISALIGNED, WORKSPACE, CUDA. */
+#define TPD_SUMSQ_WORKSPACE_BYTES ((size_t)8192)
+tpd_status tpd_sum_squares(const void* x, size_t count, int dtype, double* result, void* workspace,
+                           size_t workspace_bytes, void* stream);
+
 /* Status of the last batched call that used `workspace` (device): TPD_OK,
  * TPD_ERR_TIMEOUT (a bounded device-side wait gave up), TPD_ERR_INVALID_ARG
  * (ns_dev disagreed with ns), or TPD_ERR_CUDA if the status cannot be read.
@@ -192,7 +248,7 @@ tpd_status tpd_compose_batched(void* const* ptrs_dev, const int* ns_dev, const i
 tpd_status tpd_batch_status(const void* workspace, void* stream);
 
 /* Test hook, host only: while `on` is nonzero, batched calls that take the
- * persistent form make every tile of a pass after the first wait for one more
+ * persistent form (variant 2) make every tile of a pass after the first wait for one more
  * completed tile of the previous pass than there are, so each such wait runs
  * into its bound and tpd_batch_status reports TPD_ERR_TIMEOUT.  It exercises
  * the timeout path without any fault; the results of such calls are invalid. */

@@ -7,12 +7,15 @@ The CUDA library ``libtpd.so`` is loaded lazily on first use (the submodule
     compose(C, scale=...)      scale * sum_t w_t sigma^t (the adjoint for scale 2^-n)
     decompose_batched(mats)    many matrices of different sizes in one call
     Batch                      reusable device batch descriptor (CUDA-graph friendly)
+    Partial                    partial decomposition: weights of a list of strings only (Alg. 3)
     TPDFunction / tpd          autograd
-    string_order(n)            RC layout -> string order permutation
+    to_string_layout(W)        RC -> base-4 string order (device kernel); from_string_layout inverse
+    sum_squares(X)             fp64 sum of |x|^2 on the device (Parseval check)
+    string_order(n)            RC layout -> string order permutation (host index array)
     build()                    compile libtpd.so in-tree
 """
-__all__ = ["decompose", "compose", "decompose_batched", "compose_batched", "Batch", "TPDFunction", "tpd",
-           "string_order", "workspace_size", "build"]
+__all__ = ["decompose", "compose", "decompose_batched", "compose_batched", "Batch", "Partial", "TPDFunction", "tpd",
+           "string_order", "to_string_layout", "from_string_layout", "sum_squares", "workspace_size", "build"]
 
 
 def build(force=False, verbose=False):
@@ -21,8 +24,8 @@ def build(force=False, verbose=False):
 
 
 def __getattr__(name):
-    if name in ("decompose", "compose", "decompose_batched", "compose_batched", "Batch", "string_order",
-                "workspace_size", "make_options"):
+    if name in ("decompose", "compose", "decompose_batched", "compose_batched", "Batch", "Partial", "string_order",
+                "to_string_layout", "from_string_layout", "sum_squares", "workspace_size", "make_options"):
         from . import api
         return getattr(api, name)
     if name in ("TPDFunction", "tpd"):

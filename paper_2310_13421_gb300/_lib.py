@@ -29,10 +29,14 @@ SYMBOLS = (
     "tpd_batched_workspace_size", "tpd_decompose_batched", "tpd_compose_batched",
     "tpd_plan_describe", "tpd_status_string", "tpd_version", "tpd_decompose_noalloc",
     "tpd_tune_set", "tpd_tune_clear", "tpd_batch_status", "tpd_test_hold_batch_waits",
+    "tpd_convert_layout", "tpd_sum_squares", "tpd_partial_workspace_size", "tpd_partial_prepare",
+    "tpd_decompose_partial",
 )
 
 # size of the library's own scratch array used by tpd_decompose_noalloc
 TPD_NOALLOC_SCRATCH_BYTES = 8 << 20
+# device workspace of tpd_sum_squares
+TPD_SUMSQ_WORKSPACE_BYTES = 8192
 
 
 class tpd_options(ctypes.Structure):
@@ -77,6 +81,16 @@ def load(path=None):
         lib.tpd_tune_set.restype = i
         lib.tpd_tune_clear.argtypes = []
         lib.tpd_tune_clear.restype = None
+        lib.tpd_partial_workspace_size.argtypes = [i, i, op, sz]
+        lib.tpd_partial_workspace_size.restype = sz
+        lib.tpd_partial_prepare.argtypes = [i, i, op, ctypes.POINTER(ctypes.c_ulonglong), sz, vp, sz, vp]
+        lib.tpd_partial_prepare.restype = i
+        lib.tpd_decompose_partial.argtypes = [vp, i, i, op, sz, vp, sz, vp, vp]
+        lib.tpd_decompose_partial.restype = i
+        lib.tpd_convert_layout.argtypes = [vp, vp, i, i, i, vp]
+        lib.tpd_convert_layout.restype = i
+        lib.tpd_sum_squares.argtypes = [vp, sz, i, vp, vp, sz, vp]
+        lib.tpd_sum_squares.restype = i
         lib.tpd_batch_status.argtypes = [vp, vp]
         lib.tpd_batch_status.restype = i
         lib.tpd_test_hold_batch_waits.argtypes = [i]
@@ -140,6 +154,31 @@ def tpd_tune_set(n, dtype, precision, tuned=None):
 
 def tpd_tune_clear():
     load().tpd_tune_clear()
+
+
+def tpd_partial_workspace_size(n, dtype, opt, count):
+    return int(load().tpd_partial_workspace_size(n, dtype, _opt(opt), count))
+
+
+def tpd_partial_prepare(n, dtype, opt, strings, workspace, workspace_bytes, stream=0):
+    """strings: sequence of base-4 string indices (t_1 most significant)."""
+    arr = (ctypes.c_ulonglong * max(len(strings), 1))(*[int(x) for x in strings])
+    return int(load().tpd_partial_prepare(n, dtype, _opt(opt), arr, len(strings), workspace or None,
+                                          workspace_bytes, stream or None))
+
+
+def tpd_decompose_partial(A_ptr, n, dtype, opt, count, workspace, workspace_bytes, weights, stream=0):
+    return int(load().tpd_decompose_partial(A_ptr or None, n, dtype, _opt(opt), count, workspace or None,
+                                            workspace_bytes, weights or None, stream or None))
+
+
+def tpd_convert_layout(src, dst, n, dtype, to_string, stream=0):
+    return int(load().tpd_convert_layout(src or None, dst or None, n, dtype, int(to_string), stream or None))
+
+
+def tpd_sum_squares(x, count, dtype, result, workspace, workspace_bytes, stream=0):
+    return int(load().tpd_sum_squares(x or None, count, dtype, result or None, workspace or None, workspace_bytes,
+                                      stream or None))
 
 
 def tpd_batch_status(workspace, stream=0):

@@ -5,7 +5,7 @@ no other code path.
 Layout reminder: results are IN the input's storage order ("RC layout"): the
 weight of string t sits at row r, column c with, for every qubit j, the row
 and column bits n-j equal to (t_j >> 1, t_j & 1) -- I (0,0), X (0,1), Y (1,0),
-Z (1,1).  ``string_order`` converts to base-4 string order.
+Z (1,1).  ``to_string_layout`` converts to base-4 string order on the device.
 """
 import numpy as np
 import torch
@@ -149,7 +149,8 @@ class Batch:
 
 def decompose_batched(mats, *, inplace=False, precision=None, variant=0, stream=None):
     """Decompose a list of CUDA matrices of (possibly different) sizes; one
-    call enqueues the whole batch (by default one persistent kernel launch)."""
+    call enqueues the whole batch (one launch per qubit count and pass; with
+    variant=2 a single persistent kernel launch)."""
     work = list(mats) if inplace else [m.clone() for m in mats]
     Batch(work, precision=precision, variant=variant).decompose(stream)
     return work
@@ -159,6 +160,86 @@ def compose_batched(mats, *, adjoint=False, inplace=False, precision=None, varia
     work = list(mats) if inplace else [m.clone() for m in mats]
     Batch(work, precision=precision, variant=variant).compose(adjoint=adjoint, stream=stream)
     return work
+
+
+class Partial:
+    """Partial decomposition (Alg. 3): the weights of a fixed list of strings
+    (base-4 indices, t_1 most significant) for matrices of one size and dtype.
+    The host-side preparation runs once; ``decompose`` can then be called (and
+    captured in a CUDA graph) repeatedly."""
+
+    def __init__(self, n, strings, dtype=torch.complex128, device="cuda", precision=None, tile_bits=0,
+                 max_levels=0):
+        self.n = int(n)
+        self.code = L.TPD_C128 if dtype == torch.complex128 else L.TPD_C64
+        self.dtype = dtype
+        self.count = len(strings)
+        self.opt = make_options(precision, False, tile_bits, max_levels)
+        wsb = L.tpd_partial_workspace_size(self.n, self.code, self.opt, self.count)
+        if wsb == 0:
+            raise ValueError("invalid partial decomposition arguments")
+        self.ws = torch.empty(wsb, dtype=torch.uint8, device=device)
+        self.device = self.ws.device
+        with torch.cuda.device(self.device):
+            st = L.tpd_partial_prepare(self.n, self.code, self.opt, list(strings), self.ws.data_ptr(), wsb,
+                                       _stream(None))
+        _raise(st, "tpd_partial_prepare")
+
+    def decompose(self, A, *, inplace=False, out=None, stream=None):
+        """Requested weights (a 1-D tensor in request order); A is consumed
+        when inplace (its other elements are then unspecified)."""
+        _check_device(A)
+        if _qubits(A) != self.n or _dtype_code(A) != self.code:
+            raise ValueError("matrix does not match the prepared size / dtype")
+        work = A if inplace else A.clone()
+        if out is None:
+            out = torch.empty(self.count, dtype=self.dtype, device=A.device)
+        with torch.cuda.device(A.device):
+            st = L.tpd_decompose_partial(work.data_ptr(), self.n, self.code, self.opt, self.count, self.ws.data_ptr(),
+                                         self.ws.numel(), out.data_ptr(), _stream(stream))
+        _raise(st, "tpd_decompose_partial")
+        return out
+
+
+def to_string_layout(W, *, stream=None):
+    """Weights in STRING layout (base-4 string index, t_1 most significant) as
+    a flat tensor, converted from the RC layout on the device."""
+    _check_device(W)
+    n = _qubits(W)
+    out = torch.empty(W.numel(), dtype=W.dtype, device=W.device)
+    with torch.cuda.device(W.device):
+        st = L.tpd_convert_layout(W.data_ptr(), out.data_ptr(), n, _dtype_code(W), 1, _stream(stream))
+    _raise(st, "tpd_convert_layout")
+    return out
+
+
+def from_string_layout(S, *, stream=None):
+    """Inverse of to_string_layout: a flat STRING-layout tensor of 4^n weights
+    back to the N x N RC layout."""
+    if not S.is_cuda or not S.is_contiguous():
+        raise ValueError("tensor must be a contiguous CUDA tensor")
+    m = S.numel()
+    n = (m.bit_length() - 1) // 2
+    if m < 4 or 4 ** n != m:
+        raise ValueError("expected 4^n elements, got %d" % m)
+    out = torch.empty((2 ** n, 2 ** n), dtype=S.dtype, device=S.device)
+    with torch.cuda.device(S.device):
+        st = L.tpd_convert_layout(S.data_ptr(), out.data_ptr(), n, _dtype_code(S), 0, _stream(stream))
+    _raise(st, "tpd_convert_layout")
+    return out
+
+
+def sum_squares(X, *, stream=None):
+    """sum |x|^2 over a complex CUDA tensor, in fp64 on the device (a 0-dim
+    float64 CUDA tensor; deterministic)."""
+    _check_device(X)
+    out = torch.empty((), dtype=torch.float64, device=X.device)
+    ws = torch.empty(L.TPD_SUMSQ_WORKSPACE_BYTES, dtype=torch.uint8, device=X.device)
+    with torch.cuda.device(X.device):
+        st = L.tpd_sum_squares(X.data_ptr(), X.numel(), _dtype_code(X), out.data_ptr(), ws.data_ptr(), ws.numel(),
+                               _stream(stream))
+    _raise(st, "tpd_sum_squares")
+    return out
 
 
 def string_order(n):

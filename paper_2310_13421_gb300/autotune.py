@@ -33,19 +33,19 @@ def _gpu_key():
 
 def candidates(n, dtype, precision, batched=False):
     """Distinct valid tunings for the key (same plan text and variant = same
-    candidate).  For batches, variant 1 (one launch per qubit count and pass)
-    competes with the default single persistent launch."""
+    candidate).  For batches, variant 2 (one persistent launch for the whole
+    batch) competes with the default launch per qubit count and pass."""
     code = _DT[dtype][0]
     prec = _PREC[precision] if isinstance(precision, str) else precision
     seen, out = set(), []
-    variants = (0, 1, 3, 4) if batched else (0, 2, 3, 4)
+    variants = (0, 2, 3, 4)
     for tb, ml, var in itertools.product((0, 11, 12, 13), (0, 3, 4, 5, 6), variants):
         opt = L.options(precision=prec, tile_bits=tb, max_levels=ml, variant=var)
         npass, desc = L.tpd_plan_describe(n, code, opt)
         if npass < 0:
             continue
-        if var == 2 and (code != L.TPD_C128 or npass == 0):
-            continue          # the persistent form exists for the complex128 fixed point
+        if var == 2 and not batched and (code != L.TPD_C128 or npass == 0):
+            continue          # single matrices: the persistent form exists for the complex128 fixed point
         key = (desc, var)
         if key in seen:
             continue

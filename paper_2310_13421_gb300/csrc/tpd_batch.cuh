@@ -3,12 +3,13 @@
 // Sec. III's algorithm: every matrix independently, Eqs. 3-5).
 //
 // CTAs claim work items in order from a device counter (the work list is
-// described in tpd_launch.h: bucketing, then per segment the tiles of one pass
-// of all matrices of one qubit count, or whole small matrices).  A tile of
-// pass p > 0 of matrix m reads what the tiles of pass p-1 of m wrote, so it
-// waits until m's per-matrix completion counter of pass p-1 is full.  All
-// those tiles were claimed earlier by CTAs that are running and never wait on
-// later items, so the wait ends; it is nonetheless bounded: after
+// described in tpd_launch.h: bucketing, then per qubit count the passes of
+// its matrices software-pipelined so that a matrix's later passes find its
+// data in L2, or whole small matrices).  A tile of pass p > 0 of matrix m
+// reads what the tiles of pass p-1 of m wrote, so it waits until m's
+// completion counter of pass p-1 is full.  All those tiles were claimed
+// earlier (p-1 runs `lag` rounds ahead) by CTAs that are running and never
+// wait on later items, so the wait ends; it is nonetheless bounded: after
 // kSpinLimit polls the CTA records TPD_ERR_TIMEOUT in the status word and
 // skips the item, and every later item is skipped as soon as the status word
 // is set, so the launch always finishes and the context stays usable.
@@ -90,27 +91,28 @@ static __device__ __noinline__ void bucket_item(const BatchParams& bp, int tid, 
 }
 
 template <class A, bool kDec>
-__device__ __forceinline__ void batch_pass_tile(const BatchSeg& sg, const PassDesc& pd, void* matp,
+__device__ __forceinline__ void batch_pass_tile(const BatchSeg& sg, int p, const PassDesc& pd, void* matp,
                                                 long long j, long long tile, unsigned char* smem, int lane,
                                                 int warp) {
-  const int* q_in = sg.args.q_in ? sg.args.q_in + j * sg.args.q_in_stride : nullptr;
-  int* q_out = sg.args.q_out ? sg.args.q_out + j * sg.args.q_out_stride : nullptr;
+  const PassArgs& args = sg.args[p];
+  const int* q_in = args.q_in ? args.q_in + j * args.q_in_stride : nullptr;
+  int* q_out = args.q_out ? args.q_out + j * args.q_out_stride : nullptr;
   if constexpr (A::kFixed) {
-    switch (sg.role) {
-      case 0: pass_tile<A, kDec, 0, true>(pd, sg.args, matp, q_in, q_out, tile, smem, lane, warp); break;
+    const int role = (p > 0 ? kRoleIntIn : 0) | (p + 1 < sg.npass ? kRoleIntOut : 0);
+    switch (role) {
+      case 0: pass_tile<A, kDec, 0, true>(pd, args, matp, q_in, q_out, tile, smem, lane, warp); break;
       case kRoleIntIn:
-        pass_tile<A, kDec, kRoleIntIn, true>(pd, sg.args, matp, q_in, q_out, tile, smem, lane, warp);
+        pass_tile<A, kDec, kRoleIntIn, true>(pd, args, matp, q_in, q_out, tile, smem, lane, warp);
         break;
       case kRoleIntOut:
-        pass_tile<A, kDec, kRoleIntOut, true>(pd, sg.args, matp, q_in, q_out, tile, smem, lane, warp);
+        pass_tile<A, kDec, kRoleIntOut, true>(pd, args, matp, q_in, q_out, tile, smem, lane, warp);
         break;
       default:
-        pass_tile<A, kDec, kRoleIntIn | kRoleIntOut, true>(pd, sg.args, matp, q_in, q_out, tile, smem, lane,
-                                                           warp);
+        pass_tile<A, kDec, kRoleIntIn | kRoleIntOut, true>(pd, args, matp, q_in, q_out, tile, smem, lane, warp);
         break;
     }
   } else {
-    pass_tile<A, kDec, 0, true>(pd, sg.args, matp, q_in, q_out, tile, smem, lane, warp);
+    pass_tile<A, kDec, 0, true>(pd, args, matp, q_in, q_out, tile, smem, lane, warp);
   }
 }
 
@@ -125,7 +127,6 @@ __global__ void __launch_bounds__(256, 2) k_batch(const __grid_constant__ BatchP
   __shared__ void* s_mat;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   unsigned* status = bp.ctrl + kCtrlStatus;
-  unsigned* done = bp.ctrl + kCtrlDone;
   bool seen_bucket = false;
   for (;;) {
     if (tid == 0) s_work = atomicAdd(bp.ctrl + kCtrlWork, 1u);
@@ -141,11 +142,25 @@ __global__ void __launch_bounds__(256, 2) k_batch(const __grid_constant__ BatchP
     while (si + 1 < bp.nseg && w >= bp.seg[si + 1].first) ++si;
     const BatchSeg& sg = bp.seg[si];
     const long long rel = w - sg.first;
-    const long long j = rel / sg.tiles;       // matrix within the segment
-    const long long tile = rel - j * sg.tiles;
+    long long j = rel, tile = 0;              // small matrices: one item each
+    int p = 0;
+    if (sg.kind == kSegPipe) {
+      const long long per_round = (long long)sg.npass * sg.tiles;
+      const long long round = rel / per_round;
+      const long long sub = rel - round * per_round;
+      p = (int)(sub / sg.tiles);
+      tile = sub - p * sg.tiles;
+      j = round - (long long)p * sg.lag;
+      if (j < 0 || j >= sg.nmat) {            // empty slot of the pipeline's ramp
+        __syncthreads();                      // everyone has read s_work
+        continue;
+      }
+    }
+    unsigned* done = bp.ctrl + kCtrlDone + sg.done;
     if (tid == 0) {
       bool ok = seen_bucket || wait_count(bp.ctrl + kCtrlBucket, 1u, status);
-      if (ok && sg.wait_ctr >= 0) ok = wait_count(done + sg.wait_ctr + j, (unsigned)sg.wait_need, status);
+      if (ok && p > 0)
+        ok = wait_count(done + (long long)(p - 1) * sg.nmat + j, (unsigned)(sg.tiles + sg.wait_extra), status);
       ok = ok && ld_volatile(status) == 0;
       if (ok) {
         const int m = __ldcg(bp.items + sg.item_start + j);
@@ -160,13 +175,13 @@ __global__ void __launch_bounds__(256, 2) k_batch(const __grid_constant__ BatchP
       if (sg.kind == kSegSmall) {
         small_matrix<A, kDec>(reinterpret_cast<Store*>(matp), sg.n, 0, bp.scale_mode, smem, tid, blockDim.x);
       } else {
-        batch_pass_tile<A, kDec>(sg, bp.desc[sg.desc], matp, j, tile, smem, lane, warp);
+        batch_pass_tile<A, kDec>(sg, p, bp.desc[sg.desc + p], matp, j, tile, smem, lane, warp);
       }
     }
     __syncthreads();                          // the tile's stores are done (and smem is free)
-    if (tid == 0 && sg.post_ctr >= 0) {
+    if (tid == 0 && sg.kind == kSegPipe && p + 1 < sg.npass) {
       __threadfence();
-      atomicAdd(done + sg.post_ctr + j, 1u);
+      atomicAdd(done + (long long)p * sg.nmat + j, 1u);
     }
   }
 }

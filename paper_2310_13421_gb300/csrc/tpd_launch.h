@@ -19,6 +19,8 @@ struct PassArgs {
   long long tiles_per_mat;
   void* mat;                  // matrix base (A::Store*), device
   const uint8_t* flags_in;    // per tile of this pass: 0 = all zero, skip; nullptr = no skipping
+  const uint8_t* need;        // per tile of this pass: 0 = feeds no requested weight (partial
+                              // decomposition), skip; nullptr = every tile
   uint8_t* flags_out;         // per tile of the next pass: set to 1 when it gets a nonzero; nullptr = none
   int skip_zero;              // test loaded tiles for all-zero and leave them untouched
   int out_pow2;               // fixed point: output multiplied by 2^out_pow2 (exact)
@@ -61,30 +63,37 @@ struct SmallArgs {
 //
 // The persistent batched kernel walks one global list of work items, claimed
 // in order from a device counter: item 0 buckets the matrices by qubit count;
-// then, per *segment*, the tiles of one pass over every matrix of one qubit
-// count (tile-major within a matrix), or whole small matrices (n <= 6, one
-// item each).  Segments are ordered so that every pass comes after the pass
-// it depends on; a tile of pass p > 0 waits (bounded) until all tiles of pass
-// p-1 of ITS matrix are done, counted per matrix in `done`.
+// then one *segment* per qubit count n.  For n >= 7 a segment holds every
+// pass of every matrix of that n, software-pipelined: round r = (pass 0 of
+// matrix r, pass 1 of matrix r - lag, pass 2 of matrix r - 2 lag, ...), each
+// pass as `tiles` items (tile-major), out-of-range (pass, matrix) slots empty.
+// A matrix's later passes thus run `lag` rounds after its earlier ones, while
+// its data (16 * 4^n bytes) is still in L2, so for matrices up to a few MB a
+// pass after the first reads, and the passes overwrite, lines that have not
+// gone back to HBM.  A tile of pass p > 0 waits (bounded) until all tiles of
+// pass p-1 of ITS matrix are done, counted per (pass, matrix) in `done`.  For
+// n <= 6 a segment holds one item per whole matrix.
 constexpr int kBatchMaxDescs = 16;
-constexpr int kBatchMaxSegs = 32;
+constexpr int kBatchMaxSegs = 12;
 constexpr int kBatchMaxN = 12;
+constexpr int kSegMaxPasses = 3;
 constexpr int kSegSmall = 0;
-constexpr int kSegPass = 1;
+constexpr int kSegPipe = 1;
 
 struct BatchSeg {
-  PassArgs args;              // per-pass arguments (q arrays: pass-level bases, per matrix + j * stride)
-  int32_t kind;               // kSegSmall / kSegPass
+  PassArgs args[kSegMaxPasses];  // per pass (q arrays: pass-level bases, matrix j at + j * stride)
+  int32_t kind;               // kSegSmall / kSegPipe
   int32_t n;                  // qubits of the segment's matrices
-  int32_t desc;               // kSegPass: index into BatchParams::desc
-  int32_t role;               // fixed point: kRoleIntIn / kRoleIntOut bits of the pass
+  int32_t npass;              // kSegPipe: passes per matrix (1..kSegMaxPasses)
+  int32_t desc;               // kSegPipe: pass p uses BatchParams::desc[desc + p]
   int32_t item_start;         // first bucket position of the segment's matrices
   int32_t nmat;               // matrices in the segment
-  int32_t wait_ctr;           // done-counter base of the pass this one depends on (-1: none)
-  int32_t post_ctr;           // done-counter base this pass increments (-1: none)
+  int32_t lag;                // kSegPipe: rounds between consecutive passes of a matrix
+  int32_t done;               // kSegPipe: counter of (pass p, matrix j) at ctrl[kCtrlDone + done + p * nmat + j]
+  int32_t wait_extra;         // test hook: added to every wait's target
+  int32_t pad;
   int64_t first;              // first work index of the segment
-  int64_t tiles;              // tiles per matrix (1 for kSegSmall)
-  int64_t wait_need;          // tiles per matrix of the pass waited for
+  int64_t tiles;              // tiles per pass (1 for kSegSmall)
 };
 
 struct BatchParams {
@@ -113,6 +122,17 @@ constexpr int kCtrlDone = 4;
 
 // Persistent batched kernel for an arithmetic: `grid` CTAs of 256 threads.
 cudaError_t launch_batch(int arith, bool dec, const BatchParams& bp, int* grid_out, cudaStream_t s);
+
+// out[i] = mat[pos[i]] for i < count (elements of elem_bytes).
+cudaError_t launch_gather(const void* mat, const unsigned long long* pos, unsigned long long count, int elem_bytes,
+                          void* out, cudaStream_t s);
+
+// Layout conversion RC <-> STRING (out of place) and the fp64 sum of squared
+// magnitudes (deterministic; workspace of sumsq_workspace_bytes()).
+cudaError_t launch_layout(const void* src, void* dst, int n, int elem_bytes, int to_string, cudaStream_t s);
+size_t sumsq_workspace_bytes();
+cudaError_t launch_sumsq(const void* x, unsigned long long count, int elem_bytes, double* out, void* ws,
+                         cudaStream_t s);
 
 // Bytes per element in registers / shared memory for an arithmetic.
 inline int arith_vbytes(int arith) { return arith == kArithF32 ? 8 : 16; }

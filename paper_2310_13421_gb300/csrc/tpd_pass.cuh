@@ -554,6 +554,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
   }
   if (tile >= pd.ntiles) return;
   if (args.flags_in != nullptr && args.flags_in[tile] == 0) return;
+  if (args.need != nullptr && args.need[tile] == 0) return;
   pass_tile<A, kDec, kRole, false>(pd, args, matp, q_in, q_out, tile, smem, lane, warp);
 }
 

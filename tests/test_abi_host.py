@@ -80,6 +80,21 @@ def test_argument_errors_return_before_any_launch(L):
     assert L.tpd_decompose_batched(4096, 4096, [3, 4], L.TPD_C128, L.options(skip_zero=True), 4096,
                                    1 << 20) == L.TPD_ERR_UNSUPPORTED
     assert L.tpd_batch_status(0) == L.TPD_ERR_INVALID_ARG
+    # partial decomposition
+    assert L.tpd_partial_workspace_size(10, L.TPD_C128, None, 5) >= 5 * 8 + 2 * 256
+    assert L.tpd_partial_workspace_size(10, L.TPD_C128, L.options(skip_zero=True), 5) == 0
+    assert L.tpd_partial_prepare(4, L.TPD_C128, None, [1, 2], 0, 0) == L.TPD_ERR_WORKSPACE
+    assert L.tpd_partial_prepare(4, L.TPD_C128, None, [256], 4096, 1 << 20) == L.TPD_ERR_INVALID_ARG  # >= 4^n
+    assert L.tpd_decompose_partial(0, 4, L.TPD_C128, None, 2, 4096, 1 << 20, 8192) == L.TPD_ERR_INVALID_ARG
+    assert L.tpd_decompose_partial(4096, 4, L.TPD_C128, None, 2, 4096, 1 << 20, 8200) == L.TPD_ERR_MISALIGNED
+    # layout conversion and sums of squares
+    assert L.tpd_convert_layout(4096, 1 << 20, 0, L.TPD_C128, 1) == L.TPD_ERR_INVALID_ARG      # n = 0
+    assert L.tpd_convert_layout(4096, 4096 + 256, 4, L.TPD_C128, 1) == L.TPD_ERR_INVALID_ARG   # overlap
+    assert L.tpd_convert_layout(4104, 1 << 20, 4, L.TPD_C128, 1) == L.TPD_ERR_MISALIGNED
+    assert L.tpd_convert_layout(4096, 1 << 20, 4, L.TPD_C128, 2) == L.TPD_ERR_INVALID_ARG
+    assert L.tpd_sum_squares(4096, 10, L.TPD_C128, 8192, 0, 0) == L.TPD_ERR_WORKSPACE
+    assert L.tpd_sum_squares(4096, 10, L.TPD_C128, 0, 1 << 20, 8192) == L.TPD_ERR_INVALID_ARG
+    assert L.tpd_sum_squares(4104, 10, L.TPD_C128, 8192, 1 << 20, 8192) == L.TPD_ERR_MISALIGNED
     # workspace: control words (status, work counter, one completion counter per
     # matrix and pass but the last) + bucket list + binary points
     base = L.tpd_batched_workspace_size([3, 5], L.TPD_C128)

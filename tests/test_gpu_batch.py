@@ -1,5 +1,5 @@
-"""GPU: the batched calls in their two forms -- one persistent kernel launch
-(default) and one launch per (qubit count, pass) -- against the CPU oracle and
+"""GPU: the batched calls in their two forms -- one launch per (qubit count,
+pass) (default) and one persistent kernel launch (variant 2) -- against the CPU oracle and
 against each other, CUDA-graph replay of the persistent form, and its status
 word: a bounded wait that runs out (test hook) and device qubit counts that
 disagree with the host's, both reported without a fault."""
@@ -49,8 +49,8 @@ def mixed_sizes(seed, count=40, lo=1, hi=10):
 def test_persistent_matches_oracle_and_per_pass_form(tpd, precision):
     ns = mixed_sizes(9500)
     mats = [synth.general(n, seed=9500 + i) for i, n in enumerate(ns)]
-    one = tpd.decompose_batched([gpu(m) for m in mats], precision=precision)            # one launch
-    per = tpd.decompose_batched([gpu(m) for m in mats], precision=precision, variant=1)  # per (n, pass)
+    one = tpd.decompose_batched([gpu(m) for m in mats], precision=precision, variant=2)  # one launch
+    per = tpd.decompose_batched([gpu(m) for m in mats], precision=precision)             # per (n, pass)
     for m, o, p, n in zip(mats, one, per, ns):
         want = oracle.coeffs_fwht(m)
         assert_close(to_string_order(host(o), n), want, TOL128, "persistent n=%d" % n)
@@ -65,7 +65,7 @@ def test_persistent_integer_bit_exact_and_roundtrip(tpd):
     ns = mixed_sizes(9600)
     ints = [synth.int_general(n, seed=9600 + i) for i, n in enumerate(ns)]
     work = [gpu(m) for m in ints]
-    batch = tpd.Batch(work)
+    batch = tpd.Batch(work, variant=2)
     batch.decompose()
     assert batch.status() == STATUS_OK
     for m, w, n in zip(ints, work, ns):
@@ -84,7 +84,7 @@ def test_persistent_integer_bit_exact_and_roundtrip(tpd):
 def test_persistent_c64(tpd, precision):
     ns = mixed_sizes(9700, count=24)
     mats = [synth.hermitian(n, seed=9700 + i, dtype=np.complex64) for i, n in enumerate(ns)]
-    outs = tpd.decompose_batched([gpu(m, torch.complex64) for m in mats], precision=precision)
+    outs = tpd.decompose_batched([gpu(m, torch.complex64) for m in mats], precision=precision, variant=2)
     prec = 1 if precision == "plain" else 2
     for m, o, n in zip(mats, outs, ns):
         want = oracle.coeffs_fwht(m.astype(np.complex128))
@@ -97,7 +97,7 @@ def test_persistent_graph_replay(tpd):
     mats = [synth.general(n, seed=9800 + i) for i, n in enumerate(ns)]
     work = [gpu(m) for m in mats]
     pristine = [w.clone() for w in work]
-    batch = tpd.Batch(work)
+    batch = tpd.Batch(work, variant=2)
     s = torch.cuda.Stream()
     s.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(s):
@@ -122,7 +122,7 @@ def test_bounded_wait_reports_timeout_and_context_survives(tpd):
     ns = [7, 8, 3, 9]                      # two-pass plans: their second passes wait
     mats = [synth.general(n, seed=9900 + i) for i, n in enumerate(ns)]
     work = [gpu(m) for m in mats]
-    batch = tpd.Batch(work)
+    batch = tpd.Batch(work, variant=2)
     L.tpd_test_hold_batch_waits(1)
     try:
         batch.decompose()
@@ -131,14 +131,14 @@ def test_bounded_wait_reports_timeout_and_context_survives(tpd):
         L.tpd_test_hold_batch_waits(0)
     # the context is intact: a fresh call on new copies is correct and reports OK
     work2 = [gpu(m) for m in mats]
-    batch2 = tpd.Batch(work2)
+    batch2 = tpd.Batch(work2, variant=2)
     batch2.decompose()
     assert batch2.status() == STATUS_OK
     for m, w, n in zip(mats, work2, ns):
         assert_close(to_string_order(host(w), n), oracle.coeffs_fwht(m), TOL128, "after timeout n=%d" % n)
 
 
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", [0, 2])
 def test_inconsistent_device_sizes_touch_nothing(tpd, variant):
     from paper_2310_13421_gb300 import _lib as L
     ns = [3, 7, 5, 8]

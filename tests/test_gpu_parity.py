@@ -360,3 +360,39 @@ def test_autotune_registers_a_plan_that_matches_oracle(tpd, tmp_path):
             (P + 1) * U32 * 1.01
     finally:
         L.tpd_tune_clear()
+
+
+# ------------------------------------------------------------------ layout and norms
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 7, 10])
+def test_string_layout_is_the_base4_order(tpd, n):
+    from _helpers import rc_positions
+    for dt, npdt in ((torch.complex128, np.complex128), (torch.complex64, np.complex64)):
+        A = synth.general(n, seed=9300 + n).astype(npdt)
+        W = tpd.decompose(gpu(A, dt))
+        S = tpd.to_string_layout(W)
+        w = host(W).reshape(-1)
+        assert_exact(host(S), w[rc_positions(n)], "string layout n=%d" % n)
+        assert_exact(host(tpd.from_string_layout(S)), host(W), "back to RC n=%d" % n)
+        if dt == torch.complex128:
+            assert_close(host(S), oracle.coeffs_fwht(A), TOL128, "string order vs oracle n=%d" % n)
+
+
+def test_sum_squares_parseval_and_determinism(tpd):
+    for n in (3, 9, 12):
+        A = synth.general(n, seed=9400 + n)
+        At = gpu(A)
+        W = tpd.decompose(At)
+        a2 = tpd.sum_squares(At)
+        w2 = tpd.sum_squares(W)
+        a2_host = float(np.sum(np.abs(A) ** 2))
+        assert abs(float(a2) - a2_host) <= 1e-13 * a2_host
+        # Parseval: ||A||_F^2 = 2^n sum |w|^2
+        assert abs(float(w2) * 2 ** n - a2_host) <= 1e-12 * a2_host
+        assert float(tpd.sum_squares(At)) == float(a2)          # same bits every call
+    B = synth.hermitian(10, seed=9410, dtype=np.complex64)
+    b2 = float(tpd.sum_squares(gpu(B, torch.complex64)))
+    want = float(np.sum(np.abs(B.astype(np.complex128)) ** 2))
+    assert abs(b2 - want) <= 1e-12 * want
+    empty = torch.empty(0, dtype=torch.complex128, device="cuda")
+    assert float(tpd.sum_squares(empty)) == 0.0
