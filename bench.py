@@ -52,14 +52,15 @@ def parse():
                    help="dense: the metric's n=14 matrix (default); batch: only the batch comparison "
                         "(--batch-count matrices, n ~ U{3..10}), e.g. for profiling")
     p.add_argument("--batch-count", type=int, default=4096)
+    p.add_argument("--storage", choices=["c128", "c64"], default="c128",
+                   help="dense workload storage (c128 = the metric's; c64 for profiling the fp32 forms)")
+    p.add_argument("--precision", choices=["default", "fixed", "plain", "compensated"], default="default")
     return p.parse_args()
 
 
 def dist_env():
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return world, rank, local
+    from paper_2310_13421_gb300.dist import rank_env
+    return rank_env()
 
 
 # ------------------------------------------------------------------ clocks
@@ -304,6 +305,88 @@ def time_batch(tpd, L, torch, stream, count=4096, seed=1004, reps=5):
             "speedup_vs_loop": res["per_matrix_loop"] / ms, "identical_results": same, "one_launch_status": status}
 
 
+def _event_ms(torch, stream, fn, reps=5, setup=None):
+    times = []
+    for k in range(reps + 2):
+        if setup is not None:
+            setup()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if k >= 2:
+            times.append(e0.elapsed_time(e1))
+    return float(np.median(times))
+
+
+def alg1_baseline(A, W_rc, n, samples=1 << 20):
+    """The paper's recursive algorithm (Alg. 1) on the host, single thread, on
+    the whole matrix: coeffs/s, and its largest deviation from the GPU result
+    on a random sample of strings."""
+    import oracle
+    t0 = time.perf_counter()
+    w = oracle.tpd_alg1(A)
+    dt = time.perf_counter() - t0
+    rng = np.random.default_rng(7)
+    s = rng.integers(0, 4 ** n, size=samples, dtype=np.int64)
+    r = np.zeros_like(s)
+    c = np.zeros_like(s)
+    for beta in range(n):
+        t = (s >> (2 * beta)) & 3
+        r |= (t >> 1) << beta
+        c |= (t & 1) << beta
+    gpu = W_rc.reshape(-1)[(r << n) | c]
+    dev = float(np.max(np.abs(gpu - w[s])) / np.max(np.abs(w)))
+    return {"value": 4 ** n / dt, "unit": UNIT, "seconds": dt, "threads": 1,
+            "kind": "the paper's recursive TPD (Alg. 1) on the host, fp64, whole matrix",
+            "max_rel_dev_vs_gpu_sampled": dev}
+
+
+def time_partial(tpd, L, torch, stream, n=14, seed=1005):
+    """Partial decomposition (Alg. 3) of the planted n=14 Heisenberg chain
+    for its 53 strings, against the full decomposition of the same matrix."""
+    from paper_2310_13421_gb300 import synth
+    J, h = synth.heisenberg_params(n, seed=seed)
+    H = torch.from_numpy(synth.heisenberg(n, J, h)).cuda()
+    terms = synth.heisenberg_terms(n, J, h)
+    strings = [synth.string_index(t) for t in terms]
+    want = torch.tensor([terms[t] for t in terms], dtype=torch.complex128)
+    work = torch.empty_like(H)
+    part = tpd.Partial(n, strings)
+    out = torch.empty(len(strings), dtype=torch.complex128, device="cuda")
+    ms_part = _event_ms(torch, stream, lambda: part.decompose(work, inplace=True, out=out),
+                        setup=lambda: work.copy_(H))
+    exact = bool(torch.equal(out.cpu(), want))
+    ms_full = _event_ms(torch, stream, lambda: tpd.decompose(work, inplace=True), setup=lambda: work.copy_(H))
+    del H, work
+    torch.cuda.empty_cache()
+    return {"strings": len(strings), "partial_ms": ms_part, "full_ms": ms_full, "speedup": ms_full / ms_part,
+            "planted_weights_exact": exact}
+
+
+def time_helpers(tpd, L, torch, stream, n=14):
+    """Memory-bound helpers on the n=14 complex128 matrix: RC -> string layout
+    (read + write) and the fp64 sum of squares (read)."""
+    from paper_2310_13421_gb300 import synth
+    A = torch.from_numpy(synth.hermitian(n, seed=1002)).cuda()
+    nbytes = A.numel() * 16
+    S = torch.empty(A.numel(), dtype=A.dtype, device="cuda")
+    code = L.TPD_C128
+
+    def conv():
+        st = L.tpd_convert_layout(A.data_ptr(), S.data_ptr(), n, code, 1, stream.cuda_stream)
+        assert st == 0
+
+    ms_layout = _event_ms(torch, stream, conv)
+    ms_sumsq = _event_ms(torch, stream, lambda: tpd.sum_squares(A))
+    del A, S
+    torch.cuda.empty_cache()
+    return {"layout_ms": ms_layout, "layout_gbs": 2 * nbytes / (ms_layout * 1e-3) / 1e9,
+            "sum_squares_ms": ms_sumsq, "sum_squares_gbs": nbytes / (ms_sumsq * 1e-3) / 1e9}
+
+
 def run_ours(args, world, rank, local):
     import torch
     if not torch.cuda.is_available():
@@ -320,12 +403,10 @@ def run_ours(args, world, rank, local):
             dist.barrier()
         torch.cuda.synchronize()
 
+    from paper_2310_13421_gb300 import dist as tdist
+
     def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return tdist.max_over_ranks(x, device="cuda")
 
     import paper_2310_13421_gb300 as tpd
     from paper_2310_13421_gb300 import _lib as L, synth
@@ -334,8 +415,13 @@ def run_ours(args, world, rank, local):
     n = args.qubits
     N = 2 ** n
     coeffs = 4 ** n
-    elem = 16
-    A = synth.hermitian(n, seed=SEED + rank)
+    c64 = args.storage == "c64"
+    elem = 8 if c64 else 16
+    code = L.TPD_C64 if c64 else L.TPD_C128
+    prec = {"default": L.TPD_PREC_DEFAULT, "fixed": L.TPD_PREC_FIXED, "plain": L.TPD_PREC_PLAIN,
+            "compensated": L.TPD_PREC_COMPENSATED}[args.precision]
+    prec_eff = prec if prec != L.TPD_PREC_DEFAULT else (L.TPD_PREC_PLAIN if c64 else L.TPD_PREC_FIXED)
+    A = synth.hermitian(n, seed=SEED + rank, dtype=np.complex64 if c64 else np.complex128)
     A_pin = torch.from_numpy(A).pin_memory()
     pristine = A_pin.to("cuda", non_blocking=False)
     work = torch.empty_like(pristine)
@@ -347,12 +433,12 @@ def run_ours(args, world, rank, local):
     clocks.start()
     time.sleep(0.3)
     step_ms, pass_ms, npass = time_decompose(tpd, L, torch, work, pristine, n, args.steps, args.warmup,
-                                             L.TPD_PREC_FIXED, stream)
+                                             prec_eff, stream)
     barrier()
     clk = clocks.stop()
     total_ms = max_over_ranks(sum(step_ms))
     ms_per_step = total_ms / args.steps
-    value = world * coeffs * args.steps / (total_ms * 1e-3)
+    value = tdist.job_rate(world * coeffs * args.steps, total_ms)
 
     # roofline of the pass kernel: algorithmic bytes per launch = read + write of the matrix
     alg_bytes = 2 * coeffs * elem
@@ -368,37 +454,43 @@ def run_ours(args, world, rank, local):
         pass
     peak = float(peaks.get("hbm_gbs", 6800.0))
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": measured_traffic(n),
-                "kernel": "k_pass<FixedArith,true> (one launch per pass, %d passes)" % npass,
+                "traffic": None if (c64 or prec_eff != L.TPD_PREC_FIXED) else measured_traffic(n),
+                "kernel": "k_pass<%s,true> (one launch per pass, %d passes)" % (
+                    {L.TPD_PREC_FIXED: "Fixed32Arith" if c64 else "FixedArith",
+                     L.TPD_PREC_PLAIN: "F32Arith" if c64 else "F64Arith",
+                     L.TPD_PREC_COMPENSATED: "F32CArith"}[prec_eff], npass),
                 "bytes_per_launch": alg_bytes, "per_pass_ms": per_pass_ms,
                 "per_pass_gbs": [alg_bytes / (m * 1e-3) / 1e9 for m in per_pass_ms],
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s"}
 
     # ---- end to end through the C ABI with pinned host buffers
     W_pin = torch.empty_like(A_pin).pin_memory()
-    wsb = L.tpd_workspace_size(n, L.TPD_C128, L.options())
+    wsb = L.tpd_workspace_size(n, code, L.options(precision=prec_eff))
     ws = torch.empty(max(wsb, 16), dtype=torch.uint8, device="cuda")
     e2e_ms = []
     for k in range(args.e2e_steps + 1):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         barrier()
         e0.record(stream)
-        st = L.tpd_decompose_host(A_pin.data_ptr(), W_pin.data_ptr(), work.data_ptr(), n, L.TPD_C128,
-                                  L.options(), ws.data_ptr(), wsb, stream.cuda_stream)
+        st = L.tpd_decompose_host(A_pin.data_ptr(), W_pin.data_ptr(), work.data_ptr(), n, code,
+                                  L.options(precision=prec_eff), ws.data_ptr(), wsb, stream.cuda_stream)
         assert st == 0, L.status_string(st)
         e1.record(stream)
         torch.cuda.synchronize()
         if k > 0:  # first call is warm-up
             e2e_ms.append(e0.elapsed_time(e1))
     e2e_total = max_over_ranks(sum(e2e_ms))
-    e2e = {"value": world * coeffs * len(e2e_ms) / (e2e_total * 1e-3), "unit": UNIT,
+    e2e = {"value": tdist.job_rate(world * coeffs * len(e2e_ms), e2e_total), "unit": UNIT,
            "h2d_bytes_per_step": coeffs * elem, "d2h_bytes_per_step": coeffs * elem,
            "ms_per_step": e2e_total / len(e2e_ms)}
     # sanity: the host result equals the device result of the same plan
     ok = torch.equal(W_pin.to("cuda"), work)
+    alg1 = None
+    if rank == 0 and world == 1 and not args.no_extra and not c64:
+        alg1 = alg1_baseline(A, W_pin.numpy(), n)
 
     extra = {}
-    if not args.no_extra:
+    if not args.no_extra and not c64 and prec_eff == L.TPD_PREC_FIXED:
         # fp64 butterfly (IEEE double, rounded per level) on the same matrix
         s64, p64, np64 = time_decompose(tpd, L, torch, work, pristine, n, 5, 2, L.TPD_PREC_PLAIN, stream)
         f64_ms = float(np.mean(s64))
@@ -413,13 +505,14 @@ def run_ours(args, world, rank, local):
         p15 = torch.from_numpy(A64).cuda()
         w15 = torch.empty_like(p15)
         res = {}
-        for name, prec in (("plain", L.TPD_PREC_PLAIN), ("compensated", L.TPD_PREC_COMPENSATED)):
+        for name, prec in (("plain", L.TPD_PREC_PLAIN), ("compensated", L.TPD_PREC_COMPENSATED),
+                           ("fixed", L.TPD_PREC_FIXED)):
             s, _, npp = time_decompose(tpd, L, torch, w15, p15, n15, 5, 2, prec, stream)
             res[name] = {"ms_per_step": float(np.mean(s)), "coeffs_per_s": 4 ** n15 / (np.mean(s) * 1e-3),
                          "passes": npp, "hbm_gbs_per_pass": 2 * 4 ** n15 * 8 / (np.mean(s) / npp * 1e-3) / 1e9}
             res[name]["_out"] = w15.clone()
         ref = tpd.decompose(p15.to(torch.complex128), precision="fixed")
-        for name in ("plain", "compensated"):
+        for name in ("plain", "compensated", "fixed"):
             out = res[name].pop("_out").to(torch.complex128)
             res[name]["rel_err_vs_c128"] = float(torch.linalg.vector_norm(out - ref) / torch.linalg.vector_norm(ref))
             del out
@@ -428,26 +521,41 @@ def run_ours(args, world, rank, local):
         p128 = w128.clone()
         s, _, npp = time_decompose(tpd, L, torch, w128, p128, n15, 3, 1, L.TPD_PREC_PLAIN, stream)
         res["c128_fp64_plain"] = {"ms_per_step": float(np.mean(s)), "passes": npp}
+        s, _, npp = time_decompose(tpd, L, torch, w128, p128, n15, 3, 1, L.TPD_PREC_FIXED, stream)
+        res["c128_fixed"] = {"ms_per_step": float(np.mean(s)), "passes": npp}
         extra["n15"] = res
         extra["speedup_c64_compensated_vs_c128_fp64_n15"] = res["c128_fp64_plain"]["ms_per_step"] / \
             res["compensated"]["ms_per_step"]
+        extra["speedup_c64_compensated_vs_c128_fixed_n15"] = res["c128_fixed"]["ms_per_step"] / \
+            res["compensated"]["ms_per_step"]
+        extra["speedup_c64_fixed_vs_c128_fp64_n15"] = res["c128_fp64_plain"]["ms_per_step"] / \
+            res["fixed"]["ms_per_step"]
         del w128, p128, p15, w15
         torch.cuda.empty_cache()
-    if not args.no_extra and not args.no_batch:
+        extra["partial_n14_heisenberg"] = time_partial(tpd, L, torch, stream)
+        extra["helpers_n14"] = time_helpers(tpd, L, torch, stream)
+    if not args.no_extra and not args.no_batch and not c64:
         extra["batch_4096_n3_10"] = time_batch(tpd, L, torch, stream)
 
     cpu = None
     if rank == 0 and world == 1:
         v, cores, sample = oracle_rate(A, n)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+    if alg1 is not None:
+        extra["cpu_alg1"] = alg1
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": "n=%d dense random Hermitian, %dx%d complex128 (%.2f GB) in place; "
-                               "Re,Im of B ~ N(0,1), A=(B+B^H)/2" % (n, N, N, coeffs * elem / 1e9),
-                   "storage": "complex128", "precision": "fixed (exact int64 block fixed point per pass)",
+        "vs_baseline": None, "dtype": {L.TPD_PREC_FIXED: "int64", L.TPD_PREC_PLAIN: "f32" if c64 else "f64",
+                                       L.TPD_PREC_COMPENSATED: "f32"}[prec_eff], "data": "synthetic",
+        "config": {"workload": "n=%d dense random Hermitian, %dx%d " % (n, N, N) +
+                               ("complex64" if c64 else "complex128") +
+                               " (%.2f GB) in place; Re,Im of B ~ N(0,1), A=(B+B^H)/2" % (coeffs * elem / 1e9),
+                   "storage": "complex64" if c64 else "complex128",
+                   "precision": {L.TPD_PREC_FIXED: "fixed (exact int64 block fixed point per pass)",
+                                 L.TPD_PREC_PLAIN: "plain IEEE adds per level",
+                                 L.TPD_PREC_COMPENSATED: "compensated fp32 (TwoSum per pass)"}[prec_eff],
                    "passes": npass,
                    "l2": "inputs larger than L2 (%.2f GB vs 126 MB); restored between steps" % (coeffs * elem / 1e9),
                    "parallelism": "replicas" if world > 1 else "single GPU"},

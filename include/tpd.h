@@ -42,7 +42,8 @@ extern "C" {
 typedef enum {
   TPD_OK = 0,
   TPD_ERR_INVALID_ARG = 1,  /* bad n, dtype, precision, count, null pointer */
-  TPD_ERR_UNSUPPORTED = 2,  /* combination not implemented (e.g. COMPENSATED with C128) */
+  TPD_ERR_UNSUPPORTED = 2,  /* combination not implemented (COMPENSATED with C128, zero
+                               skipping in batched or partial calls) */
   TPD_ERR_MISALIGNED = 3,   /* pointer not aligned to the element size */
   TPD_ERR_WORKSPACE = 4,    /* workspace missing or smaller than *_workspace_size() */
   TPD_ERR_CUDA = 5,         /* a CUDA call failed (launch error, no device, ...) */
@@ -63,9 +64,12 @@ typedef enum {
   TPD_PREC_COMPENSATED = 2,  /* C64 only: fp32 sums carried with TwoSum error terms
                                 (Ogita-Rump-Oishi cascaded summation) across the
                                 levels of a pass, one rounding per pass */
-  TPD_PREC_FIXED = 3         /* C128 only: the levels of a pass are summed exactly
-                                in 64-bit integers on a per-tile binary point
-                                (block fixed point), one rounding per pass */
+  TPD_PREC_FIXED = 3         /* the levels of a pass are summed exactly in 64-bit
+                                integers on a per-tile binary point (block fixed
+                                point).  C128: int64 sums are handed between
+                                passes, one rounding per decomposition.  C64: each
+                                pass rounds to float once (RNE); whole matrices of
+                                n <= 4 run the compensated kernel */
 } tpd_precision;
 
 typedef struct {

@@ -1,4 +1,5 @@
-"""ctypes front end of the C oracle ``tpd_oracle.c`` (test infrastructure only).
+"""ctypes front end of the C oracle ``tpd_oracle.c`` and of ``tpd_alg1.c`` (the
+paper's recursive algorithm on the CPU) -- test infrastructure only.
 
 The shared library is compiled with gcc into ``oracle/_build/`` on first use
 (or by ``build_library()``), with -ffp-contract=off so that no sum in the
@@ -13,6 +14,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "tpd_oracle.c")
+_SRC_ALG1 = os.path.join(_HERE, "tpd_alg1.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
@@ -20,14 +22,14 @@ _lib = None
 
 
 def build_library(force=False):
-    """Compile tpd_oracle.c -> oracle/_build/liboracle.so (gcc, OpenMP)."""
+    """Compile tpd_oracle.c, tpd_alg1.c -> oracle/_build/liboracle.so (gcc, OpenMP)."""
     os.makedirs(_BUILD, exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+            and os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_ALG1))):
         return _LIB_PATH
     tmp = _LIB_PATH + ".%d.tmp" % os.getpid()
     cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
-           "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"]
+           "-shared", "-fPIC", "-o", tmp, _SRC, _SRC_ALG1, "-lm"]
     subprocess.check_call(cmd)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -46,8 +48,10 @@ def _load():
             lib.oracle_coeffs_xrows.argtypes = [dp, ctypes.c_int, u64p, ctypes.c_int64, dp]
             lib.oracle_compose.argtypes = [dp, ctypes.c_int, dp]
             lib.oracle_compose_fwht.argtypes = [dp, ctypes.c_int, dp]
+            lib.oracle_tpd_alg1.argtypes = [dp, ctypes.c_int, dp]
             for f in (lib.oracle_coeffs, lib.oracle_coeffs_fwht, lib.oracle_coeffs_at,
-                      lib.oracle_coeffs_xrows, lib.oracle_compose, lib.oracle_compose_fwht):
+                      lib.oracle_coeffs_xrows, lib.oracle_compose, lib.oracle_compose_fwht,
+                      lib.oracle_tpd_alg1):
                 f.restype = ctypes.c_int
             lib.oracle_num_threads.argtypes = []
             lib.oracle_num_threads.restype = ctypes.c_int
@@ -74,6 +78,16 @@ def _square(A):
 def num_threads():
     """OpenMP threads the oracle runs on."""
     return int(_load().oracle_num_threads())
+
+
+def tpd_alg1(A):
+    """All 4^n weights by the paper's recursive algorithm (Alg. 1: CMWs of
+    Eq. 4, recursion on nonzero CMWs), string order; single-threaded."""
+    A, n = _square(A)
+    out = np.empty(4 ** n, dtype=np.complex128)
+    if _load().oracle_tpd_alg1(_dptr(A), n, _dptr(out)):
+        raise RuntimeError("oracle_tpd_alg1 failed")
+    return out
 
 
 def coeffs(A):

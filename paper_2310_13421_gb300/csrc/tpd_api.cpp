@@ -30,6 +30,7 @@ int resolve_precision(int dtype, int precision) {
 
 int arith_of(int dtype, int prec) {
   if (dtype == TPD_C128) return prec == TPD_PREC_FIXED ? kArithFixed : kArithF64;
+  if (prec == TPD_PREC_FIXED) return kArithF32Fixed;
   return prec == TPD_PREC_COMPENSATED ? kArithF32C : kArithF32;
 }
 
@@ -38,7 +39,6 @@ tpd_status check_options(int dtype, const tpd_options* opt, int* prec) {
   const int p = resolve_precision(dtype, opt ? opt->precision : 0);
   if (p < TPD_PREC_PLAIN || p > TPD_PREC_FIXED) return TPD_ERR_INVALID_ARG;
   if (p == TPD_PREC_COMPENSATED && dtype != TPD_C64) return TPD_ERR_UNSUPPORTED;
-  if (p == TPD_PREC_FIXED && dtype != TPD_C128) return TPD_ERR_UNSUPPORTED;
   if (opt && opt->tile_bits != 0 && (opt->tile_bits < kMinTileBits || opt->tile_bits > kMaxTileBits))
     return TPD_ERR_INVALID_ARG;
   if (opt && (opt->max_levels < 0 || opt->max_levels > kMaxLevels)) return TPD_ERR_INVALID_ARG;
@@ -123,7 +123,7 @@ void split_scale(double scale, int* pow2, double* residual) {
 
 void pass_scaling(bool dec, int arith, const PassDesc& pd, bool last, int spow, double sres, double scale,
                   PassArgs* a) {
-  if (arith == kArithFixed) {
+  if (arith == kArithFixed || arith == kArithF32Fixed) {
     // the kernel folds the 1/2 of Eq. 4 into its binary point; only the
     // composition's scale is applied here, on the last pass
     a->out_pow2 = (!dec && last) ? spow : 0;

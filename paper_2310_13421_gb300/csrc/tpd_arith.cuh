@@ -7,7 +7,7 @@
 // applied once per pass as 2^-K, which is exact.  The composition maps
 //     a00 = I + Z,  a01 = X - iY,  a10 = X + iY,  a11 = I - Z.
 //
-// Four arithmetics share this interface:
+// Five arithmetics share this interface:
 //   FixedArith  complex128 storage; a pass loads each tile onto a common
 //               binary point in int64 (block fixed point), sums exactly, and
 //               rounds once to double (RNE) when it stores.  Only integer
@@ -18,6 +18,9 @@
 //   F32CArith   complex64, float sums with TwoSum error terms carried through
 //               the pass (cascaded summation, Ogita-Rump-Oishi 2005), one
 //               rounding fl(hi + lo) per pass.
+//   Fixed32Arith complex64 storage, every pass on its own tile binary point in
+//               int64 (exact sums), rounded to float (RNE) when it stores:
+//               one rounding per pass, integer instructions only.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -40,6 +43,7 @@ struct FixedArith {
   using Store = double2;
   struct __align__(16) V { long long re, im; };   // 16-byte aligned: one 128-bit shared access
   static constexpr bool kFixed = true;
+  static constexpr bool kFixed32 = false;
   static constexpr int kStoreBytes = 16;
 
   __device__ static __forceinline__ V add(V a, V b) { return {a.re + b.re, a.im + b.im}; }
@@ -178,6 +182,7 @@ struct F64Arith {
   using Store = double2;
   using V = double2;
   static constexpr bool kFixed = false;
+  static constexpr bool kFixed32 = false;
   static constexpr int kStoreBytes = 16;
   __device__ static __forceinline__ V add(V a, V b) { return make_double2(__dadd_rn(a.x, b.x), __dadd_rn(a.y, b.y)); }
   __device__ static __forceinline__ V sub(V a, V b) { return make_double2(__dsub_rn(a.x, b.x), __dsub_rn(a.y, b.y)); }
@@ -208,6 +213,7 @@ struct F32Arith {
   using Store = float2;
   using V = float2;
   static constexpr bool kFixed = false;
+  static constexpr bool kFixed32 = false;
   static constexpr int kStoreBytes = 8;
   __device__ static __forceinline__ V add(V a, V b) { return make_float2(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y)); }
   __device__ static __forceinline__ V sub(V a, V b) { return make_float2(__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y)); }
@@ -234,6 +240,7 @@ struct F32CArith {
   using Store = float2;
   struct __align__(16) V { float re, im, rl, il; };   // value = (re + rl) + i (im + il)
   static constexpr bool kFixed = false;
+  static constexpr bool kFixed32 = false;
   static constexpr int kStoreBytes = 8;
 
   // Knuth's TwoSum: s + e == a + b exactly, s = fl(a + b).
@@ -273,6 +280,74 @@ struct F32CArith {
   }
   __device__ static __forceinline__ bool nonzero(Store o) {
     return ((__float_as_uint(o.x) | __float_as_uint(o.y)) << 1) != 0;
+  }
+};
+
+// ================================================================ fixed point, float storage
+//
+// A tile of floats (binary exponent field E <= 254 of its largest component)
+// goes onto the binary point S = 188 - K - max(E, 1): x * 2^S is exact for
+// every component within 2^(38-K) of the largest (smaller ones are truncated
+// toward zero, an error below 2^-(62-K) of the largest), the largest lands
+// below 2^(62-K), and the 2^K-term sums of the pass stay below 2^62.
+struct Fixed32Arith {
+  using Store = float2;
+  using V = FixedArith::V;
+  static constexpr bool kFixed = false;
+  static constexpr bool kFixed32 = true;
+  static constexpr int kStoreBytes = 8;
+  __device__ static __forceinline__ V add(V a, V b) { return FixedArith::add(a, b); }
+  __device__ static __forceinline__ V sub(V a, V b) { return FixedArith::sub(a, b); }
+  __device__ static __forceinline__ V mul_i(V d) { return FixedArith::mul_i(d); }
+  __device__ static __forceinline__ V mul_mi(V d) { return FixedArith::mul_mi(d); }
+  __device__ static __forceinline__ V neg(V d) { return FixedArith::neg(d); }
+  __device__ static __forceinline__ V shfl(V v, int mask) { return FixedArith::shfl(v, mask); }
+
+  // x * 2^S truncated toward zero; rs_base = max(E_tile, 1) + K.
+  __device__ static __forceinline__ long long to_fixed(float x, int rs_base) {
+    const uint32_t bits = __float_as_uint(x);
+    const int e = (int)(bits >> 23) & 0xFF;
+    const uint32_t m = (bits & 0x007FFFFFu) | ((uint32_t)(e != 0) << 23);
+    const unsigned rs = (unsigned)(rs_base - max(e, 1));   // >= K >= 1
+    unsigned long long mag;
+    const unsigned long long ml = (unsigned long long)m << 38;   // m < 2^24
+    asm("shr.b64 %0, %1, %2;" : "=l"(mag) : "l"(ml), "r"(rs));   // clamps above 64: 0
+    const unsigned long long sg = (unsigned long long)(long long)((int)bits >> 31);
+    return (long long)((mag ^ sg) - sg);
+  }
+
+  // v * 2^-T rounded to the nearest float, ties to even (integer instructions;
+  // subnormal results and overflow to Inf included).
+  __device__ static __forceinline__ float to_float(long long v, int T) {
+    if (v == 0) return 0.0f;
+    const unsigned long long s = (unsigned long long)(v >> 63);
+    unsigned long long a = ((unsigned long long)v ^ s) - s;
+    const int lz = __clzll((long long)a);
+    a <<= lz;                                   // leading one at bit 63
+    const int be = 190 - lz - T;                // biased exponent of that bit
+    uint32_t bits;
+    if (be >= 1) {
+      const uint32_t hi = (uint32_t)(a >> 32);
+      const uint32_t mant = hi >> 8;            // 24 bits, implicit one at bit 23
+      const uint32_t r8 = hi & 0xFFu;           // the next 8 bits ...
+      const bool sticky = (uint32_t)a != 0u;    // ... and the rest
+      const uint32_t up = (r8 > 0x80u) | ((r8 == 0x80u) & (sticky | (mant & 1u)));
+      bits = be > 254 ? 0x7F800000u : ((uint32_t)(be - 1) << 23) + mant + up;   // a carry bumps the exponent
+      if (bits > 0x7F800000u) bits = 0x7F800000u;
+    } else {
+      const int rsh = 41 - be;                  // >= 41: subnormal mantissa = a >> rsh
+      if (rsh > 64) {
+        bits = 0u;
+      } else if (rsh == 64) {
+        bits = a > 0x8000000000000000ull ? 1u : 0u;
+      } else {
+        const unsigned long long mant = a >> rsh;
+        const unsigned long long rem = a & ((1ull << rsh) - 1);
+        const unsigned long long half = 1ull << (rsh - 1);
+        bits = (uint32_t)(mant + ((rem > half) | ((rem == half) & (mant & 1ull))));
+      }
+    }
+    return __uint_as_float(bits | ((uint32_t)s & 0x80000000u));
   }
 };
 

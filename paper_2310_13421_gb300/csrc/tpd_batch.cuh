@@ -20,6 +20,8 @@
 // loads of data written in this launch go through L2 (ld.global.cg).
 #pragma once
 
+#include <type_traits>
+
 #include "tpd_pass.cuh"
 
 namespace tpd {
@@ -173,7 +175,9 @@ __global__ void __launch_bounds__(256, 2) k_batch(const __grid_constant__ BatchP
     if (s_ok) {
       void* matp = s_mat;
       if (sg.kind == kSegSmall) {
-        small_matrix<A, kDec>(reinterpret_cast<Store*>(matp), sg.n, 0, bp.scale_mode, smem, tid, blockDim.x);
+        // whole small matrices of the complex64 fixed-point form: the compensated kernel
+        using SmallA = typename std::conditional<A::kFixed32, F32CArith, A>::type;
+        small_matrix<SmallA, kDec>(reinterpret_cast<Store*>(matp), sg.n, 0, bp.scale_mode, smem, tid, blockDim.x);
       } else {
         batch_pass_tile<A, kDec>(sg, p, bp.desc[sg.desc + p], matp, j, tile, smem, lane, warp);
       }

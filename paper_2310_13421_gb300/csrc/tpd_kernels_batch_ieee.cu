@@ -13,6 +13,9 @@ cudaError_t launch_batch(int arith, bool dec, const BatchParams& bp, int* grid_o
       return dec ? launch_batch_t<F64Arith, true>(bp, grid_out, s) : launch_batch_t<F64Arith, false>(bp, grid_out, s);
     case kArithF32:
       return dec ? launch_batch_t<F32Arith, true>(bp, grid_out, s) : launch_batch_t<F32Arith, false>(bp, grid_out, s);
+    case kArithF32Fixed:
+      return dec ? launch_batch_t<Fixed32Arith, true>(bp, grid_out, s)
+                 : launch_batch_t<Fixed32Arith, false>(bp, grid_out, s);
     default:
       return dec ? launch_batch_t<F32CArith, true>(bp, grid_out, s)
                  : launch_batch_t<F32CArith, false>(bp, grid_out, s);

@@ -10,7 +10,7 @@
 
 namespace tpd {
 
-enum Arith { kArithFixed = 0, kArithF64 = 1, kArithF32 = 2, kArithF32C = 3 };
+enum Arith { kArithFixed = 0, kArithF64 = 1, kArithF32 = 2, kArithF32C = 3, kArithF32Fixed = 4 };
 
 struct PassArgs {
   // batched launches: tile t of the grid belongs to matrix ptrs[items[t / tiles_per_mat]]

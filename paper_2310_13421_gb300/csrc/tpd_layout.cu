@@ -73,10 +73,12 @@ __global__ void __launch_bounds__(256) k_layout(const T* __restrict__ src, T* __
 constexpr int kSumBlocks = 1024;
 constexpr int kSumThreads = 256;
 
+// acc + |x|^2 as two fused multiply-adds: on GB300 the fp64 pipe, not
+// memory, bounds this kernel, so it gets the fewest fp64 instructions
 template <class T>
-__device__ __forceinline__ double abs2(const T& x) {
+__device__ __forceinline__ double add_abs2(double acc, const T& x) {
   const double re = x.x, im = x.y;
-  return re * re + im * im;
+  return __fma_rn(im, im, __fma_rn(re, re, acc));
 }
 
 __device__ __forceinline__ double block_sum(double v, double* sh) {
@@ -90,13 +92,30 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return t;
 }
 
+// Each thread keeps kSumUnroll loads in flight (independent partial sums,
+// combined in a fixed order at the end).
+constexpr int kSumUnroll = 8;
+
 template <class T>
 __global__ void __launch_bounds__(kSumThreads) k_sumsq_partial(const T* __restrict__ x, uint64_t count,
                                                                double* __restrict__ partial) {
   __shared__ double sh[kSumThreads / 32];
-  double v = 0.0;
+  double acc[kSumUnroll];
+#pragma unroll
+  for (int u = 0; u < kSumUnroll; ++u) acc[u] = 0.0;
   const uint64_t stride = (uint64_t)kSumBlocks * kSumThreads;
-  for (uint64_t i = (uint64_t)blockIdx.x * kSumThreads + threadIdx.x; i < count; i += stride) v += abs2(x[i]);
+  uint64_t i = (uint64_t)blockIdx.x * kSumThreads + threadIdx.x;
+  for (; i + (kSumUnroll - 1) * stride < count; i += kSumUnroll * stride) {
+    T r[kSumUnroll];
+#pragma unroll
+    for (int u = 0; u < kSumUnroll; ++u) r[u] = __ldcs(x + i + u * stride);
+#pragma unroll
+    for (int u = 0; u < kSumUnroll; ++u) acc[u] = add_abs2(acc[u], r[u]);
+  }
+  for (; i < count; i += stride) acc[0] = add_abs2(acc[0], x[i]);   // tail: fewer than kSumUnroll
+  double v = 0.0;
+#pragma unroll
+  for (int u = 0; u < kSumUnroll; ++u) v += acc[u];
   const double t = block_sum(v, sh);
   if (threadIdx.x == 0) partial[blockIdx.x] = t;
 }

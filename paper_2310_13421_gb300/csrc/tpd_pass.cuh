@@ -183,9 +183,9 @@ __device__ __forceinline__ void finish_tile(const PassDesc& pd, const PassArgs& 
   }
   const Stage& sl = pd.st[pd.nstage - 1];
   Store* mat = reinterpret_cast<Store*>(matp);
-  const long long g = base + thread_goff(pd, sl, lane, warp);
-  const long long w0 = 1ll << pd.gbit[sl.reg[0]], w1 = 1ll << pd.gbit[sl.reg[1]];
-  const long long w2 = 1ll << pd.gbit[sl.reg[2]], w3 = 1ll << pd.gbit[sl.reg[3]];
+  const uint32_t g = (uint32_t)base + (uint32_t)thread_goff(pd, sl, lane, warp);
+  const uint32_t w0 = 1u << pd.gbit[sl.reg[0]], w1 = 1u << pd.gbit[sl.reg[1]];
+  const uint32_t w2 = 1u << pd.gbit[sl.reg[2]], w3 = 1u << pd.gbit[sl.reg[3]];
   const bool flags = args.flags_out != nullptr;
   int nt = 0, n0 = 0, n1 = 0, n2 = 0, n3 = 0;
   bool lanes_inside = true;
@@ -217,11 +217,12 @@ __device__ __forceinline__ void load_tile(const PassDesc& pd, const void* matp, 
                                           Store (&raw)[kElems]) {
   const Stage& s0 = pd.st[0];
   const Store* mat = reinterpret_cast<const Store*>(matp);
-  const long long g = base + thread_goff(pd, s0, lane, warp);
-  const long long w0 = 1ll << pd.gbit[s0.reg[0]], w1 = 1ll << pd.gbit[s0.reg[1]];
-  const long long w2 = 1ll << pd.gbit[s0.reg[2]], w3 = 1ll << pd.gbit[s0.reg[3]];
+  // element indices in 32 bits: a matrix has at most 4^16 = 2^32 elements
+  const uint32_t g = (uint32_t)base + (uint32_t)thread_goff(pd, s0, lane, warp);
+  const uint32_t w0 = 1u << pd.gbit[s0.reg[0]], w1 = 1u << pd.gbit[s0.reg[1]];
+  const uint32_t w2 = 1u << pd.gbit[s0.reg[2]], w3 = 1u << pd.gbit[s0.reg[3]];
 #pragma unroll
-  for (int e = 0; e < kElems; ++e) raw[e] = ld_in<kCg>(mat + g + reg_off(e, w0, w1, w2, w3));
+  for (int e = 0; e < kElems; ++e) raw[e] = ld_in<kCg>(mat + (g + reg_off(e, w0, w1, w2, w3)));
 }
 
 // ============================================================== fixed point
@@ -445,9 +446,9 @@ __device__ __forceinline__ void fixed_tile(const PassDesc& pd, const PassArgs& a
 
   // ---- store in place
   const Stage& sl = pd.st[pd.nstage - 1];
-  const long long g = base + thread_goff(pd, sl, lane, warp);
-  const long long w0 = 1ll << pd.gbit[sl.reg[0]], w1 = 1ll << pd.gbit[sl.reg[1]];
-  const long long w2 = 1ll << pd.gbit[sl.reg[2]], w3 = 1ll << pd.gbit[sl.reg[3]];
+  const uint32_t g = (uint32_t)base + (uint32_t)thread_goff(pd, sl, lane, warp);
+  const uint32_t w0 = 1u << pd.gbit[sl.reg[0]], w1 = 1u << pd.gbit[sl.reg[1]];
+  const uint32_t w2 = 1u << pd.gbit[sl.reg[2]], w3 = 1u << pd.gbit[sl.reg[3]];
   const bool flags = args.flags_out != nullptr;
   int nt = 0, n0 = 0, n1 = 0, n2 = 0, n3 = 0;
   bool lanes_inside = true;
@@ -497,6 +498,88 @@ __device__ __forceinline__ void fixed_tile(const PassDesc& pd, const PassArgs& a
   }
 }
 
+// ============================================================== fixed point, float storage
+//
+// Every pass of the complex64 fixed-point form reads floats, sums the tile's
+// K levels exactly in int64 on the tile's own binary point, and rounds the
+// results to float (RNE) as it stores: one rounding per pass, nothing handed
+// between passes but the floats.  Tiles meeting an Inf or NaN run the IEEE
+// float butterfly instead.
+template <bool kDec, bool kCg>
+__device__ __forceinline__ void fixed32_tile(const PassDesc& pd, const PassArgs& args, void* matp, long long base,
+                                             int nbase, unsigned char* smem, int* red, int lane, int warp) {
+  using V = Fixed32Arith::V;
+  const int nwarps = 1 << (pd.D - kMinTileBits);
+  float2 raw[kElems];
+  load_tile<kCg>(pd, matp, base, lane, warp, raw);
+  uint32_t hmax = 0, nzw = 0;
+#pragma unroll
+  for (int e = 0; e < kElems; ++e) {
+    const uint32_t hx = __float_as_uint(raw[e].x) & 0x7fffffffu, hy = __float_as_uint(raw[e].y) & 0x7fffffffu;
+    hmax = max(hmax, max(hx, hy));
+    nzw |= hx | hy;
+  }
+  const uint32_t wmax = __reduce_max_sync(kFull, hmax >> 23);
+  nzw = __reduce_or_sync(kFull, nzw);
+  if (lane == 0) { red[warp] = (int)wmax; red[16 + warp] = (int)nzw; }
+  __syncthreads();
+  int emax = 0, nz = 0;
+  for (int w = 0; w < nwarps; ++w) { emax = max(emax, red[w]); nz |= red[16 + w]; }
+  if (args.skip_zero && nz == 0) return;                  // all +-0: outputs are zero already
+  if (emax == 255) {                                      // Inf/NaN in the tile
+    finish_tile<F32Arith, kDec>(pd, args, matp, raw, kDec ? pow2d(-pd.K) : pow2d(args.out_pow2) * args.out_mul,
+                                base, nbase, smem, lane, warp);
+    return;
+  }
+  const int emax_eff = max(emax, 1);
+  const int rs_base = emax_eff + pd.K;
+  V v[kElems];
+#pragma unroll
+  for (int e = 0; e < kElems; ++e) {
+    v[e].re = Fixed32Arith::to_fixed(raw[e].x, rs_base);
+    v[e].im = Fixed32Arith::to_fixed(raw[e].y, rs_base);
+  }
+  V* sm = reinterpret_cast<V*>(smem);
+  for (int s = 0; s < pd.nstage; ++s) {
+    if (s > 0) exchange(v, pd, pd.st[s - 1], pd.st[s], sm, lane, warp, s > 1);
+    stage_levels<Fixed32Arith, kDec>(v, pd.st[s], lane);
+  }
+  // value = sum * 2^-S (S = 188 - K - emax_eff), times 2^-K for the 1/2 of
+  // Eq. 4 per level, times 2^out_pow2 for a composition's scale
+  const int T = 188 - pd.K - emax_eff + (kDec ? pd.K : 0) - args.out_pow2;
+  const bool resid = args.out_mul != 1.0;
+  const Stage& sl = pd.st[pd.nstage - 1];
+  float2* mat = reinterpret_cast<float2*>(matp);
+  const uint32_t g = (uint32_t)base + (uint32_t)thread_goff(pd, sl, lane, warp);
+  const uint32_t w0 = 1u << pd.gbit[sl.reg[0]], w1 = 1u << pd.gbit[sl.reg[1]];
+  const uint32_t w2 = 1u << pd.gbit[sl.reg[2]], w3 = 1u << pd.gbit[sl.reg[3]];
+  const bool flags = args.flags_out != nullptr;
+  int nt = 0, n0 = 0, n1 = 0, n2 = 0, n3 = 0;
+  bool lanes_inside = true;
+  if (flags) {
+    nt = nbase + thread_next(pd, sl, lane, warp);
+    n0 = pd.next_w[sl.reg[0]]; n1 = pd.next_w[sl.reg[1]];
+    n2 = pd.next_w[sl.reg[2]]; n3 = pd.next_w[sl.reg[3]];
+#pragma unroll
+    for (int i = 0; i < kLaneBits; ++i) lanes_inside &= (pd.next_w[sl.lane[i]] == 0);
+  }
+#pragma unroll
+  for (int e = 0; e < kElems; ++e) {
+    float2 o = make_float2(Fixed32Arith::to_float(v[e].re, T), Fixed32Arith::to_float(v[e].im, T));
+    if (resid) { o.x = __fmul_rn(o.x, (float)args.out_mul); o.y = __fmul_rn(o.y, (float)args.out_mul); }
+    mat[g + reg_off(e, w0, w1, w2, w3)] = o;
+    if (flags) {
+      const bool nzo = (v[e].re | v[e].im) != 0;
+      const int id = nt + reg_off(e, n0, n1, n2, n3);
+      if (lanes_inside) {
+        if (__any_sync(kFull, nzo) && lane == 0) args.flags_out[id] = 1;
+      } else if (nzo) {
+        args.flags_out[id] = 1;
+      }
+    }
+  }
+}
+
 // One tile of a pass: its position from the tile id, then the arithmetic's
 // load / levels / store.  smem: the exchange area (2^D x 16 bytes) followed by
 // 64 ints of reduction slots.
@@ -516,6 +599,9 @@ __device__ __forceinline__ void pass_tile(const PassDesc& pd, const PassArgs& ar
   if constexpr (A::kFixed) {
     fixed_tile<kDec, kRole, kCg>(pd, args, matp, q_in, q_out, tile, base, pbase, nbase, nullptr, smem,
                                  reinterpret_cast<int*>(smem + ((size_t)16 << pd.D)), lane, warp);
+  } else if constexpr (A::kFixed32) {
+    fixed32_tile<kDec, kCg>(pd, args, matp, base, nbase, smem, reinterpret_cast<int*>(smem + ((size_t)16 << pd.D)),
+                            lane, warp);
   } else {
     Store raw[kElems];
     load_tile<kCg>(pd, matp, base, lane, warp, raw);

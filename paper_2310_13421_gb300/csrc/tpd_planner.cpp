@@ -112,7 +112,8 @@ std::vector<int> tile_bits(int n, int b, int K, int D) {
   return t;
 }
 
-bool build_pass(int n, int b, int K, int D, int lf, double cs, PassDesc* pd, std::string* err) {
+bool build_pass(int n, int b, int K, int D, int lf, double cs, PassDesc* pd, std::string* err,
+                double* cost_out = nullptr) {
   std::memset(pd, 0, sizeof(*pd));
   if (K < 1 || K > kMaxLevels || D < kMinTileBits || D > kMaxTileBits || 2 * K > D || D > 2 * n ||
       b < 0 || b + K > n) {
@@ -142,10 +143,12 @@ bool build_pass(int n, int b, int K, int D, int lf, double cs, PassDesc* pd, std
   }
   c.cx = 2.0; c.cs = cs;
   int nst = 0;
-  if (search(c, 0, (1u << K) - 1, &nst) >= 1e29) {
+  const double cost = search(c, 0, (1u << K) - 1, &nst);
+  if (cost >= 1e29) {
     if (err) *err = "no stage plan";
     return false;
   }
+  if (cost_out) *cost_out = cost;
   std::vector<StageChoice> chosen;
   unsigned remaining = (1u << K) - 1;
   for (int si = 0; remaining; ++si) {
@@ -212,7 +215,7 @@ void set_prev(PassDesc* cur, const PassDesc& prv) {
 
 int arith_elem_bytes(int dtype, int precision) {
   if (dtype == 0) return 16;               // fixed int64 pair or double2
-  return precision == 2 ? 16 : 8;          // compensated: hi/lo pairs in registers
+  return precision >= 2 ? 16 : 8;          // compensated hi/lo pairs, fixed-point int64 pairs in registers
 }
 
 bool build_plan(int n, int dtype, int precision, int tile_bits_opt, int max_levels_opt, Plan* plan,
@@ -235,20 +238,56 @@ bool build_plan(int n, int dtype, int precision, int tile_bits_opt, int max_leve
   int dmax = tile_bits_opt ? tile_bits_opt : 12;
   dmax = std::min(dmax, 2 * n);
   int kcap = max_levels_opt ? max_levels_opt : kMaxLevels;
-  const int k0 = std::min({n, dmax / 2, kcap});
-  const int rem = n - k0;
-  std::vector<std::pair<int, int>> groups;  // (K, D)
-  groups.push_back({k0, dmax});
-  if (rem > 0) {
-    auto kmax_for = [&](int D) { return std::max(1, std::min({(D - lf) / 2, kcap, kMaxLevels})); };
-    int D1 = dmax;
-    int m = (rem + kmax_for(D1) - 1) / kmax_for(D1);
-    if (!tile_bits_opt && D1 < kMaxTileBits && 2 * n >= D1 + 1) {
-      const int m13 = (rem + kmax_for(D1 + 1) - 1) / kmax_for(D1 + 1);
-      if (m13 < m) { D1 = D1 + 1; m = m13; }
+  auto kmax_for = [&](int D) { return std::max(1, std::min({(D - lf) / 2, kcap, kMaxLevels})); };
+  // passes for a first pass of k0 levels: the rest split evenly over as few
+  // passes as possible (2^13-element tiles only where that saves a pass)
+  auto groups_for = [&](int k0) {
+    std::vector<std::pair<int, int>> g;  // (K, D)
+    g.push_back({k0, dmax});
+    const int rem = n - k0;
+    if (rem > 0) {
+      int D1 = dmax;
+      int m = (rem + kmax_for(D1) - 1) / kmax_for(D1);
+      if (!tile_bits_opt && D1 < kMaxTileBits && 2 * n >= D1 + 1) {
+        const int m13 = (rem + kmax_for(D1 + 1) - 1) / kmax_for(D1 + 1);
+        if (m13 < m) { D1 = D1 + 1; m = m13; }
+      }
+      const int base = rem / m, extra = rem % m;
+      for (int i = 0; i < m; ++i) g.push_back({base + (i < extra ? 1 : 0), D1});
     }
-    const int base = rem / m, extra = rem % m;
-    for (int i = 0; i < m; ++i) groups.push_back({base + (i < extra ? 1 : 0), D1});
+    return g;
+  };
+  // the first pass's level count: fewest passes, then the least in-pass
+  // data movement (the stage search's cost: exchanges and shuffle levels)
+  const int k0max = std::min({n, dmax / 2, kcap});
+  std::vector<std::pair<int, int>> groups;
+  double best_cost = 1e30;
+  size_t best_passes = (size_t)-1;
+  for (int k0 = k0max; k0 >= 1; --k0) {
+    std::vector<std::pair<int, int>> g = groups_for(k0);
+    if (g.size() > best_passes) continue;
+    double cost = 0.0;
+    bool ok = true;
+    int b = 0;
+    for (const auto& kd : g) {
+      int D = std::min(kd.second, 2 * n);
+      if (D < 2 * kd.first) D = 2 * kd.first;
+      PassDesc tmp;
+      double c = 0.0;
+      if (!build_pass(n, b, kd.first, D, lf, cs, &tmp, nullptr, &c)) { ok = false; break; }
+      cost += c;
+      b += kd.first;
+    }
+    if (!ok) continue;
+    if (g.size() < best_passes || cost < best_cost - 1e-9) {
+      best_passes = g.size();
+      best_cost = cost;
+      groups = g;
+    }
+  }
+  if (groups.empty()) {
+    if (err) *err = "no pass plan";
+    return false;
   }
   if ((int)groups.size() > kMaxQubits) {
     if (err) *err = "too many passes";

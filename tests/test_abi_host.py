@@ -54,7 +54,7 @@ def test_argument_errors_return_before_any_launch(L):
     assert L.tpd_decompose(4104, 4, L.TPD_C128) == L.TPD_ERR_MISALIGNED        # 8 mod 16
     assert L.tpd_decompose(4100, 4, L.TPD_C64) == L.TPD_ERR_MISALIGNED         # 4 mod 8
     assert L.tpd_decompose(4096, 4, L.TPD_C128, L.options(precision=2)) == L.TPD_ERR_UNSUPPORTED
-    assert L.tpd_decompose(4096, 4, L.TPD_C64, L.options(precision=3)) == L.TPD_ERR_UNSUPPORTED
+    assert L.tpd_plan_describe(12, L.TPD_C64, L.options(precision=3))[0] >= 2        # complex64 fixed point
     assert L.tpd_decompose(4096, 4, L.TPD_C128, L.options(precision=9)) == L.TPD_ERR_INVALID_ARG
     assert L.tpd_decompose(4096, 4, L.TPD_C128, L.options(tile_bits=20)) == L.TPD_ERR_INVALID_ARG
     assert L.tpd_compose(4096, 8, L.TPD_C128, 0.0) == L.TPD_ERR_INVALID_ARG
@@ -190,7 +190,7 @@ def _to_string_order(flat, n):
 
 
 @pytest.mark.parametrize("n,dtype,prec", [(5, 0, 0), (6, 0, 0), (7, 0, 0), (8, 0, 0), (7, 1, 0), (8, 1, 2),
-                                          (9, 0, 0)])
+                                          (9, 0, 0), (9, 1, 3)])
 def test_plans_emulated_on_cpu_match_oracle(L, n, dtype, prec):
     npass, desc = L.tpd_plan_describe(n, dtype, L.options(precision=prec))
     passes = _parse(desc)

@@ -214,13 +214,19 @@ def test_c64_plain_and_compensated(tpd, n):
     assert e_comp <= g_comp, e_comp
     if n >= 8:
         assert e_comp < e_plain
+    # complex64 block fixed point: each pass sums exactly and rounds once, so
+    # every pass adds at most u32 relative error (normwise): <= P u32 in all
+    fixed = to_string_order(host(tpd.decompose(gpu(A64, torch.complex64), precision="fixed")), n)
+    Pf = max(npass(n, 1, 3), 1)
+    e_fixed = rel_err(fixed, want)
+    assert e_fixed <= Pf * U32 / (1 - Pf * U32), e_fixed
 
 
 @pytest.mark.parametrize("n", [4, 9, 10])
 def test_c64_integer_bit_exact(tpd, n):
     A = synth.int_general(n, seed=6100 + n)
     want = oracle.coeffs_fwht(A)
-    for prec in ("plain", "compensated"):
+    for prec in ("plain", "compensated", "fixed"):
         got = to_string_order(host(tpd.decompose(gpu(A, torch.complex64), precision=prec)), n)
         assert_exact(got.astype(np.complex128), want, prec)
 
@@ -396,3 +402,26 @@ def test_sum_squares_parseval_and_determinism(tpd):
     assert abs(b2 - want) <= 1e-12 * want
     empty = torch.empty(0, dtype=torch.complex128, device="cuda")
     assert float(tpd.sum_squares(empty)) == 0.0
+
+
+@pytest.mark.parametrize("n", [5, 9, 11])
+def test_c64_fixed_rounding_and_extremes(tpd, n):
+    A = synth.general(n, seed=6200 + n).astype(np.complex64)
+    got = to_string_order(host(tpd.decompose(gpu(A, torch.complex64), precision="fixed")), n)
+    want = oracle.coeffs_fwht(A.astype(np.complex128))
+    if npass(n, 1, 3) == 1:
+        # one pass: the exact sum, rounded once to the nearest float -- within the
+        # unit roundoff u32 = 2^-24 relative to the exact weight in each component
+        # (plus the truncation of components far below the tile's largest, < 2^-30 of it)
+        tiny = 2.0 ** -30 * np.max(np.abs(want))
+        for part in (np.real, np.imag):
+            assert np.all(np.abs(part(got) - part(want)) <= U32 * np.abs(part(want)) + tiny)
+    # magnitudes near the ends of the float range
+    for scale in (2.0 ** 100, 2.0 ** -100):
+        B = A * np.float32(scale)
+        g2 = to_string_order(host(tpd.decompose(gpu(B, torch.complex64), precision="fixed")), n)
+        w2 = oracle.coeffs_fwht(B.astype(np.complex128))
+        assert rel_err(g2, w2) <= max(npass(n, 1, 3), 1) * U32 * 1.01
+    # composition of the weights gives A back within the rounding of both directions
+    C = tpd.compose(tpd.decompose(gpu(A, torch.complex64), precision="fixed"), precision="fixed")
+    assert rel_err(host(C), A) <= 2 * max(npass(n, 1, 3), 1) * U32 * 1.01
