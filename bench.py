@@ -366,6 +366,92 @@ def time_partial(tpd, L, torch, stream, n=14, seed=1005):
             "planted_weights_exact": exact}
 
 
+def time_rows(tpd, L, torch, stream, n=14, seed=1005):
+    """The remaining rows of the path, each timed on its own: zero skipping on
+    the planted n=14 Heisenberg chain (dense storage, ~2^n(1+(n-1)/2)
+    nonzeros), the composition (adjoint, scale 2^-n) of dense n=14 weights,
+    and the autograd forward + backward at n=12 (L = sum w_t |c_t|^2)."""
+    from paper_2310_13421_gb300 import synth
+    out = {}
+    J, h = synth.heisenberg_params(n, seed=seed)
+    H = torch.from_numpy(synth.heisenberg(n, J, h)).cuda()
+    work = torch.empty_like(H)
+    wsb = L.tpd_workspace_size(n, L.TPD_C128, L.options(skip_zero=True))
+    ws = torch.empty(max(wsb, 16), dtype=torch.uint8, device="cuda")
+
+    def dec(skip):
+        st = L.tpd_decompose(work.data_ptr(), n, L.TPD_C128, L.options(skip_zero=skip), ws.data_ptr(), wsb,
+                             stream.cuda_stream)
+        assert st == 0, L.status_string(st)
+
+    ms_skip = _event_ms(torch, stream, lambda: dec(True), setup=lambda: work.copy_(H))
+    ms_dense = _event_ms(torch, stream, lambda: dec(False), setup=lambda: work.copy_(H))
+    out["zero_skip_heisenberg"] = {"skip_ms": ms_skip, "dense_ms": ms_dense, "speedup": ms_dense / ms_skip,
+                                   "nonzeros": int(torch.count_nonzero(H).item())}
+    # the same matrix from its nonzero entries (sparse input, Alg. 2 on entries)
+    idx = torch.nonzero(H, as_tuple=True)
+    rows, cols = idx[0].to(torch.int32).contiguous(), idx[1].to(torch.int32).contiguous()
+    vals = H[idx].contiguous()
+    nnz = vals.numel()
+    max_entries = 4 * nnz + 1024
+    wsp = torch.empty(L.tpd_sparse_workspace_size(max_entries), dtype=torch.uint8, device="cuda")
+    strings = torch.empty(max_entries, dtype=torch.int64, device="cuda")
+    weights = torch.empty(max_entries, dtype=torch.complex128, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    stat = torch.zeros(1, dtype=torch.int32, device="cuda")
+
+    def sparse():
+        st = L.tpd_decompose_coo(rows.data_ptr(), cols.data_ptr(), vals.data_ptr(), nnz, n, L.TPD_C128, max_entries,
+                                 strings.data_ptr(), weights.data_ptr(), max_entries, cnt.data_ptr(), stat.data_ptr(),
+                                 wsp.data_ptr(), wsp.numel(), stream.cuda_stream)
+        assert st == 0, L.status_string(st)
+
+    ms_sparse = _event_ms(torch, stream, sparse)
+    terms = synth.heisenberg_terms(n, J, h)
+    want = sorted(synth.string_index(t) for t in terms)
+    k = int(cnt.item())
+    out["sparse_coo_heisenberg"] = {"ms": ms_sparse, "nonzeros": nnz, "strings": k,
+                                    "speedup_vs_dense": ms_dense / ms_sparse,
+                                    "planted_strings_exact": int(stat.item()) == 0 and
+                                    strings[:k].cpu().tolist() == want}
+    del rows, cols, vals, wsp, strings, weights
+    # composition with the adjoint scale on the weights of a dense matrix
+    A = torch.from_numpy(synth.hermitian(n, seed=1002)).cuda()
+    Wt = tpd.decompose(A)
+    del A, H
+    wsc = L.tpd_workspace_size(n, L.TPD_C128, L.options())
+    wsc_t = torch.empty(max(wsc, 16), dtype=torch.uint8, device="cuda")
+
+    def comp():
+        st = L.tpd_compose(work.data_ptr(), n, L.TPD_C128, 2.0 ** -n, L.options(), wsc_t.data_ptr(), wsc,
+                           stream.cuda_stream)
+        assert st == 0, L.status_string(st)
+
+    ms_comp = _event_ms(torch, stream, comp, setup=lambda: work.copy_(Wt))
+    npass = L.tpd_plan_describe(n, L.TPD_C128, L.options())[0]
+    out["compose_adjoint"] = {"ms": ms_comp, "passes": npass,
+                              "hbm_gbs_per_pass": 2 * 16 * 4 ** n / (ms_comp / npass * 1e-3) / 1e9}
+    del Wt, work
+    torch.cuda.empty_cache()
+    # autograd at n = 12: forward (decomposition) and backward (composition)
+    m = 12
+    A12 = torch.from_numpy(synth.hermitian(m, seed=1006)).cuda()
+    wt = torch.rand(4 ** m, dtype=torch.float64, device="cuda",
+                    generator=torch.Generator(device="cuda").manual_seed(1007)).view(2 ** m, 2 ** m)
+    x = A12.clone().requires_grad_(True)
+
+    def fwd_bwd():
+        x.grad = None
+        c = tpd.tpd(x)
+        (wt * c.abs() ** 2).sum().backward()
+
+    ms_ag = _event_ms(torch, stream, fwd_bwd)
+    out["autograd_n12_fwd_bwd"] = {"ms": ms_ag, "note": "includes the torch loss and its gradient ops"}
+    del A12, wt, x
+    torch.cuda.empty_cache()
+    return out
+
+
 def time_helpers(tpd, L, torch, stream, n=14):
     """Memory-bound helpers on the n=14 complex128 matrix: RC -> string layout
     (read + write) and the fp64 sum of squares (read)."""
@@ -533,6 +619,7 @@ def run_ours(args, world, rank, local):
         del w128, p128, p15, w15
         torch.cuda.empty_cache()
         extra["partial_n14_heisenberg"] = time_partial(tpd, L, torch, stream)
+        extra["rows_n14"] = time_rows(tpd, L, torch, stream)
         extra["helpers_n14"] = time_helpers(tpd, L, torch, stream)
     if not args.no_extra and not args.no_batch and not c64:
         extra["batch_4096_n3_10"] = time_batch(tpd, L, torch, stream)

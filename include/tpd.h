@@ -220,6 +220,49 @@ tpd_status tpd_partial_prepare(int n, int dtype, const tpd_options* opt, const u
 tpd_status tpd_decompose_partial(void* A, int n, int dtype, const tpd_options* opt, size_t count, void* workspace,
                                  size_t workspace_bytes, void* weights, void* stream);
 
+/* The paper's output form (Alg. 1 and 2 return the list L of strings with a
+ * nonzero weight): from weights W in RC layout (device, N*N of `dtype`, as a
+ * decomposition leaves them), the entries with |Re w| > tol or |Im w| > tol
+ * (tol = 0: the exact "nonzero" of the paper; NaN is kept), in increasing
+ * base-4 string index s = sum_j t_j 4^(n-j) (t_1 most significant).
+ *   strings   device, capacity uint64: the string indices.
+ *   weights   device, capacity elements of `dtype`: their weights.
+ *   count     device, one uint64: the number of entries (all of them; only
+ *             the first `capacity` are written).
+ *   workspace device, tpd_nonzero_workspace_size(n) bytes, 256-byte aligned.
+ * The order does not depend on scheduling.  Asynchronous on `stream`.
+ * Errors: INVALID_ARG, MISALIGNED, WORKSPACE, CUDA. */
+size_t tpd_nonzero_workspace_size(int n);
+tpd_status tpd_nonzero_list(const void* W, int n, int dtype, double tol, unsigned long long* strings,
+                            void* weights, size_t capacity, unsigned long long* count, void* workspace,
+                            size_t workspace_bytes, void* stream);
+
+/* Sparse input (the cost model of Sec. IV: m nonzero entries, p contributing
+ * strings): the decomposition of a complex128 matrix given by its nonzero
+ * entries, computed level by level as in Alg. 2 -- each entry of a CMW feeds
+ * two entries of the next level's CMWs (Eq. 4), equal positions are summed,
+ * zero sums are dropped (the zero-CMW pruning) -- and returned as the paper's
+ * list L sorted by string index, in the form of tpd_nonzero_list.
+ *   rows, cols  device, nnz ints each: 0 <= r, c < 2^n (duplicates are added).
+ *   values      device, nnz complex128.
+ *   n           1..15.
+ *   max_entries the most entries any level may hold (device memory grows with
+ *               it: about 52 bytes per entry); more sets *status to
+ *               TPD_ERR_WORKSPACE and the list is incomplete.  A level holds
+ *               at most 2x the entries of the one before.
+ *   strings, weights, capacity, count   as tpd_nonzero_list.
+ *   status      device, one unsigned (may be NULL): TPD_OK or TPD_ERR_WORKSPACE.
+ *   workspace   device, tpd_sparse_workspace_size(max_entries) bytes, 256-byte aligned.
+ * Sums are exact (int64 on one binary point for the matrix), each weight is
+ * rounded once; the result does not depend on scheduling.  Enqueued on
+ * `stream` only (no host synchronisation).  C128 only (UNSUPPORTED otherwise).
+ * Errors: INVALID_ARG, UNSUPPORTED, MISALIGNED, WORKSPACE, CUDA. */
+size_t tpd_sparse_workspace_size(size_t max_entries);
+tpd_status tpd_decompose_coo(const int* rows, const int* cols, const void* values, size_t nnz, int n, int dtype,
+                             size_t max_entries, unsigned long long* strings, void* weights, size_t capacity,
+                             unsigned long long* count, unsigned* status, void* workspace, size_t workspace_bytes,
+                             void* stream);
+
 /* Layout conversion, out of place.  RC is the layout every decomposition
  * leaves (see the conventions above); STRING puts the weight of
  * t = (t_1, ..., t_n) at the base-4 index s = sum_j t_j 4^(n-j) (t_1 most

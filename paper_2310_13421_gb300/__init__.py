@@ -11,11 +11,14 @@ The CUDA library ``libtpd.so`` is loaded lazily on first use (the submodule
     TPDFunction / tpd          autograd
     to_string_layout(W)        RC -> base-4 string order (device kernel); from_string_layout inverse
     sum_squares(X)             fp64 sum of |x|^2 on the device (Parseval check)
+    nonzero_list(W)            the paper's list L of (string, weight) with nonzero weight
+    decompose_coo(r, c, v, n)  sparse input: the list L from the nonzero entries (Alg. 2 on entries)
     string_order(n)            RC layout -> string order permutation (host index array)
     build()                    compile libtpd.so in-tree
 """
 __all__ = ["decompose", "compose", "decompose_batched", "compose_batched", "Batch", "Partial", "TPDFunction", "tpd",
-           "string_order", "to_string_layout", "from_string_layout", "sum_squares", "workspace_size", "build"]
+           "string_order", "to_string_layout", "from_string_layout", "sum_squares", "nonzero_list", "decompose_coo",
+           "workspace_size", "build"]
 
 
 def build(force=False, verbose=False):
@@ -25,7 +28,8 @@ def build(force=False, verbose=False):
 
 def __getattr__(name):
     if name in ("decompose", "compose", "decompose_batched", "compose_batched", "Batch", "Partial", "string_order",
-                "to_string_layout", "from_string_layout", "sum_squares", "workspace_size", "make_options"):
+                "to_string_layout", "from_string_layout", "sum_squares", "nonzero_list", "decompose_coo",
+                "workspace_size", "make_options"):
         from . import api
         return getattr(api, name)
     if name in ("TPDFunction", "tpd"):

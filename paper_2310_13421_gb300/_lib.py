@@ -30,7 +30,8 @@ SYMBOLS = (
     "tpd_plan_describe", "tpd_status_string", "tpd_version", "tpd_decompose_noalloc",
     "tpd_tune_set", "tpd_tune_clear", "tpd_batch_status", "tpd_test_hold_batch_waits",
     "tpd_convert_layout", "tpd_sum_squares", "tpd_partial_workspace_size", "tpd_partial_prepare",
-    "tpd_decompose_partial",
+    "tpd_decompose_partial", "tpd_nonzero_workspace_size", "tpd_nonzero_list", "tpd_sparse_workspace_size",
+    "tpd_decompose_coo",
 )
 
 # size of the library's own scratch array used by tpd_decompose_noalloc
@@ -87,6 +88,14 @@ def load(path=None):
         lib.tpd_partial_prepare.restype = i
         lib.tpd_decompose_partial.argtypes = [vp, i, i, op, sz, vp, sz, vp, vp]
         lib.tpd_decompose_partial.restype = i
+        lib.tpd_sparse_workspace_size.argtypes = [sz]
+        lib.tpd_sparse_workspace_size.restype = sz
+        lib.tpd_decompose_coo.argtypes = [vp, vp, vp, sz, i, i, sz, vp, vp, sz, vp, vp, vp, sz, vp]
+        lib.tpd_decompose_coo.restype = i
+        lib.tpd_nonzero_workspace_size.argtypes = [i]
+        lib.tpd_nonzero_workspace_size.restype = sz
+        lib.tpd_nonzero_list.argtypes = [vp, i, i, ctypes.c_double, vp, vp, sz, vp, vp, sz, vp]
+        lib.tpd_nonzero_list.restype = i
         lib.tpd_convert_layout.argtypes = [vp, vp, i, i, i, vp]
         lib.tpd_convert_layout.restype = i
         lib.tpd_sum_squares.argtypes = [vp, sz, i, vp, vp, sz, vp]
@@ -170,6 +179,26 @@ def tpd_partial_prepare(n, dtype, opt, strings, workspace, workspace_bytes, stre
 def tpd_decompose_partial(A_ptr, n, dtype, opt, count, workspace, workspace_bytes, weights, stream=0):
     return int(load().tpd_decompose_partial(A_ptr or None, n, dtype, _opt(opt), count, workspace or None,
                                             workspace_bytes, weights or None, stream or None))
+
+
+def tpd_sparse_workspace_size(max_entries):
+    return int(load().tpd_sparse_workspace_size(max_entries))
+
+
+def tpd_decompose_coo(rows, cols, values, nnz, n, dtype, max_entries, strings, weights, capacity, count, status,
+                      workspace, workspace_bytes, stream=0):
+    return int(load().tpd_decompose_coo(rows or None, cols or None, values or None, nnz, n, dtype, max_entries,
+                                        strings or None, weights or None, capacity, count or None, status or None,
+                                        workspace or None, workspace_bytes, stream or None))
+
+
+def tpd_nonzero_workspace_size(n):
+    return int(load().tpd_nonzero_workspace_size(n))
+
+
+def tpd_nonzero_list(W, n, dtype, tol, strings, weights, capacity, count, workspace, workspace_bytes, stream=0):
+    return int(load().tpd_nonzero_list(W or None, n, dtype, float(tol), strings or None, weights or None, capacity,
+                                       count or None, workspace or None, workspace_bytes, stream or None))
 
 
 def tpd_convert_layout(src, dst, n, dtype, to_string, stream=0):

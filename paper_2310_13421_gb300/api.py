@@ -201,6 +201,69 @@ class Partial:
         return out
 
 
+def decompose_coo(rows, cols, values, n, *, max_entries=None, capacity=None, stream=None):
+    """Pauli weights of a sparse complex128 2^n x 2^n matrix given by its
+    nonzero entries (CUDA tensors rows, cols: int32, values: complex128):
+    the paper's list L as (string indices, weights), sorted by string index.
+    max_entries: entries a level may hold (default 4 * nnz + 1024, doubled
+    and retried while too small); synchronises to read the count."""
+    for t in (rows, cols, values):
+        if not t.is_cuda or not t.is_contiguous():
+            raise ValueError("rows, cols, values must be contiguous CUDA tensors")
+    if rows.dtype != torch.int32 or cols.dtype != torch.int32 or values.dtype != torch.complex128:
+        raise TypeError("rows, cols: int32; values: complex128")
+    nnz = values.numel()
+    dev = values.device
+    cap_entries = int(max_entries) if max_entries else 4 * nnz + 1024
+    count = torch.zeros(1, dtype=torch.int64, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    while True:
+        ws = torch.empty(L.tpd_sparse_workspace_size(cap_entries), dtype=torch.uint8, device=dev)
+        cap = int(capacity) if capacity is not None else cap_entries
+        strings = torch.empty(max(cap, 1), dtype=torch.int64, device=dev)
+        weights = torch.empty(max(cap, 1), dtype=torch.complex128, device=dev)
+        with torch.cuda.device(dev):
+            st = L.tpd_decompose_coo(rows.data_ptr(), cols.data_ptr(), values.data_ptr(), nnz, int(n), L.TPD_C128,
+                                     cap_entries, strings.data_ptr(), weights.data_ptr(), cap, count.data_ptr(),
+                                     status.data_ptr(), ws.data_ptr(), ws.numel(), _stream(stream))
+        _raise(st, "tpd_decompose_coo")
+        if int(status.item()) == 0:
+            k = min(int(count.item()), cap)
+            return strings[:k], weights[:k]
+        if max_entries:
+            raise L.TPDError(L.TPD_ERR_WORKSPACE, "tpd_decompose_coo (max_entries too small)")
+        cap_entries *= 2
+
+
+def nonzero_list(W, *, tol=0.0, capacity=None, stream=None):
+    """The paper's list L: (string indices, weights) of the weights in W (RC
+    layout) with |re| > tol or |im| > tol, in increasing string index.
+    Synchronises to size the result unless `capacity` is given."""
+    _check_device(W)
+    n = _qubits(W)
+    code = _dtype_code(W)
+    ws = torch.empty(L.tpd_nonzero_workspace_size(n), dtype=torch.uint8, device=W.device)
+    count = torch.zeros(1, dtype=torch.int64, device=W.device)
+    if capacity is None:
+        cap = 0
+        with torch.cuda.device(W.device):
+            st = L.tpd_nonzero_list(W.data_ptr(), n, code, tol, 0, 0, 0, count.data_ptr(), ws.data_ptr(),
+                                    ws.numel(), _stream(stream))
+        _raise(st, "tpd_nonzero_list")
+        cap = int(count.item())
+    else:
+        cap = int(capacity)
+    strings = torch.empty(max(cap, 1), dtype=torch.int64, device=W.device)
+    weights = torch.empty(max(cap, 1), dtype=W.dtype, device=W.device)
+    with torch.cuda.device(W.device):
+        st = L.tpd_nonzero_list(W.data_ptr(), n, code, tol, strings.data_ptr(), weights.data_ptr(), cap,
+                                count.data_ptr(), ws.data_ptr(), ws.numel(), _stream(stream))
+    _raise(st, "tpd_nonzero_list")
+    if capacity is None:
+        return strings[:cap], weights[:cap]
+    return strings, weights, count
+
+
 def to_string_layout(W, *, stream=None):
     """Weights in STRING layout (base-4 string index, t_1 most significant) as
     a flat tensor, converted from the RC layout on the device."""

@@ -19,7 +19,8 @@ LIB = os.path.join(BUILD, "libtpd.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 CU_SOURCES = ["tpd_kernels_fixed_dec.cu", "tpd_kernels_fixed_com.cu", "tpd_kernels_batch_fixed.cu",
-              "tpd_kernels_batch_ieee.cu", "tpd_kernels_c128.cu", "tpd_kernels_c64.cu", "tpd_noalloc.cu", "tpd_layout.cu"]
+              "tpd_kernels_batch_ieee.cu", "tpd_kernels_c128.cu", "tpd_kernels_c64.cu", "tpd_noalloc.cu", "tpd_layout.cu",
+              "tpd_sparse.cu"]
 CPP_SOURCES = ["tpd_api.cpp", "tpd_planner.cpp"]
 
 

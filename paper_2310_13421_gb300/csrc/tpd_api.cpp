@@ -662,6 +662,52 @@ tpd_status tpd_decompose_partial(void* A, int n, int dtype, const tpd_options* o
   return TPD_OK;
 }
 
+size_t tpd_sparse_workspace_size(size_t max_entries) { return sparse_workspace_bytes(max_entries); }
+
+tpd_status tpd_decompose_coo(const int* rows, const int* cols, const void* values, size_t nnz, int n, int dtype,
+                             size_t max_entries, unsigned long long* strings, void* weights, size_t capacity,
+                             unsigned long long* count, unsigned* status, void* workspace, size_t workspace_bytes,
+                             void* stream) {
+  if (dtype != TPD_C128) return TPD_ERR_UNSUPPORTED;
+  if (n < 1 || n > 15 || count == nullptr || max_entries == 0) return TPD_ERR_INVALID_ARG;
+  if (nnz > 0 && (rows == nullptr || cols == nullptr || values == nullptr)) return TPD_ERR_INVALID_ARG;
+  if (capacity > 0 && (strings == nullptr || weights == nullptr)) return TPD_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(values) % 16 || reinterpret_cast<uintptr_t>(weights) % 16 ||
+      reinterpret_cast<uintptr_t>(strings) % 8 || reinterpret_cast<uintptr_t>(count) % 8 ||
+      reinterpret_cast<uintptr_t>(rows) % 4 || reinterpret_cast<uintptr_t>(cols) % 4 ||
+      reinterpret_cast<uintptr_t>(status) % 4)
+    return TPD_ERR_MISALIGNED;
+  if (workspace == nullptr || workspace_bytes < sparse_workspace_bytes(max_entries)) return TPD_ERR_WORKSPACE;
+  if (reinterpret_cast<uintptr_t>(workspace) % 256) return TPD_ERR_MISALIGNED;
+  if (launch_sparse(rows, cols, values, nnz, n, max_entries, strings, weights, capacity, count, workspace, status,
+                    static_cast<cudaStream_t>(stream)) != cudaSuccess)
+    return TPD_ERR_CUDA;
+  return TPD_OK;
+}
+
+size_t tpd_nonzero_workspace_size(int n) {
+  if (n < 1 || n > kMaxQubits) return 0;
+  return nonzero_workspace_bytes(n);
+}
+
+tpd_status tpd_nonzero_list(const void* W, int n, int dtype, double tol, unsigned long long* strings,
+                            void* weights, size_t capacity, unsigned long long* count, void* workspace,
+                            size_t workspace_bytes, void* stream) {
+  if (n < 1 || n > kMaxQubits || (dtype != TPD_C128 && dtype != TPD_C64)) return TPD_ERR_INVALID_ARG;
+  if (W == nullptr || count == nullptr || !(tol >= 0.0) || (capacity > 0 && (strings == nullptr || weights == nullptr)))
+    return TPD_ERR_INVALID_ARG;
+  const size_t eb = dtype == TPD_C128 ? 16 : 8;
+  if (reinterpret_cast<uintptr_t>(W) % eb || reinterpret_cast<uintptr_t>(weights) % eb ||
+      reinterpret_cast<uintptr_t>(strings) % 8 || reinterpret_cast<uintptr_t>(count) % 8)
+    return TPD_ERR_MISALIGNED;
+  if (workspace == nullptr || workspace_bytes < nonzero_workspace_bytes(n)) return TPD_ERR_WORKSPACE;
+  if (reinterpret_cast<uintptr_t>(workspace) % 256) return TPD_ERR_MISALIGNED;
+  if (launch_nonzero(W, n, (int)eb, tol, strings, weights, capacity, count, workspace,
+                     static_cast<cudaStream_t>(stream)) != cudaSuccess)
+    return TPD_ERR_CUDA;
+  return TPD_OK;
+}
+
 tpd_status tpd_convert_layout(const void* src, void* dst, int n, int dtype, int to_string, void* stream) {
   if (n < 1 || n > kMaxQubits || (dtype != TPD_C128 && dtype != TPD_C64)) return TPD_ERR_INVALID_ARG;
   if (src == nullptr || dst == nullptr || (to_string != 0 && to_string != 1)) return TPD_ERR_INVALID_ARG;

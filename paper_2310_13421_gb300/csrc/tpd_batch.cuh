@@ -118,8 +118,9 @@ __device__ __forceinline__ void batch_pass_tile(const BatchSeg& sg, int p, const
   }
 }
 
-// 256 threads; dynamic shared memory: 2^12 x 16 bytes + 256 (a D = 12 tile or
-// a whole n <= 6 matrix, plus reduction slots).
+// 256 threads; dynamic shared memory: 2^12 x 16 bytes + 256 + 2^kMaxPrevBits
+// ints (a D = 12 tile or a whole n <= 6 matrix, reduction slots, gathered
+// binary points).
 template <class A, bool kDec>
 __global__ void __launch_bounds__(256, 2) k_batch(const __grid_constant__ BatchParams bp) {
   using Store = typename A::Store;
@@ -192,7 +193,7 @@ __global__ void __launch_bounds__(256, 2) k_batch(const __grid_constant__ BatchP
 
 template <class A, bool kDec>
 cudaError_t launch_batch_t(const BatchParams& bp, int* grid_out, cudaStream_t s) {
-  const size_t smem = ((size_t)16 << 12) + 256;
+  const size_t smem = ((size_t)16 << 12) + 256 + (sizeof(int) << kMaxPrevBits);
   auto kfn = k_batch<A, kDec>;
   cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

@@ -19,7 +19,10 @@ template <class A, bool kDec>
 cudaError_t launch_pass_t(const PassDesc& pd, const PassArgs& args, long long ntiles_total, cudaStream_t s) {
   const int threads = 1 << (pd.D - kRegBits);
   const size_t vbytes = A::kFixed ? 16 : sizeof(typename A::V);
-  const size_t smem = ((size_t)1 << pd.D) * vbytes + 256;
+  // exchange area, reduction slots, and (fixed point reading int64 sums) the
+  // gathered binary points -- the first pass keeps its occupancy without them
+  const size_t smem =
+      ((size_t)1 << pd.D) * vbytes + 256 + ((A::kFixed && args.q_in) ? sizeof(int) << kMaxPrevBits : 0);
   PassKernel kfn;
   if constexpr (A::kFixed) {
     switch ((args.q_in ? kRoleIntIn : 0) | (args.q_out ? kRoleIntOut : 0)) {
@@ -55,7 +58,8 @@ cudaError_t launch_small_t(const SmallArgs& args, int blocks, int n_max, cudaStr
 template <bool kDec>
 cudaError_t launch_pass_pipe_t(const PassDesc& pd, const PassArgs& args, int nsm, cudaStream_t s) {
   const int threads = 1 << (pd.D - kRegBits);
-  const size_t smem = ((size_t)32 << pd.D) + 256;   // two tile buffers + reduction slots
+  // two tile buffers, reduction slots, gathered binary points (passes reading int64 sums)
+  const size_t smem = ((size_t)32 << pd.D) + 256 + (args.q_in ? sizeof(int) << kMaxPrevBits : 0);
   PassKernel kfn;
   switch ((args.q_in ? kRoleIntIn : 0) | (args.q_out ? kRoleIntOut : 0)) {
     case 0: kfn = k_pass_pipe<kDec, 0>; break;

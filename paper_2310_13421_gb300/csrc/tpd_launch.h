@@ -123,6 +123,22 @@ constexpr int kCtrlDone = 4;
 // Persistent batched kernel for an arithmetic: `grid` CTAs of 256 threads.
 cudaError_t launch_batch(int arith, bool dec, const BatchParams& bp, int* grid_out, cudaStream_t s);
 
+// Nonzero weights in string order (|re| > tol or |im| > tol; NaN kept): the
+// first `capacity` go to strings / weights, the number of all to *total.
+size_t nonzero_workspace_bytes(int n);
+cudaError_t launch_nonzero(const void* W, int n, int elem_bytes, double tol, unsigned long long* strings,
+                           void* weights, unsigned long long capacity, unsigned long long* total, void* ws,
+                           cudaStream_t s);
+
+// Sparse (COO, complex128) decomposition into the list of nonzero weights,
+// sorted by string index; max_entries bounds the live entries of a level
+// (*status = 4 if exceeded).
+size_t sparse_workspace_bytes(unsigned long long max_entries);
+cudaError_t launch_sparse(const int* rows, const int* cols, const void* vals, unsigned long long m, int n,
+                          unsigned long long max_entries, unsigned long long* strings, void* weights,
+                          unsigned long long capacity, unsigned long long* count, void* ws, unsigned* status,
+                          cudaStream_t s);
+
 // out[i] = mat[pos[i]] for i < count (elements of elem_bytes).
 cudaError_t launch_gather(const void* mat, const unsigned long long* pos, unsigned long long count, int elem_bytes,
                           void* out, cudaStream_t s);

@@ -146,7 +146,136 @@ __global__ void __launch_bounds__(256) k_gather(const T* __restrict__ mat, const
   if (i < count) out[i] = mat[pos[i]];
 }
 
+// ---------------------------------------------------------------- nonzero list
+//
+// The paper's output form (Alg. 1/2: the list L of strings with nonzero
+// weight), in string order.  Blocks of 256 consecutive string indices (the
+// blocks of k_layout) count their entries, one CTA turns the counts into
+// offsets, and the blocks write their entries at those offsets: the order is
+// the string order, independent of scheduling.
+template <class T>
+__device__ __forceinline__ bool keep(const T& w, double tol) {
+  const double re = w.x, im = w.y;
+  return !(fabs(re) <= tol && fabs(im) <= tol);            // NaN is kept
+}
+
+// element of the CTA's block held by this thread, in string order (s = s_base + tid)
+template <class T>
+__device__ __forceinline__ T string_element(const T* __restrict__ W, int n, int k, uint64_t b, uint32_t tid,
+                                            T* tile) {
+  const uint32_t K = 1u << k;
+  const uint32_t ch = compact16((uint32_t)b) | (compact16((uint32_t)(b >> 32)) << 16);
+  const uint32_t rh = compact16((uint32_t)(b >> 1)) | (compact16((uint32_t)(b >> 33)) << 16);
+  const uint64_t N = 1ull << n;
+  const uint64_t rc_base = ((uint64_t)rh << k) * N + ((uint64_t)ch << k);
+  const uint32_t rl = tid >> k, cl = tid & (K - 1);
+  const uint32_t sl = spread16(cl) | (spread16(rl) << 1);
+  tile[sl] = W[rc_base + (uint64_t)rl * N + cl];              // coalesced RC read
+  __syncthreads();
+  return tile[tid];
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_nz_count(const T* __restrict__ W, int n, int k, double tol,
+                                                  unsigned* __restrict__ counts) {
+  __shared__ T tile[256];
+  const uint64_t b = blockIdx.x + (uint64_t)blockIdx.y * gridDim.x;
+  const T w = string_element(W, n, k, b, threadIdx.x, tile);
+  const int c = __syncthreads_count(keep(w, tol));
+  if (threadIdx.x == 0) counts[b] = (unsigned)c;
+}
+
+// exclusive scan of nb counts into offsets (one CTA of 1024 threads), total into *total
+__global__ void __launch_bounds__(1024) k_nz_scan(const unsigned* __restrict__ counts, uint64_t nb,
+                                                  unsigned long long* __restrict__ offsets,
+                                                  unsigned long long* __restrict__ total) {
+  __shared__ unsigned long long part[1024];
+  const uint64_t per = (nb + 1023) / 1024;
+  const uint64_t lo = threadIdx.x * per, hi = lo + per < nb ? lo + per : nb;
+  unsigned long long sum = 0;
+  for (uint64_t i = lo; i < hi; ++i) sum += counts[i];
+  part[threadIdx.x] = sum;
+  __syncthreads();
+  for (int d = 1; d < 1024; d <<= 1) {                      // inclusive scan of the chunk sums
+    const unsigned long long v = threadIdx.x >= (unsigned)d ? part[threadIdx.x - d] : 0ull;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  unsigned long long run = threadIdx.x ? part[threadIdx.x - 1] : 0ull;
+  for (uint64_t i = lo; i < hi; ++i) { offsets[i] = run; run += counts[i]; }
+  if (threadIdx.x == 1023) *total = part[1023];
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_nz_write(const T* __restrict__ W, int n, int k, double tol,
+                                                  const unsigned long long* __restrict__ offsets,
+                                                  unsigned long long capacity,
+                                                  unsigned long long* __restrict__ strings, T* __restrict__ weights) {
+  __shared__ T tile[256];
+  __shared__ unsigned warp_base[8];
+  const uint64_t b = blockIdx.x + (uint64_t)blockIdx.y * gridDim.x;
+  const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const T w = string_element(W, n, k, b, tid, tile);
+  const bool kp = keep(w, tol);
+  // blocks of n < 3 qubits have fewer than 32 threads
+  const unsigned active = blockDim.x >= 32 ? 0xffffffffu : ((1u << blockDim.x) - 1u);
+  const unsigned ball = __ballot_sync(active, kp);
+  if (lane == 0) warp_base[warp] = __popc(ball);
+  __syncthreads();
+  if (tid == 0) {
+    unsigned acc = 0;
+    for (int i = 0; i < (int)((blockDim.x + 31) >> 5); ++i) {
+      const unsigned c = warp_base[i];
+      warp_base[i] = acc;
+      acc += c;
+    }
+  }
+  __syncthreads();
+  if (kp) {
+    const unsigned long long pos = offsets[b] + warp_base[warp] + __popc(ball & ((1u << lane) - 1u));
+    if (pos < capacity) {
+      strings[pos] = (b << (2 * k)) + tid;
+      weights[pos] = w;
+    }
+  }
+}
+
+template <class T>
+cudaError_t launch_nonzero_t(const void* W, int n, double tol, unsigned long long* strings, void* weights,
+                             unsigned long long capacity, unsigned long long* total, void* ws, cudaStream_t s) {
+  const int k = n < 4 ? n : 4;
+  const uint64_t blocks = 1ull << (2 * (n - k));
+  const unsigned gx = blocks > 65536 ? 65536u : (unsigned)blocks;
+  const unsigned gy = (unsigned)(blocks / gx);
+  unsigned* counts = static_cast<unsigned*>(ws);
+  unsigned long long* offsets =
+      reinterpret_cast<unsigned long long*>(static_cast<char*>(ws) + ((blocks * 4 + 255) & ~255ull));
+  const T* w = static_cast<const T*>(W);
+  k_nz_count<T><<<dim3(gx, gy), 1u << (2 * k), 0, s>>>(w, n, k, tol, counts);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_nz_scan<<<1, 1024, 0, s>>>(counts, blocks, offsets, total);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_nz_write<T><<<dim3(gx, gy), 1u << (2 * k), 0, s>>>(w, n, k, tol, offsets, capacity, strings,
+                                                      static_cast<T*>(weights));
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+size_t nonzero_workspace_bytes(int n) {
+  const int k = n < 4 ? n : 4;
+  const uint64_t blocks = 1ull << (2 * (n - k));
+  return ((blocks * 4 + 255) & ~255ull) + blocks * 8;
+}
+
+cudaError_t launch_nonzero(const void* W, int n, int elem_bytes, double tol, unsigned long long* strings,
+                           void* weights, unsigned long long capacity, unsigned long long* total, void* ws,
+                           cudaStream_t s) {
+  return elem_bytes == 16 ? launch_nonzero_t<double2>(W, n, tol, strings, weights, capacity, total, ws, s)
+                          : launch_nonzero_t<float2>(W, n, tol, strings, weights, capacity, total, ws, s);
+}
 
 cudaError_t launch_gather(const void* mat, const unsigned long long* pos, unsigned long long count, int elem_bytes,
                           void* out, cudaStream_t s) {

@@ -391,22 +391,32 @@ __device__ __forceinline__ void fixed_tile(const PassDesc& pd, const PassArgs& a
     longlong2 raw[kElems];
     if (inbuf) load_tile_smem(pd, inbuf, lane, warp, raw);
     else load_tile<kCg>(pd, matp, base, lane, warp, raw);
+    // The tile's elements come from 2^prev_nb previous tiles (<= 2^kMaxPrevBits):
+    // their binary points are loaded once each into shared memory (qs), and
+    // each element finds its own there by its combination index.
     const Stage& s0 = pd.st[0];
-    long long pt = pbase;
+    int* qs = red + 64;
+    int qmax = kQValidMin, ieee = 0;
+    {
+      const int nq = 1 << pd.prev_nb, nthr = 32 * nwarps;
+      for (int j = lane + 32 * warp; j < nq; j += nthr) {
+        long long idx = pbase;
+        for (int k = 0; k < pd.prev_nb; ++k)
+          if ((j >> k) & 1) idx += pd.prev_cw[k];
+        const int q = ld_in<kCg>(q_in + idx);
+        qs[j] = q;
+        qmax = max(qmax, q);
+        ieee |= (q == kQIeee);
+      }
+    }
+    int qj = 0;
 #pragma unroll
     for (int i = 0; i < kLaneBits; ++i)
-      if ((lane >> i) & 1) pt += pd.prev_w[s0.lane[i]];
+      if ((lane >> i) & 1) qj += pd.prev_qw[s0.lane[i]];
     for (int i = 0; i < pd.D - kMinTileBits; ++i)
-      if ((warp >> i) & 1) pt += pd.prev_w[s0.warp[i]];
-    const int p0 = pd.prev_w[s0.reg[0]], p1 = pd.prev_w[s0.reg[1]], p2 = pd.prev_w[s0.reg[2]],
-              p3 = pd.prev_w[s0.reg[3]];
-    int qmax = kQValidMin, ieee = 0;
-#pragma unroll
-    for (int e = 0; e < kElems; ++e) {
-      const int q = ld_in<kCg>(q_in + pt + reg_off(e, p0, p1, p2, p3));
-      qmax = max(qmax, q);
-      ieee |= (q == kQIeee);
-    }
+      if ((warp >> i) & 1) qj += pd.prev_qw[s0.warp[i]];
+    const int j0 = pd.prev_qw[s0.reg[0]], j1 = pd.prev_qw[s0.reg[1]], j2 = pd.prev_qw[s0.reg[2]],
+              j3 = pd.prev_qw[s0.reg[3]];
     // kQIeee sits below kQValidMin, so it never wins the max
     qmax = __reduce_max_sync(kFull, qmax);
     ieee = __reduce_or_sync(kFull, ieee);
@@ -425,7 +435,7 @@ __device__ __forceinline__ void fixed_tile(const PassDesc& pd, const PassArgs& a
     qin = qmax + pd.K;
 #pragma unroll
     for (int e = 0; e < kElems; ++e) {
-      const int q = ld_in<kCg>(q_in + pt + reg_off(e, p0, p1, p2, p3));   // again, from L1 / L2
+      const int q = qs[qj + reg_off(e, j0, j1, j2, j3)];   // written before the barrier above
       if (q_is_valid(q)) {
         const unsigned sh = (unsigned)(qin - q);
         v[e].re = TPD_ALIGN(raw[e].x, sh);

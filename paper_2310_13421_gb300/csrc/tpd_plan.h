@@ -70,7 +70,19 @@ struct PassDesc {
   int32_t has_prev;
   int32_t prev_w[kMaxTileBits];
   int64_t prev_rest_w[2 * kMaxQubits];
+  // The tile's elements come from 2^prev_nb previous tiles: those that differ
+  // in the prev_nb tile bits i with prev_w[i] != 0.  prev_qw[i] numbers these
+  // combinations (1 << rank of bit i among them, 0 for the other bits) and
+  // prev_cw[k] is the previous-tile id step of the k-th of them.
+  int32_t prev_nb;
+  int32_t prev_qw[kMaxTileBits];
+  int32_t prev_cw[kMaxTileBits];
 };
+
+// Binary points of previous tiles gathered into shared memory by a pass that
+// reads int64 sums (prev_nb <= kMaxPrevBits; more falls back to per-element
+// loads from global memory).
+constexpr int kMaxPrevBits = 10;
 
 // A whole-matrix plan: one pass per group of levels.
 struct Plan {

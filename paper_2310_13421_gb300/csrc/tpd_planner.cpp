@@ -199,7 +199,8 @@ void set_next(PassDesc* cur, const PassDesc& nxt) {
 }
 
 // Tile id in the previous pass of an element of `cur`, as linear weights.
-void set_prev(PassDesc* cur, const PassDesc& prv) {
+// false if the tile's elements came from more than 2^kMaxPrevBits tiles.
+bool set_prev(PassDesc* cur, const PassDesc& prv) {
   std::vector<int> rest_prev(prv.rest_gbit, prv.rest_gbit + prv.nrest);
   auto w = [&](int g) -> long long {
     auto it = std::find(rest_prev.begin(), rest_prev.end(), g);
@@ -209,6 +210,17 @@ void set_prev(PassDesc* cur, const PassDesc& prv) {
   cur->has_prev = 1;
   for (int i = 0; i < cur->D; ++i) cur->prev_w[i] = (int32_t)w(cur->gbit[i]);
   for (int j = 0; j < cur->nrest; ++j) cur->prev_rest_w[j] = w(cur->rest_gbit[j]);
+  cur->prev_nb = 0;
+  for (int i = 0; i < cur->D; ++i) {
+    cur->prev_qw[i] = 0;
+    if (cur->prev_w[i] != 0) {
+      cur->prev_qw[i] = 1 << cur->prev_nb;
+      cur->prev_cw[cur->prev_nb++] = cur->prev_w[i];
+    }
+  }
+  // every tile holds the three lowest column bits, so at most D - 3 <= 10
+  // tile bits select among previous tiles
+  return cur->prev_nb <= kMaxPrevBits;
 }
 
 }  // namespace
@@ -303,7 +315,11 @@ bool build_plan(int n, int dtype, int precision, int tile_bits_opt, int max_leve
     b += K;
   }
   for (int p = 0; p + 1 < plan->npass; ++p) set_next(&plan->pass[p], plan->pass[p + 1]);
-  for (int p = 1; p < plan->npass; ++p) set_prev(&plan->pass[p], plan->pass[p - 1]);
+  for (int p = 1; p < plan->npass; ++p)
+    if (!set_prev(&plan->pass[p], plan->pass[p - 1])) {
+      if (err) *err = "a tile reads from too many previous tiles";
+      return false;
+    }
   // Occupancy: the fixed point's first pass (double -> int64, long integer
   // chains, few live values) gains from a third CTA per SM at a smaller
   // register budget; the others keep two (measured on GB300: the last pass

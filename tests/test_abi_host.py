@@ -87,6 +87,18 @@ def test_argument_errors_return_before_any_launch(L):
     assert L.tpd_partial_prepare(4, L.TPD_C128, None, [256], 4096, 1 << 20) == L.TPD_ERR_INVALID_ARG  # >= 4^n
     assert L.tpd_decompose_partial(0, 4, L.TPD_C128, None, 2, 4096, 1 << 20, 8192) == L.TPD_ERR_INVALID_ARG
     assert L.tpd_decompose_partial(4096, 4, L.TPD_C128, None, 2, 4096, 1 << 20, 8200) == L.TPD_ERR_MISALIGNED
+    # sparse input
+    assert L.tpd_sparse_workspace_size(1000) > 1000 * 40
+    assert L.tpd_decompose_coo(4096, 4096, 4096, 1, 16, L.TPD_C128, 10, 0, 0, 0, 8192, 0, 1 << 20, 1 << 20) == \
+        L.TPD_ERR_INVALID_ARG
+    assert L.tpd_decompose_coo(4096, 4096, 4096, 1, 8, L.TPD_C64, 10, 0, 0, 0, 8192, 0, 1 << 20, 1 << 20) == \
+        L.TPD_ERR_UNSUPPORTED
+    assert L.tpd_decompose_coo(4096, 4096, 4096, 1, 8, L.TPD_C128, 10, 0, 0, 0, 8192, 0, 0, 0) == L.TPD_ERR_WORKSPACE
+    # nonzero list
+    assert L.tpd_nonzero_workspace_size(0) == 0 and L.tpd_nonzero_workspace_size(14) > 4 ** 10 * 4
+    assert L.tpd_nonzero_list(4096, 4, L.TPD_C128, 0.0, 0, 0, 0, 8192, 0, 0) == L.TPD_ERR_WORKSPACE
+    assert L.tpd_nonzero_list(4096, 4, L.TPD_C128, -1.0, 0, 0, 0, 8192, 1 << 20, 4096) == L.TPD_ERR_INVALID_ARG
+    assert L.tpd_nonzero_list(4096, 4, L.TPD_C128, 0.0, 0, 0, 5, 8192, 1 << 20, 4096) == L.TPD_ERR_INVALID_ARG
     # layout conversion and sums of squares
     assert L.tpd_convert_layout(4096, 1 << 20, 0, L.TPD_C128, 1) == L.TPD_ERR_INVALID_ARG      # n = 0
     assert L.tpd_convert_layout(4096, 4096 + 256, 4, L.TPD_C128, 1) == L.TPD_ERR_INVALID_ARG   # overlap

@@ -425,3 +425,27 @@ def test_c64_fixed_rounding_and_extremes(tpd, n):
     # composition of the weights gives A back within the rounding of both directions
     C = tpd.compose(tpd.decompose(gpu(A, torch.complex64), precision="fixed"), precision="fixed")
     assert rel_err(host(C), A) <= 2 * max(npass(n, 1, 3), 1) * U32 * 1.01
+
+
+def test_nonzero_list_is_the_papers_list(tpd):
+    # planted Hamiltonians: exactly the planted strings, in string order, exact weights
+    for n in (2, 5, 10):
+        J, h = synth.heisenberg_params(n, seed=9500 + n)
+        terms = synth.heisenberg_terms(n, J, h)
+        want = sorted((synth.string_index(t), v) for t, v in terms.items())
+        s, w = tpd.nonzero_list(tpd.decompose(gpu(synth.heisenberg(n, J, h))))
+        assert host(s).tolist() == [k for k, _ in want]
+        assert_exact(host(w), np.array([v for _, v in want], dtype=np.complex128))
+    # a threshold, complex64, and a capacity smaller than the list
+    n = 6
+    A = synth.general(n, seed=9510).astype(np.complex64)
+    W = tpd.decompose(gpu(A, torch.complex64))
+    full = to_string_order(host(W), n)
+    tol = 0.05
+    keep = np.flatnonzero((np.abs(full.real) > tol) | (np.abs(full.imag) > tol))
+    s, w = tpd.nonzero_list(W, tol=tol)
+    assert host(s).tolist() == keep.tolist()
+    assert_exact(host(w), full[keep])
+    s2, w2, cnt = tpd.nonzero_list(W, tol=tol, capacity=10)
+    assert int(host(cnt)[0]) == keep.size
+    assert host(s2).tolist() == keep[:10].tolist()
