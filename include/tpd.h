@@ -94,8 +94,19 @@ typedef struct {
   void** pass_events; /* profiling, may be NULL: num_events cudaEvent_t handles
                        (created by the caller); tpd_decompose / tpd_compose
                        record event 0 before the first pass and event p+1 after
-                       pass p, on `stream`, for p < num_events - 1 */
+                       pass p, on `stream`, for p < num_events - 1 (passes run
+                       in L2 chunks record their events together after the last
+                       of them) */
   int num_events;
+  int l2_chunk_mb;  /* single matrices: 0 = off (default), > 0 = chunk size in MB.
+                       The first passes whose tiles together leave global bits
+                       free run chunk by chunk (the elements agreeing on those
+                       bits), so a chunk stays in the GPU's L2 from one pass to
+                       the next and HBM sees one read and one write for all of
+                       them.  On GB300 the many smaller launches cost more than
+                       the traffic saves (n = 14: 6.2 ms with 64 MB chunks
+                       against 5.2 ms), hence off by default.  Not with
+                       skip_zero, partial masks or variant 2. */
 } tpd_options;
 
 /* Zero-initialised defaults (precision DEFAULT, no skip, planner tiles). */

@@ -43,7 +43,8 @@ TPD_SUMSQ_WORKSPACE_BYTES = 8192
 class tpd_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("skip_zero", ctypes.c_int),
                 ("tile_bits", ctypes.c_int), ("max_levels", ctypes.c_int), ("variant", ctypes.c_int),
-                ("pass_events", ctypes.POINTER(ctypes.c_void_p)), ("num_events", ctypes.c_int)]
+                ("pass_events", ctypes.POINTER(ctypes.c_void_p)), ("num_events", ctypes.c_int),
+                ("l2_chunk_mb", ctypes.c_int)]
 
 
 class TPDError(RuntimeError):
@@ -124,9 +125,11 @@ def load(path=None):
         return lib
 
 
-def options(precision=TPD_PREC_DEFAULT, skip_zero=False, tile_bits=0, max_levels=0, variant=0, pass_events=None):
+def options(precision=TPD_PREC_DEFAULT, skip_zero=False, tile_bits=0, max_levels=0, variant=0, pass_events=None,
+            l2_chunk_mb=0):
     """tpd_options; pass_events: sequence of cudaEvent_t handles (ints) for the profiling hook."""
-    o = tpd_options(int(precision), int(bool(skip_zero)), int(tile_bits), int(max_levels), int(variant), None, 0)
+    o = tpd_options(int(precision), int(bool(skip_zero)), int(tile_bits), int(max_levels), int(variant), None, 0,
+                    int(l2_chunk_mb))
     if pass_events:
         arr = (ctypes.c_void_p * len(pass_events))(*[int(e) for e in pass_events])
         o.pass_events = ctypes.cast(arr, ctypes.POINTER(ctypes.c_void_p))

@@ -54,10 +54,10 @@ def _raise(st, what):
         raise L.TPDError(st, what)
 
 
-def make_options(precision=None, skip_zero=False, tile_bits=0, max_levels=0, variant=0):
+def make_options(precision=None, skip_zero=False, tile_bits=0, max_levels=0, variant=0, l2_chunk_mb=0):
     if isinstance(precision, str) or precision is None:
         precision = _PREC[precision]
-    return L.options(precision, skip_zero, tile_bits, max_levels, variant)
+    return L.options(precision, skip_zero, tile_bits, max_levels, variant, l2_chunk_mb=l2_chunk_mb)
 
 
 def workspace_size(n, dtype, **kw):
@@ -66,13 +66,13 @@ def workspace_size(n, dtype, **kw):
 
 
 def decompose(A, *, inplace=False, precision=None, skip_zero=False, tile_bits=0, max_levels=0, variant=0,
-              workspace=None, stream=None):
+              l2_chunk_mb=0, workspace=None, stream=None):
     """Pauli weights w_t = 2^-n tr(sigma^t A) of a 2^n x 2^n CUDA matrix, in RC layout."""
     _check_device(A)
     n = _qubits(A)
     code = _dtype_code(A)
     out = A if inplace else A.clone()
-    opt = make_options(precision, skip_zero, tile_bits, max_levels, variant)
+    opt = make_options(precision, skip_zero, tile_bits, max_levels, variant, l2_chunk_mb)
     wsb = L.tpd_workspace_size(n, code, opt)
     ws = workspace
     if wsb and (ws is None or ws.numel() < wsb):

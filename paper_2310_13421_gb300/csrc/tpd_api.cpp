@@ -89,6 +89,7 @@ const Plan* get_plan(int n, int dtype, int prec, const tpd_options* opt) {
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
+
 // Workspace of one matrix's plan:
 //   zero-skip flags: one byte per tile of every pass after the first (skip only)
 //   binary points:   one int per tile of every pass but the last (fixed point only)
@@ -158,6 +159,49 @@ void record_event(const tpd_options* opt, int k, cudaStream_t s) {
     cudaEventRecord(static_cast<cudaEvent_t>(opt->pass_events[k]), s);
 }
 
+// L2 chunking of a single matrix's first passes: F passes (0 = none) and the
+// global bits fixed per chunk (ascending).  The union U of the first F
+// passes' tile bits leaves 2n - |U| bits outside every one of their tiles;
+// all but the lowest g of them are fixed per chunk, g chosen so a chunk
+// (2^(|U| + g) elements) fits the budget.  F is the most passes whose chunk
+// still fits; chunking pays only when F >= 2.
+struct L2Chunks {
+  int F = 0;
+  std::vector<int> fixed;
+};
+
+L2Chunks l2_chunks(const Plan& plan, const tpd_options* opt, bool off) {
+  L2Chunks r;
+  const int mb = opt ? opt->l2_chunk_mb : 0;
+  if (off || mb <= 0 || plan.npass < 2) return r;
+  const double budget = mb * 1048576.0;
+  const int nb = 2 * plan.n;
+  unsigned long long uni = 0;
+  int best_F = 0;
+  unsigned long long best_uni = 0;
+  for (int F = 1; F < plan.npass; ++F) {
+    const PassDesc& pd = plan.pass[F - 1];
+    for (int i = 0; i < pd.D; ++i) uni |= 1ull << pd.gbit[i];
+    const int u = __builtin_popcountll(uni);
+    if (u >= nb || std::ldexp((double)plan.elem_bytes, u) > budget) break;
+    best_F = F;
+    best_uni = uni;
+  }
+  if (best_F < 2) return r;
+  const int u = __builtin_popcountll(best_uni);
+  int g = 0;
+  while (u + g + 1 <= nb && std::ldexp((double)plan.elem_bytes, u + g + 1) <= budget) ++g;
+  int skipped = 0;
+  for (int b = 0; b < nb; ++b) {
+    if ((best_uni >> b) & 1ull) continue;
+    if (skipped < g) { ++skipped; continue; }      // the lowest g outside bits stay free in a chunk
+    r.fixed.push_back(b);
+  }
+  if (r.fixed.empty()) return r;
+  r.F = best_F;
+  return r;
+}
+
 tpd_status run_single(bool dec, int arith, void* mat, const Plan& plan, int skip, double scale, void* ws,
                       cudaStream_t s, const tpd_options* opt, const uint8_t* const* need = nullptr) {
   record_event(opt, 0, s);
@@ -179,7 +223,8 @@ tpd_status run_single(bool dec, int arith, void* mat, const Plan& plan, int skip
   int spow = 0;
   double sres = 1.0;
   if (!dec) split_scale(scale, &spow, &sres);
-  for (int p = 0; p < plan.npass; ++p) {
+  const int variant = opt ? opt->variant : 0;
+  auto pass_args = [&](int p) {
     const PassDesc& pd = plan.pass[p];
     const bool last = p + 1 == plan.npass;
     PassArgs a;
@@ -194,10 +239,43 @@ tpd_status run_single(bool dec, int arith, void* mat, const Plan& plan, int skip
       if (!last) a.q_out = reinterpret_cast<int*>(w + lay.q_off[p]);
     }
     pass_scaling(dec, arith, pd, last, spow, sres, scale, &a);
-    const int variant = opt ? opt->variant : 0;
+    return a;
+  };
+  auto tuned_desc = [&](int p) {
+    PassDesc tuned = plan.pass[p];            // occupancy override (variants 3 and 4)
+    if (tuned.D <= 12 && (variant == 3 || variant == 4)) tuned.min_blocks = variant == 3 ? 2 : 3;
+    return tuned;
+  };
+  // L2 chunking: the first F passes run chunk by chunk, each chunk (the
+  // elements that agree on the global bits outside all F passes' tiles) small
+  // enough to stay in L2 from one pass to the next.
+  const L2Chunks ch = l2_chunks(plan, opt, skip || need || variant == 2);
+  int p0 = 0;
+  if (ch.F >= 2) {
+    const int nfix = (int)ch.fixed.size();
+    for (unsigned long long c = 0; c < (1ull << nfix); ++c)
+      for (int p = 0; p < ch.F; ++p) {
+        const PassDesc& pd = plan.pass[p];
+        PassArgs a = pass_args(p);
+        a.chunked = 1;
+        a.chunk_or = 0;
+        a.nfree = 0;
+        for (int j = 0; j < pd.nrest; ++j) {
+          int k = 0;
+          while (k < nfix && ch.fixed[k] != pd.rest_gbit[j]) ++k;
+          if (k < nfix) a.chunk_or |= ((c >> k) & 1ull) << j;
+          else a.chunk_free[a.nfree++] = (int8_t)j;
+        }
+        if (launch_pass(arith, dec, tuned_desc(p), a, 1ll << a.nfree, s) != cudaSuccess) return TPD_ERR_CUDA;
+      }
+    for (int p = 0; p < ch.F; ++p) record_event(opt, p + 1, s);
+    p0 = ch.F;
+  }
+  for (int p = p0; p < plan.npass; ++p) {
+    const PassDesc& pd = plan.pass[p];
+    const PassArgs a = pass_args(p);
     const bool pipe = arith == kArithFixed && !skip && !need && pd.D <= 12 && variant == 2;
-    PassDesc tuned = pd;                       // occupancy override (variants 3 and 4)
-    if (pd.D <= 12 && (variant == 3 || variant == 4)) tuned.min_blocks = variant == 3 ? 2 : 3;
+    const PassDesc tuned = tuned_desc(p);
     cudaError_t e = pipe ? launch_pass_pipe_c128(dec, tuned, a, sm_count(), s)
                          : launch_pass(arith, dec, tuned, a, pd.ntiles, s);
     if (e != cudaSuccess) return TPD_ERR_CUDA;
@@ -815,7 +893,18 @@ int tpd_plan_describe(int n, int dtype, const tpd_options* opt_in, char* buf, si
   const tpd_options eff = effective_options(n, dtype, prec, opt_in);
   const Plan* plan = get_plan(n, dtype, prec, &eff);
   if (!plan) return -1;
-  const std::string s = describe_plan(*plan);
+  std::string s = describe_plan(*plan);
+  const L2Chunks ch = l2_chunks(*plan, &eff, eff.skip_zero != 0 || eff.variant == 2);
+  if (ch.F >= 2) {
+    char tmp[64];
+    std::snprintf(tmp, sizeof(tmp), "l2 chunks: passes=%d fixed=", ch.F);
+    s += tmp;
+    for (size_t k = 0; k < ch.fixed.size(); ++k) {
+      std::snprintf(tmp, sizeof(tmp), "%s%d", k ? "," : "", ch.fixed[k]);
+      s += tmp;
+    }
+    s += "\n";
+  }
   if (buf && len) {
     std::strncpy(buf, s.c_str(), len - 1);
     buf[len - 1] = 0;

@@ -35,6 +35,11 @@ struct PassArgs {
   int* q_out;                 // nullptr: output is IEEE doubles
   long long q_in_stride;      // batched: q entries per matrix (previous pass's tile count)
   long long q_out_stride;     // batched: q entries per matrix (this pass's tile count)
+  // L2 chunk of a single matrix: CTA b runs tile chunk_or | (bit k of b) << chunk_free[k]
+  int chunked;
+  int nfree;
+  unsigned long long chunk_or;
+  int8_t chunk_free[2 * kMaxQubits];
 };
 
 // Role of a fixed-point pass: input IEEE doubles (0) or int64 sums of a

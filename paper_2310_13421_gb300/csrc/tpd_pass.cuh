@@ -639,6 +639,12 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
   void* matp = args.mat;
   const int* q_in = args.q_in;
   int* q_out = args.q_out;
+  if (args.chunked) {                      // one L2-sized chunk of the matrix: spread the CTA index
+    unsigned long long t = args.chunk_or;
+    for (int k = 0; k < args.nfree; ++k)
+      if ((tile >> k) & 1) t |= 1ull << args.chunk_free[k];
+    tile = (long long)t;
+  }
   if (args.ptrs != nullptr) {              // batched: tiles of matrix items[m] are contiguous in the grid
     const long long m = tile / args.tiles_per_mat;
     tile -= m * args.tiles_per_mat;

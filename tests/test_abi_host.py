@@ -120,6 +120,8 @@ def test_argument_errors_return_before_any_launch(L):
 def _parse(desc):
     passes = []
     for line in desc.strip().splitlines():
+        if not line.startswith("pass "):
+            continue
         head, *stages = line.split(" | ")
         m = re.match(r"pass \d+: levels \[(\d+),(\d+)\) D=(\d+) tiles=(\d+) gbits=([\d,]+)", head)
         b, e, D, ntiles, gbits = m.groups()
@@ -277,3 +279,30 @@ def test_autotune_candidates_are_distinct_valid_plans(L):
             assert npass == c["passes"] >= 0
             keys.add((desc, c["variant"]))
         assert len(keys) == len(cands)
+
+
+@pytest.mark.parametrize("n,dtype,prec", [(14, 0, 0), (15, 0, 0), (15, 1, 2), (13, 0, 0), (16, 1, 1)])
+def test_l2_chunks_cover_each_fused_pass_once(L, n, dtype, prec):
+    assert "l2 chunks" not in L.tpd_plan_describe(n, dtype, L.options(precision=prec))[1]   # off by default
+    npass, desc = L.tpd_plan_describe(n, dtype, L.options(precision=prec, l2_chunk_mb=48))
+    passes = _parse(desc)
+    m = re.search(r"l2 chunks: passes=(\d+) fixed=([\d,]+)", desc)
+    if m is None:
+        assert n == 15 and dtype == 0 or n == 16                # no two passes fit 48 MB chunks
+        return
+    F = int(m.group(1))
+    fixed = [int(x) for x in m.group(2).split(",")]
+    assert 2 <= F < npass
+    union = set()
+    for p in passes[:F]:
+        union |= set(p["gbits"])
+    assert not union & set(fixed)                       # fixed bits lie outside every fused pass's tile
+    elem = 16 if (dtype == 0 or prec >= 2) else 8
+    assert 2 ** (2 * n - len(fixed)) * elem <= 48 << 20    # a chunk fits the default L2 budget
+    # every tile of a fused pass lies in exactly one chunk: its tile-id bits hold all fixed bits
+    for p in passes[:F]:
+        rest = sorted(set(range(2 * n)) - set(p["gbits"]))
+        assert set(fixed) <= set(rest)
+    # off switch and the options that exclude chunking
+    for opt in (L.options(precision=prec), L.options(precision=prec, skip_zero=True, l2_chunk_mb=48)):
+        assert "l2 chunks" not in L.tpd_plan_describe(n, dtype, opt)[1]

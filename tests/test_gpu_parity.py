@@ -449,3 +449,15 @@ def test_nonzero_list_is_the_papers_list(tpd):
     s2, w2, cnt = tpd.nonzero_list(W, tol=tol, capacity=10)
     assert int(host(cnt)[0]) == keep.size
     assert host(s2).tolist() == keep[:10].tolist()
+
+
+@pytest.mark.parametrize("n,mb", [(12, 1), (12, 8), (13, 4)])
+def test_l2_chunked_passes_identical(tpd, n, mb):
+    # the first passes run chunk by chunk: every tile is computed exactly as in
+    # the plain launch sequence, so the weights are the same bits
+    A = synth.general(n, seed=9800 + n)
+    for prec in ("fixed", "plain"):
+        plain = host(tpd.decompose(gpu(A), precision=prec))
+        chunked = host(tpd.decompose(gpu(A), precision=prec, l2_chunk_mb=mb))
+        assert_exact(chunked, plain, "chunked n=%d %s" % (n, prec))
+    assert_close(to_string_order(chunked, n), oracle.coeffs_fwht(A), TOL128, "vs oracle")
