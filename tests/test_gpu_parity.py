@@ -461,3 +461,55 @@ def test_l2_chunked_passes_identical(tpd, n, mb):
         chunked = host(tpd.decompose(gpu(A), precision=prec, l2_chunk_mb=mb))
         assert_exact(chunked, plain, "chunked n=%d %s" % (n, prec))
     assert_close(to_string_order(chunked, n), oracle.coeffs_fwht(A), TOL128, "vs oracle")
+
+
+@pytest.mark.parametrize("n,pinned,inplace", [(6, True, False), (10, True, True), (11, False, False)])
+def test_decompose_from_host_buffers(tpd, n, pinned, inplace):
+    # tpd_decompose_host: host -> device copy, decomposition and device -> host
+    # copy, all enqueued on the stream (the end-to-end path of the benchmark)
+    from paper_2310_13421_gb300 import _lib as L
+    A = synth.general(n, seed=9900 + n)
+    src = torch.from_numpy(A.copy())
+    if pinned:
+        src = src.pin_memory()
+    dst = src if inplace else torch.empty_like(src)
+    dev = torch.empty(A.shape, dtype=torch.complex128, device="cuda")
+    wsb = L.tpd_workspace_size(n, L.TPD_C128, None)
+    ws = torch.empty(max(wsb, 16), dtype=torch.uint8, device="cuda")
+    s = torch.cuda.current_stream()
+    st = L.tpd_decompose_host(src.data_ptr(), dst.data_ptr(), dev.data_ptr(), n, L.TPD_C128, None, ws.data_ptr(), wsb,
+                              s.cuda_stream)
+    assert st == L.TPD_OK
+    torch.cuda.synchronize()
+    got = dst.numpy()
+    assert_exact(got, host(dev))                       # the host copy is the device result
+    assert_close(to_string_order(got, n), oracle.coeffs_fwht(A), TOL128, "host path n=%d" % n)
+
+
+def test_single_decomposition_in_cuda_graph(tpd):
+    # the whole launch sequence of one call is captured and replayed
+    n = 12
+    A = synth.general(n, seed=9950)
+    src = gpu(A)
+    work = src.clone()
+    from paper_2310_13421_gb300 import _lib as L
+    for prec, skip in (("fixed", False), ("plain", True)):
+        opt = tpd.make_options(prec, skip)
+        wsb = L.tpd_workspace_size(n, L.TPD_C128, opt)
+        ws = torch.empty(max(wsb, 16), dtype=torch.uint8, device="cuda")
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            st = L.tpd_decompose(work.data_ptr(), n, L.TPD_C128, opt, ws.data_ptr(), wsb, s.cuda_stream)
+            assert st == L.TPD_OK
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            st = L.tpd_decompose(work.data_ptr(), n, L.TPD_C128, opt, ws.data_ptr(), wsb,
+                                 torch.cuda.current_stream().cuda_stream)
+        assert st == L.TPD_OK
+        for _ in range(2):
+            work.copy_(src)
+            g.replay()
+            assert_close(to_string_order(host(work), n), oracle.coeffs_fwht(A), TOL128, "graph %s" % prec)
