@@ -135,6 +135,32 @@ def heisenberg(n, J, h, dtype=np.complex128):
     return H
 
 
+def heisenberg_into(H, n, J, h):
+    """Write the chain of heisenberg(n, J, h) into the zero torch tensor H
+    (N x N complex, any device) without building it on the host: the same
+    entries, the diagonal accumulated in the same order.  For sizes whose
+    dense host copy would not fit (n = 16: 64 GB)."""
+    import torch
+    N = 1 << n
+    dev = H.device
+    idx = torch.arange(N, device=dev, dtype=torch.int64)
+    z = [1.0 - 2.0 * ((idx >> (n - 1 - j)) & 1).to(torch.float64) for j in range(n)]
+    diag = torch.zeros(N, dtype=torch.float64, device=dev)
+    for j in range(n - 1):
+        diag += float(J[j]) * z[j] * z[j + 1]
+    for j in range(n):
+        diag += float(h[j]) * z[j]
+    flat = H.view(-1)
+    flat[idx * (N + 1)] = diag.to(H.dtype)
+    for j in range(n - 1):
+        b_hi, b_lo = n - 1 - j, n - 2 - j
+        flip = ((idx >> b_hi) & 1) != ((idx >> b_lo) & 1)
+        r = idx[flip]
+        rp = r ^ ((1 << b_hi) | (1 << b_lo))
+        flat[rp * N + r] = 2.0 * float(J[j])
+    return H
+
+
 def heisenberg_terms(n, J, h):
     """The planted decomposition: {quaternary string tuple: weight}."""
     terms = {}

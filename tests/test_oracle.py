@@ -202,6 +202,14 @@ def test_heisenberg_generator_matches_kronecker(n):
     assert np.array_equal(H, K)
 
 
+@pytest.mark.parametrize("n", [2, 5, 7])
+def test_heisenberg_device_writer_matches_dense_generator(n):
+    torch = pytest.importorskip("torch")
+    J, h = synth.heisenberg_params(n, seed=40 + n)
+    H = torch.zeros((1 << n, 1 << n), dtype=torch.complex128)
+    assert np.array_equal(synth.heisenberg_into(H, n, J, h).numpy(), synth.heisenberg(n, J, h))
+
+
 @pytest.mark.parametrize("n", [3, 6, 8])
 def test_heisenberg_terms_recovered_exactly(n):
     J, h = synth.heisenberg_params(n, seed=12 + n)
