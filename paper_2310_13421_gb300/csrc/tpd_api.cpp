@@ -1,6 +1,10 @@
-// C ABI of libtpd.so (declared in include/tpd.h): argument checks, the plan
-// cache, workspace layout and the launch sequence of each call.  Host code
-// only; the kernels are behind the launchers of tpd_launch.h.
+// C ABI of libtpd.so (declared in include/tpd.h), single-matrix calls:
+// argument checks, the plan cache, workspace layout and the launch sequence
+// of a decomposition or composition, the tuned-default table and the plan
+// description.  Host code only; the kernels are behind the launchers of
+// tpd_launch.h.  The batched calls live in tpd_api_batched.cpp, the partial
+// decomposition, list output, sparse input and layout helpers in
+// tpd_api_extra.cpp.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -13,12 +17,11 @@
 #include <tuple>
 #include <vector>
 
-#include "tpd.h"
-#include "tpd_launch.h"
-#include "tpd_planner.h"
+#include "tpd_api_internal.h"
 
 namespace tpd {
-namespace {
+namespace detail {
+
 
 std::mutex g_plan_mu;
 std::map<std::tuple<int, int, int, int, int>, Plan> g_plans;
@@ -203,7 +206,7 @@ L2Chunks l2_chunks(const Plan& plan, const tpd_options* opt, bool off) {
 }
 
 tpd_status run_single(bool dec, int arith, void* mat, const Plan& plan, int skip, double scale, void* ws,
-                      cudaStream_t s, const tpd_options* opt, const uint8_t* const* need = nullptr) {
+                      cudaStream_t s, const tpd_options* opt, const uint8_t* const* need) {
   record_event(opt, 0, s);
   if (plan.npass == 0) {
     SmallArgs a;
@@ -311,327 +314,11 @@ tpd_status single(bool dec, void* mat, int n, int dtype, double scale, const tpd
   return run_single(dec, arith, mat, *plan, skip, scale, ws, static_cast<cudaStream_t>(stream), opt);
 }
 
-// ------------------------------------------------------------------ partial decomposition
-//
-// Only the weights of a requested list of strings (Alg. 3: a quaternary
-// subtree T of the strings of interest).  The passes run in place as usual,
-// but a pass skips every tile that no requested weight depends on: the last
-// pass needs the tiles holding a requested position; an earlier pass needs
-// the tiles that share elements with a needed tile of the pass after it
-// (tiles of consecutive passes share elements iff they agree on the global
-// bits fixed in both).  Needed tiles are computed exactly as in the full
-// decomposition, so the requested weights carry the same bits.
-
-// workspace: RC positions of the requested strings | per pass, one byte per
-// tile: needed | the plan's own workspace (binary points between passes)
-struct PartialLayout {
-  size_t need_off[kMaxQubits];
-  size_t run_off, run_bytes, total;
-};
-
-PartialLayout partial_layout(const Plan& plan, int arith, size_t count) {
-  PartialLayout L;
-  std::memset(&L, 0, sizeof(L));
-  size_t off = align256(count * sizeof(unsigned long long));
-  for (int p = 0; p < plan.npass; ++p) { L.need_off[p] = off; off += align256((size_t)plan.pass[p].ntiles); }
-  L.run_off = off;
-  L.run_bytes = single_ws(plan, arith, 0);
-  L.total = off + L.run_bytes;
-  return L;
-}
-
-// base-4 string index (t_1 most significant: digit b from the right is the
-// symbol of qubit n-b, on row bit r_b and column bit c_b) -> RC position
-unsigned long long rc_of_string(unsigned long long sidx, int n) {
-  unsigned long long r = 0, c = 0;
-  for (int b = 0; b < n; ++b) {
-    c |= ((sidx >> (2 * b)) & 1ull) << b;
-    r |= ((sidx >> (2 * b + 1)) & 1ull) << b;
-  }
-  return (r << n) | c;
-}
-
-unsigned long long tile_base_of(const PassDesc& pd, unsigned long long t) {
-  unsigned long long b = 0;
-  for (int j = 0; j < pd.nrest; ++j)
-    if ((t >> j) & 1ull) b |= 1ull << pd.rest_gbit[j];
-  return b;
-}
-unsigned long long tile_of(const PassDesc& pd, unsigned long long pos) {
-  unsigned long long t = 0;
-  for (int j = 0; j < pd.nrest; ++j) t |= ((pos >> pd.rest_gbit[j]) & 1ull) << j;
-  return t;
-}
-unsigned long long fixed_mask(const PassDesc& pd) {
-  unsigned long long m = 0;
-  for (int j = 0; j < pd.nrest; ++j) m |= 1ull << pd.rest_gbit[j];
-  return m;
-}
-
-void partial_need(const Plan& plan, const std::vector<unsigned long long>& pos,
-                  std::vector<std::vector<uint8_t>>* need) {
-  const int P = plan.npass;
-  need->assign(P, {});
-  for (int p = 0; p < P; ++p) (*need)[p].assign((size_t)plan.pass[p].ntiles, 0);
-  for (unsigned long long x : pos) (*need)[P - 1][tile_of(plan.pass[P - 1], x)] = 1;
-  for (int q = P - 2; q >= 0; --q) {
-    const PassDesc& a = plan.pass[q];
-    const PassDesc& b = plan.pass[q + 1];
-    const unsigned long long C = fixed_mask(a) & fixed_mask(b);
-    std::vector<unsigned long long> keys;
-    for (unsigned long long t = 0; t < (unsigned long long)b.ntiles; ++t)
-      if ((*need)[q + 1][t]) keys.push_back(tile_base_of(b, t) & C);
-    std::sort(keys.begin(), keys.end());
-    keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
-    for (unsigned long long t = 0; t < (unsigned long long)a.ntiles; ++t)
-      (*need)[q][t] = std::binary_search(keys.begin(), keys.end(), tile_base_of(a, t) & C) ? 1 : 0;
-  }
-}
-
-tpd_status partial_setup(int n, int dtype, const tpd_options* opt_in, int* prec, int* arith, const Plan** plan,
-                         tpd_options* eff) {
-  tpd_status st = check_common(n, dtype, opt_in, prec);
-  if (st != TPD_OK) return st;
-  if (opt_in && opt_in->skip_zero) return TPD_ERR_UNSUPPORTED;
-  *eff = effective_options(n, dtype, *prec, opt_in);
-  *plan = get_plan(n, dtype, *prec, eff);
-  if (!*plan) return TPD_ERR_INVALID_ARG;
-  *arith = arith_of(dtype, *prec);
-  return TPD_OK;
-}
-
-// ------------------------------------------------------------------ batched
-constexpr int kBatchMaxQubits = kBatchMaxN;
-static_assert(kBatchStatusTimeout == TPD_ERR_TIMEOUT && kBatchStatusBadSizes == TPD_ERR_INVALID_ARG,
-              "device status codes are tpd_status values");
-static_assert(sizeof(BatchParams) <= 32000, "kernel parameter space");
-
-bool g_hold_batch_waits = false;   // test hook (tpd_test_hold_batch_waits)
-
-// workspace: control words (status, work counter, per-matrix pass completion
-// counters of the persistent kernel) | items[count] (matrix indices bucketed
-// by qubit count, on the device) | per qubit count n (ascending), for the fixed point: binary
-// points of hist[n] matrices for every pass but the last
-size_t batched_q_bytes(const Plan& plan, int arith, int count_n) {
-  if (arith != kArithFixed || plan.npass < 2) return 0;
-  size_t b = 0;
-  for (int i = 0; i + 1 < plan.npass; ++i) b += (size_t)plan.pass[i].ntiles * sizeof(int) * (size_t)count_n;
-  return align256(b);
-}
-size_t batched_ctrl(const int* hist, const std::vector<const Plan*>& plans) {
-  size_t words = kCtrlDone;
-  for (int n = 1; n <= kBatchMaxQubits; ++n)
-    if (hist[n] && plans[n]->npass > 1) words += (size_t)hist[n] * (plans[n]->npass - 1);
-  return align256(words * sizeof(unsigned));
-}
-size_t batched_head(int count) { return align256((size_t)count * sizeof(int)); }
-
-// Options a batched call plans qubit count n with: the caller's (or tuned)
-// choices; for the one-launch form (variant 2) n >= 7 defaults to
-// 2^12-element tiles, the persistent kernel's tile.
-tpd_options batch_options(int n, int dtype, int prec, const tpd_options* opt) {
-  tpd_options eff = effective_options(n, dtype, prec, opt);
-  const int caller_variant = opt ? opt->variant : 0;
-  if (caller_variant == 2 && n >= 7 && eff.tile_bits == 0) eff.tile_bits = 12;
-  return eff;
-}
-
-// The persistent form applies when every matrix is either small (n <= 6: one
-// work item, whole matrix in shared memory) or planned with 2^12-element
-// tiles (256-thread CTAs) in at most kSegMaxPasses passes, and the work list
-// fits the kernel's parameters.
-bool persistent_fits(const int* hist, const std::vector<const Plan*>& plans) {
-  int ndesc = 0;
-  long long items = 1;
-  for (int n = 1; n <= kBatchMaxQubits; ++n) {
-    if (!hist[n]) continue;
-    const Plan& p = *plans[n];
-    if (n <= 6) { items += hist[n]; continue; }
-    if (p.npass > kSegMaxPasses) return false;
-    for (int i = 0; i < p.npass; ++i)
-      if (p.pass[i].D != 12) return false;
-    ndesc += p.npass;
-    items += (long long)(hist[n] + (p.npass - 1) * 4096) * p.npass * p.pass[0].ntiles;   // lag <= 4096
-  }
-  return ndesc <= kBatchMaxDescs && items < 0x7fffffffll;
-}
-
-// Work list of the persistent kernel (see tpd_launch.h): bucketing, one
-// pipelined segment per qubit count n >= 7 (largest first), then the small
-// matrices (largest first).
-tpd_status run_persistent(bool dec, int arith, void* const* ptrs_dev, const int* ns_dev, int count, const int* hist,
-                          const std::vector<const Plan*>& plans, int scale_mode, unsigned* ctrl, int* items,
-                          char* qbase0, size_t ctrl_bytes, cudaStream_t s) {
-  static BatchParams bp;               // large: built under the lock, copied into the launch
-  static std::mutex mu;
-  std::lock_guard<std::mutex> lk(mu);
-  std::memset(&bp, 0, sizeof(bp));
-  bp.count = count;
-  for (int n = 0; n <= kBatchMaxQubits; ++n) bp.hist[n] = hist[n];
-  bp.scale_mode = dec ? 0 : scale_mode;
-  bp.ptrs = ptrs_dev; bp.ns = ns_dev; bp.items = items; bp.ctrl = ctrl;
-  int item_start[kBatchMaxQubits + 2] = {0};
-  for (int n = 1; n <= kBatchMaxQubits + 1; ++n) item_start[n] = item_start[n - 1] + hist[n - 1];
-  // per n (ascending, as the workspace lays them out): q area and done-counter base
-  size_t qbase_n[kBatchMaxQubits + 1] = {0};
-  int dbase_n[kBatchMaxQubits + 1] = {0};
-  {
-    size_t q = 0;
-    int d = 0;
-    for (int n = 1; n <= kBatchMaxQubits; ++n) {
-      if (!hist[n]) continue;
-      qbase_n[n] = q;
-      dbase_n[n] = d;
-      q += batched_q_bytes(*plans[n], arith, hist[n]);
-      if (plans[n]->npass > 1) d += hist[n] * (plans[n]->npass - 1);
-    }
-  }
-  // CTAs in flight: 2 per SM; a matrix's later pass trails its previous pass
-  // by at least twice that many items, so the tiles it waits for are done
-  const long long inflight = 2ll * sm_count();
-  long long first = 1;
-  int nseg = 0, ndesc = 0;
-  for (int n = kBatchMaxQubits; n >= 7; --n) {
-    if (!hist[n]) continue;
-    const Plan& p = *plans[n];
-    BatchSeg& sg = bp.seg[nseg++];
-    sg.kind = kSegPipe; sg.n = n; sg.npass = p.npass; sg.desc = ndesc;
-    sg.item_start = item_start[n]; sg.nmat = hist[n];
-    sg.tiles = p.pass[0].ntiles;
-    const long long per_round = (long long)p.npass * sg.tiles;
-    long long lag = (2 * inflight + per_round - 1) / per_round;
-    sg.lag = (int)(lag < 1 ? 1 : (lag > 4096 ? 4096 : lag));
-    sg.done = dbase_n[n];
-    sg.wait_extra = g_hold_batch_waits ? 1 : 0;
-    sg.first = first;
-    size_t qoff = qbase_n[n];
-    for (int i = 0; i < p.npass; ++i) {
-      const PassDesc& pd = p.pass[i];
-      const bool last = i + 1 == p.npass;
-      bp.desc[ndesc++] = pd;
-      PassArgs& a = sg.args[i];
-      if (arith == kArithFixed) {
-        if (i > 0) {
-          a.q_in = sg.args[i - 1].q_out;
-          a.q_in_stride = p.pass[i - 1].ntiles;
-        }
-        if (!last) {
-          a.q_out = reinterpret_cast<int*>(qbase0 + qoff);
-          a.q_out_stride = pd.ntiles;
-          qoff += (size_t)pd.ntiles * sizeof(int) * hist[n];
-        }
-      }
-      const double scale = scale_mode ? std::ldexp(1.0, -n) : 1.0;
-      pass_scaling(dec, arith, pd, last, scale_mode ? -n : 0, 1.0, scale, &a);
-    }
-    first += (long long)(hist[n] + (long long)(p.npass - 1) * sg.lag) * per_round;
-  }
-  for (int n = 6; n >= 1; --n) {
-    if (!hist[n]) continue;
-    BatchSeg& sg = bp.seg[nseg++];
-    sg.kind = kSegSmall; sg.n = n; sg.npass = 0; sg.desc = -1;
-    sg.item_start = item_start[n]; sg.nmat = hist[n];
-    sg.first = first; sg.tiles = 1;
-    first += hist[n];
-  }
-  bp.nseg = nseg;
-  bp.total = first;
-  if (cudaMemsetAsync(ctrl, 0, ctrl_bytes, s) != cudaSuccess) return TPD_ERR_CUDA;
-  if (launch_batch(arith, dec, bp, nullptr, s) != cudaSuccess) return TPD_ERR_CUDA;
-  return TPD_OK;
-}
-
-tpd_status batched(bool dec, void* const* ptrs_dev, const int* ns_dev, const int* ns, int count, int dtype,
-                   int scale_mode, const tpd_options* opt, void* ws, size_t ws_bytes, void* stream) {
-  int prec = 0;
-  tpd_status st = check_options(dtype, opt, &prec);
-  if (st != TPD_OK) return st;
-  if (count < 0 || (count > 0 && (ptrs_dev == nullptr || ns_dev == nullptr || ns == nullptr)))
-    return TPD_ERR_INVALID_ARG;
-  if (scale_mode != 0 && scale_mode != 1) return TPD_ERR_INVALID_ARG;
-  if (opt && opt->skip_zero) return TPD_ERR_UNSUPPORTED;
-  if (count == 0) return TPD_OK;
-  int hist[kBatchMaxQubits + 1] = {0};
-  for (int i = 0; i < count; ++i) {
-    if (ns[i] < 1 || ns[i] > kBatchMaxQubits) return TPD_ERR_INVALID_ARG;
-    hist[ns[i]]++;
-  }
-  const int arith = arith_of(dtype, prec);
-  std::vector<const Plan*> plans(kBatchMaxQubits + 1, nullptr);
-  std::vector<int> variants(kBatchMaxQubits + 1, 0);
-  size_t need = batched_head(count);
-  for (int n = 1; n <= kBatchMaxQubits; ++n) {
-    if (!hist[n]) continue;
-    const tpd_options eff = batch_options(n, dtype, prec, opt);   // tuned per qubit count
-    if (!(plans[n] = get_plan(n, dtype, prec, &eff))) return TPD_ERR_INVALID_ARG;
-    variants[n] = eff.variant;
-    need += batched_q_bytes(*plans[n], arith, hist[n]);
-  }
-  const size_t ctrl_bytes = batched_ctrl(hist, plans);
-  need += ctrl_bytes;
-  if (ws == nullptr || ws_bytes < need) return TPD_ERR_WORKSPACE;
-  if (reinterpret_cast<uintptr_t>(ws) % 16) return TPD_ERR_MISALIGNED;
-  unsigned* ctrl = static_cast<unsigned*>(ws);
-  int* items = reinterpret_cast<int*>(static_cast<char*>(ws) + ctrl_bytes);
-  char* qbase = reinterpret_cast<char*>(items) + batched_head(count);
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const int caller_variant = opt ? opt->variant : 0;
-  if (caller_variant == 2 && persistent_fits(hist, plans))
-    return run_persistent(dec, arith, ptrs_dev, ns_dev, count, hist, plans, scale_mode, ctrl, items, qbase,
-                          ctrl_bytes, s);
-  if (cudaMemsetAsync(ctrl, 0, ctrl_bytes, s) != cudaSuccess) return TPD_ERR_CUDA;   // status word: OK
-  BucketHist bh;
-  for (int n = 0; n <= kBatchMaxQubits; ++n) bh.h[n] = hist[n];
-  if (launch_bucket(ns_dev, count, bh, items, ctrl + kCtrlStatus, s) != cudaSuccess) return TPD_ERR_CUDA;
-  int start = 0;  // first bucket position of qubit count n: buckets are in increasing n
-  for (int n = 1; n <= kBatchMaxQubits; ++n) {
-    if (!hist[n]) continue;
-    const Plan& plan = *plans[n];
-    const int* its = items + start;
-    if (plan.npass == 0) {
-      SmallArgs a;
-      std::memset(&a, 0, sizeof(a));
-      a.ptrs = ptrs_dev; a.ns = ns_dev; a.items = its;
-      a.scale_mode = dec ? 0 : scale_mode;
-      if (launch_small(arith, dec, a, hist[n], n, s) != cudaSuccess) return TPD_ERR_CUDA;
-    } else {
-      size_t qoff = 0;
-      const int* q_prev = nullptr;
-      long long q_prev_stride = 0;
-      for (int p = 0; p < plan.npass; ++p) {
-        const PassDesc& pd = plan.pass[p];
-        const bool last = p + 1 == plan.npass;
-        PassArgs a;
-        std::memset(&a, 0, sizeof(a));
-        a.ptrs = ptrs_dev; a.items = its; a.tiles_per_mat = pd.ntiles;
-        if (arith == kArithFixed) {
-          a.q_in = q_prev;
-          a.q_in_stride = q_prev_stride;
-          if (!last) {
-            a.q_out = reinterpret_cast<int*>(qbase + qoff);
-            a.q_out_stride = pd.ntiles;
-            qoff += (size_t)pd.ntiles * sizeof(int) * (size_t)hist[n];
-            q_prev = a.q_out;
-            q_prev_stride = pd.ntiles;
-          }
-        }
-        const double scale = scale_mode ? std::ldexp(1.0, -n) : 1.0;
-        pass_scaling(dec, arith, pd, last, scale_mode ? -n : 0, 1.0, scale, &a);
-        PassDesc tuned = pd;                   // occupancy override (variants 3 and 4)
-        if (pd.D <= 12 && (variants[n] == 3 || variants[n] == 4)) tuned.min_blocks = variants[n] == 3 ? 2 : 3;
-        if (launch_pass(arith, dec, tuned, a, pd.ntiles * hist[n], s) != cudaSuccess) return TPD_ERR_CUDA;
-      }
-      qbase += batched_q_bytes(plan, arith, hist[n]);
-    }
-    start += hist[n];
-  }
-  return TPD_OK;
-}
-
-}  // namespace
+}  // namespace detail
 }  // namespace tpd
 
 using namespace tpd;
+using namespace tpd::detail;
 
 extern "C" {
 
@@ -674,190 +361,6 @@ tpd_status tpd_decompose_host(const void* A_host, void* W_host, void* dev_A, int
   if (st != TPD_OK) return st;
   if (cudaMemcpyAsync(W_host, dev_A, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return TPD_ERR_CUDA;
   return TPD_OK;
-}
-
-size_t tpd_partial_workspace_size(int n, int dtype, const tpd_options* opt, size_t count) {
-  int prec = 0, arith = 0;
-  const Plan* plan = nullptr;
-  tpd_options eff;
-  if (partial_setup(n, dtype, opt, &prec, &arith, &plan, &eff) != TPD_OK) return 0;
-  return partial_layout(*plan, arith, count).total;
-}
-
-tpd_status tpd_partial_prepare(int n, int dtype, const tpd_options* opt, const unsigned long long* strings,
-                               size_t count, void* workspace, size_t workspace_bytes, void* stream) {
-  int prec = 0, arith = 0;
-  const Plan* plan = nullptr;
-  tpd_options eff;
-  tpd_status st = partial_setup(n, dtype, opt, &prec, &arith, &plan, &eff);
-  if (st != TPD_OK) return st;
-  if (count > 0 && strings == nullptr) return TPD_ERR_INVALID_ARG;
-  const PartialLayout lay = partial_layout(*plan, arith, count);
-  if (workspace == nullptr || workspace_bytes < lay.total) return TPD_ERR_WORKSPACE;
-  if (reinterpret_cast<uintptr_t>(workspace) % 16) return TPD_ERR_MISALIGNED;
-  const unsigned long long nstr = 1ull << (2 * n);
-  std::vector<unsigned long long> pos(count);
-  for (size_t i = 0; i < count; ++i) {
-    if (strings[i] >= nstr) return TPD_ERR_INVALID_ARG;
-    pos[i] = rc_of_string(strings[i], n);
-  }
-  std::vector<std::vector<uint8_t>> need;
-  if (plan->npass > 0) partial_need(*plan, pos, &need);
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  char* w = static_cast<char*>(workspace);
-  if (count && cudaMemcpyAsync(w, pos.data(), count * sizeof(unsigned long long), cudaMemcpyHostToDevice, s) !=
-                   cudaSuccess)
-    return TPD_ERR_CUDA;
-  for (int p = 0; p < plan->npass; ++p)
-    if (cudaMemcpyAsync(w + lay.need_off[p], need[p].data(), need[p].size(), cudaMemcpyHostToDevice, s) !=
-        cudaSuccess)
-      return TPD_ERR_CUDA;
-  if (cudaStreamSynchronize(s) != cudaSuccess) return TPD_ERR_CUDA;   // the host vectors go out of scope
-  return TPD_OK;
-}
-
-tpd_status tpd_decompose_partial(void* A, int n, int dtype, const tpd_options* opt, size_t count, void* workspace,
-                                 size_t workspace_bytes, void* weights, void* stream) {
-  int prec = 0, arith = 0;
-  const Plan* plan = nullptr;
-  tpd_options eff;
-  tpd_status st = partial_setup(n, dtype, opt, &prec, &arith, &plan, &eff);
-  if (st != TPD_OK) return st;
-  if (A == nullptr || (count > 0 && weights == nullptr)) return TPD_ERR_INVALID_ARG;
-  const size_t eb = dtype == TPD_C128 ? 16 : 8;
-  if (reinterpret_cast<uintptr_t>(A) % eb || reinterpret_cast<uintptr_t>(weights) % eb) return TPD_ERR_MISALIGNED;
-  const PartialLayout lay = partial_layout(*plan, arith, count);
-  if (workspace == nullptr || workspace_bytes < lay.total) return TPD_ERR_WORKSPACE;
-  if (reinterpret_cast<uintptr_t>(workspace) % 16) return TPD_ERR_MISALIGNED;
-  char* w = static_cast<char*>(workspace);
-  const uint8_t* need[kMaxQubits];
-  for (int p = 0; p < plan->npass; ++p) need[p] = reinterpret_cast<const uint8_t*>(w + lay.need_off[p]);
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  st = run_single(true, arith, A, *plan, 0, 1.0, w + lay.run_off, s, &eff, plan->npass > 0 ? need : nullptr);
-  if (st != TPD_OK) return st;
-  if (launch_gather(A, reinterpret_cast<const unsigned long long*>(w), count, (int)eb, weights, s) != cudaSuccess)
-    return TPD_ERR_CUDA;
-  return TPD_OK;
-}
-
-size_t tpd_sparse_workspace_size(size_t max_entries) { return sparse_workspace_bytes(max_entries); }
-
-tpd_status tpd_decompose_coo(const int* rows, const int* cols, const void* values, size_t nnz, int n, int dtype,
-                             size_t max_entries, unsigned long long* strings, void* weights, size_t capacity,
-                             unsigned long long* count, unsigned* status, void* workspace, size_t workspace_bytes,
-                             void* stream) {
-  if (dtype != TPD_C128) return TPD_ERR_UNSUPPORTED;
-  if (n < 1 || n > 15 || count == nullptr || max_entries == 0) return TPD_ERR_INVALID_ARG;
-  if (nnz > 0 && (rows == nullptr || cols == nullptr || values == nullptr)) return TPD_ERR_INVALID_ARG;
-  if (capacity > 0 && (strings == nullptr || weights == nullptr)) return TPD_ERR_INVALID_ARG;
-  if (reinterpret_cast<uintptr_t>(values) % 16 || reinterpret_cast<uintptr_t>(weights) % 16 ||
-      reinterpret_cast<uintptr_t>(strings) % 8 || reinterpret_cast<uintptr_t>(count) % 8 ||
-      reinterpret_cast<uintptr_t>(rows) % 4 || reinterpret_cast<uintptr_t>(cols) % 4 ||
-      reinterpret_cast<uintptr_t>(status) % 4)
-    return TPD_ERR_MISALIGNED;
-  if (workspace == nullptr || workspace_bytes < sparse_workspace_bytes(max_entries)) return TPD_ERR_WORKSPACE;
-  if (reinterpret_cast<uintptr_t>(workspace) % 256) return TPD_ERR_MISALIGNED;
-  if (launch_sparse(rows, cols, values, nnz, n, max_entries, strings, weights, capacity, count, workspace, status,
-                    static_cast<cudaStream_t>(stream)) != cudaSuccess)
-    return TPD_ERR_CUDA;
-  return TPD_OK;
-}
-
-size_t tpd_nonzero_workspace_size(int n) {
-  if (n < 1 || n > kMaxQubits) return 0;
-  return nonzero_workspace_bytes(n);
-}
-
-tpd_status tpd_nonzero_list(const void* W, int n, int dtype, double tol, unsigned long long* strings,
-                            void* weights, size_t capacity, unsigned long long* count, void* workspace,
-                            size_t workspace_bytes, void* stream) {
-  if (n < 1 || n > kMaxQubits || (dtype != TPD_C128 && dtype != TPD_C64)) return TPD_ERR_INVALID_ARG;
-  if (W == nullptr || count == nullptr || !(tol >= 0.0) || (capacity > 0 && (strings == nullptr || weights == nullptr)))
-    return TPD_ERR_INVALID_ARG;
-  const size_t eb = dtype == TPD_C128 ? 16 : 8;
-  if (reinterpret_cast<uintptr_t>(W) % eb || reinterpret_cast<uintptr_t>(weights) % eb ||
-      reinterpret_cast<uintptr_t>(strings) % 8 || reinterpret_cast<uintptr_t>(count) % 8)
-    return TPD_ERR_MISALIGNED;
-  if (workspace == nullptr || workspace_bytes < nonzero_workspace_bytes(n)) return TPD_ERR_WORKSPACE;
-  if (reinterpret_cast<uintptr_t>(workspace) % 256) return TPD_ERR_MISALIGNED;
-  if (launch_nonzero(W, n, (int)eb, tol, strings, weights, capacity, count, workspace,
-                     static_cast<cudaStream_t>(stream)) != cudaSuccess)
-    return TPD_ERR_CUDA;
-  return TPD_OK;
-}
-
-tpd_status tpd_convert_layout(const void* src, void* dst, int n, int dtype, int to_string, void* stream) {
-  if (n < 1 || n > kMaxQubits || (dtype != TPD_C128 && dtype != TPD_C64)) return TPD_ERR_INVALID_ARG;
-  if (src == nullptr || dst == nullptr || (to_string != 0 && to_string != 1)) return TPD_ERR_INVALID_ARG;
-  const size_t eb = dtype == TPD_C128 ? 16 : 8;
-  if (reinterpret_cast<uintptr_t>(src) % eb || reinterpret_cast<uintptr_t>(dst) % eb) return TPD_ERR_MISALIGNED;
-  const size_t bytes = ((size_t)1 << (2 * n)) * eb;
-  const uintptr_t a = reinterpret_cast<uintptr_t>(src), b = reinterpret_cast<uintptr_t>(dst);
-  if (a < b + bytes && b < a + bytes) return TPD_ERR_INVALID_ARG;
-  if (launch_layout(src, dst, n, (int)eb, to_string, static_cast<cudaStream_t>(stream)) != cudaSuccess)
-    return TPD_ERR_CUDA;
-  return TPD_OK;
-}
-
-tpd_status tpd_sum_squares(const void* x, size_t count, int dtype, double* result, void* workspace,
-                           size_t workspace_bytes, void* stream) {
-  if ((dtype != TPD_C128 && dtype != TPD_C64) || result == nullptr || (count > 0 && x == nullptr))
-    return TPD_ERR_INVALID_ARG;
-  static_assert(TPD_SUMSQ_WORKSPACE_BYTES >= 1024 * sizeof(double), "workspace constant");
-  if (workspace == nullptr || workspace_bytes < sumsq_workspace_bytes()) return TPD_ERR_WORKSPACE;
-  const size_t eb = dtype == TPD_C128 ? 16 : 8;
-  if ((x && reinterpret_cast<uintptr_t>(x) % eb) || reinterpret_cast<uintptr_t>(result) % 8 ||
-      reinterpret_cast<uintptr_t>(workspace) % 8)
-    return TPD_ERR_MISALIGNED;
-  if (launch_sumsq(x, count, (int)eb, result, workspace, static_cast<cudaStream_t>(stream)) != cudaSuccess)
-    return TPD_ERR_CUDA;
-  return TPD_OK;
-}
-
-tpd_status tpd_batch_status(const void* workspace, void* stream) {
-  if (workspace == nullptr) return TPD_ERR_INVALID_ARG;
-  unsigned st = 0;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (cudaMemcpyAsync(&st, static_cast<const unsigned*>(workspace) + kCtrlStatus, sizeof(st), cudaMemcpyDeviceToHost,
-                      s) != cudaSuccess)
-    return TPD_ERR_CUDA;
-  if (cudaStreamSynchronize(s) != cudaSuccess) return TPD_ERR_CUDA;
-  return static_cast<tpd_status>(st);
-}
-
-void tpd_test_hold_batch_waits(int on) { g_hold_batch_waits = on != 0; }
-
-size_t tpd_batched_workspace_size(const int* ns, int count, int dtype, const tpd_options* opt) {
-  int prec = 0;
-  if (check_options(dtype, opt, &prec) != TPD_OK || count < 0 || (count > 0 && ns == nullptr)) return 0;
-  int hist[kBatchMaxQubits + 1] = {0};
-  for (int i = 0; i < count; ++i) {
-    if (ns[i] < 1 || ns[i] > kBatchMaxQubits) return 0;
-    hist[ns[i]]++;
-  }
-  const int arith = arith_of(dtype, prec);
-  size_t need = batched_head(count);
-  std::vector<const Plan*> plans(kBatchMaxQubits + 1, nullptr);
-  for (int n = 1; n <= kBatchMaxQubits; ++n) {
-    if (!hist[n]) continue;
-    const tpd_options eff = batch_options(n, dtype, prec, opt);
-    const Plan* plan = get_plan(n, dtype, prec, &eff);
-    if (!plan) return 0;
-    plans[n] = plan;
-    need += batched_q_bytes(*plan, arith, hist[n]);
-  }
-  return need + batched_ctrl(hist, plans);
-}
-
-tpd_status tpd_decompose_batched(void* const* ptrs_dev, const int* ns_dev, const int* ns, int count, int dtype,
-                                 const tpd_options* opt, void* workspace, size_t workspace_bytes, void* stream) {
-  return batched(true, ptrs_dev, ns_dev, ns, count, dtype, 0, opt, workspace, workspace_bytes, stream);
-}
-
-tpd_status tpd_compose_batched(void* const* ptrs_dev, const int* ns_dev, const int* ns, int count, int dtype,
-                               int scale_mode, const tpd_options* opt, void* workspace, size_t workspace_bytes,
-                               void* stream) {
-  return batched(false, ptrs_dev, ns_dev, ns, count, dtype, scale_mode, opt, workspace, workspace_bytes, stream);
 }
 
 tpd_status tpd_tune_set(int n, int dtype, int precision, const tpd_options* tuned) {
@@ -926,5 +429,6 @@ const char* tpd_status_string(int status) {
 }
 
 int tpd_version(void) { return 100; }
+
 
 }  // extern "C"
