@@ -49,9 +49,10 @@ def _load():
             lib.oracle_compose.argtypes = [dp, ctypes.c_int, dp]
             lib.oracle_compose_fwht.argtypes = [dp, ctypes.c_int, dp]
             lib.oracle_tpd_alg1.argtypes = [dp, ctypes.c_int, dp]
+            lib.oracle_tpd_alg2.argtypes = [dp, ctypes.c_int, dp]
             for f in (lib.oracle_coeffs, lib.oracle_coeffs_fwht, lib.oracle_coeffs_at,
                       lib.oracle_coeffs_xrows, lib.oracle_compose, lib.oracle_compose_fwht,
-                      lib.oracle_tpd_alg1):
+                      lib.oracle_tpd_alg1, lib.oracle_tpd_alg2):
                 f.restype = ctypes.c_int
             lib.oracle_num_threads.argtypes = []
             lib.oracle_num_threads.restype = ctypes.c_int
@@ -87,6 +88,18 @@ def tpd_alg1(A):
     out = np.empty(4 ** n, dtype=np.complex128)
     if _load().oracle_tpd_alg1(_dptr(A), n, _dptr(out)):
         raise RuntimeError("oracle_tpd_alg1 failed")
+    return out
+
+
+def tpd_alg2(A, overwrite=False):
+    """All 4^n weights by the paper's iterative algorithm (Alg. 2: every CMW of
+    a level split at once, in place, OpenMP over quads), string order.  With
+    overwrite, A (complex128, contiguous) is used as the working array."""
+    A, n = _square(A)
+    W = A if overwrite else A.copy()
+    out = np.empty(4 ** n, dtype=np.complex128)
+    if _load().oracle_tpd_alg2(_dptr(W), n, _dptr(out)):
+        raise RuntimeError("oracle_tpd_alg2 failed")
     return out
 
 

@@ -282,6 +282,32 @@ def test_alg1_prunes_zero_cmws_exactly():
     assert np.allclose(w, oracle.coeffs_fwht(D), rtol=0, atol=1e-15)
 
 
+@pytest.mark.parametrize("n", [1, 2, 3])
+def test_alg2_matches_kronecker(n):
+    A = synth.general(n, seed=340 + n)
+    assert np.allclose(oracle.tpd_alg2(A), kron.coeffs_kron(A), rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("n", [4, 7, 9])
+def test_alg2_integer_exact_and_random_bound(n):
+    Ai = synth.int_general(n, seed=350 + n)
+    assert np.array_equal(oracle.tpd_alg2(Ai), oracle.coeffs_fwht(Ai))
+    A = synth.general(n, seed=360 + n)
+    want = oracle.coeffs_fwht(A)
+    assert np.linalg.norm(oracle.tpd_alg2(A) - want) <= 2 * n * 2.0 ** -53 * np.linalg.norm(want)
+    # the in-place form leaves the weights in the working array (RC layout)
+    W = A.copy()
+    oracle.tpd_alg2(W, overwrite=True)
+    assert not np.array_equal(W, A)
+
+
+def test_alg2_agrees_with_alg1_on_planted_chain():
+    n = 9
+    J, h = synth.heisenberg_params(n, seed=370)
+    H = synth.heisenberg(n, J, h)
+    assert np.array_equal(oracle.tpd_alg2(H), oracle.tpd_alg1(H))
+
+
 # ---------------------------------------------------------------- gradient and adjoint
 
 def test_adjoint_dot_product():
