@@ -113,8 +113,11 @@ typedef struct {
 void tpd_options_init(tpd_options* opt);
 
 /* Bytes of device workspace tpd_decompose / tpd_compose need for (n, dtype,
- * opt): 0 unless opt->skip_zero.  The workspace holds the per-tile nonzero
- * flags a pass hands to the next.  Returns 0 for invalid arguments. */
+ * opt): what one pass hands to the next -- the per-tile binary points of the
+ * complex128 block fixed point (plans of two or more passes) and, with
+ * opt->skip_zero, the per-tile nonzero flags.  0 for one-pass plans and for
+ * the IEEE / complex64 forms without skip_zero.  Returns 0 for invalid
+ * arguments. */
 size_t tpd_workspace_size(int n, int dtype, const tpd_options* opt);
 
 /* Pauli decomposition in place (Eq. 2 via Eqs. 3-5).
