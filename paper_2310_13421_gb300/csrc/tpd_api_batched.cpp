@@ -29,8 +29,9 @@ bool g_hold_batch_waits = false;   // test hook (tpd_test_hold_batch_waits)
 
 // workspace: control words (status, work counter, per-matrix pass completion
 // counters of the persistent kernel) | items[count] (matrix indices bucketed
-// by qubit count, on the device) | per qubit count n (ascending), for the fixed point: binary
-// points of hist[n] matrices for every pass but the last
+// by qubit count, on the device) | bptrs[count] (their pointers, persistent
+// form) | per qubit count n (ascending), for the fixed point: binary points of
+// hist[n] matrices for every pass but the last
 size_t batched_q_bytes(const Plan& plan, int arith, int count_n) {
   if (arith != kArithFixed || plan.npass < 2) return 0;
   size_t b = 0;
@@ -43,7 +44,10 @@ size_t batched_ctrl(const int* hist, const std::vector<const Plan*>& plans) {
     if (hist[n] && plans[n]->npass > 1) words += (size_t)hist[n] * (plans[n]->npass - 1);
   return align256(words * sizeof(unsigned));
 }
-size_t batched_head(int count) { return align256((size_t)count * sizeof(int)); }
+size_t batched_items_bytes(int count) { return align256((size_t)count * sizeof(int)); }
+size_t batched_head(int count) {
+  return batched_items_bytes(count) + align256((size_t)count * sizeof(unsigned long long));
+}
 
 // Options a batched call plans qubit count n with: the caller's (or tuned)
 // choices; for the one-launch form (variant 2) n >= 7 defaults to
@@ -80,7 +84,7 @@ bool persistent_fits(const int* hist, const std::vector<const Plan*>& plans) {
 // matrices (largest first).
 tpd_status run_persistent(bool dec, int arith, void* const* ptrs_dev, const int* ns_dev, int count, const int* hist,
                           const std::vector<const Plan*>& plans, int scale_mode, unsigned* ctrl, int* items,
-                          char* qbase0, size_t ctrl_bytes, cudaStream_t s) {
+                          unsigned long long* bptrs, char* qbase0, size_t ctrl_bytes, cudaStream_t s) {
   static BatchParams bp;               // large: built under the lock, copied into the launch
   static std::mutex mu;
   std::lock_guard<std::mutex> lk(mu);
@@ -88,7 +92,7 @@ tpd_status run_persistent(bool dec, int arith, void* const* ptrs_dev, const int*
   bp.count = count;
   for (int n = 0; n <= kBatchMaxQubits; ++n) bp.hist[n] = hist[n];
   bp.scale_mode = dec ? 0 : scale_mode;
-  bp.ptrs = ptrs_dev; bp.ns = ns_dev; bp.items = items; bp.ctrl = ctrl;
+  bp.ptrs = ptrs_dev; bp.ns = ns_dev; bp.items = items; bp.bptrs = bptrs; bp.ctrl = ctrl;
   int item_start[kBatchMaxQubits + 2] = {0};
   for (int n = 1; n <= kBatchMaxQubits + 1; ++n) item_start[n] = item_start[n - 1] + hist[n - 1];
   // per n (ascending, as the workspace lays them out): q area and done-counter base
@@ -105,9 +109,10 @@ tpd_status run_persistent(bool dec, int arith, void* const* ptrs_dev, const int*
       if (plans[n]->npass > 1) d += hist[n] * (plans[n]->npass - 1);
     }
   }
-  // CTAs in flight: 2 per SM; a matrix's later pass trails its previous pass
-  // by at least twice that many items, so the tiles it waits for are done
-  const long long inflight = 2ll * sm_count();
+  // claimed items in flight: 2 CTAs per SM, each holding its current and its
+  // next item; a matrix's later pass trails its previous pass by at least
+  // twice that many items, so the tiles it waits for are done
+  const long long inflight = 4ll * sm_count();
   long long first = 1;
   int nseg = 0, ndesc = 0;
   for (int n = kBatchMaxQubits; n >= 7; --n) {
@@ -192,11 +197,13 @@ tpd_status batched(bool dec, void* const* ptrs_dev, const int* ns_dev, const int
   if (reinterpret_cast<uintptr_t>(ws) % 16) return TPD_ERR_MISALIGNED;
   unsigned* ctrl = static_cast<unsigned*>(ws);
   int* items = reinterpret_cast<int*>(static_cast<char*>(ws) + ctrl_bytes);
+  unsigned long long* bptrs =
+      reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(items) + batched_items_bytes(count));
   char* qbase = reinterpret_cast<char*>(items) + batched_head(count);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int caller_variant = opt ? opt->variant : 0;
   if (caller_variant == 2 && persistent_fits(hist, plans))
-    return run_persistent(dec, arith, ptrs_dev, ns_dev, count, hist, plans, scale_mode, ctrl, items, qbase,
+    return run_persistent(dec, arith, ptrs_dev, ns_dev, count, hist, plans, scale_mode, ctrl, items, bptrs, qbase,
                           ctrl_bytes, s);
   if (cudaMemsetAsync(ctrl, 0, ctrl_bytes, s) != cudaSuccess) return TPD_ERR_CUDA;   // status word: OK
   BucketHist bh;

@@ -8,16 +8,24 @@
 // data in L2, or whole small matrices).  A tile of pass p > 0 of matrix m
 // reads what the tiles of pass p-1 of m wrote, so it waits until m's
 // completion counter of pass p-1 is full.  All those tiles were claimed
-// earlier (p-1 runs `lag` rounds ahead) by CTAs that are running and never
-// wait on later items, so the wait ends; it is nonetheless bounded: after
-// kSpinLimit polls the CTA records TPD_ERR_TIMEOUT in the status word and
-// skips the item, and every later item is skipped as soon as the status word
-// is set, so the launch always finishes and the context stays usable.
+// earlier (p-1 runs `lag` rounds ahead).
 //
-// Publication: the CTA finishes a tile's stores, barriers, and one thread
-// issues a gpu-scope fence and increments the counter; the waiting thread
-// polls with ld.acquire.gpu and the CTA barriers before loading, and the
-// loads of data written in this launch go through L2 (ld.global.cg).
+// Claim ahead: a CTA claims its next item when it starts the current one, so
+// the counter's round trip overlaps the current item's lookups.  A CTA thus
+// holds at most two claimed items, the current and the next (not begun), and
+// only running CTAs hold claims.  Every item waits only on lower items, and
+// the lowest unfinished item is always some CTA's current item (a CTA's next
+// item lies above its current one), whose dependencies are all finished: the
+// waits end.  They are nonetheless bounded: after kSpinLimit polls the CTA
+// records TPD_ERR_TIMEOUT in the status word and skips the item, and every
+// later item is skipped as soon as the status word is set, so the launch
+// always finishes and the context stays usable.
+//
+// Publication: the CTA finishes a tile's stores, barriers, and one thread (of
+// warp 1, so that warp 0 goes straight on to the next item) issues a
+// gpu-scope fence and increments the counter; the waiting thread polls with
+// ld.acquire.gpu and the CTA barriers before loading, and the loads of data
+// written in this launch go through L2 (ld.global.cg).
 #pragma once
 
 #include <type_traits>
@@ -55,8 +63,8 @@ static __device__ __noinline__ bool wait_count(const unsigned* p, unsigned need,
 }
 
 // Work item 0: counting sort of the matrix indices by qubit count into
-// bp.items (ascending n, as the host laid out the segments), checking the
-// counts against the host's histogram.
+// bp.items, and of their pointers into bp.bptrs (ascending n, as the host
+// laid out the segments), checking the counts against the host's histogram.
 static __device__ __noinline__ void bucket_item(const BatchParams& bp, int tid, int nthr) {
   __shared__ int cnt[kBatchMaxN + 1];
   __shared__ int cur[kBatchMaxN + 1];
@@ -82,7 +90,9 @@ static __device__ __noinline__ void bucket_item(const BatchParams& bp, int tid, 
   if (!bad)
     for (int i = tid; i < bp.count; i += nthr) {
       const int n = __ldg(bp.ns + i);
-      bp.items[atomicAdd(&cur[n], 1)] = i;
+      const int pos = atomicAdd(&cur[n], 1);
+      bp.items[pos] = i;
+      bp.bptrs[pos] = __ldg(reinterpret_cast<const unsigned long long*>(bp.ptrs) + i);
     }
   __syncthreads();
   if (tid == 0) {
@@ -120,23 +130,27 @@ __device__ __forceinline__ void batch_pass_tile(const BatchSeg& sg, int p, const
 
 // 256 threads; dynamic shared memory: 2^12 x 16 bytes + 256 + 2^kMaxPrevBits
 // ints (a D = 12 tile or a whole n <= 6 matrix, reduction slots, gathered
-// binary points).
+// binary points).  Thread 0 keeps the claimed-ahead item in s_next (its own
+// slot: kept out of registers, which the tile needs) and hands it to the CTA
+// through s_work at the top of the loop.
 template <class A, bool kDec>
 __global__ void __launch_bounds__(256, 2) k_batch(const __grid_constant__ BatchParams bp) {
   using Store = typename A::Store;
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ unsigned s_work;
+  __shared__ unsigned s_work, s_next;
   __shared__ int s_ok;
   __shared__ void* s_mat;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   unsigned* status = bp.ctrl + kCtrlStatus;
   bool seen_bucket = false;
+  if (tid == 0) s_next = atomicAdd(bp.ctrl + kCtrlWork, 1u);
   for (;;) {
-    if (tid == 0) s_work = atomicAdd(bp.ctrl + kCtrlWork, 1u);
+    if (tid == 0) s_work = s_next;
     __syncthreads();
     const long long w = s_work;
     if (w >= bp.total) break;
     if (w == 0) {
+      if (tid == 0) s_next = atomicAdd(bp.ctrl + kCtrlWork, 1u);
       bucket_item(bp, tid, blockDim.x);       // ends with barriers: s_work may be rewritten after it
       seen_bucket = true;
       continue;
@@ -155,21 +169,21 @@ __global__ void __launch_bounds__(256, 2) k_batch(const __grid_constant__ BatchP
       tile = sub - p * sg.tiles;
       j = round - (long long)p * sg.lag;
       if (j < 0 || j >= sg.nmat) {            // empty slot of the pipeline's ramp
+        if (tid == 0) s_next = atomicAdd(bp.ctrl + kCtrlWork, 1u);
         __syncthreads();                      // everyone has read s_work
         continue;
       }
     }
     unsigned* done = bp.ctrl + kCtrlDone + sg.done;
     if (tid == 0) {
+      const unsigned nxt = atomicAdd(bp.ctrl + kCtrlWork, 1u);   // claimed ahead: overlaps the lookups
       bool ok = seen_bucket || wait_count(bp.ctrl + kCtrlBucket, 1u, status);
       if (ok && p > 0)
         ok = wait_count(done + (long long)(p - 1) * sg.nmat + j, (unsigned)(sg.tiles + sg.wait_extra), status);
       ok = ok && ld_volatile(status) == 0;
-      if (ok) {
-        const int m = __ldcg(bp.items + sg.item_start + j);
-        s_mat = bp.ptrs[m];
-      }
+      if (ok) s_mat = reinterpret_cast<void*>(__ldcg(bp.bptrs + sg.item_start + j));
       s_ok = ok;
+      s_next = nxt;
     }
     __syncthreads();
     seen_bucket = true;
@@ -184,7 +198,7 @@ __global__ void __launch_bounds__(256, 2) k_batch(const __grid_constant__ BatchP
       }
     }
     __syncthreads();                          // the tile's stores are done (and smem is free)
-    if (tid == 0 && sg.kind == kSegPipe && p + 1 < sg.npass) {
+    if (tid == 32 && sg.kind == kSegPipe && p + 1 < sg.npass) {   // warp 0 goes on to the next item
       __threadfence();
       atomicAdd(done + (long long)p * sg.nmat + j, 1u);
     }

@@ -77,7 +77,8 @@ struct SmallArgs {
 // pass after the first reads, and the passes overwrite, lines that have not
 // gone back to HBM.  A tile of pass p > 0 waits (bounded) until all tiles of
 // pass p-1 of ITS matrix are done, counted per (pass, matrix) in `done`.  For
-// n <= 6 a segment holds one item per whole matrix.
+// n <= 6 a segment holds one item per whole matrix.  A CTA claims its next
+// item as it starts the current one (two claims per CTA in flight).
 constexpr int kBatchMaxDescs = 16;
 constexpr int kBatchMaxSegs = 12;
 constexpr int kBatchMaxN = 12;
@@ -112,6 +113,7 @@ struct BatchParams {
   void* const* ptrs;          // device array of matrix pointers
   const int* ns;              // device array of n_i
   int* items;                 // bucketed matrix indices (written by item 0)
+  unsigned long long* bptrs;  // bucketed matrix pointers, ptrs[items[k]] (written by item 0)
   unsigned* ctrl;             // [0] next work item, [1] status, [2] bucket done, [3] -, then done counters
 };
 
