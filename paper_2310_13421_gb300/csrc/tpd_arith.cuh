@@ -158,6 +158,14 @@ struct FixedArith {
     return a == 0 ? 0.0 : __longlong_as_double((long long)bits);
   }
 
+  // to_double_fast through the fp64 conversion unit: round to nearest even,
+  // then an exact exponent shift (fast_range(T): every nonzero |v| < 2^62
+  // lands in the normal range).
+  __device__ static __forceinline__ double to_double_cvt_fast(long long v, int T) {
+    const long long b = __double_as_longlong(__ll2double_rn(v)) - ((long long)T << 52);
+    return __longlong_as_double(v == 0 ? 0ll : b);
+  }
+
   // v * 2^-T: the int64 -> double conversion (round to nearest even) followed
   // by an exact exponent shift; out-of-range exponents take the integer path.
   __device__ static __forceinline__ double to_double_cvt(long long v, int T) {
