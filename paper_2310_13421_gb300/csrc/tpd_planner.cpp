@@ -264,8 +264,16 @@ bool build_plan(int n, int dtype, int precision, int tile_bits_opt, int max_leve
         const int m13 = (rem + kmax_for(D1 + 1) - 1) / kmax_for(D1 + 1);
         if (m13 < m) { D1 = D1 + 1; m = m13; }
       }
+      // where 2^13-element tiles save a pass, only the passes that need them
+      // get them; the others take the smallest tile with 128-byte runs, 2K +
+      // lf bits (measured on GB300, n = 15 last pass of 4 levels: 9.72 ms
+      // with 2^13, 8.09 ms with 2^12, 7.28 ms with 2^11 elements)
       const int base = rem / m, extra = rem % m;
-      for (int i = 0; i < m; ++i) g.push_back({base + (i < extra ? 1 : 0), D1});
+      for (int i = 0; i < m; ++i) {
+        const int K = base + (i < extra ? 1 : 0);
+        const int Dsmall = std::max(kMinTileBits, 2 * K + lf);
+        g.push_back({K, (D1 > dmax && K <= kmax_for(dmax)) ? Dsmall : D1});
+      }
     }
     return g;
   };

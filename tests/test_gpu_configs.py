@@ -107,6 +107,38 @@ def test_config_n15_c64_plain_and_compensated(tpd):
     assert e <= 1e-6
 
 
+def test_n15_complex128_sampled_rows_and_planted_chain(tpd):
+    """n = 15 in complex128: the plan mixes 2^12- and 2^13-element tiles (the
+    middle pass of 5 levels needs the larger tile); sampled X-rows against
+    the oracle for a random Hermitian matrix, and the planted Heisenberg
+    chain's weights exactly."""
+    n = 15
+    from paper_2310_13421_gb300 import _lib as L
+    desc = L.tpd_plan_describe(n, 0, L.options())[1]
+    assert "D=13" in desc and "D=12" in desc
+    A = synth.hermitian(n, seed=1015)
+    Ag = torch.from_numpy(A).cuda()
+    rng = np.random.default_rng(1015)
+    xs = [0, 2 ** n - 1, 2 ** (n - 1)] + list(rng.integers(0, 2 ** n, size=9))
+    for prec in ("fixed", "plain"):
+        C = tpd.decompose(Ag, precision=prec)
+        got, want = sample_rows(A, C, n, xs)
+        assert_close(got, want, 1e-12, "n=15 " + prec)
+        assert parseval(Ag, C, n) <= 1e-12
+        del C
+    del Ag
+    J, h = synth.heisenberg_params(n, seed=1016)
+    H = torch.zeros((1 << n, 1 << n), dtype=torch.complex128, device="cuda")
+    synth.heisenberg_into(H, n, J, h)
+    tpd.decompose(H, inplace=True)
+    s, w = tpd.nonzero_list(H)
+    want = sorted((synth.string_index(t), v) for t, v in synth.heisenberg_terms(n, J, h).items())
+    assert s.cpu().tolist() == [k for k, _ in want]
+    assert np.array_equal(w.cpu().numpy(), np.array([v for _, v in want], dtype=np.complex128))
+    del H
+    torch.cuda.empty_cache()
+
+
 def test_config_batch_4096(tpd):
     ns = synth.batch_sizes(4096, seed=1004)
     mats = [torch.empty((2 ** int(n), 2 ** int(n)), dtype=torch.complex128, device="cuda") for n in ns]
