@@ -81,7 +81,10 @@ typedef struct {
                        tile (9..13), for tuning */
   int max_levels;   /* 0 = planner default; otherwise the most qubit levels fused
                        into one pass (1..6), for tuning */
-  int variant;      /* kernel form, for tuning: 0 = default, 1 = one CTA per tile,
+  int variant;      /* kernel form, for tuning: 0 = default, 1 = one CTA per tile
+                       (complex128 tiles of 2^13 elements otherwise run as a
+                       cluster of two 256-thread CTAs sharing the tile through
+                       distributed shared memory),
                        2 = persistent CTAs that prefetch the next tile (complex128
                        fixed point, single matrix, no zero skipping),
                        3 / 4 = one CTA per tile compiled for 2 / 3 CTAs per SM

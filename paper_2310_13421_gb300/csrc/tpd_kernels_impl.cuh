@@ -1,6 +1,8 @@
 // Launch helpers shared by the per-storage-type kernel translation units.
 #pragma once
 
+#include <type_traits>
+
 #include "tpd_launch.h"
 #include "tpd_pass.cuh"
 
@@ -15,9 +17,38 @@ PassKernel pick_pass_kernel(const PassDesc& pd, int threads) {
   return pd.min_blocks >= 3 ? k_pass<A, kDec, 256, 3, kRole> : k_pass<A, kDec, 256, 2, kRole>;
 }
 
+// complex128 tiles of 2^13 elements planned as two-CTA clusters (min_blocks 2)
+template <class A>
+constexpr bool kClusterArith = std::is_same<A, FixedArith>::value || std::is_same<A, F64Arith>::value;
+
+template <class A, bool kDec>
+cudaError_t launch_pass_cl_t(const PassDesc& pd, const PassArgs& args, long long ntiles_total, cudaStream_t s) {
+  const size_t smem = ((size_t)16 << (pd.D - 1)) + 256 + ((A::kFixed && args.q_in) ? sizeof(int) << kMaxPrevBits : 0);
+  PassKernel kfn;
+  if constexpr (A::kFixed) {
+    switch ((args.q_in ? kRoleIntIn : 0) | (args.q_out ? kRoleIntOut : 0)) {
+      case 0: kfn = k_pass_cl<A, kDec, 0>; break;
+      case kRoleIntIn: kfn = k_pass_cl<A, kDec, kRoleIntIn>; break;
+      case kRoleIntOut: kfn = k_pass_cl<A, kDec, kRoleIntOut>; break;
+      default: kfn = k_pass_cl<A, kDec, kRoleIntIn | kRoleIntOut>; break;
+    }
+  } else {
+    kfn = k_pass_cl<A, kDec, 0>;
+  }
+  cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (ntiles_total <= 0) return cudaSuccess;
+  if (2 * ntiles_total > 0x7fffffffll) return cudaErrorInvalidValue;
+  kfn<<<(unsigned)(2 * ntiles_total), 256, smem, s>>>(pd, args);
+  return cudaGetLastError();
+}
+
 template <class A, bool kDec>
 cudaError_t launch_pass_t(const PassDesc& pd, const PassArgs& args, long long ntiles_total, cudaStream_t s) {
   const int threads = 1 << (pd.D - kRegBits);
+  if constexpr (kClusterArith<A>) {
+    if (pd.D == kMaxTileBits && pd.min_blocks == 2) return launch_pass_cl_t<A, kDec>(pd, args, ntiles_total, s);
+  }
   const size_t vbytes = A::kFixed ? 16 : sizeof(typename A::V);
   // exchange area, reduction slots, and (fixed point reading int64 sums) the
   // gathered binary points -- the first pass keeps its occupancy without them

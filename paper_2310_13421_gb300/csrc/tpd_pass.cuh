@@ -15,6 +15,7 @@
 //      mapping, and flag the next pass's tiles that received a nonzero.
 #pragma once
 
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -26,6 +27,41 @@ namespace tpd {
 
 
 constexpr uint32_t kFull = 0xffffffffu;
+
+// -------------------------------------------------------------- two-CTA clusters
+//
+// A complex128 tile of 2^13 elements runs as a cluster of two 256-thread CTAs
+// (kCl = true) instead of one 512-thread CTA: the stage layouts are the
+// 512-thread ones, with the CTA's rank in the cluster as the highest warp
+// bit, so the register budget stays at two CTAs per SM.  Each CTA keeps half
+// of the exchange area -- the elements whose tile bit on that warp bit (in
+// the stage being entered) equals its rank -- and writes the other half into
+// its peer's shared memory.  Protocol per tile: every thread arrives
+// (relaxed) at the cluster barrier on entry and waits right after issuing its
+// global loads, so the peer is running before any access to its shared
+// memory; every exchange and the block-wide reduction end their remote
+// writes with a full cluster barrier before anything reads them, and no
+// remote access follows the last barrier, so either CTA may exit after it.
+// Decisions that end a tile early (all-zero, Inf/NaN) are taken from
+// cluster-wide values, so both CTAs take the same path and meet the same
+// barriers.
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_arrive_relaxed() {
+  asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.aligned;\n\tbarrier.cluster.wait.aligned;" ::: "memory");
+}
+// the same shared-memory location in the other CTA of the cluster
+template <class T>
+__device__ __forceinline__ T* peer_smem(T* p) {
+  return cooperative_groups::this_cluster().map_shared_rank(p, cluster_rank() ^ 1u);
+}
 
 // Loads of data a pass reads.  kCg = false: the read-only path (ld.global.nc),
 // valid when nothing in the same launch writes the data; kCg = true: loads
@@ -146,10 +182,43 @@ __device__ __forceinline__ void stage_levels(typename A::V (&v)[kElems], const S
   }
 }
 
-// Shared-memory exchange from stage `a`'s mapping to stage `b`'s.
-template <class V>
+// Shared-memory exchange from stage `a`'s mapping to stage `b`'s.  kCl: the
+// tile is split over a two-CTA cluster (see above): an element goes to the
+// CTA whose rank equals its tile bit on b's highest warp bit, at its tile
+// index with that bit removed.
+template <bool kCl = false, class V>
 __device__ __forceinline__ void exchange(V (&v)[kElems], const PassDesc& pd, const Stage& a,
                                          const Stage& b, V* sm, int lane, int warp, bool sync_first) {
+  if constexpr (kCl) {
+    if (sync_first) cluster_sync();           // both CTAs have read the previous exchange
+    const int cb = b.warp[3];                 // >= 3: lanes hold tile bits 0..2
+    const int lowm = (1 << cb) - 1;
+    auto squeeze = [&](int x) { return (x & lowm) | ((x >> 1) & ~lowm); };
+    V* const mine = sm;
+    V* const peer = peer_smem(sm);
+    const int rank = (int)cluster_rank();
+    {
+      const int t = thread_sidx(pd, a, lane, warp);
+      const int lt = squeeze(t), ot = (t >> cb) & 1;
+      const int w0 = squeeze(1 << a.reg[0]), w1 = squeeze(1 << a.reg[1]);
+      const int w2 = squeeze(1 << a.reg[2]), w3 = squeeze(1 << a.reg[3]);
+      const int o0 = a.reg[0] == cb, o1 = a.reg[1] == cb, o2 = a.reg[2] == cb, o3 = a.reg[3] == cb;
+#pragma unroll
+      for (int e = 0; e < kElems; ++e) {
+        const int own = ot ^ reg_off(e, o0, o1, o2, o3);
+        (own == rank ? mine : peer)[lt + reg_off(e, w0, w1, w2, w3)] = v[e];
+      }
+    }
+    cluster_sync();
+    {
+      const int lt = squeeze(thread_sidx(pd, b, lane, warp));
+      const int w0 = squeeze(1 << b.reg[0]), w1 = squeeze(1 << b.reg[1]);
+      const int w2 = squeeze(1 << b.reg[2]), w3 = squeeze(1 << b.reg[3]);
+#pragma unroll
+      for (int e = 0; e < kElems; ++e) v[e] = mine[lt + reg_off(e, w0, w1, w2, w3)];
+    }
+    return;
+  }
   if (sync_first) __syncthreads();
   {
     const int t = thread_sidx(pd, a, lane, warp);
@@ -167,7 +236,7 @@ __device__ __forceinline__ void exchange(V (&v)[kElems], const PassDesc& pd, con
 }
 
 // Stages, rounding and the in-place store, for arithmetic A on loaded data.
-template <class A, bool kDec, class Raw>
+template <class A, bool kDec, bool kCl = false, class Raw>
 __device__ __forceinline__ void finish_tile(const PassDesc& pd, const PassArgs& args, void* matp,
                                             const Raw (&raw)[kElems], double mul, long long base,
                                             int nbase, unsigned char* smem, int lane, int warp) {
@@ -178,7 +247,7 @@ __device__ __forceinline__ void finish_tile(const PassDesc& pd, const PassArgs& 
   for (int e = 0; e < kElems; ++e) v[e] = A::load(raw[e]);
   V* sm = reinterpret_cast<V*>(smem);
   for (int s = 0; s < pd.nstage; ++s) {
-    if (s > 0) exchange(v, pd, pd.st[s - 1], pd.st[s], sm, lane, warp, s > 1);
+    if (s > 0) exchange<kCl>(v, pd, pd.st[s - 1], pd.st[s], sm, lane, warp, s > 1);
     stage_levels<A, kDec>(v, pd.st[s], lane);
   }
   const Stage& sl = pd.st[pd.nstage - 1];
@@ -289,7 +358,7 @@ __device__ __forceinline__ long long shr_floor(long long v, unsigned sh) {
 // line (never taken for finite data) so the hot path stays small in the
 // instruction cache.  Elements are re-read: doubles as such, int64 sums of a
 // previous pass converted with their tile's binary point.
-template <bool kDec, bool kCg = false>
+template <bool kDec, bool kCg = false, bool kCl = false>
 __device__ __noinline__ void ieee_tile(const PassDesc& pd, const PassArgs& args, void* matp, const int* q_in,
                                        int* q_out, long long tile, long long base, long long pbase, int nbase,
                                        unsigned char* smem, int lane, int warp) {
@@ -315,8 +384,8 @@ __device__ __noinline__ void ieee_tile(const PassDesc& pd, const PassArgs& args,
   }
   const bool last = q_out == nullptr;
   const double mul = kDec ? pow2d(-pd.K) : (last ? pow2d(args.out_pow2) * args.out_mul : 1.0);
-  finish_tile<F64Arith, kDec>(pd, args, matp, raw, mul, base, nbase, smem, lane, warp);
-  if (!last && threadIdx.x == 0) q_out[tile] = kQIeee;
+  finish_tile<F64Arith, kDec, kCl>(pd, args, matp, raw, mul, base, nbase, smem, lane, warp);
+  if (!last && threadIdx.x == 0 && (!kCl || cluster_rank() == 0)) q_out[tile] = kQIeee;
 }
 
 // The tile's elements in the stage-0 mapping from a shared-memory copy.
@@ -338,13 +407,16 @@ __device__ __forceinline__ void load_tile_smem(const PassDesc& pd, const unsigne
 // xbuf: shared-memory exchange area (2^D x 16 bytes); red: 64 ints;
 // inbuf: the tile already copied to shared memory (stage-0 positions), or
 // nullptr to read it from global memory.
-template <bool kDec, int kRole, bool kCg = false>
+// kCl: one CTA of a two-CTA cluster (warp: the virtual warp, rank * 8 + the
+// CTA's own warp; red: this CTA's reduction slots).
+template <bool kDec, int kRole, bool kCg = false, bool kCl = false>
 __device__ __forceinline__ void fixed_tile(const PassDesc& pd, const PassArgs& args, void* matp, const int* q_in,
                                            int* q_out, long long tile, long long base, long long pbase, int nbase,
                                            const unsigned char* inbuf, unsigned char* xbuf, int* red, int lane,
                                            int warp) {
   using V = FixedArith::V;
-  const int nwarps = 1 << (pd.D - kMinTileBits);
+  const int nwarps = 1 << (pd.D - kMinTileBits - (kCl ? 1 : 0));   // this CTA's warps
+  const int lwarp = kCl ? (warp & 7) : warp;
   unsigned char* smem = xbuf;
   V v[kElems];
   int qin;
@@ -353,6 +425,7 @@ __device__ __forceinline__ void fixed_tile(const PassDesc& pd, const PassArgs& a
     double2 raw[kElems];
     if (inbuf) load_tile_smem(pd, inbuf, lane, warp, raw);
     else load_tile<kCg>(pd, matp, base, lane, warp, raw);
+    if constexpr (kCl) cluster_wait();                   // the peer CTA is running
     uint32_t hmax = 0, nzw = 0;
 #pragma unroll
     for (int e = 0; e < kElems; ++e) {
@@ -368,13 +441,27 @@ __device__ __forceinline__ void fixed_tile(const PassDesc& pd, const PassArgs& a
       nzw = __reduce_or_sync(kFull, nzw);
     }
     const uint32_t wmax = __reduce_max_sync(kFull, hmax >> 20);
-    if (lane == 0) { red[warp] = (int)wmax; red[16 + warp] = (int)nzw; }
-    __syncthreads();
     int emax = 0, nz = 0;
-    for (int w = 0; w < nwarps; ++w) { emax = max(emax, red[w]); nz |= red[16 + w]; }
+    if constexpr (kCl) {
+      // this CTA's warp maxima into its own slots 0..15 and the peer's 32..47
+      int* pred = peer_smem(red);
+      if (lane == 0) {
+        red[lwarp] = (int)wmax; red[16 + lwarp] = (int)nzw;
+        pred[32 + lwarp] = (int)wmax; pred[48 + lwarp] = (int)nzw;
+      }
+      cluster_sync();
+      for (int w = 0; w < nwarps; ++w) {
+        emax = max(emax, max(red[w], red[32 + w]));
+        nz |= red[16 + w] | red[48 + w];
+      }
+    } else {
+      if (lane == 0) { red[warp] = (int)wmax; red[16 + warp] = (int)nzw; }
+      __syncthreads();
+      for (int w = 0; w < nwarps; ++w) { emax = max(emax, red[w]); nz |= red[16 + w]; }
+    }
     if (args.skip_zero && nz == 0) return;                // all +-0: outputs are zero already
     if (emax == 2047) {                                   // Inf/NaN in the tile
-      ieee_tile<kDec, kCg>(pd, args, matp, nullptr, q_out, tile, base, pbase, nbase, smem, lane, warp);
+      ieee_tile<kDec, kCg, kCl>(pd, args, matp, nullptr, q_out, tile, base, pbase, nbase, smem, lane, warp);
       return;
     }
     // x * 2^S with S = 1084 - K - emax_eff puts the largest element below 2^(62-K)
@@ -391,6 +478,7 @@ __device__ __forceinline__ void fixed_tile(const PassDesc& pd, const PassArgs& a
     longlong2 raw[kElems];
     if (inbuf) load_tile_smem(pd, inbuf, lane, warp, raw);
     else load_tile<kCg>(pd, matp, base, lane, warp, raw);
+    if constexpr (kCl) cluster_wait();                   // the peer CTA is running
     // The tile's elements come from 2^prev_nb previous tiles (<= 2^kMaxPrevBits):
     // their binary points are loaded once each into shared memory (qs), and
     // each element finds its own there by its combination index.
@@ -398,8 +486,9 @@ __device__ __forceinline__ void fixed_tile(const PassDesc& pd, const PassArgs& a
     int* qs = red + 64;
     int qmax = kQValidMin, ieee = 0;
     {
+      // (each CTA of a cluster gathers all of them: both see the same maximum)
       const int nq = 1 << pd.prev_nb, nthr = 32 * nwarps;
-      for (int j = lane + 32 * warp; j < nq; j += nthr) {
+      for (int j = lane + 32 * lwarp; j < nq; j += nthr) {
         long long idx = pbase;
         for (int k = 0; k < pd.prev_nb; ++k)
           if ((j >> k) & 1) idx += pd.prev_cw[k];
@@ -420,12 +509,12 @@ __device__ __forceinline__ void fixed_tile(const PassDesc& pd, const PassArgs& a
     // kQIeee sits below kQValidMin, so it never wins the max
     qmax = __reduce_max_sync(kFull, qmax);
     ieee = __reduce_or_sync(kFull, ieee);
-    if (lane == 0) { red[warp] = qmax; red[16 + warp] = ieee; }
+    if (lane == 0) { red[lwarp] = qmax; red[16 + lwarp] = ieee; }
     __syncthreads();
     qmax = kQValidMin; ieee = 0;
     for (int w = 0; w < nwarps; ++w) { qmax = max(qmax, red[w]); ieee |= red[16 + w]; }
     if (ieee) {
-      ieee_tile<kDec, kCg>(pd, args, matp, q_in, q_out, tile, base, pbase, nbase, smem, lane, warp);
+      ieee_tile<kDec, kCg, kCl>(pd, args, matp, q_in, q_out, tile, base, pbase, nbase, smem, lane, warp);
       return;
     }
     if (qmax == kQValidMin) {                              // every source tile was zero
@@ -449,7 +538,7 @@ __device__ __forceinline__ void fixed_tile(const PassDesc& pd, const PassArgs& a
   // ---- the pass's levels
   V* sm = reinterpret_cast<V*>(smem);
   for (int s = 0; s < pd.nstage; ++s) {
-    if (s > 0) exchange(v, pd, pd.st[s - 1], pd.st[s], sm, lane, warp, s > 1);
+    if (s > 0) exchange<kCl>(v, pd, pd.st[s - 1], pd.st[s], sm, lane, warp, s > 1);
     stage_levels<FixedArith, kDec>(v, pd.st[s], lane);
   }
   const int qout = qin - (kDec ? pd.K : 0);                // the 1/2 of Eq. 4 per level
@@ -473,7 +562,7 @@ __device__ __forceinline__ void fixed_tile(const PassDesc& pd, const PassArgs& a
     longlong2* mat = reinterpret_cast<longlong2*>(matp);
 #pragma unroll
     for (int e = 0; e < kElems; ++e) mat[g + reg_off(e, w0, w1, w2, w3)] = make_longlong2(v[e].re, v[e].im);
-    if (threadIdx.x == 0) q_out[tile] = qout;
+    if (threadIdx.x == 0 && (!kCl || cluster_rank() == 0)) q_out[tile] = qout;
   } else {
     double2* mat = reinterpret_cast<double2*>(matp);
     const int T = -(qout + args.out_pow2);
@@ -595,12 +684,14 @@ __device__ __forceinline__ void fixed32_tile(const PassDesc& pd, const PassArgs&
 }
 
 // One tile of a pass: its position from the tile id, then the arithmetic's
-// load / levels / store.  smem: the exchange area (2^D x 16 bytes) followed by
-// 64 ints of reduction slots.
-template <class A, bool kDec, int kRole, bool kCg>
+// load / levels / store.  smem: the exchange area (2^D x 16 bytes; half of it
+// per CTA of a two-CTA cluster) followed by 64 ints of reduction slots.
+template <class A, bool kDec, int kRole, bool kCg, bool kCl = false>
 __device__ __forceinline__ void pass_tile(const PassDesc& pd, const PassArgs& args, void* matp, const int* q_in,
                                           int* q_out, long long tile, unsigned char* smem, int lane, int warp) {
   using Store = typename A::Store;
+  static_assert(!(kCl && A::kFixed32), "two-CTA clusters serve complex128 tiles only");
+  int* red = reinterpret_cast<int*>(smem + ((size_t)16 << (pd.D - (kCl ? 1 : 0))));
   long long base = 0, pbase = 0;
   int nbase = 0;
   for (int j = 0; j < pd.nrest; ++j)
@@ -611,21 +702,27 @@ __device__ __forceinline__ void pass_tile(const PassDesc& pd, const PassArgs& ar
     }
 
   if constexpr (A::kFixed) {
-    fixed_tile<kDec, kRole, kCg>(pd, args, matp, q_in, q_out, tile, base, pbase, nbase, nullptr, smem,
-                                 reinterpret_cast<int*>(smem + ((size_t)16 << pd.D)), lane, warp);
+    fixed_tile<kDec, kRole, kCg, kCl>(pd, args, matp, q_in, q_out, tile, base, pbase, nbase, nullptr, smem, red,
+                                      lane, warp);
   } else if constexpr (A::kFixed32) {
-    fixed32_tile<kDec, kCg>(pd, args, matp, base, nbase, smem, reinterpret_cast<int*>(smem + ((size_t)16 << pd.D)),
-                            lane, warp);
+    fixed32_tile<kDec, kCg>(pd, args, matp, base, nbase, smem, red, lane, warp);
   } else {
     Store raw[kElems];
     load_tile<kCg>(pd, matp, base, lane, warp, raw);
+    if constexpr (kCl) cluster_wait();                   // the peer CTA is running
     if (args.skip_zero) {
       int nz = 0;
 #pragma unroll
       for (int e = 0; e < kElems; ++e) nz |= A::nonzero(raw[e]);
-      if (!__syncthreads_or(nz)) return;
+      nz = __syncthreads_or(nz);
+      if constexpr (kCl) {                               // cluster-wide: slot 0 here, slot 1 at the peer
+        if (threadIdx.x == 0) { red[0] = nz; peer_smem(red)[1] = nz; }
+        cluster_sync();
+        nz = red[0] | red[1];
+      }
+      if (!nz) return;
     }
-    finish_tile<A, kDec>(pd, args, matp, raw, args.out_mul, base, nbase, smem, lane, warp);
+    finish_tile<A, kDec, kCl>(pd, args, matp, raw, args.out_mul, base, nbase, smem, lane, warp);
   }
 }
 
@@ -662,6 +759,41 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
   if (args.flags_in != nullptr && args.flags_in[tile] == 0) return;
   if (args.need != nullptr && args.need[tile] == 0) return;
   pass_tile<A, kDec, kRole, false>(pd, args, matp, q_in, q_out, tile, smem, lane, warp);
+}
+
+// Complex128 tiles of 2^13 elements as two-CTA clusters of 256 threads (see
+// the top of this file): grid = 2 x tiles, tile = cluster index.
+template <class A, bool kDec, int kRole = 0>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 2)
+    k_pass_cl(const __grid_constant__ PassDesc pd, const __grid_constant__ PassArgs args) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int warp = (int)(cluster_rank() << 3) | (tid >> 5);   // the 512-thread layout's warp
+  long long tile = (long long)(blockIdx.x >> 1);
+  void* matp = args.mat;
+  const int* q_in = args.q_in;
+  int* q_out = args.q_out;
+  if (args.chunked) {
+    unsigned long long t = args.chunk_or;
+    for (int k = 0; k < args.nfree; ++k)
+      if ((tile >> k) & 1) t |= 1ull << args.chunk_free[k];
+    tile = (long long)t;
+  }
+  if (args.ptrs != nullptr) {
+    const long long m = tile / args.tiles_per_mat;
+    tile -= m * args.tiles_per_mat;
+    const int idx = args.items[m];
+    if (idx < 0) return;
+    matp = args.ptrs[idx];
+    if (q_in) q_in += m * args.q_in_stride;
+    if (q_out) q_out += m * args.q_out_stride;
+  }
+  // both CTAs of a cluster share the tile, so they leave here together
+  if (tile >= pd.ntiles) return;
+  if (args.flags_in != nullptr && args.flags_in[tile] == 0) return;
+  if (args.need != nullptr && args.need[tile] == 0) return;
+  cluster_arrive_relaxed();
+  pass_tile<A, kDec, kRole, false, true>(pd, args, matp, q_in, q_out, tile, smem, lane, warp);
 }
 
 // -------------------------------------------------------------- persistent, double buffered

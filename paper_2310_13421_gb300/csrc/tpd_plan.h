@@ -66,7 +66,8 @@ struct PassDesc {
   int64_t next_rest_w[2 * kMaxQubits];
   // Fixed point between passes: an element's tile id in the PREVIOUS pass
   // (whose per-tile binary point it was stored with), by the same linear rule.
-  int32_t min_blocks;        // CTAs per SM the pass kernel is compiled for (2 or 3; 1 for 512 threads)
+  int32_t min_blocks;        // CTAs per SM the pass kernel is compiled for (2 or 3); D = 13: 1 = one
+                             // CTA of 512 threads, 2 = a two-CTA cluster of 256 (complex128)
   int32_t has_prev;
   int32_t prev_w[kMaxTileBits];
   int64_t prev_rest_w[2 * kMaxQubits];

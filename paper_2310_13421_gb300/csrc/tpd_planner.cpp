@@ -335,7 +335,9 @@ bool build_plan(int n, int dtype, int precision, int tile_bits_opt, int max_leve
   for (int p = 0; p < plan->npass; ++p) {
     PassDesc& pd = plan->pass[p];
     const bool first_of_many = p == 0 && plan->npass > 1;
-    pd.min_blocks = pd.D > 12 ? 1 : ((dtype == 0 && precision == 3 && first_of_many) ? 3 : 2);
+    // 2^13-element complex128 tiles: a two-CTA cluster of 256 threads
+    // (min_blocks 2); other 2^13 tiles: one CTA of 512 threads (1)
+    pd.min_blocks = pd.D > 12 ? (dtype == 0 ? 2 : 1) : ((dtype == 0 && precision == 3 && first_of_many) ? 3 : 2);
   }
   return true;
 }

@@ -157,6 +157,31 @@ def test_c128_nonfinite_tiles_follow_ieee(tpd):
     assert fin.any() and np.allclose(fixed[fin], plain[fin], rtol=1e-12, atol=1e-12)
 
 
+@pytest.mark.parametrize("n,opt", [(11, {}), (12, dict(tile_bits=13)), (13, dict(tile_bits=13, max_levels=5))])
+def test_c128_cluster_tiles_match_one_cta(tpd, n, opt):
+    """Complex128 tiles of 2^13 elements run as a cluster of two 256-thread
+    CTAs; one 512-thread CTA per tile (variant 1) computes the same sums in
+    the same order: identical bits, decomposition and composition, with and
+    without zero skipping (also on a matrix with all-zero tiles), fixed
+    point and fp64; and the oracle where it is cheap."""
+    from paper_2310_13421_gb300 import _lib as L
+    assert "D=13" in L.tpd_plan_describe(n, 0, L.options(**opt))[1]
+    A = synth.general(n, seed=4100 + n)
+    H = synth.heisenberg(n, *synth.heisenberg_params(n, seed=4150 + n))
+    for prec in ("fixed", "plain"):
+        for M in (A, H):
+            for skip in (False, True):
+                cl = host(tpd.decompose(gpu(M), precision=prec, skip_zero=skip, **opt))
+                one = host(tpd.decompose(gpu(M), precision=prec, skip_zero=skip, variant=1, **opt))
+                assert_exact(cl, one, "decompose n=%d %s skip=%s" % (n, prec, skip))
+        c_cl = host(tpd.compose(gpu(A), precision=prec, **opt))
+        c_one = host(tpd.compose(gpu(A), precision=prec, variant=1, **opt))
+        assert_exact(c_cl, c_one, "compose n=%d %s" % (n, prec))
+        if n <= 12:
+            got = to_string_order(host(tpd.decompose(gpu(A), precision=prec, **opt)), n)
+            assert_close(got, oracle.coeffs_fwht(A), TOL128, "oracle n=%d %s" % (n, prec))
+
+
 def test_c128_zero_matrix_and_skip(tpd):
     for n in (3, 7, 10):
         Z = torch.zeros((2 ** n, 2 ** n), dtype=torch.complex128, device="cuda")
@@ -274,7 +299,8 @@ def test_adjoint_dot_product(tpd):
 
 def test_batched_mixed_sizes(tpd):
     rng = np.random.default_rng(8000)
-    ns = [1, 2, 3, 4, 5, 6, 7, 8, 9, 10] + list(rng.integers(1, 11, size=22))
+    # n = 11: a second pass of 2^13-element tiles (two-CTA clusters); n = 12: the largest batched size
+    ns = [1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 11] + list(rng.integers(1, 11, size=22))
     mats = [synth.general(int(n), seed=8000 + i) for i, n in enumerate(ns)]
     for prec in ("fixed", "plain"):
         outs = tpd.decompose_batched([gpu(m) for m in mats], precision=prec)
