@@ -251,41 +251,57 @@ bool build_plan(int n, int dtype, int precision, int tile_bits_opt, int max_leve
   dmax = std::min(dmax, 2 * n);
   int kcap = max_levels_opt ? max_levels_opt : kMaxLevels;
   auto kmax_for = [&](int D) { return std::max(1, std::min({(D - lf) / 2, kcap, kMaxLevels})); };
+  // A pass over 2^13-element tiles (the 5-level passes) runs ~1.6x longer than
+  // one over 2^12 on GB300 (128-byte runs; measured 3.2-4.6 against 5.1-5.7
+  // TB/s), so it counts as 1.6 passes when plans are compared.
+  constexpr double kWeightD13 = 1.6;
+  auto weight = [&](const std::vector<std::pair<int, int>>& g) {
+    double w = 0.0;
+    for (const auto& kd : g) w += kd.second > 12 ? kWeightD13 : 1.0;
+    return w;
+  };
   // passes for a first pass of k0 levels: the rest split evenly over as few
-  // passes as possible (2^13-element tiles only where that saves a pass)
+  // passes as possible (2^13-element tiles only where that weighs less)
   auto groups_for = [&](int k0) {
     std::vector<std::pair<int, int>> g;  // (K, D)
     g.push_back({k0, dmax});
     const int rem = n - k0;
     if (rem > 0) {
-      int D1 = dmax;
-      int m = (rem + kmax_for(D1) - 1) / kmax_for(D1);
-      if (!tile_bits_opt && D1 < kMaxTileBits && 2 * n >= D1 + 1) {
-        const int m13 = (rem + kmax_for(D1 + 1) - 1) / kmax_for(D1 + 1);
-        if (m13 < m) { D1 = D1 + 1; m = m13; }
-      }
-      // where 2^13-element tiles save a pass, only the passes that need them
+      // where 2^13-element tiles are chosen, only the passes that need them
       // get them; the others take the smallest tile with 128-byte runs, 2K +
       // lf bits (measured on GB300, n = 15 last pass of 4 levels: 9.72 ms
       // with 2^13, 8.09 ms with 2^12, 7.28 ms with 2^11 elements)
-      const int base = rem / m, extra = rem % m;
-      for (int i = 0; i < m; ++i) {
-        const int K = base + (i < extra ? 1 : 0);
-        const int Dsmall = std::max(kMinTileBits, 2 * K + lf);
-        g.push_back({K, (D1 > dmax && K <= kmax_for(dmax)) ? Dsmall : D1});
+      auto split = [&](int D1) {
+        std::vector<std::pair<int, int>> r;
+        const int m = (rem + kmax_for(D1) - 1) / kmax_for(D1);
+        const int base = rem / m, extra = rem % m;
+        for (int i = 0; i < m; ++i) {
+          const int K = base + (i < extra ? 1 : 0);
+          const int Dsmall = std::max(kMinTileBits, 2 * K + lf);
+          r.push_back({K, (D1 > dmax && K <= kmax_for(dmax)) ? Dsmall : D1});
+        }
+        return r;
+      };
+      std::vector<std::pair<int, int>> rest = split(dmax);
+      if (!tile_bits_opt && dmax < kMaxTileBits && 2 * n >= dmax + 1) {
+        std::vector<std::pair<int, int>> r13 = split(dmax + 1);
+        if (weight(r13) < weight(rest) - 1e-9) rest = r13;
       }
+      g.insert(g.end(), rest.begin(), rest.end());
     }
     return g;
   };
-  // the first pass's level count: fewest passes, then the least in-pass
-  // data movement (the stage search's cost: exchanges and shuffle levels)
+  // the first pass's level count: the least weighted pass count, then the
+  // least in-pass data movement (the stage search's cost: exchanges and
+  // shuffle levels)
   const int k0max = std::min({n, dmax / 2, kcap});
   std::vector<std::pair<int, int>> groups;
   double best_cost = 1e30;
-  size_t best_passes = (size_t)-1;
+  double best_passes = 1e30;
   for (int k0 = k0max; k0 >= 1; --k0) {
     std::vector<std::pair<int, int>> g = groups_for(k0);
-    if (g.size() > best_passes) continue;
+    const double wg = weight(g);
+    if (wg > best_passes + 1e-9) continue;
     double cost = 0.0;
     bool ok = true;
     int b = 0;
@@ -299,8 +315,8 @@ bool build_plan(int n, int dtype, int precision, int tile_bits_opt, int max_leve
       b += kd.first;
     }
     if (!ok) continue;
-    if (g.size() < best_passes || cost < best_cost - 1e-9) {
-      best_passes = g.size();
+    if (wg < best_passes - 1e-9 || cost < best_cost - 1e-9) {
+      best_passes = wg;
       best_cost = cost;
       groups = g;
     }
