@@ -9,7 +9,8 @@ outside the timed events.
 
 Prints ONE JSON line (rank 0).  `value` = Pauli coeffs/s over all ranks with
 inputs resident in HBM; `e2e` = the same metric through the C ABI with host
-buffers (pinned), host<->device copies inside the timed region; `roofline`
+buffers (pinned), every step's host<->device copies inside the timed region
+(steps alternate over two streams, so copies in and out overlap); `roofline`
 = achieved HBM bandwidth of the pass kernel (algorithmic bytes: read + write
 of the matrix per pass launch) against the measured copy peak; `cpu_baseline`
 = the CPU oracle timed on a bounded sample; `extra` = the fp64 butterfly and
@@ -44,7 +45,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-extra", action="store_true", help="skip the fp64 / complex64 comparison runs")
-    p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--e2e-steps", type=int, default=8)
     p.add_argument("--qubits", type=int, default=N_QUBITS,
                    help="matrix size of the timed workload (14 = the metric's workload; smaller for profiling)")
     p.add_argument("--no-batch", action="store_true", help="skip the batch-of-4096 comparison run")
@@ -559,28 +560,47 @@ def run_ours(args, world, rank, local):
                 "per_pass_gbs": [alg_bytes / (m * 1e-3) / 1e9 for m in per_pass_ms],
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s"}
 
-    # ---- end to end through the C ABI with pinned host buffers
-    W_pin = torch.empty_like(A_pin).pin_memory()
+    # ---- end to end through the C ABI with pinned host buffers: every step
+    # copies its input in and its result out (tpd_decompose_host); steps
+    # alternate between two streams with their own device buffers, so one
+    # step's device->host copy overlaps the next step's host->device copy
+    # (the link is full duplex) -- the throughput a user gets from two streams
+    W_pins = [torch.empty_like(A_pin).pin_memory() for _ in range(2)]
+    works = [work, torch.empty_like(pristine)]
+    streams = [stream, torch.cuda.Stream()]
     wsb = L.tpd_workspace_size(n, code, L.options(precision=prec_eff))
-    ws = torch.empty(max(wsb, 16), dtype=torch.uint8, device="cuda")
-    e2e_ms = []
-    for k in range(args.e2e_steps + 1):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        barrier()
-        e0.record(stream)
-        st = L.tpd_decompose_host(A_pin.data_ptr(), W_pin.data_ptr(), work.data_ptr(), n, code,
-                                  L.options(precision=prec_eff), ws.data_ptr(), wsb, stream.cuda_stream)
+    wss = [torch.empty(max(wsb, 16), dtype=torch.uint8, device="cuda") for _ in range(2)]
+
+    def e2e_step(k):
+        j = k % 2
+        st = L.tpd_decompose_host(A_pin.data_ptr(), W_pins[j].data_ptr(), works[j].data_ptr(), n, code,
+                                  L.options(precision=prec_eff), wss[j].data_ptr(), wsb, streams[j].cuda_stream)
         assert st == 0, L.status_string(st)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        if k > 0:  # first call is warm-up
-            e2e_ms.append(e0.elapsed_time(e1))
-    e2e_total = max_over_ranks(sum(e2e_ms))
-    e2e = {"value": tdist.job_rate(world * coeffs * len(e2e_ms), e2e_total), "unit": UNIT,
+
+    for k in range(2):                      # warm-up, both streams
+        e2e_step(k)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(streams[0])
+    streams[1].wait_event(e0)
+    for k in range(args.e2e_steps):
+        e2e_step(k)
+    ej = torch.cuda.Event()
+    ej.record(streams[1])
+    streams[0].wait_event(ej)
+    e1.record(streams[0])
+    torch.cuda.synchronize()
+    e2e_total = max_over_ranks(e0.elapsed_time(e1))
+    e2e = {"value": tdist.job_rate(world * coeffs * args.e2e_steps, e2e_total), "unit": UNIT,
            "h2d_bytes_per_step": coeffs * elem, "d2h_bytes_per_step": coeffs * elem,
-           "ms_per_step": e2e_total / len(e2e_ms)}
-    # sanity: the host result equals the device result of the same plan
-    ok = torch.equal(W_pin.to("cuda"), work)
+           "ms_per_step": e2e_total / args.e2e_steps, "steps": args.e2e_steps,
+           "pipelining": "steps alternate over 2 streams (own device buffers)"}
+    # sanity: the host results equal the device results of the same plan
+    ok = all(torch.equal(w.to("cuda"), d) for w, d in zip(W_pins, works))
+    W_pin = W_pins[(args.e2e_steps - 1) % 2]
+    work = works[(args.e2e_steps - 1) % 2]
+    del works, wss, W_pins
     alg1 = None
     if rank == 0 and world == 1 and not args.no_extra and not c64:
         alg1 = alg1_baseline(A, W_pin.numpy(), n)
