@@ -46,6 +46,7 @@ def parse():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-extra", action="store_true", help="skip the fp64 / complex64 comparison runs")
     p.add_argument("--e2e-steps", type=int, default=8)
+    p.add_argument("--e2e-streams", type=int, default=3, help="streams the end-to-end steps alternate over")
     p.add_argument("--qubits", type=int, default=N_QUBITS,
                    help="matrix size of the timed workload (14 = the metric's workload; smaller for profiling)")
     p.add_argument("--no-batch", action="store_true", help="skip the batch-of-4096 comparison run")
@@ -564,42 +565,45 @@ def run_ours(args, world, rank, local):
     # copies its input in and its result out (tpd_decompose_host); steps
     # alternate between two streams with their own device buffers, so one
     # step's device->host copy overlaps the next step's host->device copy
-    # (the link is full duplex) -- the throughput a user gets from two streams
-    W_pins = [torch.empty_like(A_pin).pin_memory() for _ in range(2)]
-    works = [work, torch.empty_like(pristine)]
-    streams = [stream, torch.cuda.Stream()]
+    # (the link is full duplex) -- the throughput a user gets from several streams
+    ns_ = max(1, args.e2e_streams)
+    W_pins = [torch.empty_like(A_pin).pin_memory() for _ in range(ns_)]
+    works = [work] + [torch.empty_like(pristine) for _ in range(ns_ - 1)]
+    streams = [stream] + [torch.cuda.Stream() for _ in range(ns_ - 1)]
     wsb = L.tpd_workspace_size(n, code, L.options(precision=prec_eff))
-    wss = [torch.empty(max(wsb, 16), dtype=torch.uint8, device="cuda") for _ in range(2)]
+    wss = [torch.empty(max(wsb, 16), dtype=torch.uint8, device="cuda") for _ in range(ns_)]
 
     def e2e_step(k):
-        j = k % 2
+        j = k % ns_
         st = L.tpd_decompose_host(A_pin.data_ptr(), W_pins[j].data_ptr(), works[j].data_ptr(), n, code,
                                   L.options(precision=prec_eff), wss[j].data_ptr(), wsb, streams[j].cuda_stream)
         assert st == 0, L.status_string(st)
 
-    for k in range(2):                      # warm-up, both streams
+    for k in range(ns_):                    # warm-up, every stream
         e2e_step(k)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     e0.record(streams[0])
-    streams[1].wait_event(e0)
+    for st_ in streams[1:]:
+        st_.wait_event(e0)
     for k in range(args.e2e_steps):
         e2e_step(k)
-    ej = torch.cuda.Event()
-    ej.record(streams[1])
-    streams[0].wait_event(ej)
+    for st_ in streams[1:]:
+        ej = torch.cuda.Event()
+        ej.record(st_)
+        streams[0].wait_event(ej)
     e1.record(streams[0])
     torch.cuda.synchronize()
     e2e_total = max_over_ranks(e0.elapsed_time(e1))
     e2e = {"value": tdist.job_rate(world * coeffs * args.e2e_steps, e2e_total), "unit": UNIT,
            "h2d_bytes_per_step": coeffs * elem, "d2h_bytes_per_step": coeffs * elem,
            "ms_per_step": e2e_total / args.e2e_steps, "steps": args.e2e_steps,
-           "pipelining": "steps alternate over 2 streams (own device buffers)"}
+           "pipelining": "steps alternate over %d streams (own device buffers)" % ns_}
     # sanity: the host results equal the device results of the same plan
     ok = all(torch.equal(w.to("cuda"), d) for w, d in zip(W_pins, works))
-    W_pin = W_pins[(args.e2e_steps - 1) % 2]
-    work = works[(args.e2e_steps - 1) % 2]
+    W_pin = W_pins[(args.e2e_steps - 1) % ns_]
+    work = works[(args.e2e_steps - 1) % ns_]
     del works, wss, W_pins
     alg1 = None
     if rank == 0 and world == 1 and not args.no_extra and not c64:
