@@ -39,7 +39,7 @@ def request(n, count, seed):
     return [int(x) for x in s]
 
 
-@pytest.mark.parametrize("n", [2, 5, 8, 10, 12])
+@pytest.mark.parametrize("n", [2, 5, 8, 10, 11, 12])    # n = 11: a pass of 2^13-element cluster tiles
 @pytest.mark.parametrize("precision", ["fixed", "plain"])
 def test_partial_matches_oracle_and_full(tpd, n, precision):
     A = synth.general(n, seed=9600 + n)
