@@ -176,12 +176,26 @@ __global__ void __launch_bounds__(256, 2) k_batch(const __grid_constant__ BatchP
     }
     unsigned* done = bp.ctrl + kCtrlDone + sg.done;
     if (tid == 0) {
-      const unsigned nxt = atomicAdd(bp.ctrl + kCtrlWork, 1u);   // claimed ahead: overlaps the lookups
-      bool ok = seen_bucket || wait_count(bp.ctrl + kCtrlBucket, 1u, status);
-      if (ok && p > 0)
-        ok = wait_count(done + (long long)(p - 1) * sg.nmat + j, (unsigned)(sg.tiles + sg.wait_extra), status);
-      ok = ok && ld_volatile(status) == 0;
-      if (ok) s_mat = reinterpret_cast<void*>(__ldcg(bp.bptrs + sg.item_start + j));
+      // The claim, the status word, the matrix pointer (once the bucketing is
+      // known to be done) and the first poll of the dependency are issued
+      // back to back, so their round trips overlap; only a dependency not yet
+      // met takes the polling loop.
+      const unsigned nxt = atomicAdd(bp.ctrl + kCtrlWork, 1u);   // claimed ahead
+      const unsigned st0 = ld_volatile(status);
+      unsigned long long mp = seen_bucket ? __ldcg(bp.bptrs + sg.item_start + j) : 0ull;
+      bool ok = st0 == 0;
+      if (ok && !seen_bucket) {
+        // the bucketing sets the status word (sizes disagreeing) before it
+        // releases its flag: read it again after acquiring the flag
+        ok = wait_count(bp.ctrl + kCtrlBucket, 1u, status) && ld_volatile(status) == 0;
+        if (ok) mp = __ldcg(bp.bptrs + sg.item_start + j);
+      }
+      if (ok && p > 0) {
+        const unsigned* dep = done + (long long)(p - 1) * sg.nmat + j;
+        const unsigned need = (unsigned)(sg.tiles + sg.wait_extra);
+        if (ld_acquire_gpu(dep) < need) ok = wait_count(dep, need, status);
+      }
+      s_mat = reinterpret_cast<void*>(mp);
       s_ok = ok;
       s_next = nxt;
     }
