@@ -258,6 +258,7 @@ struct F32CArith {
     const float aa = __fsub_rn(s, bb);
     e = __fadd_rn(__fsub_rn(a, aa), __fsub_rn(b, bb));
   }
+#ifdef TPD_F32C_SCALAR
   __device__ static __forceinline__ V add(V a, V b) {
     V o; float e;
     two_sum(a.re, b.re, o.re, e); o.rl = __fadd_rn(__fadd_rn(a.rl, b.rl), e);
@@ -270,6 +271,30 @@ struct F32CArith {
     two_sum(a.im, -b.im, o.im, e); o.il = __fadd_rn(__fsub_rn(a.il, b.il), e);
     return o;
   }
+#else
+  // The same TwoSum on the (re, im) pair at once with packed fp32x2
+  // instructions (sm_100 family): half the instructions of the scalar form,
+  // identical roundings -- y - x is fma(x, -1, y), rounded once.
+  __device__ static __forceinline__ float2 sub2(float2 y, float2 x) {
+    return __ffma2_rn(x, make_float2(-1.0f, -1.0f), y);
+  }
+  __device__ static __forceinline__ V add2(float2 ah, float2 al, float2 bh, float2 bl) {
+    const float2 s = __fadd2_rn(ah, bh);
+    const float2 bb = sub2(s, ah);
+    const float2 aa = sub2(s, bb);
+    const float2 e = __fadd2_rn(sub2(ah, aa), sub2(bh, bb));
+    const float2 l = __fadd2_rn(__fadd2_rn(al, bl), e);
+    return {s.x, s.y, l.x, l.y};
+  }
+  __device__ static __forceinline__ V add(V a, V b) {
+    return add2(make_float2(a.re, a.im), make_float2(a.rl, a.il), make_float2(b.re, b.im),
+                make_float2(b.rl, b.il));
+  }
+  __device__ static __forceinline__ V sub(V a, V b) {
+    return add2(make_float2(a.re, a.im), make_float2(a.rl, a.il), make_float2(-b.re, -b.im),
+                make_float2(-b.rl, -b.il));
+  }
+#endif
   __device__ static __forceinline__ V mul_i(V d) { return {-d.im, d.re, -d.il, d.rl}; }
   __device__ static __forceinline__ V mul_mi(V d) { return {d.im, -d.re, d.il, -d.rl}; }
   __device__ static __forceinline__ V neg(V d) { return {-d.re, -d.im, -d.rl, -d.il}; }
