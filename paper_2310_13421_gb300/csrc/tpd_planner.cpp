@@ -353,9 +353,10 @@ bool build_plan(int n, int dtype, int precision, int tile_bits_opt, int max_leve
     const bool first_of_many = p == 0 && plan->npass > 1;
     // 2^13-element complex128 tiles: a two-CTA cluster of 256 threads
     // (min_blocks 2); other 2^13 tiles: one CTA of 512 threads (1)
-    // Compensated complex64 (127 registers at two CTAs per SM) runs faster at
-    // three despite a few spilled registers (n = 15: 22.34 -> 21.51 ms).
-    const bool three = (dtype == 0 && precision == 3 && first_of_many) || (dtype == 1 && precision == 2);
+    // Compensated and fixed-point complex64 (127-128 registers at two CTAs per
+    // SM) run faster at three despite a few spilled registers (n = 15:
+    // 22.34 -> 21.69 ms and 38.18 -> 37.34 ms).
+    const bool three = (dtype == 0 && precision == 3 && first_of_many) || (dtype == 1 && precision >= 2);
     pd.min_blocks = pd.D > 12 ? (dtype == 0 ? 2 : 1) : (three ? 3 : 2);
   }
   return true;
