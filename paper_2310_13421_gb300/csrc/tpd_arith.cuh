@@ -286,13 +286,31 @@ struct F32CArith {
     const float2 l = __fadd2_rn(__fadd2_rn(al, bl), e);
     return {s.x, s.y, l.x, l.y};
   }
+  // TwoSum of a + (-b) without negating b: s = a - b; the error of adding -b,
+  // (a - aa) + (-b - bb), is (a - aa) - (b + bb) (rounding to nearest is
+  // symmetric), so every rounding is the scalar form's.
+  __device__ static __forceinline__ V sub2(float2 ah, float2 al, float2 bh, float2 bl) {
+    const float2 s = sub2(ah, bh);
+    const float2 bb = sub2(s, ah);
+    const float2 aa = sub2(s, bb);
+    const float2 e = sub2(sub2(ah, aa), __fadd2_rn(bh, bb));
+    const float2 l = __fadd2_rn(sub2(al, bl), e);
+    return {s.x, s.y, l.x, l.y};
+  }
   __device__ static __forceinline__ V add(V a, V b) {
     return add2(make_float2(a.re, a.im), make_float2(a.rl, a.il), make_float2(b.re, b.im),
                 make_float2(b.rl, b.il));
   }
   __device__ static __forceinline__ V sub(V a, V b) {
-    return add2(make_float2(a.re, a.im), make_float2(a.rl, a.il), make_float2(-b.re, -b.im),
-                make_float2(-b.rl, -b.il));
+    return sub2(make_float2(a.re, a.im), make_float2(a.rl, a.il), make_float2(b.re, b.im),
+                make_float2(b.rl, b.il));
+  }
+  // i (a - b) = (b.im - a.im) + i (a.re - b.re), as one packed subtraction
+  // (the TwoSum error of the swapped operands is the exact negative, so the
+  // bits are those of mul_i(sub(a, b)), up to the sign of an exact zero)
+  __device__ static __forceinline__ V isub(V a, V b) {
+    return sub2(make_float2(b.im, a.re), make_float2(b.il, a.rl), make_float2(a.im, b.re),
+                make_float2(a.il, b.rl));
   }
 #endif
   __device__ static __forceinline__ V mul_i(V d) { return {-d.im, d.re, -d.il, d.rl}; }

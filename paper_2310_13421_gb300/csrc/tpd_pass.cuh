@@ -19,6 +19,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "tpd_arith.cuh"
 #include "tpd_launch.h"
 #include "tpd_plan.h"
@@ -115,6 +117,17 @@ __device__ __forceinline__ T reg_off(int e, T w0, T w1, T w2, T w3) {
 
 // -------------------------------------------------------------- levels
 
+// i (a - b): the arithmetic's fused form where it has one
+template <class A, class = void>
+struct HasIsub : std::false_type {};
+template <class A>
+struct HasIsub<A, decltype((void)A::isub(typename A::V{}, typename A::V{}))> : std::true_type {};
+template <class A>
+__device__ __forceinline__ typename A::V isub(typename A::V a, typename A::V b) {
+  if constexpr (HasIsub<A>::value) return A::isub(a, b);
+  else return A::mul_i(A::sub(a, b));
+}
+
 // In-register level: register bits RC (column) and RR (row).
 template <class A, bool kDec, int RC, int RR>
 __device__ __forceinline__ void pair_level(typename A::V (&v)[kElems]) {
@@ -127,7 +140,7 @@ __device__ __forceinline__ void pair_level(typename A::V (&v)[kElems]) {
     if (kDec) {
       v[e] = A::add(a00, a11);                  // I
       v[e01] = A::add(a01, a10);                // X
-      v[e10] = A::mul_i(A::sub(a01, a10));      // Y
+      v[e10] = isub<A>(a01, a10);               // Y
       v[e11] = A::sub(a00, a11);                // Z
     } else {
       const typename A::V iy = A::mul_i(a10);   // positions hold I, X, Y, Z
