@@ -144,17 +144,23 @@ def test_c128_magnitude_extremes(tpd):
     assert_close(to_string_order(host(tpd.decompose(gpu(A))), n), oracle.coeffs_fwht(A), TOL128, "mixed")
 
 
-def test_c128_nonfinite_tiles_follow_ieee(tpd):
-    n = 8
+@pytest.mark.parametrize("n,opt", [(8, {}), (12, dict(tile_bits=13))])   # 12: two-CTA cluster tiles
+def test_c128_nonfinite_tiles_follow_ieee(tpd, n, opt):
     A = synth.general(n, seed=4200)
     A[3, 7] = np.inf
     A[100, 5] = np.nan
-    fixed = host(tpd.decompose(gpu(A), precision="fixed"))
-    plain = host(tpd.decompose(gpu(A), precision="plain"))
+    fixed = host(tpd.decompose(gpu(A), precision="fixed", **opt))
+    plain = host(tpd.decompose(gpu(A), precision="plain", **opt))
     assert np.array_equal(np.isnan(fixed), np.isnan(plain))
     assert np.array_equal(np.isinf(fixed), np.isinf(plain))
     fin = np.isfinite(fixed) & np.isfinite(plain)
     assert fin.any() and np.allclose(fixed[fin], plain[fin], rtol=1e-12, atol=1e-12)
+    if opt:
+        # the Inf/NaN fallback of a cluster tile: the same bits as one 512-thread CTA (NaN payloads aside)
+        one = host(tpd.decompose(gpu(A), precision="fixed", variant=1, **opt))
+        assert np.array_equal(np.isnan(fixed), np.isnan(one))
+        ok = ~np.isnan(fixed)
+        assert np.array_equal(fixed[ok], one[ok])
 
 
 @pytest.mark.parametrize("n,opt", [(11, {}), (12, dict(tile_bits=13)), (13, dict(tile_bits=13, max_levels=5))])
