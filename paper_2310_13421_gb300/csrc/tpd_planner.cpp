@@ -243,7 +243,12 @@ bool build_plan(int n, int dtype, int precision, int tile_bits_opt, int max_leve
     plan->npass = 0;
     return true;
   }
-  const int lf = dtype == 1 ? 4 : 3;                       // low tile bits always on lanes
+  // Low tile bits always on lanes: 128-byte runs (complex64: 4 bits).  The
+  // complex64 fixed point takes 3 (64-byte runs): its passes are bound by the
+  // double conversions per element, so the fewer passes that 5-level passes
+  // allow win (n = 15: 4 passes 37.3 ms, 3 passes 31.4 ms); the compensated
+  // form loses with them (20.8 against 22.2 ms) and keeps 4.
+  const int lf = (dtype == 1 && precision != 3) ? 4 : 3;
   const double cs = plan->elem_bytes == 16 ? 1.0 : 0.5;    // shuffle cost per level
   // 2^12-element tiles by default: two CTAs of 256 threads fit an SM; 2^13
   // (512 threads, one CTA per SM) only where it saves a pass (below)
