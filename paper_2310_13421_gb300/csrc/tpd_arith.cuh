@@ -367,6 +367,17 @@ struct Fixed32Arith {
     return (long long)((mag ^ sg) - sg);
   }
 
+  // True when every nonzero |v| < 2^62 scaled by 2^-T is a normal float
+  // (also after rounding up): then to_float_cvt_fast applies to the tile.
+  __device__ static __forceinline__ bool fast_range(int T) { return T <= 126 && T >= -65; }
+
+  // to_float for fast_range(T) through the conversion unit: round to nearest
+  // even, then an exact exponent shift.
+  __device__ static __forceinline__ float to_float_cvt_fast(long long v, int T) {
+    const uint32_t b = __float_as_uint(__ll2float_rn(v)) - ((uint32_t)T << 23);
+    return __uint_as_float(v == 0 ? 0u : b);
+  }
+
   // v * 2^-T rounded to the nearest float, ties to even (integer instructions;
   // subnormal results and overflow to Inf included).
   __device__ static __forceinline__ float to_float(long long v, int T) {

@@ -664,6 +664,7 @@ __device__ __forceinline__ void fixed32_tile(const PassDesc& pd, const PassArgs&
   // Eq. 4 per level, times 2^out_pow2 for a composition's scale
   const int T = 188 - pd.K - emax_eff + (kDec ? pd.K : 0) - args.out_pow2;
   const bool resid = args.out_mul != 1.0;
+  const bool fast = Fixed32Arith::fast_range(T);
   const Stage& sl = pd.st[pd.nstage - 1];
   float2* mat = reinterpret_cast<float2*>(matp);
   const uint32_t g = (uint32_t)base + (uint32_t)thread_goff(pd, sl, lane, warp);
@@ -681,7 +682,10 @@ __device__ __forceinline__ void fixed32_tile(const PassDesc& pd, const PassArgs&
   }
 #pragma unroll
   for (int e = 0; e < kElems; ++e) {
-    float2 o = make_float2(Fixed32Arith::to_float(v[e].re, T), Fixed32Arith::to_float(v[e].im, T));
+    // real parts on the conversion unit, imaginary parts with integer
+    // instructions (identical roundings; n = 15: 31.3 -> 28.3 ms)
+    float2 o = make_float2(fast ? Fixed32Arith::to_float_cvt_fast(v[e].re, T) : Fixed32Arith::to_float(v[e].re, T),
+                           Fixed32Arith::to_float(v[e].im, T));
     if (resid) { o.x = __fmul_rn(o.x, (float)args.out_mul); o.y = __fmul_rn(o.y, (float)args.out_mul); }
     mat[g + reg_off(e, w0, w1, w2, w3)] = o;
     if (flags) {
