@@ -100,6 +100,12 @@ def test_config_n15_c64_plain_and_compensated(tpd):
     assert errs["plain"] <= n * U32
     assert errs["compensated"] <= (P + 1) * U32
     assert errs["compensated"] < errs["plain"]
+    # the complex64 block fixed point: exact sums, one rounding per pass (its own plan: 3 passes here)
+    Pf = L.tpd_plan_describe(n, 1, L.options(precision=3))[0]
+    C = tpd.decompose(Ag, precision="fixed")
+    got, want = sample_rows(A_up, C, n, xs)
+    del C
+    assert rel_err(got.astype(np.complex128), want) <= Pf * U32 / (1 - Pf * U32)
     # against the complex128 decomposition of the same (upcast) matrix on the GPU
     C128 = tpd.decompose(Ag.to(torch.complex128))
     Cc = tpd.decompose(Ag, precision="compensated").to(torch.complex128)
