@@ -118,10 +118,10 @@ __device__ __forceinline__ void sp_insert(uint32_t key, long long re, long long 
 
 // one qubit level: every entry emits its two children into the table
 __global__ void k_sp_level(const uint32_t* __restrict__ keys, const longlong2* __restrict__ v,
-                           const unsigned long long* __restrict__ count, int n, int beta,
+                           const unsigned long long* __restrict__ count, unsigned long long cap, int n, int beta,
                            uint32_t* __restrict__ tkeys, unsigned long long* __restrict__ tv, uint32_t mask,
                            unsigned long long* __restrict__ overflow) {
-  const unsigned long long E = count[0];
+  const unsigned long long E = min(*count, cap);
   for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < E;
        i += (unsigned long long)gridDim.x * blockDim.x) {
     const uint32_t k = keys[i];
@@ -142,35 +142,38 @@ __global__ void k_sp_level(const uint32_t* __restrict__ keys, const longlong2* _
   }
 }
 
-// nonzero table entries -> the next level's entry list (any order)
-__global__ void k_sp_compact(const uint32_t* __restrict__ tkeys, const unsigned long long* __restrict__ tv,
-                             uint32_t slots, uint32_t* __restrict__ keys, longlong2* __restrict__ v,
-                             unsigned long long* __restrict__ count, unsigned long long cap,
+// nonzero table entries -> the next level's entry list (any order); every
+// slot is cleared after it is read, so the table starts the next level empty
+__global__ void k_sp_compact(uint32_t* __restrict__ tkeys, unsigned long long* __restrict__ tv, uint32_t slots,
+                             uint32_t* __restrict__ keys, longlong2* __restrict__ v,
+                             unsigned long long* __restrict__ count_out, unsigned long long cap,
                              unsigned long long* __restrict__ overflow) {
   for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < slots; s += gridDim.x * blockDim.x) {
-    if (tkeys[s] == kEmpty) continue;
+    const uint32_t key = tkeys[s];
+    if (key == kEmpty) continue;
     const long long re = (long long)tv[2 * s], im = (long long)tv[2 * s + 1];
+    tkeys[s] = kEmpty;
+    tv[2 * s] = 0ull;
+    tv[2 * s + 1] = 0ull;
     if ((re | im) == 0) continue;                              // zero CMW: pruned
-    const unsigned long long pos = atomicAdd(count + 1, 1ull);
-    if (pos < cap) { keys[pos] = tkeys[s]; v[pos] = make_longlong2(re, im); }
+    const unsigned long long pos = atomicAdd(count_out, 1ull);
+    if (pos < cap) { keys[pos] = key; v[pos] = make_longlong2(re, im); }
     else atomicExch(overflow, 1ull);
   }
 }
 
+// Counters (unsigned long long): [0] overflow flag, [1 + beta] entries
+// entering level beta (beta = 0..n-1), [1 + n] the final entries.
+constexpr int kSpCounters = 18;                                // n <= 15
+
 // entries of the first level (the input's nonzeros, at most the capacity)
-__global__ void k_sp_start(unsigned long long* count, unsigned long long m, unsigned long long cap) {
-  count[0] = m < cap ? m : cap;
-  count[1] = 0;
-  count[2] = m > cap ? 1ull : 0ull;
+__global__ void k_sp_start(unsigned long long* ctr, unsigned long long m, unsigned long long cap) {
+  ctr[1] = m < cap ? m : cap;
+  if (m > cap) ctr[0] = 1ull;
 }
 
 // status word: TPD_ERR_WORKSPACE (4) if some level had more entries than the capacity
-__global__ void k_sp_status(const unsigned long long* count, unsigned* status) { *status = count[2] ? 4u : 0u; }
-
-__global__ void k_sp_advance(unsigned long long* count, unsigned long long cap) {
-  count[0] = count[1] < cap ? count[1] : cap;
-  count[1] = 0;
-}
+__global__ void k_sp_status(const unsigned long long* ctr, unsigned* status) { *status = ctr[0] ? 4u : 0u; }
 
 // RC key -> base-4 string index (bit 2b = c_b, bit 2b+1 = r_b)
 __device__ __forceinline__ unsigned long long sp_string(uint32_t key, int n) {
@@ -182,10 +185,27 @@ __device__ __forceinline__ unsigned long long sp_string(uint32_t key, int n) {
   return s;
 }
 
-// final entries: string keys into a power-of-two sort buffer (padding = max)
-__global__ void k_sp_keys(const uint32_t* __restrict__ keys, const unsigned long long* __restrict__ count, int n,
-                          unsigned long long P, unsigned long long* __restrict__ skey, uint32_t* __restrict__ sidx) {
-  const unsigned long long E = count[0];
+// The final entries, sorted by string index: a bitonic sort over the
+// entries padded to Pd = the power of two >= E (padding keys = max), E read on
+// the device.  Steps whose stride is below kSpChunk run inside a CTA on its
+// chunk of the keys in shared memory; the launches for sizes above Pd return
+// at once, so the host plans the launches for the largest possible E.
+constexpr int kSpChunk = 2048;                 // keys per CTA in shared memory
+constexpr int kSpLocalThreads = kSpChunk / 2;  // one compare-exchange pair per thread
+
+__device__ __forceinline__ unsigned long long sp_padded(const unsigned long long* final_count,
+                                                        unsigned long long cap) {
+  const unsigned long long E = min(*final_count, cap);
+  unsigned long long P = 1;
+  while (P < E) P <<= 1;
+  return P;
+}
+
+// string keys of the final entries into the sort buffer (padding = max)
+__global__ void k_sp_keys(const uint32_t* __restrict__ keys, const unsigned long long* __restrict__ final_count,
+                          unsigned long long cap, int n, unsigned long long* __restrict__ skey,
+                          uint32_t* __restrict__ sidx) {
+  const unsigned long long E = min(*final_count, cap), P = sp_padded(final_count, cap);
   for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < P;
        i += (unsigned long long)gridDim.x * blockDim.x) {
     skey[i] = i < E ? sp_string(keys[i], n) : ~0ull;
@@ -193,9 +213,12 @@ __global__ void k_sp_keys(const uint32_t* __restrict__ keys, const unsigned long
   }
 }
 
-// one compare-exchange step (j, k) of a bitonic sort over P = 2^p elements
+// one compare-exchange step (j >= kSpChunk, k) over the global buffer
 __global__ void k_sp_bitonic(unsigned long long* __restrict__ skey, uint32_t* __restrict__ sidx,
-                             unsigned long long P, unsigned long long j, unsigned long long k) {
+                             const unsigned long long* __restrict__ final_count, unsigned long long cap,
+                             unsigned long long j, unsigned long long k) {
+  const unsigned long long P = sp_padded(final_count, cap);
+  if (k > P) return;
   for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < P;
        i += (unsigned long long)gridDim.x * blockDim.x) {
     const unsigned long long l = i ^ j;
@@ -209,12 +232,48 @@ __global__ void k_sp_bitonic(unsigned long long* __restrict__ skey, uint32_t* __
   }
 }
 
-__global__ void k_sp_emit(const longlong2* __restrict__ v, const unsigned long long* __restrict__ count,
-                          const unsigned long long* __restrict__ skey, const uint32_t* __restrict__ sidx, int n,
-                          const int* __restrict__ emax, unsigned long long capacity,
-                          unsigned long long* __restrict__ strings, double2* __restrict__ weights,
-                          unsigned long long* __restrict__ out_count) {
-  const unsigned long long E = count[0];
+// the steps j < kSpChunk of sizes k in [k_lo, k_hi] on each CTA's chunk, in
+// shared memory (k_lo = 2, k_hi = kSpChunk: the chunks' own sort; k_lo =
+// k_hi = k > kSpChunk: the end of a merge of size k)
+__global__ void __launch_bounds__(kSpLocalThreads) k_sp_local(unsigned long long* __restrict__ skey,
+                                                              uint32_t* __restrict__ sidx,
+                                                              const unsigned long long* __restrict__ final_count,
+                                                              unsigned long long cap, unsigned long long k_lo,
+                                                              unsigned long long k_hi) {
+  __shared__ unsigned long long sk[kSpChunk];
+  __shared__ uint32_t si[kSpChunk];
+  const unsigned long long P = sp_padded(final_count, cap);
+  const unsigned long long base = (unsigned long long)blockIdx.x * kSpChunk;
+  if (base >= P || k_lo > P) return;
+  const unsigned cnt = (unsigned)min((unsigned long long)kSpChunk, P - base);   // a power of two
+  for (unsigned t = threadIdx.x; t < cnt; t += blockDim.x) { sk[t] = skey[base + t]; si[t] = sidx[base + t]; }
+  __syncthreads();
+  const unsigned long long kmax = min(k_hi, P);
+  for (unsigned long long k = k_lo; k <= kmax; k <<= 1) {
+    for (unsigned long long j = min(k >> 1, (unsigned long long)kSpChunk >> 1); j > 0; j >>= 1) {
+      const unsigned t = threadIdx.x;
+      const unsigned i = (unsigned)((t / j) * 2 * j + (t % j));
+      const unsigned l = i + (unsigned)j;
+      if (l < cnt) {
+        const bool up = ((base + i) & k) == 0;
+        const unsigned long long a = sk[i], b = sk[l];
+        if ((a > b) == up) {
+          sk[i] = b; sk[l] = a;
+          const uint32_t x = si[i]; si[i] = si[l]; si[l] = x;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (unsigned t = threadIdx.x; t < cnt; t += blockDim.x) { skey[base + t] = sk[t]; sidx[base + t] = si[t]; }
+}
+
+__global__ void k_sp_emit(const longlong2* __restrict__ v, const unsigned long long* __restrict__ final_count,
+                          unsigned long long cap, const unsigned long long* __restrict__ skey,
+                          const uint32_t* __restrict__ sidx, int n, const int* __restrict__ emax,
+                          unsigned long long capacity, unsigned long long* __restrict__ strings,
+                          double2* __restrict__ weights, unsigned long long* __restrict__ out_count) {
+  const unsigned long long E = min(*final_count, cap);
   const int emax_eff = max(*emax, 1);
   const int T = 1084 - n - emax_eff + n;          // S of the input, and the 1/2 of Eq. 4 per level
   for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < E && i < capacity;
@@ -250,7 +309,7 @@ static SparseLayout sparse_layout(unsigned long long max_entries) {
   L.sortn = 1;
   while (L.sortn < L.entries) L.sortn <<= 1;
   size_t off = 0;
-  L.ctr = off; off += al(4 * sizeof(unsigned long long));
+  L.ctr = off; off += al(kSpCounters * sizeof(unsigned long long));
   L.emax = off; off += al(sizeof(int));
   L.keys = off; off += al(L.entries * 4);
   L.vals = off; off += al(L.entries * 16);
@@ -270,7 +329,7 @@ cudaError_t launch_sparse(const int* rows, const int* cols, const void* vals, un
                           cudaStream_t s) {
   const SparseLayout L = sparse_layout(max_entries);
   char* w = static_cast<char*>(ws);
-  unsigned long long* ctr = reinterpret_cast<unsigned long long*>(w + L.ctr);   // [0] E, [1] next, [2] overflow
+  unsigned long long* ctr = reinterpret_cast<unsigned long long*>(w + L.ctr);   // see kSpCounters
   int* emax = reinterpret_cast<int*>(w + L.emax);
   uint32_t* keys = reinterpret_cast<uint32_t*>(w + L.keys);
   longlong2* v = reinterpret_cast<longlong2*>(w + L.vals);
@@ -278,10 +337,13 @@ cudaError_t launch_sparse(const int* rows, const int* cols, const void* vals, un
   unsigned long long* tv = reinterpret_cast<unsigned long long*>(w + L.tvals);
   unsigned long long* skey = reinterpret_cast<unsigned long long*>(w + L.skey);
   uint32_t* sidx = reinterpret_cast<uint32_t*>(w + L.sidx);
+  const unsigned long long cap = L.entries;
   cudaError_t e;
   if ((e = cudaMemsetAsync(w, 0, L.keys, s)) != cudaSuccess) return e;        // counters, emax
-  const unsigned long long m0 = m < L.entries ? m : L.entries;
-  k_sp_start<<<1, 1, 0, s>>>(ctr, m, L.entries);
+  if ((e = cudaMemsetAsync(tkeys, 0xFF, L.slots * 4, s)) != cudaSuccess) return e;   // the table starts empty;
+  if ((e = cudaMemsetAsync(tv, 0, L.slots * 16, s)) != cudaSuccess) return e;        // each level leaves it so
+  const unsigned long long m0 = m < cap ? m : cap;
+  k_sp_start<<<1, 1, 0, s>>>(ctr, m, cap);
   if (m0 > 0) {
     k_sp_emax<<<grid_for(m0), 256, 0, s>>>(static_cast<const double2*>(vals), m0, emax);
     k_sp_init<<<(unsigned)((m0 + 255) / 256), 256, 0, s>>>(rows, cols, static_cast<const double2*>(vals), m0, n, emax,
@@ -290,19 +352,21 @@ cudaError_t launch_sparse(const int* rows, const int* cols, const void* vals, un
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const uint32_t mask = (uint32_t)(L.slots - 1);
   for (int beta = 0; beta < n; ++beta) {
-    if ((e = cudaMemsetAsync(tkeys, 0xFF, L.slots * 4, s)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(tv, 0, L.slots * 16, s)) != cudaSuccess) return e;
-    k_sp_level<<<grid_for(L.entries), 256, 0, s>>>(keys, v, ctr, n, beta, tkeys, tv, mask, ctr + 2);
-    k_sp_compact<<<grid_for(L.slots), 256, 0, s>>>(tkeys, tv, (uint32_t)L.slots, keys, v, ctr, L.entries, ctr + 2);
-    k_sp_advance<<<1, 1, 0, s>>>(ctr, L.entries);
+    k_sp_level<<<grid_for(cap), 256, 0, s>>>(keys, v, ctr + 1 + beta, cap, n, beta, tkeys, tv, mask, ctr);
+    k_sp_compact<<<grid_for(L.slots), 256, 0, s>>>(tkeys, tv, (uint32_t)L.slots, keys, v, ctr + 2 + beta, cap, ctr);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  k_sp_keys<<<grid_for(L.sortn), 256, 0, s>>>(keys, ctr, n, L.sortn, skey, sidx);
-  for (unsigned long long k = 2; k <= L.sortn; k <<= 1)
-    for (unsigned long long j = k >> 1; j > 0; j >>= 1)
-      k_sp_bitonic<<<grid_for(L.sortn), 256, 0, s>>>(skey, sidx, L.sortn, j, k);
-  k_sp_emit<<<grid_for(L.entries), 256, 0, s>>>(v, ctr, skey, sidx, n, emax, capacity, strings,
-                                                 static_cast<double2*>(weights), count);
+  const unsigned long long* fin = ctr + 1 + n;
+  k_sp_keys<<<grid_for(L.sortn), 256, 0, s>>>(keys, fin, cap, n, skey, sidx);
+  const unsigned chunks = (unsigned)((L.sortn + kSpChunk - 1) / kSpChunk);
+  k_sp_local<<<chunks, kSpLocalThreads, 0, s>>>(skey, sidx, fin, cap, 2, kSpChunk);
+  for (unsigned long long k = 2ull * kSpChunk; k <= L.sortn; k <<= 1) {
+    for (unsigned long long j = k >> 1; j >= (unsigned long long)kSpChunk; j >>= 1)
+      k_sp_bitonic<<<grid_for(L.sortn), 256, 0, s>>>(skey, sidx, fin, cap, j, k);
+    k_sp_local<<<chunks, kSpLocalThreads, 0, s>>>(skey, sidx, fin, cap, k, k);
+  }
+  k_sp_emit<<<grid_for(cap), 256, 0, s>>>(v, fin, cap, skey, sidx, n, emax, capacity, strings,
+                                          static_cast<double2*>(weights), count);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (status) k_sp_status<<<1, 1, 0, s>>>(ctr, status);
   return cudaGetLastError();
