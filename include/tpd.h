@@ -226,9 +226,13 @@ tpd_status tpd_compose_batched(void* const* ptrs_dev, const int* ns_dev, const i
  *   elements are unspecified.  The same (n, dtype, opt, count) as the prepare
  *   call, and the workspace it filled; the call enqueues only, so it can be
  *   captured in a CUDA graph and repeated.
- * The requested weights are bit-identical to those of tpd_decompose with the
- * same options (the needed tiles are computed the same way).  The first pass
- * reads every element (dense input); later passes shrink with the subtree.
+ * A weight depends on the positions whose already-applied levels hold its
+ * symbols and whose later levels lie on its quads' diagonal (I, Z) or
+ * anti-diagonal (X, Y) (Eq. 4); every pass skips the tiles holding none of
+ * them (2^(levels after the pass) tile ids per string at most).  The
+ * requested weights equal those of tpd_decompose with the same options: bit
+ * for bit in the IEEE precisions and on dyadic inputs, within the same error
+ * bound in the fixed point (skipped tiles enter binary points as zeros).
  * opt->skip_zero is not supported (TPD_ERR_UNSUPPORTED).
  * Errors: as tpd_decompose; INVALID_ARG also for a string index >= 4^n. */
 size_t tpd_partial_workspace_size(int n, int dtype, const tpd_options* opt, size_t count);

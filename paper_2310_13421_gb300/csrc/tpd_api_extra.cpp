@@ -23,12 +23,22 @@ using namespace detail;
 //
 // Only the weights of a requested list of strings (Alg. 3: a quaternary
 // subtree T of the strings of interest).  The passes run in place as usual,
-// but a pass skips every tile that no requested weight depends on: the last
-// pass needs the tiles holding a requested position; an earlier pass needs
-// the tiles that share elements with a needed tile of the pass after it
-// (tiles of consecutive passes share elements iff they agree on the global
-// bits fixed in both).  Needed tiles are computed exactly as in the full
-// decomposition, so the requested weights carry the same bits.
+// but a pass skips every tile that no requested weight depends on.  The
+// weight of string t depends, at the input of the pass over levels [b, b+K),
+// only on the positions whose bits of every level beta < b already hold t's
+// symbol (r_beta, c_beta) and whose bits of every level beta >= b+K satisfy
+// r_beta xor c_beta = x_beta(t) (I and Z read the quad's diagonal, X and Y its
+// anti-diagonal, Eq. 4): a pass needs the tiles containing such positions,
+// enumerated per string (2^(levels after the pass) tile ids at most).  Where
+// that enumeration would be longer than the pass has tiles, the pass takes
+// instead every tile that shares elements with a needed tile of the pass after
+// it (a superset).  Skipped tiles keep what the previous pass left there: the
+// later passes read those positions only into weights nobody asked for, and
+// the fixed point's binary points of skipped tiles are marked zero before the
+// run, so their elements enter a tile's binary point as zeros.  The requested
+// weights thus have the full decomposition's values: bit for bit in the IEEE
+// arithmetics and on dyadic inputs, and within the same error bound otherwise
+// (a tile's binary point can only be finer).
 
 // workspace: RC positions of the requested strings | per pass, one byte per
 // tile: needed | the plan's own workspace (binary points between passes)
@@ -76,23 +86,56 @@ unsigned long long fixed_mask(const PassDesc& pd) {
   return m;
 }
 
-void partial_need(const Plan& plan, const std::vector<unsigned long long>& pos,
+// tiles of pass q that share elements with a needed tile of pass q + 1
+void closure_need(const PassDesc& a, const PassDesc& b, const std::vector<uint8_t>& need_b,
+                  std::vector<uint8_t>* need_a) {
+  const unsigned long long C = fixed_mask(a) & fixed_mask(b);
+  std::vector<unsigned long long> keys;
+  for (unsigned long long t = 0; t < (unsigned long long)b.ntiles; ++t)
+    if (need_b[t]) keys.push_back(tile_base_of(b, t) & C);
+  std::sort(keys.begin(), keys.end());
+  keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
+  for (unsigned long long t = 0; t < (unsigned long long)a.ntiles; ++t)
+    (*need_a)[t] = std::binary_search(keys.begin(), keys.end(), tile_base_of(a, t) & C) ? 1 : 0;
+}
+
+void partial_need(const Plan& plan, int n, const std::vector<unsigned long long>& pos,
                   std::vector<std::vector<uint8_t>>* need) {
   const int P = plan.npass;
   need->assign(P, {});
   for (int p = 0; p < P; ++p) (*need)[p].assign((size_t)plan.pass[p].ntiles, 0);
-  for (unsigned long long x : pos) (*need)[P - 1][tile_of(plan.pass[P - 1], x)] = 1;
-  for (int q = P - 2; q >= 0; --q) {
-    const PassDesc& a = plan.pass[q];
-    const PassDesc& b = plan.pass[q + 1];
-    const unsigned long long C = fixed_mask(a) & fixed_mask(b);
-    std::vector<unsigned long long> keys;
-    for (unsigned long long t = 0; t < (unsigned long long)b.ntiles; ++t)
-      if ((*need)[q + 1][t]) keys.push_back(tile_base_of(b, t) & C);
-    std::sort(keys.begin(), keys.end());
-    keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
-    for (unsigned long long t = 0; t < (unsigned long long)a.ntiles; ++t)
-      (*need)[q][t] = std::binary_search(keys.begin(), keys.end(), tile_base_of(a, t) & C) ? 1 : 0;
+  for (int p = P - 1; p >= 0; --p) {
+    const PassDesc& pd = plan.pass[p];
+    // tile-id position of each global bit (-1: a bit of the tile)
+    int at[2 * kMaxQubits];
+    for (int g = 0; g < 2 * n; ++g) at[g] = -1;
+    for (int j = 0; j < pd.nrest; ++j) at[pd.rest_gbit[j]] = j;
+    std::vector<int> future;                 // levels after the pass with a bit outside the tile
+    for (int beta = pd.b + pd.K; beta < n; ++beta)
+      if (at[beta] >= 0 || at[n + beta] >= 0) future.push_back(beta);
+    const unsigned long long per = 1ull << future.size();
+    if (p < P - 1 && (unsigned long long)pos.size() * per > 4ull * (unsigned long long)pd.ntiles) {
+      closure_need(pd, plan.pass[p + 1], (*need)[p + 1], &(*need)[p]);
+      continue;
+    }
+    for (unsigned long long x : pos) {
+      unsigned long long base = 0;           // the levels before the pass: t's symbol bits
+      for (int beta = 0; beta < pd.b; ++beta) {
+        if (at[beta] >= 0) base |= ((x >> beta) & 1ull) << at[beta];
+        if (at[n + beta] >= 0) base |= ((x >> (n + beta)) & 1ull) << at[n + beta];
+      }
+      for (unsigned long long f = 0; f < per; ++f) {
+        unsigned long long t = base;
+        for (size_t i = 0; i < future.size(); ++i) {
+          const int beta = future[i];
+          const unsigned long long r = (f >> i) & 1ull;
+          const unsigned long long c = r ^ (((x >> beta) ^ (x >> (n + beta))) & 1ull);
+          if (at[n + beta] >= 0) t |= r << at[n + beta];
+          if (at[beta] >= 0) t |= c << at[beta];
+        }
+        (*need)[p][t] = 1;
+      }
+    }
   }
 }
 
@@ -142,7 +185,7 @@ tpd_status tpd_partial_prepare(int n, int dtype, const tpd_options* opt, const u
     pos[i] = rc_of_string(strings[i], n);
   }
   std::vector<std::vector<uint8_t>> need;
-  if (plan->npass > 0) partial_need(*plan, pos, &need);
+  if (plan->npass > 0) partial_need(*plan, n, pos, &need);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   char* w = static_cast<char*>(workspace);
   if (count && cudaMemcpyAsync(w, pos.data(), count * sizeof(unsigned long long), cudaMemcpyHostToDevice, s) !=
@@ -173,6 +216,9 @@ tpd_status tpd_decompose_partial(void* A, int n, int dtype, const tpd_options* o
   const uint8_t* need[kMaxQubits];
   for (int p = 0; p < plan->npass; ++p) need[p] = reinterpret_cast<const uint8_t*>(w + lay.need_off[p]);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // binary points of skipped tiles read as zero tiles (see above)
+  if (lay.run_bytes && cudaMemsetAsync(w + lay.run_off, kQFillByte, lay.run_bytes, s) != cudaSuccess)
+    return TPD_ERR_CUDA;
   st = run_single(true, arith, A, *plan, 0, 1.0, w + lay.run_off, s, &eff, plan->npass > 0 ? need : nullptr);
   if (st != TPD_OK) return st;
   if (launch_gather(A, reinterpret_cast<const unsigned long long*>(w), count, (int)eb, weights, s) != cudaSuccess)
