@@ -243,12 +243,13 @@ bool build_plan(int n, int dtype, int precision, int tile_bits_opt, int max_leve
     plan->npass = 0;
     return true;
   }
-  // Low tile bits always on lanes: 128-byte runs (complex64: 4 bits).  The
-  // complex64 fixed point takes 3 (64-byte runs): its passes are bound by the
-  // double conversions per element, so the fewer passes that 5-level passes
-  // allow win (n = 15: 4 passes 37.3 ms, 3 passes 31.4 ms); the compensated
-  // form loses with them (20.8 against 22.2 ms) and keeps 4.
-  const int lf = (dtype == 1 && precision != 3) ? 4 : 3;
+  // Low tile bits always on lanes: 3 (complex128: 128-byte runs; complex64:
+  // 64-byte runs, which let 5-level passes fit in 2^13-element tiles and save
+  // a pass: measured on GB300 at n = 15, fixed point 37.3 -> 31.3 ms, plain
+  // 12.24 -> 11.66 ms, equal at n = 13 and 14).  The compensated complex64
+  // form keeps 4 (128-byte runs): its passes slow down more with the shorter
+  // runs than a pass saves (20.8 against 22.2 ms at n = 15).
+  const int lf = (dtype == 1 && precision == 2) ? 4 : 3;
   const double cs = plan->elem_bytes == 16 ? 1.0 : 0.5;    // shuffle cost per level
   // 2^12-element tiles by default: two CTAs of 256 threads fit an SM; 2^13
   // (512 threads, one CTA per SM) only where it saves a pass (below)

@@ -239,17 +239,17 @@ def test_plans_exist_for_every_size(L, n):
 def test_plan_choices_measured_on_gb300(L):
     """The planner's measured choices: complex128 n = 15 takes one 5-level pass
     over 2^13-element tiles between 2^12 and 2^11 ones, n = 16 four passes over
-    2^12 rather than two 2^13 passes; the complex64 fixed point plans with
-    64-byte runs (n = 15 in three passes), the other complex64 forms with
-    128-byte runs (four)."""
+    2^12 rather than two 2^13 passes; the plain and fixed-point complex64
+    forms plan with 64-byte runs (n = 15 in three passes), the compensated
+    one with 128-byte runs (four)."""
     def shape(n, dtype, prec):
         npass, desc = L.tpd_plan_describe(n, dtype, L.options(precision=prec))
         return [(p["K"], p["D"]) for p in _parse(desc)]
     assert shape(15, 0, 0) == [(6, 12), (5, 13), (4, 11)]
     assert shape(16, 0, 0) == [(4, 12)] * 4
     assert shape(14, 0, 0) == [(6, 12), (4, 12), (4, 12)]
-    assert len(shape(15, 1, 3)) == 3
-    assert len(shape(15, 1, 1)) == 4 and len(shape(15, 1, 2)) == 4
+    assert len(shape(15, 1, 3)) == 3 and len(shape(15, 1, 1)) == 3
+    assert len(shape(15, 1, 2)) == 4
 
 
 def test_tuned_defaults_apply_only_when_fields_are_zero(L):
