@@ -181,14 +181,24 @@ KERNEL_SOURCES = ("tpd_pass.cuh", "tpd_arith.cuh", "tpd_plan.h", "tpd_launch.h",
                   "tpd_kernels_impl.cuh", "tpd_kernels_fixed_dec.cu", "tpd_kernels_fixed_com.cu")
 
 
-def kernel_digest():
-    """Hash of the sources that decide the complex128 pass kernels and their plans."""
+def _code_only(text):
+    """C/C++ source without comments and blank space (a comment edit leaves
+    the compiled kernels, and so the recorded traffic, unchanged)."""
+    import re
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
+def kernel_digest(csrc=None):
+    """Hash of the code (comments excluded) that decides the complex128 pass
+    kernels and their plans."""
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_2310_13421_gb300", "csrc")
+    csrc = csrc or os.path.join(ROOT, "paper_2310_13421_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
         if f in KERNEL_SOURCES:
-            with open(os.path.join(csrc, f), "rb") as fh:
-                h.update(f.encode() + fh.read())
+            with open(os.path.join(csrc, f), encoding="utf-8") as fh:
+                h.update(f.encode() + _code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

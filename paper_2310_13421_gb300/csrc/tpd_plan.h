@@ -18,8 +18,10 @@
 // and row bit are both register bits) or across lanes with shuffles (column
 // bit a lane bit, row bit a register bit).  Consecutive stages exchange the
 // tile through shared memory.  Lanes always cover tile bits 0..2 (0..3 for
-// 8-byte elements), so shared-memory accesses are conflict-free and global
-// accesses cover whole 128-byte lines.
+// the compensated complex64 form), so accesses of 16-byte elements to shared
+// memory are conflict-free, and global accesses cover runs of 8 elements
+// (128 bytes in complex128, 64 in complex64; 16 elements for the compensated
+// form).
 #pragma once
 
 #include <stdint.h>
