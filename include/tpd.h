@@ -335,8 +335,9 @@ tpd_status tpd_tune_set(int n, int dtype, int precision, const tpd_options* tune
 void tpd_tune_clear(void);
 
 /* Describe the pass plan the library uses for (n, dtype, opt) as a
- * NUL-terminated text (one line per pass: levels, tile bits, stages) written
- * to buf (at most len bytes).  Host only, no device call.  Returns the number
+ * NUL-terminated text (one line per pass: levels, tile bits, tile count, the
+ * CTAs per SM its kernel is compiled for, stages) written to buf (at most len
+ * bytes).  Host only, no device call.  Returns the number
  * of passes, or -1 on invalid arguments. */
 int tpd_plan_describe(int n, int dtype, const tpd_options* opt, char* buf, size_t len);
 

@@ -361,8 +361,18 @@ bool build_plan(int n, int dtype, int precision, int tile_bits_opt, int max_leve
     // (min_blocks 2); other 2^13 tiles: one CTA of 512 threads (1)
     // Compensated and fixed-point complex64 (127-128 registers at two CTAs per
     // SM) run faster at three despite a few spilled registers (n = 15:
-    // 22.34 -> 21.69 ms and 38.18 -> 37.34 ms).
-    const bool three = (dtype == 0 && precision == 3 && first_of_many) || (dtype == 1 && precision >= 2);
+    // 22.34 -> 21.69 ms and 38.18 -> 37.34 ms), except in passes built only
+    // of stages with two in-register levels each: compensated ones keep two
+    // (n = 15 passes 2-3: 5.57 / 5.61 -> 5.43 / 5.50 ms; n = 14 passes 2-3:
+    // 1.41 / 1.41 -> 1.35 / 1.36 ms), fixed-point ones two on 2^11-element
+    // tiles only (n = 15 pass 3: 8.00 -> 7.68 ms; on 2^12 tiles, n = 14
+    // passes 2-3, three wins: 1.85 / 1.60 against 2.23 / 1.98 ms).
+    bool pairs_only = pd.nstage > 1;
+    for (int s = 0; s < pd.nstage; ++s)
+      if (pd.st[s].npair != 2 || pd.st[s].nshfl != 0) pairs_only = false;
+    const bool two_c64 = pairs_only && (precision == 2 || pd.D < 12);
+    const bool three = (dtype == 0 && precision == 3 && first_of_many) ||
+                       (dtype == 1 && precision >= 2 && !two_c64);
     pd.min_blocks = pd.D > 12 ? (dtype == 0 ? 2 : 1) : (three ? 3 : 2);
   }
   return true;
@@ -378,8 +388,8 @@ std::string describe_plan(const Plan& plan) {
   }
   for (int p = 0; p < plan.npass; ++p) {
     const PassDesc& pd = plan.pass[p];
-    std::snprintf(buf, sizeof(buf), "pass %d: levels [%d,%d) D=%d tiles=%lld gbits=", p, pd.b, pd.b + pd.K,
-                  pd.D, (long long)pd.ntiles);
+    std::snprintf(buf, sizeof(buf), "pass %d: levels [%d,%d) D=%d tiles=%lld ctas=%d gbits=", p, pd.b,
+                  pd.b + pd.K, pd.D, (long long)pd.ntiles, pd.min_blocks);
     s += buf;
     for (int i = 0; i < pd.D; ++i) {
       std::snprintf(buf, sizeof(buf), "%s%d", i ? "," : "", pd.gbit[i]);

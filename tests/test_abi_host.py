@@ -123,9 +123,9 @@ def _parse(desc):
         if not line.startswith("pass "):
             continue
         head, *stages = line.split(" | ")
-        m = re.match(r"pass \d+: levels \[(\d+),(\d+)\) D=(\d+) tiles=(\d+) gbits=([\d,]+)", head)
-        b, e, D, ntiles, gbits = m.groups()
-        p = dict(b=int(b), K=int(e) - int(b), D=int(D), ntiles=int(ntiles),
+        m = re.match(r"pass \d+: levels \[(\d+),(\d+)\) D=(\d+) tiles=(\d+) ctas=(\d+) gbits=([\d,]+)", head)
+        b, e, D, ntiles, ctas, gbits = m.groups()
+        p = dict(b=int(b), K=int(e) - int(b), D=int(D), ntiles=int(ntiles), ctas=int(ctas),
                  gbits=[int(x) for x in gbits.split(",")], stages=[])
         for st in stages:
             kv = dict(re.findall(r"(\w+)=([\d,]*)", st))
@@ -250,6 +250,29 @@ def test_plan_choices_measured_on_gb300(L):
     assert shape(14, 0, 0) == [(6, 12), (4, 12), (4, 12)]
     assert len(shape(15, 1, 3)) == 3 and len(shape(15, 1, 1)) == 3
     assert len(shape(15, 1, 2)) == 4
+
+
+def test_pass_occupancy_choices(L):
+    """CTAs per SM per pass: complex128 fixed point three in its first pass
+    only, a 2^13-element complex128 tile a two-CTA cluster (2), other 2^13
+    tiles one CTA of 512 threads (1); compensated and fixed-point complex64
+    three, except in passes made only of two-level in-register stages: two
+    for the compensated form, and for the fixed point on tiles below 2^12."""
+    def ctas(n, dtype, prec):
+        return [p["ctas"] for p in _parse(L.tpd_plan_describe(n, dtype, L.options(precision=prec))[1])]
+    assert ctas(14, 0, 0) == [3, 2, 2]
+    assert ctas(15, 0, 0) == [3, 2, 2]
+    assert ctas(14, 0, 1) == [2, 2, 2]
+    assert ctas(15, 1, 2) == [3, 2, 2, 3]
+    assert ctas(15, 1, 3) == [3, 1, 2]
+    assert ctas(14, 1, 3) == [3, 3, 3]
+    assert ctas(14, 1, 2) == [3, 2, 2]
+    assert ctas(14, 1, 1) == [2] * len(ctas(14, 1, 1))
+    for n, dtype, prec in [(14, 1, 2), (15, 1, 2), (14, 1, 3), (15, 1, 3), (13, 1, 2)]:
+        for p in _parse(L.tpd_plan_describe(n, dtype, L.options(precision=prec))[1]):
+            pairs_only = len(p["stages"]) > 1 and all(s["npair"] == 2 and s["nshfl"] == 0 for s in p["stages"])
+            two = pairs_only and (prec == 2 or p["D"] < 12)
+            assert p["ctas"] == (1 if p["D"] > 12 else 2 if two else 3)
 
 
 def test_tuned_defaults_apply_only_when_fields_are_zero(L):
