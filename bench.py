@@ -333,15 +333,64 @@ def _event_ms(torch, stream, fn, reps=5, setup=None):
     return float(np.median(times))
 
 
-def alg1_baseline(A, W_rc, n, samples=1 << 20):
-    """The paper's algorithm on the host over the whole matrix -- recursive
-    (Alg. 1, one thread) and iterative (Alg. 2, in place, all cores):
-    coeffs/s, and the largest deviation from the GPU result on a random
-    sample of strings."""
+def _digit_add(x, y, d, n):
+    """digit-wise (x + y) mod d of base-d integers (arrays)"""
+    out, p = np.zeros_like(x), 1
+    for _ in range(n):
+        out += ((x // p) % d + (y // p) % d) % d * p
+        p *= d
+    return out
+
+
+def time_weyl(tpd, L, torch, stream, d=3, n=9, seed=1006, shifts=8):
+    """Decomposition in the Weyl (clock-and-shift) basis of n qudits of
+    dimension d (the basis Sec. V names): a random d^n x d^n Hermitian matrix,
+    complex128 (fp64 arithmetic) and complex64 (fp32), one launch per qudit
+    level, each reading and writing the whole matrix.  Returns the timings
+    and, for the accuracy leg, the weights of a few shifts a (row digits b,
+    column digits a + b) of each result."""
+    from paper_2310_13421_gb300 import synth
+    N = d ** n
+    A = synth.hermitian_side(N, seed)
+    rng = np.random.default_rng(seed)
+    a_s = np.array([0, 1, N - 1] + [int(v) for v in rng.integers(0, N, shifts - 3)], dtype=np.int64)
+    b = np.arange(N, dtype=np.int64)
+    pos = np.concatenate([b * N + _digit_add(b, np.full(N, a), d, n) for a in a_s])
+    out, rows = {"d": d, "n": n, "side": N}, {}
+    for name, tt, code, elem in (("c128", torch.complex128, L.TPD_C128, 16), ("c64", torch.complex64, L.TPD_C64, 8)):
+        src = torch.from_numpy(A).to("cuda", tt)
+        work = torch.empty_like(src)
+
+        def step():
+            st = L.tpd_weyl_decompose(work.data_ptr(), n, d, code, stream.cuda_stream)
+            assert st == 0, L.status_string(st)
+
+        ms = _event_ms(torch, stream, step, setup=lambda: work.copy_(src))
+        alg = 2 * n * N * N * elem
+        out[name] = {"ms": ms, "coeffs_per_s": N * N / (ms * 1e-3), "hbm_gbs_algorithmic": alg / (ms * 1e-3) / 1e9,
+                     "launches": n, "arithmetic": "fp64" if elem == 16 else "fp32"}
+        rows[name] = work.reshape(-1).index_select(0, torch.from_numpy(pos).cuda()).cpu().numpy() \
+            .astype(np.complex128).reshape(len(a_s), N)
+        del src, work
+        torch.cuda.empty_cache()
+    return out, (A, d, a_s, rows)
+
+
+def weyl_accuracy(A, d, a_s, results):
+    """Accuracy leg for the Weyl basis: the sampled shifts' weights against
+    the Weyl oracle (fp64) on the same matrix, normwise over the sample."""
+    from oracle import core
+    want = core.weyl_rows(A, d, a_s)
+    return {name: {"normwise": float(np.linalg.norm(got - want) / np.linalg.norm(want)), "weights": int(want.size)}
+            for name, got in results.items()}
+
+
+def alg2_baseline(A, W_rc, n, samples=1 << 20):
+    """The paper's algorithm on the host over the whole matrix -- the
+    iterative form (Alg. 2, the CMWs of Eq. 4 level by level in place) on one
+    host thread and on all host cores: coeffs/s, and the largest deviation
+    from the GPU result on a random sample of strings."""
     import oracle
-    t0 = time.perf_counter()
-    w = oracle.tpd_alg1(A)
-    dt = time.perf_counter() - t0
     rng = np.random.default_rng(7)
     s = rng.integers(0, 4 ** n, size=samples, dtype=np.int64)
     r = np.zeros_like(s)
@@ -351,18 +400,17 @@ def alg1_baseline(A, W_rc, n, samples=1 << 20):
         r |= (t >> 1) << beta
         c |= (t & 1) << beta
     gpu = W_rc.reshape(-1)[(r << n) | c]
-    dev = float(np.max(np.abs(gpu - w[s])) / np.max(np.abs(w)))
-    out = {"alg1": {"value": 4 ** n / dt, "unit": UNIT, "seconds": dt, "threads": 1,
-                    "kind": "the paper's recursive TPD (Alg. 1) on the host, fp64, whole matrix",
-                    "max_rel_dev_vs_gpu_sampled": dev}}
-    # the iterative form (Alg. 2), in place level by level, OpenMP on all host cores
-    t0 = time.perf_counter()
-    w2 = oracle.tpd_alg2(A)
-    dt2 = time.perf_counter() - t0
-    dev2 = float(np.max(np.abs(gpu - w2[s])) / np.max(np.abs(w2)))
-    out["alg2"] = {"value": 4 ** n / dt2, "unit": UNIT, "seconds": dt2, "threads": oracle.num_threads(),
-                   "kind": "the paper's iterative TPD (Alg. 2) on the host, in place, fp64, whole matrix",
-                   "max_rel_dev_vs_gpu_sampled": dev2}
+    out = {}
+    for key, threads in (("alg2_1thread", 1), ("alg2", 0)):
+        t0 = time.perf_counter()
+        w = oracle.tpd_alg2(A, threads=threads)
+        dt = time.perf_counter() - t0
+        dev = float(np.max(np.abs(gpu - w[s])) / np.max(np.abs(w)))
+        out[key] = {"value": 4 ** n / dt, "unit": UNIT, "seconds": dt,
+                    "threads": threads or oracle.num_threads(),
+                    "kind": "the paper's iterative TPD (Alg. 2) on the host, in place, fp64, whole matrix",
+                    "max_rel_dev_vs_gpu_sampled": dev}
+        del w
     return out
 
 
@@ -495,6 +543,50 @@ def time_helpers(tpd, L, torch, stream, n=14):
             "sum_squares_ms": ms_sumsq, "sum_squares_gbs": nbytes / (ms_sumsq * 1e-3) / 1e9}
 
 
+# X-masks whose weights the accuracy leg compares with the oracle: all-I/Z,
+# the extremes, and a fixed random sample
+def accuracy_xs(n, count=16, seed=77):
+    rng = np.random.default_rng(seed)
+    base = [0, 1, 2 ** (n - 1), 2 ** n - 1]
+    return np.array(base + [int(v) for v in rng.integers(1, 2 ** n, count - len(base))], dtype=np.int64)
+
+
+def rows_of(W, n, xs):
+    """The weights w_(x,z), z = 0..N-1, of each X-mask x in xs from a result
+    W in RC layout (a CUDA tensor or a host array): row bits = z, column
+    bits = x xor z."""
+    z = np.arange(2 ** n, dtype=np.int64)
+    pos = np.concatenate([((z << n) | (int(x) ^ z)) for x in xs])
+    if hasattr(W, "is_cuda"):
+        import torch
+        got = W.reshape(-1).index_select(0, torch.from_numpy(pos).to(W.device)).cpu().numpy()
+    else:
+        got = np.asarray(W).reshape(-1)[pos]
+    return got.astype(np.complex128).reshape(len(xs), 2 ** n)
+
+
+def oracle_accuracy(A, n, xs, results):
+    """Accuracy leg (CPU, after the timed regions, rank 0): each GPU result's
+    error against the fp64 oracle on the sampled X-rows of the same input
+    (a complex64 input widened exactly).  Reported per result: the normwise
+    relative error over the sample; the largest error in units of
+    m_x = 2^-n sum_r |A[r^x][r]| (the scale of fp64's componentwise bound);
+    and the largest relative error among weights with |w| >= 1e-2 m_x."""
+    import oracle
+    want = oracle.coeffs_xrows(A, xs)
+    r = np.arange(2 ** n, dtype=np.int64)
+    m = np.array([np.abs(A[r ^ int(x), r].astype(np.complex128)).sum() / 2 ** n for x in xs])[:, None]
+    out = {}
+    for name, got in results.items():
+        err = np.abs(got - want)
+        big = np.abs(want) >= 1e-2 * m
+        out[name] = {"normwise": float(np.linalg.norm(err) / np.linalg.norm(want)),
+                     "max_over_m_x": float(np.max(err / m)),
+                     "max_rel_above_1e-2_m_x": float(np.max(err[big] / np.abs(want[big]))),
+                     "weights": int(want.size)}
+    return out
+
+
 def run_ours(args, world, rank, local):
     import torch
     if not torch.cuda.is_available():
@@ -615,15 +707,21 @@ def run_ours(args, world, rank, local):
     W_pin = W_pins[(args.e2e_steps - 1) % ns_]
     work = works[(args.e2e_steps - 1) % ns_]
     del works, wss, W_pins
-    alg1 = None
+    alg2 = None
     if rank == 0 and world == 1 and not args.no_extra and not c64:
-        alg1 = alg1_baseline(A, W_pin.numpy(), n)
+        alg2 = alg2_baseline(A, W_pin.numpy(), n)
 
     extra = {}
+    acc_rows = {}            # results sampled for the accuracy leg: config -> (A, n, xs, {form: rows})
+    weyl_rows = None
     if not args.no_extra and not c64 and prec_eff == L.TPD_PREC_FIXED:
         # fp64 butterfly (IEEE double, rounded per level) on the same matrix
         s64, p64, np64 = time_decompose(tpd, L, torch, work, pristine, n, 5, 2, L.TPD_PREC_PLAIN, stream)
         f64_ms = float(np.mean(s64))
+        if rank == 0 and world == 1:
+            xs14 = accuracy_xs(n)
+            acc_rows["n%d_c128" % n] = (A, n, xs14, {"fixed": rows_of(W_pin.numpy(), n, xs14),
+                                                    "fp64": rows_of(work, n, xs14)})
         extra["c128_fp64_plain_n%d" % n] = {"ms_per_step": f64_ms, "coeffs_per_s": coeffs / (f64_ms * 1e-3),
                                         "passes": np64}
         extra["c128_fixed_n%d" % n] = {"ms_per_step": ms_per_step, "coeffs_per_s": coeffs / (ms_per_step * 1e-3)}
@@ -642,8 +740,12 @@ def run_ours(args, world, rank, local):
                          "passes": npp, "hbm_gbs_per_pass": 2 * 4 ** n15 * 8 / (np.mean(s) / npp * 1e-3) / 1e9}
             res[name]["_out"] = w15.clone()
         ref = tpd.decompose(p15.to(torch.complex128), precision="fixed")
+        xs15 = accuracy_xs(n15)
+        rows15 = {}
         for name in ("plain", "compensated", "fixed"):
-            out = res[name].pop("_out").to(torch.complex128)
+            out = res[name].pop("_out")
+            rows15["c64_" + name] = rows_of(out, n15, xs15)
+            out = out.to(torch.complex128)
             res[name]["rel_err_vs_c128"] = float(torch.linalg.vector_norm(out - ref) / torch.linalg.vector_norm(ref))
             del out
         del ref
@@ -651,8 +753,12 @@ def run_ours(args, world, rank, local):
         p128 = w128.clone()
         s, _, npp = time_decompose(tpd, L, torch, w128, p128, n15, 3, 1, L.TPD_PREC_PLAIN, stream)
         res["c128_fp64_plain"] = {"ms_per_step": float(np.mean(s)), "passes": npp}
+        rows15["c128_fp64"] = rows_of(w128, n15, xs15)
         s, _, npp = time_decompose(tpd, L, torch, w128, p128, n15, 3, 1, L.TPD_PREC_FIXED, stream)
         res["c128_fixed"] = {"ms_per_step": float(np.mean(s)), "passes": npp}
+        rows15["c128_fixed"] = rows_of(w128, n15, xs15)
+        if rank == 0 and world == 1:
+            acc_rows["n15_c64_input"] = (A64, n15, xs15, rows15)
         extra["n15"] = res
         extra["speedup_c64_compensated_vs_c128_fp64_n15"] = res["c128_fp64_plain"]["ms_per_step"] / \
             res["compensated"]["ms_per_step"]
@@ -665,6 +771,7 @@ def run_ours(args, world, rank, local):
         extra["partial_n14_heisenberg"] = time_partial(tpd, L, torch, stream)
         extra["rows_n14"] = time_rows(tpd, L, torch, stream)
         extra["helpers_n14"] = time_helpers(tpd, L, torch, stream)
+        extra["weyl_d3_n9"], weyl_rows = time_weyl(tpd, L, torch, stream)
     if not args.no_extra and not args.no_batch and not c64:
         extra["batch_4096_n3_10"] = time_batch(tpd, L, torch, stream)
 
@@ -672,9 +779,15 @@ def run_ours(args, world, rank, local):
     if rank == 0 and world == 1:
         v, cores, sample = oracle_rate(A, n)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
-    if alg1 is not None:
-        extra["cpu_alg1"] = alg1["alg1"]
-        extra["cpu_alg2"] = alg1["alg2"]
+    if alg2 is not None:
+        extra["cpu_alg2_1thread"] = alg2["alg2_1thread"]
+        extra["cpu_alg2"] = alg2["alg2"]
+    if acc_rows:
+        extra["error_vs_fp64_oracle"] = {cfg: oracle_accuracy(*v) for cfg, v in acc_rows.items()}
+        acc_rows.clear()
+    if weyl_rows is not None and rank == 0 and world == 1:
+        extra["weyl_d3_n9"]["error_vs_fp64_oracle"] = weyl_accuracy(*weyl_rows)
+        weyl_rows = None
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

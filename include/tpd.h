@@ -64,12 +64,21 @@ typedef enum {
   TPD_PREC_COMPENSATED = 2,  /* C64 only: fp32 sums carried with TwoSum error terms
                                 (Ogita-Rump-Oishi cascaded summation) across the
                                 levels of a pass, one rounding per pass */
-  TPD_PREC_FIXED = 3         /* the levels of a pass are summed exactly in 64-bit
-                                integers on a per-tile binary point (block fixed
-                                point).  C128: int64 sums are handed between
-                                passes, one rounding per decomposition.  C64: each
-                                pass rounds to float once (RNE); whole matrices of
-                                n <= 4 run the compensated kernel */
+  TPD_PREC_FIXED = 3         /* block fixed point: a pass of K levels only adds
+                                elements of one "class" (the same X-mask on its
+                                levels, Eq. 4, and the same other column bits);
+                                each class is put on its own binary point, its
+                                2^K-term sums are exact in 64-bit integers, and
+                                every output is rounded to the storage type once
+                                per pass (round to nearest even).  A component
+                                is truncated (toward zero) only where it lies far
+                                below its class's largest: the error stays below
+                                2^(K-61) of that largest.  So a weight's error is
+                                set by its own X-mask's entries, as in IEEE
+                                arithmetic, never by larger entries elsewhere in
+                                the matrix, and Hermitian inputs give exactly real
+                                weights.  Whole complex64 matrices of n <= 4 run
+                                the compensated kernel */
 } tpd_precision;
 
 typedef struct {
@@ -86,7 +95,7 @@ typedef struct {
                        cluster of two 256-thread CTAs sharing the tile through
                        distributed shared memory),
                        2 = persistent CTAs that prefetch the next tile (complex128
-                       fixed point, single matrix, no zero skipping),
+                       block fixed point, single matrix, no zero skipping),
                        3 / 4 = one CTA per tile compiled for 2 / 3 CTAs per SM
                        (tiles of up to 2^12 elements).
                        Batched calls: 0, 1, 3, 4 = one launch per (qubit count,
@@ -116,10 +125,9 @@ typedef struct {
 void tpd_options_init(tpd_options* opt);
 
 /* Bytes of device workspace tpd_decompose / tpd_compose need for (n, dtype,
- * opt): what one pass hands to the next -- the per-tile binary points of the
- * complex128 block fixed point (plans of two or more passes) and, with
- * opt->skip_zero, the per-tile nonzero flags.  0 for one-pass plans and for
- * the IEEE / complex64 forms without skip_zero.  Returns 0 for invalid
+ * opt): what one pass hands to the next besides the matrix itself -- with
+ * opt->skip_zero, one nonzero flag byte per tile of every pass after the
+ * first.  0 without skip_zero and for one-pass plans.  Returns 0 for invalid
  * arguments. */
 size_t tpd_workspace_size(int n, int dtype, const tpd_options* opt);
 
@@ -161,21 +169,28 @@ tpd_status tpd_decompose_host(const void* A_host, void* W_host, void* dev_A, int
  * not call cudaMalloc or an allocating library -- for instance code running
  * where a custom allocator owns all device memory, or a real-time path that
  * must not allocate or synchronise.  It behaves like tpd_decompose, but its
- * workspace (the per-tile binary points and zero-skip flags passes hand to
- * one another) is a fixed array of TPD_NOALLOC_SCRATCH_BYTES in the library's
- * own device memory, present on every GPU that loads the library until the
- * process exits.  The caller still passes the matrix A (device, in place).
+ * workspace (the per-class binary points of the complex128 block fixed point
+ * and the zero-skip flags that passes hand to one another) is a fixed array
+ * of TPD_NOALLOC_SCRATCH_BYTES in the library's own device memory, present on
+ * every GPU that loads the library until the process exits; the default
+ * complex128 plans fit up to n = 14 (40 MiB at n = 14).  The caller still
+ * passes the matrix A (device, in place).
  *   - Plans whose workspace (tpd_workspace_size) exceeds the array are
  *     rejected with TPD_ERR_WORKSPACE before anything is enqueued; use
  *     tpd_decompose with a caller buffer for those.
  *   - The first call on a device looks up the array's device address with
- *     that device current; make that first call before any stream capture.
+ *     that device current.  That look-up loads the library's device code for
+ *     this entry point, and with CUDA's lazy module loading (the default) the
+ *     array is allocated by the CUDA runtime at that moment: make one call on
+ *     each device (any n, e.g. n = 1) before any stream capture and before the
+ *     point from which nothing may be allocated.  Later calls allocate nothing.
  *   - All calls on a device share the one array, and a call leaves its
  *     contents behind (each call clears what it needs cleared).  Calls whose
  *     work overlaps on the GPU (different streams, no ordering) race on it.
- *   - Nothing is allocated or freed, by the library or by a library it calls.
+ *   - Nothing is allocated or freed after that first call, by the library or
+ *     by a library it calls.
  * Arguments and other errors as tpd_decompose. */
-#define TPD_NOALLOC_SCRATCH_BYTES ((size_t)8 << 20)
+#define TPD_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
 tpd_status tpd_decompose_noalloc(void* A, int n, int dtype, const tpd_options* opt, void* stream);
 
 /* Device workspace for the batched calls over `count` matrices with qubit
@@ -230,9 +245,10 @@ tpd_status tpd_compose_batched(void* const* ptrs_dev, const int* ns_dev, const i
  * symbols and whose later levels lie on its quads' diagonal (I, Z) or
  * anti-diagonal (X, Y) (Eq. 4); every pass skips the tiles holding none of
  * them (2^(levels after the pass) tile ids per string at most).  The
- * requested weights equal those of tpd_decompose with the same options: bit
- * for bit in the IEEE precisions and on dyadic inputs, within the same error
- * bound in the fixed point (skipped tiles enter binary points as zeros).
+ * requested weights equal those of tpd_decompose with the same options bit
+ * for bit, for finite inputs, in every precision (in the block fixed point
+ * the elements a requested weight's class sums lie in its dependency cone, so
+ * skipped tiles never enter its binary point).
  * opt->skip_zero is not supported (TPD_ERR_UNSUPPORTED).
  * Errors: as tpd_decompose; INVALID_ARG also for a string index >= 4^n. */
 size_t tpd_partial_workspace_size(int n, int dtype, const tpd_options* opt, size_t count);
@@ -274,8 +290,9 @@ tpd_status tpd_nonzero_list(const void* W, int n, int dtype, double tol, unsigne
  *   strings, weights, capacity, count   as tpd_nonzero_list.
  *   status      device, one unsigned (may be NULL): TPD_OK or TPD_ERR_WORKSPACE.
  *   workspace   device, tpd_sparse_workspace_size(max_entries) bytes, 256-byte aligned.
- * Sums are exact (int64 on one binary point for the matrix), each weight is
- * rounded once; the result does not depend on scheduling.  Enqueued on
+ * Sums are exact (int64 on one binary point per X-mask r xor c, which no
+ * level changes), each weight is rounded once; the result does not depend on
+ * scheduling.  Enqueued on
  * `stream` only (no host synchronisation).  C128 only (UNSUPPORTED otherwise).
  * Errors: INVALID_ARG, UNSUPPORTED, MISALIGNED, WORKSPACE, CUDA. */
 size_t tpd_sparse_workspace_size(size_t max_entries);
@@ -283,6 +300,36 @@ tpd_status tpd_decompose_coo(const int* rows, const int* cols, const void* value
                              size_t max_entries, unsigned long long* strings, void* weights, size_t capacity,
                              unsigned long long* count, unsigned* status, void* workspace, size_t workspace_bytes,
                              void* stream);
+
+/* Decomposition in the Weyl (clock-and-shift) basis of n qudits of dimension
+ * d -- the tensorized basis Sec. V (Conclusion and Outlook) names as the
+ * natural next candidate for the method.  With omega = exp(2 pi i / d),
+ * X|j> = |j+1 mod d>, Z|j> = omega^j |j> and W_{a,b} = X^a Z^b (a tensor
+ * product over the qudits, qudit 1 the most significant base-d digit of the
+ * row and column index), it computes in place
+ *
+ *     c_{a,b} = d^-n tr(W_{a,b}^* A),          A = sum_{a,b} c_{a,b} W_{a,b},
+ *
+ * by the recursion of Eqs. 3-5 with d x d blocks: each qudit level turns
+ * every d x d block into the d^2 cumulative weights
+ * Omega_{a,b} = d^-1 sum_c omega^(-b c) A_{c+a, c}.
+ *   A       device, d^n x d^n complex of `dtype` (row-major, 16- / 8-byte
+ *           aligned); on return the weight c_{a,b} sits at the position whose
+ *           row digit of each qudit is b_j and column digit (a_j + b_j) mod d
+ *           (for d = 2 the Pauli RC layout, with c_{1,1} = i w_Y since
+ *           XZ = -iY).
+ *   n, d    1 <= n, 2 <= d <= 5, d^n <= 65536.
+ *   dtype   TPD_C128 (IEEE fp64 arithmetic) or TPD_C64 (fp32), rounded every
+ *           level.
+ * One kernel launch per qudit; no workspace; asynchronous on `stream`.
+ * Errors: INVALID_ARG, MISALIGNED, CUDA. */
+tpd_status tpd_weyl_decompose(void* A, int n, int d, int dtype, void* stream);
+
+/* Weyl-basis composition in place: C holds the weights c_{a,b} in the layout
+ * tpd_weyl_decompose leaves; on return it holds scale * sum c_{a,b} W_{a,b}
+ * (scale = d^-n: the adjoint of tpd_weyl_decompose, W_{a,b} being unitary).
+ * scale finite and nonzero.  Arguments and errors as tpd_weyl_decompose. */
+tpd_status tpd_weyl_compose(void* C, int n, int d, int dtype, double scale, void* stream);
 
 /* Layout conversion, out of place.  RC is the layout every decomposition
  * leaves (see the conventions above); STRING puts the weight of

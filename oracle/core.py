@@ -1,5 +1,5 @@
-"""ctypes front end of the C oracle ``tpd_oracle.c`` and of ``tpd_alg1.c`` (the
-paper's recursive algorithm on the CPU) -- test infrastructure only.
+"""ctypes front end of the C oracle ``tpd_oracle.c`` and of ``tpd_alg2.c`` (the
+paper's iterative algorithm on the CPU) -- test infrastructure only.
 
 The shared library is compiled with gcc into ``oracle/_build/`` on first use
 (or by ``build_library()``), with -ffp-contract=off so that no sum in the
@@ -14,7 +14,9 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "tpd_oracle.c")
-_SRC_ALG1 = os.path.join(_HERE, "tpd_alg1.c")
+_SRC_ALG2 = os.path.join(_HERE, "tpd_alg2.c")
+_SRC_WEYL = os.path.join(_HERE, "tpd_weyl.c")
+_SOURCES = (_SRC, _SRC_ALG2, _SRC_WEYL)
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
@@ -22,14 +24,14 @@ _lib = None
 
 
 def build_library(force=False):
-    """Compile tpd_oracle.c, tpd_alg1.c -> oracle/_build/liboracle.so (gcc, OpenMP)."""
+    """Compile tpd_oracle.c, tpd_alg2.c, tpd_weyl.c -> oracle/_build/liboracle.so (gcc, OpenMP)."""
     os.makedirs(_BUILD, exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_ALG1))):
+            and os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(f) for f in _SOURCES)):
         return _LIB_PATH
     tmp = _LIB_PATH + ".%d.tmp" % os.getpid()
     cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
-           "-shared", "-fPIC", "-o", tmp, _SRC, _SRC_ALG1, "-lm"]
+           "-shared", "-fPIC", "-o", tmp] + list(_SOURCES) + ["-lm"]
     subprocess.check_call(cmd)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -46,13 +48,22 @@ def _load():
             lib.oracle_coeffs_fwht.argtypes = [dp, ctypes.c_int, dp]
             lib.oracle_coeffs_at.argtypes = [dp, ctypes.c_int, u64p, ctypes.c_int64, dp]
             lib.oracle_coeffs_xrows.argtypes = [dp, ctypes.c_int, u64p, ctypes.c_int64, dp]
+            lib.oracle_coeffs_xdiags.argtypes = [dp, ctypes.c_int, u64p, ctypes.c_int64]
             lib.oracle_compose.argtypes = [dp, ctypes.c_int, dp]
             lib.oracle_compose_fwht.argtypes = [dp, ctypes.c_int, dp]
-            lib.oracle_tpd_alg1.argtypes = [dp, ctypes.c_int, dp]
-            lib.oracle_tpd_alg2.argtypes = [dp, ctypes.c_int, dp]
+            lib.oracle_tpd_alg2.argtypes = [dp, ctypes.c_int, dp, ctypes.c_int]
             for f in (lib.oracle_coeffs, lib.oracle_coeffs_fwht, lib.oracle_coeffs_at,
-                      lib.oracle_coeffs_xrows, lib.oracle_compose, lib.oracle_compose_fwht,
-                      lib.oracle_tpd_alg1, lib.oracle_tpd_alg2):
+                      lib.oracle_coeffs_xrows, lib.oracle_coeffs_xdiags, lib.oracle_compose,
+                      lib.oracle_compose_fwht,
+                      lib.oracle_tpd_alg2):
+                f.restype = ctypes.c_int
+            lib.oracle_weyl_rows.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
+                                             ctypes.c_int64, dp]
+            lib.oracle_weyl_rows.restype = ctypes.c_int
+            lib.oracle_weyl_diags.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_int64]
+            lib.oracle_weyl_diags.restype = ctypes.c_int
+            for f in (lib.oracle_weyl_coeffs, lib.oracle_weyl_coeffs_dft, lib.oracle_weyl_compose):
+                f.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp]
                 f.restype = ctypes.c_int
             lib.oracle_num_threads.argtypes = []
             lib.oracle_num_threads.restype = ctypes.c_int
@@ -81,24 +92,15 @@ def num_threads():
     return int(_load().oracle_num_threads())
 
 
-def tpd_alg1(A):
-    """All 4^n weights by the paper's recursive algorithm (Alg. 1: CMWs of
-    Eq. 4, recursion on nonzero CMWs), string order; single-threaded."""
-    A, n = _square(A)
-    out = np.empty(4 ** n, dtype=np.complex128)
-    if _load().oracle_tpd_alg1(_dptr(A), n, _dptr(out)):
-        raise RuntimeError("oracle_tpd_alg1 failed")
-    return out
-
-
-def tpd_alg2(A, overwrite=False):
+def tpd_alg2(A, overwrite=False, threads=0):
     """All 4^n weights by the paper's iterative algorithm (Alg. 2: every CMW of
     a level split at once, in place, OpenMP over quads), string order.  With
-    overwrite, A (complex128, contiguous) is used as the working array."""
+    overwrite, A (complex128, contiguous) is used as the working array;
+    threads: OpenMP threads (0: all)."""
     A, n = _square(A)
     W = A if overwrite else A.copy()
     out = np.empty(4 ** n, dtype=np.complex128)
-    if _load().oracle_tpd_alg2(_dptr(W), n, _dptr(out)):
+    if _load().oracle_tpd_alg2(_dptr(W), n, _dptr(out), int(threads)):
         raise RuntimeError("oracle_tpd_alg2 failed")
     return out
 
@@ -134,7 +136,22 @@ def coeffs_at(A, strings):
 
 def coeffs_xrows(A, xs):
     """For each X-mask x in xs, the N weights w_(x,z), z = 0..N-1.
-    Returns (count, N) complex array; string of (i, z) is string_of_xz(xs[i], z, n)."""
+    Returns (count, N) complex array; string of (i, z) is string_of_xz(xs[i], z, n).
+    A complex64 matrix is not widened as a whole: the entries A[r^x][r] of
+    each requested x are gathered and widened to complex128 (exact)."""
+    if isinstance(A, np.ndarray) and A.dtype == np.complex64 and A.ndim == 2:
+        N = A.shape[0]
+        if A.shape[1] != N or N & (N - 1):
+            raise ValueError("A must be a 2^n x 2^n matrix")
+        n = N.bit_length() - 1
+        x = np.ascontiguousarray(xs, dtype=np.uint64)
+        r = np.arange(N, dtype=np.int64)
+        V = np.stack([A[r ^ int(xi), r].astype(np.complex128) for xi in x]) if x.size else \
+            np.empty((0, N), dtype=np.complex128)
+        V = np.ascontiguousarray(V)
+        if _load().oracle_coeffs_xdiags(_dptr(V), n, _u64ptr(x), x.shape[0]):
+            raise RuntimeError("oracle_coeffs_xdiags failed")
+        return V
     A, n = _square(A)
     x = np.ascontiguousarray(xs, dtype=np.uint64)
     out = np.empty((x.shape[0], 2 ** n), dtype=np.complex128)
@@ -188,3 +205,91 @@ def string_of_xz(x, z, n):
         zb = (z >> np.uint64(b)) & np.uint64(1)
         s |= code[(xb * np.uint64(2) + zb).astype(np.int64)] << np.uint64(2 * b)
     return s
+
+
+# ---------------------------------------------------------------- Weyl basis (qudits)
+
+def _square_d(A, d):
+    A = np.ascontiguousarray(A, dtype=np.complex128)
+    N = A.shape[0]
+    n = 0
+    while d ** n < N:
+        n += 1
+    if A.ndim != 2 or A.shape[1] != N or d ** n != N or n < 1:
+        raise ValueError("A must be a d^n x d^n matrix")
+    return A, n
+
+
+def weyl_coeffs(A, d):
+    """All d^2n weights c_{a,b} = d^-n tr(W_{a,b}^* A) in the Weyl
+    (clock-and-shift) basis W_{a,b} = X^a Z^b, as a (d^n, d^n) array indexed
+    [a, b] (see tpd_weyl.c for the digit convention).  O(d^3n)."""
+    A, n = _square_d(A, d)
+    N = d ** n
+    out = np.empty((N, N), dtype=np.complex128)
+    if _load().oracle_weyl_coeffs(_dptr(A), n, d, _dptr(out)):
+        raise RuntimeError("oracle_weyl_coeffs failed")
+    return out
+
+
+def weyl_coeffs_dft(A, d):
+    """The same weights with the sum over c per shift a done as a
+    tensor-product DFT over the base-d digits.  O(n d^(2n+1))."""
+    A, n = _square_d(A, d)
+    N = d ** n
+    out = np.empty((N, N), dtype=np.complex128)
+    if _load().oracle_weyl_coeffs_dft(_dptr(A), n, d, _dptr(out)):
+        raise RuntimeError("oracle_weyl_coeffs_dft failed")
+    return out
+
+
+def _digit_add(c, a, d, n):
+    """digit-wise (c + a) mod d of base-d integers (c an array, a a scalar)"""
+    out = np.zeros_like(c)
+    p = 1
+    for _ in range(n):
+        out += ((c // p) % d + (a // p) % d) % d * p
+        p *= d
+    return out
+
+
+def weyl_rows(A, d, shifts):
+    """Weights c_{a,b}, b = 0..d^n-1, of the given shifts a: (count, d^n)
+    array.  A matrix in another storage type (complex64) is not widened as a
+    whole: the entries A[c + a][c] of each requested shift are gathered and
+    widened to complex128 exactly."""
+    N = A.shape[0]
+    n = 0
+    while d ** n < N:
+        n += 1
+    if A.ndim != 2 or A.shape[1] != N or d ** n != N:
+        raise ValueError("A must be a d^n x d^n matrix")
+    a_s = np.ascontiguousarray(shifts, dtype=np.int64)
+    if np.any(a_s < 0) or np.any(a_s >= N):
+        raise ValueError("shift out of range")
+    if A.dtype == np.complex128 and A.flags.c_contiguous:
+        out = np.empty((a_s.shape[0], N), dtype=np.complex128)
+        if _load().oracle_weyl_rows(_dptr(A), n, d, a_s.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                    a_s.shape[0], _dptr(out)):
+            raise RuntimeError("oracle_weyl_rows failed")
+        return out
+    c = np.arange(N, dtype=np.int64)
+    V = np.ascontiguousarray(np.stack([A[_digit_add(c, int(a), d, n), c].astype(np.complex128) for a in a_s]))
+    if _load().oracle_weyl_diags(_dptr(V), n, d, a_s.shape[0]):
+        raise RuntimeError("oracle_weyl_diags failed")
+    return V
+
+
+def weyl_compose(C, d):
+    """A = sum_{a,b} c_{a,b} W_{a,b} from the (d^n, d^n) weight array [a, b]."""
+    C = np.ascontiguousarray(C, dtype=np.complex128)
+    N = C.shape[0]
+    n = 0
+    while d ** n < N:
+        n += 1
+    if C.shape != (N, N) or d ** n != N:
+        raise ValueError("C must be a d^n x d^n array of weights")
+    A = np.empty((N, N), dtype=np.complex128)
+    if _load().oracle_weyl_compose(_dptr(C), n, d, _dptr(A)):
+        raise RuntimeError("oracle_weyl_compose failed")
+    return A

@@ -49,3 +49,40 @@ def compose_kron(w, n):
     for s, t in enumerate(_strings(n)):
         A += w[s] * pauli_string_matrix(t)
     return A
+
+
+# ---------------------------------------------------------------- Weyl basis (qudits)
+
+def weyl_single(d, a, b):
+    """X^a Z^b for one qudit: X|j> = |j+1 mod d>, Z|j> = omega^j |j>, omega = e^(2 pi i/d)."""
+    X = np.zeros((d, d), dtype=np.complex128)
+    for j in range(d):
+        X[(j + 1) % d, j] = 1.0
+    Z = np.diag(np.exp(2j * np.pi * np.arange(d) / d))
+    return np.linalg.matrix_power(X, a) @ np.linalg.matrix_power(Z, b)
+
+
+def weyl_operator(d, a_digits, b_digits):
+    """The tensor product over qudits (qudit 1 outermost) of X^a_j Z^b_j."""
+    m = np.ones((1, 1), dtype=np.complex128)
+    for aj, bj in zip(a_digits, b_digits):
+        m = np.kron(m, weyl_single(d, aj, bj))
+    return m
+
+
+def _digits(x, d, n):
+    """Base-d digits of x, qudit 1 (most significant) first."""
+    return [(x // d ** (n - 1 - j)) % d for j in range(n)]
+
+
+def weyl_coeffs_kron(A, d):
+    """c_{a,b} = d^-n tr(W_{a,b}^* A) for all a, b by dense products: (d^n, d^n) array [a, b]."""
+    A = np.asarray(A, dtype=np.complex128)
+    N = A.shape[0]
+    n = int(round(np.log(N) / np.log(d)))
+    out = np.empty((N, N), dtype=np.complex128)
+    for a in range(N):
+        for b in range(N):
+            W = weyl_operator(d, _digits(a, d, n), _digits(b, d, n))
+            out[a, b] = np.trace(W.conj().T @ A) / N
+    return out

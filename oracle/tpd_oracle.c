@@ -39,6 +39,7 @@
  *                          sum over r done by a Walsh-Hadamard transform,
  *                          a textbook routine for sum_r (-1)^{popc(z&r)} v[r]
  *                                                                    O(count n 2^n)
+ *   oracle_coeffs_xdiags   the same from the gathered entries A[r^x][r]
  *   oracle_coeffs_fwht     the same for every x                      O(n 4^n)
  *   oracle_compose         A = sum_t w_t sigma^t (Eq. 2, left side)  O(8^n)
  *   oracle_compose_fwht    the same, the sum over z per x-mask done by
@@ -197,6 +198,24 @@ int oracle_coeffs_xrows(const double* A_, int n, const uint64_t* xs, int64_t cou
     uint64_t x = xs[i];
     cplx* v = out + (uint64_t)i * N;
     for (uint64_t r = 0; r < N; ++r) v[r] = A[(r ^ x) * N + r];
+    wht(v, N);
+    for (uint64_t z = 0; z < N; ++z) v[z] = finish(v[z], n, x, z);
+  }
+  return 0;
+}
+
+/* The same rows from the gathered entries: V (count x N complex, in place)
+ * holds V[i][r] = A[r ^ x[i]][r] on entry and w_{(x[i], z)} at [i][z] on
+ * return -- for matrices the caller holds in another storage type (the
+ * entries gathered and widened to double exactly by the caller). */
+int oracle_coeffs_xdiags(double* V_, int n, const uint64_t* xs, int64_t count) {
+  if (n < 0 || n > 20) return 1;
+  cplx* V = (cplx*)V_;
+  const uint64_t N = (uint64_t)1 << n;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t i = 0; i < count; ++i) {
+    uint64_t x = xs[i];
+    cplx* v = V + (uint64_t)i * N;
     wht(v, N);
     for (uint64_t z = 0; z < N; ++z) v[z] = finish(v[z], n, x, z);
   }

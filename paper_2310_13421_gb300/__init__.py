@@ -13,12 +13,14 @@ The CUDA library ``libtpd.so`` is loaded lazily on first use (the submodule
     sum_squares(X)             fp64 sum of |x|^2 on the device (Parseval check)
     nonzero_list(W)            the paper's list L of (string, weight) with nonzero weight
     decompose_coo(r, c, v, n)  sparse input: the list L from the nonzero entries (Alg. 2 on entries)
+    weyl_decompose(A, d)       the same recursion in the Weyl (clock-and-shift) basis of qudits (Sec. V)
+    weyl_compose(C, d)         its inverse / adjoint
     string_order(n)            RC layout -> string order permutation (host index array)
     build()                    compile libtpd.so in-tree
 """
 __all__ = ["decompose", "compose", "decompose_batched", "compose_batched", "Batch", "Partial", "TPDFunction", "tpd",
            "string_order", "to_string_layout", "from_string_layout", "sum_squares", "nonzero_list", "decompose_coo",
-           "workspace_size", "build"]
+           "workspace_size", "weyl_decompose", "weyl_compose", "build"]
 
 
 def build(force=False, verbose=False):
@@ -29,7 +31,7 @@ def build(force=False, verbose=False):
 def __getattr__(name):
     if name in ("decompose", "compose", "decompose_batched", "compose_batched", "Batch", "Partial", "string_order",
                 "to_string_layout", "from_string_layout", "sum_squares", "nonzero_list", "decompose_coo",
-                "workspace_size", "make_options"):
+                "workspace_size", "make_options", "weyl_decompose", "weyl_compose"):
         from . import api
         return getattr(api, name)
     if name in ("TPDFunction", "tpd"):

@@ -31,11 +31,11 @@ SYMBOLS = (
     "tpd_tune_set", "tpd_tune_clear", "tpd_batch_status", "tpd_test_hold_batch_waits",
     "tpd_convert_layout", "tpd_sum_squares", "tpd_partial_workspace_size", "tpd_partial_prepare",
     "tpd_decompose_partial", "tpd_nonzero_workspace_size", "tpd_nonzero_list", "tpd_sparse_workspace_size",
-    "tpd_decompose_coo",
+    "tpd_decompose_coo", "tpd_weyl_decompose", "tpd_weyl_compose",
 )
 
 # size of the library's own scratch array used by tpd_decompose_noalloc
-TPD_NOALLOC_SCRATCH_BYTES = 8 << 20
+TPD_NOALLOC_SCRATCH_BYTES = 64 << 20
 # device workspace of tpd_sum_squares
 TPD_SUMSQ_WORKSPACE_BYTES = 8192
 
@@ -97,6 +97,10 @@ def load(path=None):
         lib.tpd_nonzero_workspace_size.restype = sz
         lib.tpd_nonzero_list.argtypes = [vp, i, i, ctypes.c_double, vp, vp, sz, vp, vp, sz, vp]
         lib.tpd_nonzero_list.restype = i
+        lib.tpd_weyl_decompose.argtypes = [vp, i, i, i, vp]
+        lib.tpd_weyl_decompose.restype = i
+        lib.tpd_weyl_compose.argtypes = [vp, i, i, i, ctypes.c_double, vp]
+        lib.tpd_weyl_compose.restype = i
         lib.tpd_convert_layout.argtypes = [vp, vp, i, i, i, vp]
         lib.tpd_convert_layout.restype = i
         lib.tpd_sum_squares.argtypes = [vp, sz, i, vp, vp, sz, vp]
@@ -202,6 +206,14 @@ def tpd_nonzero_workspace_size(n):
 def tpd_nonzero_list(W, n, dtype, tol, strings, weights, capacity, count, workspace, workspace_bytes, stream=0):
     return int(load().tpd_nonzero_list(W or None, n, dtype, float(tol), strings or None, weights or None, capacity,
                                        count or None, workspace or None, workspace_bytes, stream or None))
+
+
+def tpd_weyl_decompose(A, n, d, dtype, stream=0):
+    return int(load().tpd_weyl_decompose(A or None, n, d, dtype, stream or None))
+
+
+def tpd_weyl_compose(C, n, d, dtype, scale, stream=0):
+    return int(load().tpd_weyl_compose(C or None, n, d, dtype, float(scale), stream or None))
 
 
 def tpd_convert_layout(src, dst, n, dtype, to_string, stream=0):

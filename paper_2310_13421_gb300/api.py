@@ -7,6 +7,8 @@ weight of string t sits at row r, column c with, for every qubit j, the row
 and column bits n-j equal to (t_j >> 1, t_j & 1) -- I (0,0), X (0,1), Y (1,0),
 Z (1,1).  ``to_string_layout`` converts to base-4 string order on the device.
 """
+import contextlib
+
 import numpy as np
 import torch
 
@@ -49,6 +51,28 @@ def _stream(stream):
     return s.cuda_stream
 
 
+@contextlib.contextmanager
+def _enqueue(device, stream, *inputs):
+    """Device and stream (yields the cudaStream_t) for enqueueing library
+    work.  The work and every tensor made for it inside the block (a clone of
+    the input, a workspace, the outputs) belong to `stream` (default: the
+    current stream).  A stream other than the current one first waits for
+    the work already enqueued on the current stream, which produced the
+    inputs, and the inputs are recorded on it, so that the caching allocator
+    does not hand their memory to other work while the stream still uses
+    them.  Results are ready on `stream`."""
+    with torch.cuda.device(device):
+        cur = torch.cuda.current_stream()
+        s = stream if stream is not None else cur
+        if s != cur:
+            s.wait_stream(cur)
+            for t in inputs:
+                if t is not None:
+                    t.record_stream(s)
+        with torch.cuda.stream(s):
+            yield s.cuda_stream
+
+
 def _raise(st, what):
     if st != L.TPD_OK:
         raise L.TPDError(st, what)
@@ -71,14 +95,14 @@ def decompose(A, *, inplace=False, precision=None, skip_zero=False, tile_bits=0,
     _check_device(A)
     n = _qubits(A)
     code = _dtype_code(A)
-    out = A if inplace else A.clone()
     opt = make_options(precision, skip_zero, tile_bits, max_levels, variant, l2_chunk_mb)
     wsb = L.tpd_workspace_size(n, code, opt)
-    ws = workspace
-    if wsb and (ws is None or ws.numel() < wsb):
-        ws = torch.empty(wsb, dtype=torch.uint8, device=A.device)
-    with torch.cuda.device(A.device):
-        st = L.tpd_decompose(out.data_ptr(), n, code, opt, ws.data_ptr() if wsb else 0, wsb, _stream(stream))
+    with _enqueue(A.device, stream, A, workspace) as s:
+        out = A if inplace else A.clone()
+        ws = workspace
+        if wsb and (ws is None or ws.numel() < wsb):
+            ws = torch.empty(wsb, dtype=torch.uint8, device=A.device)
+        st = L.tpd_decompose(out.data_ptr(), n, code, opt, ws.data_ptr() if wsb else 0, wsb, s)
     _raise(st, "tpd_decompose")
     return out
 
@@ -89,15 +113,14 @@ def compose(C, *, scale=1.0, inplace=False, precision=None, skip_zero=False, til
     _check_device(C)
     n = _qubits(C)
     code = _dtype_code(C)
-    out = C if inplace else C.clone()
     opt = make_options(precision, skip_zero, tile_bits, max_levels, variant)
     wsb = L.tpd_workspace_size(n, code, opt)
-    ws = workspace
-    if wsb and (ws is None or ws.numel() < wsb):
-        ws = torch.empty(wsb, dtype=torch.uint8, device=C.device)
-    with torch.cuda.device(C.device):
-        st = L.tpd_compose(out.data_ptr(), n, code, float(scale), opt, ws.data_ptr() if wsb else 0, wsb,
-                           _stream(stream))
+    with _enqueue(C.device, stream, C, workspace) as s:
+        out = C if inplace else C.clone()
+        ws = workspace
+        if wsb and (ws is None or ws.numel() < wsb):
+            ws = torch.empty(wsb, dtype=torch.uint8, device=C.device)
+        st = L.tpd_compose(out.data_ptr(), n, code, float(scale), opt, ws.data_ptr() if wsb else 0, wsb, s)
     _raise(st, "tpd_compose")
     return out
 
@@ -128,10 +151,13 @@ class Batch:
         self.ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
         self.device = dev
 
+    def _inputs(self):
+        return [self.ptrs, self.ns_dev, self.ws] + self.mats
+
     def decompose(self, stream=None):
-        with torch.cuda.device(self.device):
+        with _enqueue(self.device, stream, *self._inputs()) as s:
             st = L.tpd_decompose_batched(self.ptrs.data_ptr(), self.ns_dev.data_ptr(), self.ns, self.code,
-                                         self.opt, self.ws.data_ptr(), self.ws.numel(), _stream(stream))
+                                         self.opt, self.ws.data_ptr(), self.ws.numel(), s)
         _raise(st, "tpd_decompose_batched")
 
     def status(self, stream=None):
@@ -140,10 +166,9 @@ class Batch:
             return L.tpd_batch_status(self.ws.data_ptr(), _stream(stream))
 
     def compose(self, adjoint=False, stream=None):
-        with torch.cuda.device(self.device):
+        with _enqueue(self.device, stream, *self._inputs()) as s:
             st = L.tpd_compose_batched(self.ptrs.data_ptr(), self.ns_dev.data_ptr(), self.ns, self.code,
-                                       1 if adjoint else 0, self.opt, self.ws.data_ptr(), self.ws.numel(),
-                                       _stream(stream))
+                                       1 if adjoint else 0, self.opt, self.ws.data_ptr(), self.ws.numel(), s)
         _raise(st, "tpd_compose_batched")
 
 
@@ -191,12 +216,12 @@ class Partial:
         _check_device(A)
         if _qubits(A) != self.n or _dtype_code(A) != self.code:
             raise ValueError("matrix does not match the prepared size / dtype")
-        work = A if inplace else A.clone()
-        if out is None:
-            out = torch.empty(self.count, dtype=self.dtype, device=A.device)
-        with torch.cuda.device(A.device):
+        with _enqueue(A.device, stream, A, self.ws, out) as s:
+            work = A if inplace else A.clone()
+            if out is None:
+                out = torch.empty(self.count, dtype=self.dtype, device=A.device)
             st = L.tpd_decompose_partial(work.data_ptr(), self.n, self.code, self.opt, self.count, self.ws.data_ptr(),
-                                         self.ws.numel(), out.data_ptr(), _stream(stream))
+                                         self.ws.numel(), out.data_ptr(), s)
         _raise(st, "tpd_decompose_partial")
         return out
 
@@ -215,17 +240,17 @@ def decompose_coo(rows, cols, values, n, *, max_entries=None, capacity=None, str
     nnz = values.numel()
     dev = values.device
     cap_entries = int(max_entries) if max_entries else 4 * nnz + 1024
-    count = torch.zeros(1, dtype=torch.int64, device=dev)
-    status = torch.zeros(1, dtype=torch.int32, device=dev)
     while True:
-        ws = torch.empty(L.tpd_sparse_workspace_size(cap_entries), dtype=torch.uint8, device=dev)
-        cap = int(capacity) if capacity is not None else cap_entries
-        strings = torch.empty(max(cap, 1), dtype=torch.int64, device=dev)
-        weights = torch.empty(max(cap, 1), dtype=torch.complex128, device=dev)
-        with torch.cuda.device(dev):
+        with _enqueue(dev, stream, rows, cols, values) as s:
+            count = torch.zeros(1, dtype=torch.int64, device=dev)
+            status = torch.zeros(1, dtype=torch.int32, device=dev)
+            ws = torch.empty(L.tpd_sparse_workspace_size(cap_entries), dtype=torch.uint8, device=dev)
+            cap = int(capacity) if capacity is not None else cap_entries
+            strings = torch.empty(max(cap, 1), dtype=torch.int64, device=dev)
+            weights = torch.empty(max(cap, 1), dtype=torch.complex128, device=dev)
             st = L.tpd_decompose_coo(rows.data_ptr(), cols.data_ptr(), values.data_ptr(), nnz, int(n), L.TPD_C128,
                                      cap_entries, strings.data_ptr(), weights.data_ptr(), cap, count.data_ptr(),
-                                     status.data_ptr(), ws.data_ptr(), ws.numel(), _stream(stream))
+                                     status.data_ptr(), ws.data_ptr(), ws.numel(), s)
         _raise(st, "tpd_decompose_coo")
         if int(status.item()) == 0:
             k = min(int(count.item()), cap)
@@ -242,22 +267,20 @@ def nonzero_list(W, *, tol=0.0, capacity=None, stream=None):
     _check_device(W)
     n = _qubits(W)
     code = _dtype_code(W)
-    ws = torch.empty(L.tpd_nonzero_workspace_size(n), dtype=torch.uint8, device=W.device)
-    count = torch.zeros(1, dtype=torch.int64, device=W.device)
-    if capacity is None:
-        cap = 0
-        with torch.cuda.device(W.device):
+    with _enqueue(W.device, stream, W) as s:
+        ws = torch.empty(L.tpd_nonzero_workspace_size(n), dtype=torch.uint8, device=W.device)
+        count = torch.zeros(1, dtype=torch.int64, device=W.device)
+        if capacity is None:
             st = L.tpd_nonzero_list(W.data_ptr(), n, code, tol, 0, 0, 0, count.data_ptr(), ws.data_ptr(),
-                                    ws.numel(), _stream(stream))
-        _raise(st, "tpd_nonzero_list")
-        cap = int(count.item())
-    else:
-        cap = int(capacity)
-    strings = torch.empty(max(cap, 1), dtype=torch.int64, device=W.device)
-    weights = torch.empty(max(cap, 1), dtype=W.dtype, device=W.device)
-    with torch.cuda.device(W.device):
+                                    ws.numel(), s)
+            _raise(st, "tpd_nonzero_list")
+            cap = int(count.item())
+        else:
+            cap = int(capacity)
+        strings = torch.empty(max(cap, 1), dtype=torch.int64, device=W.device)
+        weights = torch.empty(max(cap, 1), dtype=W.dtype, device=W.device)
         st = L.tpd_nonzero_list(W.data_ptr(), n, code, tol, strings.data_ptr(), weights.data_ptr(), cap,
-                                count.data_ptr(), ws.data_ptr(), ws.numel(), _stream(stream))
+                                count.data_ptr(), ws.data_ptr(), ws.numel(), s)
     _raise(st, "tpd_nonzero_list")
     if capacity is None:
         return strings[:cap], weights[:cap]
@@ -269,9 +292,9 @@ def to_string_layout(W, *, stream=None):
     a flat tensor, converted from the RC layout on the device."""
     _check_device(W)
     n = _qubits(W)
-    out = torch.empty(W.numel(), dtype=W.dtype, device=W.device)
-    with torch.cuda.device(W.device):
-        st = L.tpd_convert_layout(W.data_ptr(), out.data_ptr(), n, _dtype_code(W), 1, _stream(stream))
+    with _enqueue(W.device, stream, W) as s:
+        out = torch.empty(W.numel(), dtype=W.dtype, device=W.device)
+        st = L.tpd_convert_layout(W.data_ptr(), out.data_ptr(), n, _dtype_code(W), 1, s)
     _raise(st, "tpd_convert_layout")
     return out
 
@@ -285,9 +308,9 @@ def from_string_layout(S, *, stream=None):
     n = (m.bit_length() - 1) // 2
     if m < 4 or 4 ** n != m:
         raise ValueError("expected 4^n elements, got %d" % m)
-    out = torch.empty((2 ** n, 2 ** n), dtype=S.dtype, device=S.device)
-    with torch.cuda.device(S.device):
-        st = L.tpd_convert_layout(S.data_ptr(), out.data_ptr(), n, _dtype_code(S), 0, _stream(stream))
+    with _enqueue(S.device, stream, S) as s:
+        out = torch.empty((2 ** n, 2 ** n), dtype=S.dtype, device=S.device)
+        st = L.tpd_convert_layout(S.data_ptr(), out.data_ptr(), n, _dtype_code(S), 0, s)
     _raise(st, "tpd_convert_layout")
     return out
 
@@ -296,12 +319,47 @@ def sum_squares(X, *, stream=None):
     """sum |x|^2 over a complex CUDA tensor, in fp64 on the device (a 0-dim
     float64 CUDA tensor; deterministic)."""
     _check_device(X)
-    out = torch.empty((), dtype=torch.float64, device=X.device)
-    ws = torch.empty(L.TPD_SUMSQ_WORKSPACE_BYTES, dtype=torch.uint8, device=X.device)
-    with torch.cuda.device(X.device):
-        st = L.tpd_sum_squares(X.data_ptr(), X.numel(), _dtype_code(X), out.data_ptr(), ws.data_ptr(), ws.numel(),
-                               _stream(stream))
+    with _enqueue(X.device, stream, X) as s:
+        out = torch.empty((), dtype=torch.float64, device=X.device)
+        ws = torch.empty(L.TPD_SUMSQ_WORKSPACE_BYTES, dtype=torch.uint8, device=X.device)
+        st = L.tpd_sum_squares(X.data_ptr(), X.numel(), _dtype_code(X), out.data_ptr(), ws.data_ptr(), ws.numel(), s)
     _raise(st, "tpd_sum_squares")
+    return out
+
+
+def _qudits(t, d):
+    if t.dim() != 2 or t.shape[0] != t.shape[1]:
+        raise ValueError("expected a square matrix, got shape %s" % (tuple(t.shape),))
+    N, n = int(t.shape[0]), 0
+    while d ** n < N:
+        n += 1
+    if n < 1 or d ** n != N:
+        raise ValueError("matrix side must be a power of d = %d, got %d" % (d, N))
+    return n
+
+
+def weyl_decompose(A, d, *, inplace=False, stream=None):
+    """Weights c_{a,b} = d^-n tr(W_{a,b}^* A) of a d^n x d^n CUDA matrix in the
+    Weyl (clock-and-shift) basis W_{a,b} = X^a Z^b; the weight of (a, b)
+    sits at row digits b, column digits a + b mod d (see tpd_weyl_decompose)."""
+    _check_device(A)
+    n = _qudits(A, d)
+    with _enqueue(A.device, stream, A) as s:
+        out = A if inplace else A.clone()
+        st = L.tpd_weyl_decompose(out.data_ptr(), n, int(d), _dtype_code(A), s)
+    _raise(st, "tpd_weyl_decompose")
+    return out
+
+
+def weyl_compose(C, d, *, scale=1.0, inplace=False, stream=None):
+    """scale * sum c_{a,b} W_{a,b} from weights in the layout of weyl_decompose
+    (scale d^-n: its adjoint)."""
+    _check_device(C)
+    n = _qudits(C, d)
+    with _enqueue(C.device, stream, C) as s:
+        out = C if inplace else C.clone()
+        st = L.tpd_weyl_compose(out.data_ptr(), n, int(d), _dtype_code(C), float(scale), s)
+    _raise(st, "tpd_weyl_compose")
     return out
 
 

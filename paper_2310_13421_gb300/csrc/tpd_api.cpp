@@ -95,7 +95,10 @@ size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 // Workspace of one matrix's plan:
 //   zero-skip flags: one byte per tile of every pass after the first (skip only)
-//   binary points:   one int per tile of every pass but the last (fixed point only)
+//   binary points:   one int16 per class of every pass but the last (block
+//                    fixed point only): 4^n / 2^K entries for a pass of K levels
+size_t class_count(const PassDesc& pd) { return (size_t)pd.ntiles << (pd.D - pd.K); }
+
 struct Layout {
   size_t flags_off[kMaxQubits];
   size_t q_off[kMaxQubits];
@@ -111,9 +114,9 @@ Layout layout_of(const Plan& p, int arith, int skip) {
   L.flags_bytes = align256(off);
   off = L.flags_bytes;
   if (arith == kArithFixed)
-    for (int i = 0; i + 1 < p.npass; ++i) { L.q_off[i] = off; off += (size_t)p.pass[i].ntiles * sizeof(int); }
-  L.q_bytes = align256(off) - L.flags_bytes;
-  L.total = L.flags_bytes + L.q_bytes;
+    for (int i = 0; i + 1 < p.npass; ++i) { L.q_off[i] = off; off += align256(class_count(p.pass[i]) * sizeof(int16_t)); }
+  L.q_bytes = off - L.flags_bytes;
+  L.total = off;
   return L;
 }
 
@@ -220,8 +223,9 @@ tpd_status run_single(bool dec, int arith, void* mat, const Plan& plan, int skip
   const Layout lay = layout_of(plan, arith, skip);
   char* w = static_cast<char*>(ws);
   if (skip && lay.flags_bytes && cudaMemsetAsync(w, 0, lay.flags_bytes, s) != cudaSuccess) return TPD_ERR_CUDA;
-  // with skipping, tiles a pass never visits keep the "zero tile" fill
-  if (skip && lay.q_bytes && cudaMemsetAsync(w + lay.flags_bytes, kQFillByte, lay.q_bytes, s) != cudaSuccess)
+  // with skipping (or a partial decomposition), classes of tiles a pass never
+  // visits keep the "zero class" fill
+  if ((skip || need) && lay.q_bytes && cudaMemsetAsync(w + lay.flags_bytes, kQFillByte, lay.q_bytes, s) != cudaSuccess)
     return TPD_ERR_CUDA;
   int spow = 0;
   double sres = 1.0;
@@ -238,8 +242,8 @@ tpd_status run_single(bool dec, int arith, void* mat, const Plan& plan, int skip
     if (skip && !last) a.flags_out = reinterpret_cast<uint8_t*>(w + lay.flags_off[p + 1]);
     if (need) a.need = need[p];
     if (arith == kArithFixed) {
-      if (p > 0) a.q_in = reinterpret_cast<const int*>(w + lay.q_off[p - 1]);
-      if (!last) a.q_out = reinterpret_cast<int*>(w + lay.q_off[p]);
+      if (p > 0) a.q_in = reinterpret_cast<const int16_t*>(w + lay.q_off[p - 1]);
+      if (!last) a.q_out = reinterpret_cast<int16_t*>(w + lay.q_off[p]);
     }
     pass_scaling(dec, arith, pd, last, spow, sres, scale, &a);
     return a;

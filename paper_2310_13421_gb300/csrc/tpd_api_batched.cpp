@@ -30,12 +30,12 @@ bool g_hold_batch_waits = false;   // test hook (tpd_test_hold_batch_waits)
 // workspace: control words (status, work counter, per-matrix pass completion
 // counters of the persistent kernel) | items[count] (matrix indices bucketed
 // by qubit count, on the device) | bptrs[count] (their pointers, persistent
-// form) | per qubit count n (ascending), for the fixed point: binary points of
-// hist[n] matrices for every pass but the last
+// form) | per qubit count n (ascending), for the block fixed point: the class
+// binary points of hist[n] matrices for every pass but the last
 size_t batched_q_bytes(const Plan& plan, int arith, int count_n) {
   if (arith != kArithFixed || plan.npass < 2) return 0;
   size_t b = 0;
-  for (int i = 0; i + 1 < plan.npass; ++i) b += (size_t)plan.pass[i].ntiles * sizeof(int) * (size_t)count_n;
+  for (int i = 0; i + 1 < plan.npass; ++i) b += class_count(plan.pass[i]) * sizeof(int16_t) * (size_t)count_n;
   return align256(b);
 }
 size_t batched_ctrl(const int* hist, const std::vector<const Plan*>& plans) {
@@ -95,7 +95,8 @@ tpd_status run_persistent(bool dec, int arith, void* const* ptrs_dev, const int*
   bp.ptrs = ptrs_dev; bp.ns = ns_dev; bp.items = items; bp.bptrs = bptrs; bp.ctrl = ctrl;
   int item_start[kBatchMaxQubits + 2] = {0};
   for (int n = 1; n <= kBatchMaxQubits + 1; ++n) item_start[n] = item_start[n - 1] + hist[n - 1];
-  // per n (ascending, as the workspace lays them out): q area and done-counter base
+  // per n (ascending, as the workspace lays them out): binary-point area and
+  // the base of its matrices' completion counters
   size_t qbase_n[kBatchMaxQubits + 1] = {0};
   int dbase_n[kBatchMaxQubits + 1] = {0};
   {
@@ -137,12 +138,12 @@ tpd_status run_persistent(bool dec, int arith, void* const* ptrs_dev, const int*
       if (arith == kArithFixed) {
         if (i > 0) {
           a.q_in = sg.args[i - 1].q_out;
-          a.q_in_stride = p.pass[i - 1].ntiles;
+          a.q_in_stride = (long long)class_count(p.pass[i - 1]);
         }
         if (!last) {
-          a.q_out = reinterpret_cast<int*>(qbase0 + qoff);
-          a.q_out_stride = pd.ntiles;
-          qoff += (size_t)pd.ntiles * sizeof(int) * hist[n];
+          a.q_out = reinterpret_cast<int16_t*>(qbase0 + qoff);
+          a.q_out_stride = (long long)class_count(pd);
+          qoff += class_count(pd) * sizeof(int16_t) * hist[n];
         }
       }
       const double scale = scale_mode ? std::ldexp(1.0, -n) : 1.0;
@@ -222,7 +223,7 @@ tpd_status batched(bool dec, void* const* ptrs_dev, const int* ns_dev, const int
       if (launch_small(arith, dec, a, hist[n], n, s) != cudaSuccess) return TPD_ERR_CUDA;
     } else {
       size_t qoff = 0;
-      const int* q_prev = nullptr;
+      const int16_t* q_prev = nullptr;
       long long q_prev_stride = 0;
       for (int p = 0; p < plan.npass; ++p) {
         const PassDesc& pd = plan.pass[p];
@@ -234,11 +235,11 @@ tpd_status batched(bool dec, void* const* ptrs_dev, const int* ns_dev, const int
           a.q_in = q_prev;
           a.q_in_stride = q_prev_stride;
           if (!last) {
-            a.q_out = reinterpret_cast<int*>(qbase + qoff);
-            a.q_out_stride = pd.ntiles;
-            qoff += (size_t)pd.ntiles * sizeof(int) * (size_t)hist[n];
+            a.q_out = reinterpret_cast<int16_t*>(qbase + qoff);
+            a.q_out_stride = (long long)class_count(pd);
+            qoff += class_count(pd) * sizeof(int16_t) * (size_t)hist[n];
             q_prev = a.q_out;
-            q_prev_stride = pd.ntiles;
+            q_prev_stride = a.q_out_stride;
           }
         }
         const double scale = scale_mode ? std::ldexp(1.0, -n) : 1.0;

@@ -33,15 +33,15 @@ using namespace detail;
 // that enumeration would be longer than the pass has tiles, the pass takes
 // instead every tile that shares elements with a needed tile of the pass after
 // it (a superset).  Skipped tiles keep what the previous pass left there: the
-// later passes read those positions only into weights nobody asked for, and
-// the fixed point's binary points of skipped tiles are marked zero before the
-// run, so their elements enter a tile's binary point as zeros.  The requested
-// weights thus have the full decomposition's values: bit for bit in the IEEE
-// arithmetics and on dyadic inputs, and within the same error bound otherwise
-// (a tile's binary point can only be finer).
+// later passes read those positions only into weights nobody asked for.  In
+// the block fixed point the elements a pass sums together (one class, on one
+// binary point) all lie in the same dependency cone, so a needed class never
+// contains a skipped position: the requested weights are bit for bit those of
+// the full decomposition in every arithmetic, for finite inputs (a tile that
+// meets an Inf or NaN anywhere runs the IEEE butterfly).
 
 // workspace: RC positions of the requested strings | per pass, one byte per
-// tile: needed | the plan's own workspace (binary points between passes)
+// tile: needed | the plan's own workspace (the binary points between passes)
 struct PartialLayout {
   size_t need_off[kMaxQubits];
   size_t run_off, run_bytes, total;
@@ -216,9 +216,6 @@ tpd_status tpd_decompose_partial(void* A, int n, int dtype, const tpd_options* o
   const uint8_t* need[kMaxQubits];
   for (int p = 0; p < plan->npass; ++p) need[p] = reinterpret_cast<const uint8_t*>(w + lay.need_off[p]);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  // binary points of skipped tiles read as zero tiles (see above)
-  if (lay.run_bytes && cudaMemsetAsync(w + lay.run_off, kQFillByte, lay.run_bytes, s) != cudaSuccess)
-    return TPD_ERR_CUDA;
   st = run_single(true, arith, A, *plan, 0, 1.0, w + lay.run_off, s, &eff, plan->npass > 0 ? need : nullptr);
   if (st != TPD_OK) return st;
   if (launch_gather(A, reinterpret_cast<const unsigned long long*>(w), count, (int)eb, weights, s) != cudaSuccess)

@@ -30,6 +30,8 @@ void pass_scaling(bool dec, int arith, const PassDesc& pd, bool last, int spow, 
 int sm_count();
 // workspace bytes of one matrix's plan
 size_t single_ws(const Plan& plan, int arith, int skip);
+// classes of a pass (binary points it hands on): tiles x 2^(D-K)
+size_t class_count(const PassDesc& pd);
 // the passes of one matrix, in place; need: per-pass tile masks (partial decomposition) or nullptr
 tpd_status run_single(bool dec, int arith, void* mat, const Plan& plan, int skip, double scale, void* ws,
                       cudaStream_t s, const tpd_options* opt, const uint8_t* const* need = nullptr);

@@ -92,6 +92,22 @@ struct FixedArith {
     return to_fixed(x, shift_base);
   }
 
+  // to_fixed through the fp64 conversion unit, for elements of a class whose
+  // largest exponent field is E (shift_base = 9 - K - max(E, 1), so e + S
+  // <= 1084 - K stays in the normal range for every element of the class):
+  // scale by 2^S with an exact exponent shift, then convert truncating
+  // toward zero.  A scaled exponent below the normal range means
+  // |x| 2^S < 1: the result is 0.  Zeros are 0; subnormal x (rare) take the
+  // integer path out of line.
+  __device__ static __forceinline__ long long to_fixed_cvt_class(double x, int shift_base) {
+    const long long bits = __double_as_longlong(x);
+    const int e = (int)(bits >> 52) & 0x7FF;
+    const int S = shift_base + 1075;          // = 1084 - K - max(E, 1)
+    if (e == 0) return ((unsigned long long)bits << 1) == 0 ? 0ll : to_fixed_rare(x, shift_base);
+    return e + S >= 1 ? __double2ll_rz(__longlong_as_double(bits + ((long long)S << 52))) : 0ll;
+  }
+  static __device__ __noinline__ long long to_fixed_rare(double x, int shift_base) { return to_fixed(x, shift_base); }
+
   // Magnitude bits of a * 2^(be - 1086) (a has its leading one at bit 63)
   // rounded to nearest even, when that falls outside the normal range:
   // overflow to Inf or a subnormal result.  Out of line: never taken for
@@ -174,6 +190,14 @@ struct FixedArith {
     const int e = (int)(b >> 52) & 0x7FF;       // >= 1023 for v != 0
     if (v != 0 && e - T >= 1 && e - T <= 2046) return __longlong_as_double(b - ((long long)T << 52));
     return to_double_int(v, T);
+  }
+
+  // Both components rounded with integer instructions (any T): the rare
+  // case of the block fixed point's stores, out of line.
+  static __device__ __noinline__ double2 to_double2_rare(long long re, long long im, int T, double mul) {
+    double2 o = make_double2(to_double_int(re, T), to_double_int(im, T));
+    if (mul != 1.0) { o.x *= mul; o.y *= mul; }
+    return o;
   }
 
   __device__ static __forceinline__ double to_double(long long v, int T) {

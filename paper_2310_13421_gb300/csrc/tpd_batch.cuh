@@ -30,7 +30,7 @@
 
 #include <type_traits>
 
-#include "tpd_pass.cuh"
+#include "tpd_kernels_impl.cuh"
 
 namespace tpd {
 
@@ -107,8 +107,8 @@ __device__ __forceinline__ void batch_pass_tile(const BatchSeg& sg, int p, const
                                                 long long j, long long tile, unsigned char* smem, int lane,
                                                 int warp) {
   const PassArgs& args = sg.args[p];
-  const int* q_in = args.q_in ? args.q_in + j * args.q_in_stride : nullptr;
-  int* q_out = args.q_out ? args.q_out + j * args.q_out_stride : nullptr;
+  const int16_t* q_in = args.q_in ? args.q_in + j * args.q_in_stride : nullptr;
+  int16_t* q_out = args.q_out ? args.q_out + j * args.q_out_stride : nullptr;
   if constexpr (A::kFixed) {
     const int role = (p > 0 ? kRoleIntIn : 0) | (p + 1 < sg.npass ? kRoleIntOut : 0);
     switch (role) {
@@ -128,9 +128,9 @@ __device__ __forceinline__ void batch_pass_tile(const BatchSeg& sg, int p, const
   }
 }
 
-// 256 threads; dynamic shared memory: 2^12 x 16 bytes + 256 + 2^kMaxPrevBits
-// ints (a D = 12 tile or a whole n <= 6 matrix, reduction slots, gathered
-// binary points).  Thread 0 keeps the claimed-ahead item in s_next (its own
+// 256 threads; dynamic shared memory: 2^12 x 16 bytes + 256 + 2^11 ints (a
+// D = 12 tile or a whole n <= 6 matrix, reduction slots, class slots of the
+// block fixed point).  Thread 0 keeps the claimed-ahead item in s_next (its own
 // slot: kept out of registers, which the tile needs) and hands it to the CTA
 // through s_work at the top of the loop.
 template <class A, bool kDec>
@@ -221,9 +221,9 @@ __global__ void __launch_bounds__(256, 2) k_batch(const __grid_constant__ BatchP
 
 template <class A, bool kDec>
 cudaError_t launch_batch_t(const BatchParams& bp, int* grid_out, cudaStream_t s) {
-  const size_t smem = ((size_t)16 << 12) + 256 + (sizeof(int) << kMaxPrevBits);
+  const size_t smem = ((size_t)16 << 12) + 256 + (sizeof(int) << 11);
   auto kfn = k_batch<A, kDec>;
-  cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = ensure_smem_limit((const void*)kfn, smem);
   if (e != cudaSuccess) return e;
   int dev = 0, nsm = 0, per_sm = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;

@@ -2,7 +2,25 @@
 // helpers; the block-fixed-point passes sit in tpd_kernels_fixed_{dec,com}.cu.
 #include "tpd_kernels_impl.cuh"
 
+#include <map>
+#include <mutex>
+#include <utility>
+
 namespace tpd {
+
+cudaError_t ensure_smem_limit(const void* fn, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, size_t> set;   // (kernel, device) -> limit set
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& cur = set[std::make_pair(fn, dev)];
+  if (cur >= bytes) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) cur = bytes;
+  return e;
+}
 
 cudaError_t launch_pass_fixed_dec(const PassDesc& pd, const PassArgs& args, long long ntiles_total, cudaStream_t s);
 cudaError_t launch_pass_fixed_com(const PassDesc& pd, const PassArgs& args, long long ntiles_total, cudaStream_t s);

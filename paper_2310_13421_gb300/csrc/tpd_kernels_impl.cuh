@@ -10,11 +10,30 @@ namespace tpd {
 
 using PassKernel = void (*)(const PassDesc, const PassArgs);
 
-// the instantiation for a pass's CTA size, occupancy and (fixed point) role
+// Raise kernel fn's dynamic shared-memory limit to `bytes`, the largest
+// launch it can ever get, once per device (tpd_kernels_c128.cu).  The limit is
+// never set to one launch's own size: a kernel node captured in a CUDA graph
+// keeps the shared-memory size of its capture, and relaunching it (a graph
+// replay on some drivers, or a profiler replaying graph nodes one by one) after
+// a smaller launch of the same kernel had lowered the limit would fail to
+// launch.
+cudaError_t ensure_smem_limit(const void* fn, size_t bytes);
+
+// Class slots of the block fixed point: 2^(D-K) ints, at most 2^(D-1) (K >= 1).
+template <class A>
+constexpr bool kBlockFixed = A::kFixed || A::kFixed32;
+inline size_t class_slot_bytes(const PassDesc& pd) { return sizeof(int) << (pd.D - pd.K); }
+
+// the instantiation for a pass's CTA size, occupancy and (block fixed point) role
 template <class A, bool kDec, int kRole>
 PassKernel pick_pass_kernel(const PassDesc& pd, int threads) {
   if (threads > 256) return k_pass<A, kDec, 512, 1, kRole>;
   return pd.min_blocks >= 3 ? k_pass<A, kDec, 256, 3, kRole> : k_pass<A, kDec, 256, 2, kRole>;
+}
+
+// the role of a complex128 block-fixed-point pass from its binary-point arrays
+inline int fixed_role(const PassArgs& args) {
+  return (args.q_in ? kRoleIntIn : 0) | (args.q_out ? kRoleIntOut : 0);
 }
 
 // complex128 tiles of 2^13 elements planned as two-CTA clusters (min_blocks 2)
@@ -23,19 +42,18 @@ constexpr bool kClusterArith = std::is_same<A, FixedArith>::value || std::is_sam
 
 template <class A, bool kDec>
 cudaError_t launch_pass_cl_t(const PassDesc& pd, const PassArgs& args, long long ntiles_total, cudaStream_t s) {
-  const size_t smem = ((size_t)16 << (pd.D - 1)) + 256 + ((A::kFixed && args.q_in) ? sizeof(int) << kMaxPrevBits : 0);
-  PassKernel kfn;
+  const size_t smem = ((size_t)16 << (pd.D - 1)) + 256 + (kBlockFixed<A> ? class_slot_bytes(pd) : 0);
+  const size_t smem_max = ((size_t)16 << (kMaxTileBits - 1)) + 256 + (kBlockFixed<A> ? sizeof(int) << (kMaxTileBits - 1) : 0);
+  PassKernel kfn = k_pass_cl<A, kDec, 0>;
   if constexpr (A::kFixed) {
-    switch ((args.q_in ? kRoleIntIn : 0) | (args.q_out ? kRoleIntOut : 0)) {
-      case 0: kfn = k_pass_cl<A, kDec, 0>; break;
+    switch (fixed_role(args)) {
       case kRoleIntIn: kfn = k_pass_cl<A, kDec, kRoleIntIn>; break;
       case kRoleIntOut: kfn = k_pass_cl<A, kDec, kRoleIntOut>; break;
-      default: kfn = k_pass_cl<A, kDec, kRoleIntIn | kRoleIntOut>; break;
+      case kRoleIntIn | kRoleIntOut: kfn = k_pass_cl<A, kDec, kRoleIntIn | kRoleIntOut>; break;
+      default: break;
     }
-  } else {
-    kfn = k_pass_cl<A, kDec, 0>;
   }
-  cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = ensure_smem_limit((const void*)kfn, smem_max);
   if (e != cudaSuccess) return e;
   if (ntiles_total <= 0) return cudaSuccess;
   if (2 * ntiles_total > 0x7fffffffll) return cudaErrorInvalidValue;
@@ -49,23 +67,21 @@ cudaError_t launch_pass_t(const PassDesc& pd, const PassArgs& args, long long nt
   if constexpr (kClusterArith<A>) {
     if (pd.D == kMaxTileBits && pd.min_blocks == 2) return launch_pass_cl_t<A, kDec>(pd, args, ntiles_total, s);
   }
-  const size_t vbytes = A::kFixed ? 16 : sizeof(typename A::V);
-  // exchange area, reduction slots, and (fixed point reading int64 sums) the
-  // gathered binary points -- the first pass keeps its occupancy without them
-  const size_t smem =
-      ((size_t)1 << pd.D) * vbytes + 256 + ((A::kFixed && args.q_in) ? sizeof(int) << kMaxPrevBits : 0);
-  PassKernel kfn;
+  const size_t vbytes = kBlockFixed<A> ? 16 : sizeof(typename A::V);
+  // exchange area, reduction slots, class slots (block fixed point)
+  const size_t smem = ((size_t)1 << pd.D) * vbytes + 256 + (kBlockFixed<A> ? class_slot_bytes(pd) : 0);
+  const int dmax = threads > 256 ? kMaxTileBits : 12;
+  const size_t smem_max = ((size_t)1 << dmax) * vbytes + 256 + (kBlockFixed<A> ? sizeof(int) << (dmax - 1) : 0);
+  PassKernel kfn = pick_pass_kernel<A, kDec, 0>(pd, threads);
   if constexpr (A::kFixed) {
-    switch ((args.q_in ? kRoleIntIn : 0) | (args.q_out ? kRoleIntOut : 0)) {
-      case 0: kfn = pick_pass_kernel<A, kDec, 0>(pd, threads); break;
+    switch (fixed_role(args)) {
       case kRoleIntIn: kfn = pick_pass_kernel<A, kDec, kRoleIntIn>(pd, threads); break;
       case kRoleIntOut: kfn = pick_pass_kernel<A, kDec, kRoleIntOut>(pd, threads); break;
-      default: kfn = pick_pass_kernel<A, kDec, kRoleIntIn | kRoleIntOut>(pd, threads); break;
+      case kRoleIntIn | kRoleIntOut: kfn = pick_pass_kernel<A, kDec, kRoleIntIn | kRoleIntOut>(pd, threads); break;
+      default: break;
     }
-  } else {
-    kfn = pick_pass_kernel<A, kDec, 0>(pd, threads);
   }
-  cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = ensure_smem_limit((const void*)kfn, smem_max);
   if (e != cudaSuccess) return e;
   if (ntiles_total <= 0) return cudaSuccess;
   if (ntiles_total > 0x7fffffffll) return cudaErrorInvalidValue;
@@ -73,13 +89,17 @@ cudaError_t launch_pass_t(const PassDesc& pd, const PassArgs& args, long long nt
   return cudaGetLastError();
 }
 
+// whole matrices of n <= 6 qubits: 4^n elements (16 bytes in registers for
+// every arithmetic but plain fp32) and, block fixed point, 2^n class slots
 template <class A, bool kDec>
 cudaError_t launch_small_t(const SmallArgs& args, int blocks, int n_max, cudaStream_t s) {
   const size_t vbytes = A::kFixed ? 16 : sizeof(typename A::V);
-  size_t smem = ((size_t)1 << (2 * n_max)) * vbytes;
+  const size_t cls = A::kFixed ? sizeof(int) << n_max : 0;
+  size_t smem = ((size_t)1 << (2 * n_max)) * vbytes + cls;
   if (smem < 256) smem = 256;
+  const size_t smem_max = ((size_t)1 << 12) * vbytes + (A::kFixed ? sizeof(int) << 6 : 0);
   auto kfn = k_small<A, kDec>;
-  cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = ensure_smem_limit((const void*)kfn, smem_max);
   if (e != cudaSuccess) return e;
   if (blocks <= 0) return cudaSuccess;
   kfn<<<blocks, 128, smem, s>>>(args);
@@ -89,16 +109,17 @@ cudaError_t launch_small_t(const SmallArgs& args, int blocks, int n_max, cudaStr
 template <bool kDec>
 cudaError_t launch_pass_pipe_t(const PassDesc& pd, const PassArgs& args, int nsm, cudaStream_t s) {
   const int threads = 1 << (pd.D - kRegBits);
-  // two tile buffers, reduction slots, gathered binary points (passes reading int64 sums)
-  const size_t smem = ((size_t)32 << pd.D) + 256 + (args.q_in ? sizeof(int) << kMaxPrevBits : 0);
+  // two tile buffers, reduction slots, class slots
+  const size_t smem = ((size_t)32 << pd.D) + 256 + class_slot_bytes(pd);
+  const size_t smem_max = ((size_t)32 << 12) + 256 + (sizeof(int) << 11);
   PassKernel kfn;
-  switch ((args.q_in ? kRoleIntIn : 0) | (args.q_out ? kRoleIntOut : 0)) {
-    case 0: kfn = k_pass_pipe<kDec, 0>; break;
+  switch (fixed_role(args)) {
     case kRoleIntIn: kfn = k_pass_pipe<kDec, kRoleIntIn>; break;
     case kRoleIntOut: kfn = k_pass_pipe<kDec, kRoleIntOut>; break;
-    default: kfn = k_pass_pipe<kDec, kRoleIntIn | kRoleIntOut>; break;
+    case kRoleIntIn | kRoleIntOut: kfn = k_pass_pipe<kDec, kRoleIntIn | kRoleIntOut>; break;
+    default: kfn = k_pass_pipe<kDec, 0>; break;
   }
-  cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = ensure_smem_limit((const void*)kfn, smem_max);
   if (e != cudaSuccess) return e;
   const long long grid = pd.ntiles < nsm ? pd.ntiles : nsm;
   kfn<<<(unsigned)grid, threads, smem, s>>>(pd, args);

@@ -26,15 +26,17 @@ struct PassArgs {
   int out_pow2;               // fixed point: output multiplied by 2^out_pow2 (exact)
   double out_mul;             // IEEE paths: output multiplier (exact power of two or user scale);
                               // fixed point: non-power-of-two residual factor (1.0 normally)
-  // Fixed point between passes.  A pass that does not end the plan stores its
-  // int64 sums in place and its tile's binary point q (value = v * 2^q) in
-  // q_out[tile]; the next pass reads q_in[previous tile] per element.
-  // Markers: kQZero (tile never written: its elements are zero) and kQIeee
-  // (tile holds IEEE doubles: it met an Inf or NaN).
-  const int* q_in;            // nullptr: input is IEEE doubles
-  int* q_out;                 // nullptr: output is IEEE doubles
-  long long q_in_stride;      // batched: q entries per matrix (previous pass's tile count)
-  long long q_out_stride;     // batched: q entries per matrix (this pass's tile count)
+  // Block fixed point between passes.  A pass that does not end the plan
+  // stores its int64 sums in place and each class's binary point q (value =
+  // v * 2^q) in q_out[(tile << (D - K)) | class]; the next pass reads, per
+  // element, the binary point of the class it came from (PassDesc::src_w).
+  // Markers: kQIeee (the class holds IEEE doubles: its tile met an Inf or
+  // NaN); any other value at or below kQValidMin (e.g. the 0x80 byte fill of
+  // a cleared array) a class whose elements are all zero.
+  const int16_t* q_in;        // nullptr: input is IEEE numbers
+  int16_t* q_out;             // nullptr: output is IEEE numbers
+  long long q_in_stride;      // batched: q entries per matrix (previous pass's classes)
+  long long q_out_stride;     // batched: q entries per matrix (this pass's classes)
   // L2 chunk of a single matrix: CTA b runs tile chunk_or | (bit k of b) << chunk_free[k]
   int chunked;
   int nfree;
@@ -42,17 +44,17 @@ struct PassArgs {
   int8_t chunk_free[2 * kMaxQubits];
 };
 
-// Role of a fixed-point pass: input IEEE doubles (0) or int64 sums of a
-// previous pass (kRoleIntIn); output IEEE doubles (0) or int64 sums for a next
-// pass (kRoleIntOut).
+// Role of a block-fixed-point pass: input IEEE numbers (0) or int64 sums of a
+// previous pass (kRoleIntIn); output IEEE numbers (0) or int64 sums for a
+// next pass (kRoleIntOut).
 constexpr int kRoleIntIn = 1;
 constexpr int kRoleIntOut = 2;
 
-// q values above kQValidMin are binary points; kQIeee marks an IEEE tile; any
-// other value (e.g. the 0xC0 byte fill of a cleared array) a zero tile.
-constexpr int kQValidMin = -0x20000000;
-constexpr int kQIeee = -0x30000000;
-constexpr unsigned char kQFillByte = 0xC0;
+// binary points are in [-1100, 1100]; kQIeee marks an IEEE class; any other
+// value at or below kQValidMin a zero class
+constexpr int kQValidMin = -4096;
+constexpr int kQIeee = -30000;
+constexpr unsigned char kQFillByte = 0x80;
 
 struct SmallArgs {
   void* const* ptrs;          // batched: device array of matrix pointers (nullptr: use `mat`)

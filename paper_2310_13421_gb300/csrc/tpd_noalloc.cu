@@ -9,7 +9,7 @@
 
 namespace {
 
-constexpr size_t kNoAllocScratchBytes = (size_t)8 << 20;   // 8 MiB
+constexpr size_t kNoAllocScratchBytes = (size_t)64 << 20;   // 64 MiB
 
 // Lives in every GPU that loads the library, until the process exits.  In
 // host code this name is only a host-side stand-in: the device address comes
@@ -44,12 +44,14 @@ extern "C" {
 tpd_status tpd_decompose_noalloc(void* A, int n, int dtype, const tpd_options* opt, void* stream) {
   const size_t need = tpd_workspace_size(n, dtype, opt);
   if (need > kNoAllocScratchBytes) return TPD_ERR_WORKSPACE;   // this size needs tpd_decompose
+  // Looked up on every device's first call, whether or not this call needs
+  // the array, so that the set-up (which loads this file's device code and,
+  // under lazy module loading, the array with it) happens on that first call.
   void* scratch = nullptr;
-  if (need > 0) {
-    const tpd_status st = scratch_address(&scratch);
-    if (st != TPD_OK) return st;
-  }
-  return tpd_decompose(A, n, dtype, opt, scratch, need > 0 ? kNoAllocScratchBytes : 0, stream);
+  const tpd_status st = scratch_address(&scratch);
+  if (st != TPD_OK) return st;
+  return tpd_decompose(A, n, dtype, opt, need > 0 ? scratch : nullptr, need > 0 ? kNoAllocScratchBytes : 0,
+                       stream);
 }
 
 }  // extern "C"

@@ -7,8 +7,9 @@
 //      pruning of Alg. 1/2: a zero block has only zero weights below it);
 //   2. load its 16 elements per thread from HBM with the stage-0 mapping
 //      (lanes on the lowest tile bits: 128-byte runs);
-//   3. fixed point: CTA-wide max exponent -> common binary point; optional
-//      all-zero test (then nothing is written);
+//   3. block fixed point: the largest exponent of each class of elements the
+//      pass adds together -> one binary point per class; optional all-zero
+//      test (then nothing is written);
 //   4. per stage: apply the stage's levels in registers / across lanes, then
 //      exchange through shared memory into the next stage's mapping;
 //   5. round back to the storage type, store in place with the last stage's
@@ -307,24 +308,104 @@ __device__ __forceinline__ void load_tile(const PassDesc& pd, const void* matp, 
   for (int e = 0; e < kElems; ++e) raw[e] = ld_in<kCg>(mat + (g + reg_off(e, w0, w1, w2, w3)));
 }
 
-// ============================================================== fixed point
+// ============================================================== block fixed point
 //
-// A pass of the complex128 fixed-point path reads either IEEE doubles (the
-// first pass) or the int64 sums the previous pass stored in place together
-// with one binary point per previous tile (value = v * 2^q), and writes
-// either int64 sums plus its own tiles' binary points (a pass that does not
-// end the plan) or IEEE doubles rounded once (the last pass).  Between
-// passes the data stay 16-byte int64 pairs, so only the first pass converts
-// from double and only the last back to double.
-//
-// Headroom: every stored |v| < 2^62.  A reading pass of K levels aligns all
-// its elements to q_in = max(q_src) + K, i.e. shifts each right by at least
-// K bits (toward zero, so that conjugate inputs stay exactly conjugate),
-// after which 2^K-term sums stay below 2^62.
+// A pass of the block fixed point reads IEEE numbers and writes IEEE numbers.
+// Its tile splits into classes (PassDesc::cls_w): the 2^K elements the pass's
+// levels add together, i.e. those agreeing on x_j = r_j xor c_j of every
+// level j of the pass and on every passenger bit.  Each class goes onto its
+// own binary point, set by the largest exponent field E_c among the
+// components of its elements, so that its largest element lands below
+// 2^(62-K) and the 2^K-term sums of the pass are exact in int64; each output
+// is rounded once, to nearest even, when the pass stores it.  Components far
+// below their class's largest (more than 2^(9-K) binades for complex128,
+// 2^(38-K) for complex64) are truncated toward zero on loading, an error
+// below 2^-(62-K) of that largest.  Elements of different X-masks never share
+// a binary point, so a weight's error is bounded by the magnitudes of its own
+// class, not by those of a large neighbour (a strong diagonal beside weak
+// couplings).  Truncation toward zero and rounding to nearest are odd
+// functions, and a class and its conjugate partner (the same positions with
+// the row and column bits of the unprocessed levels swapped) hold conjugate
+// values with the same E_c, so conjugate symmetry is kept exactly: Hermitian
+// matrices give exactly real weights.
+
+// Class of a thread's register 0 in stage st: XOR of its lane and warp bits' class bits.
+__device__ __forceinline__ int cls_thread(const PassDesc& pd, const Stage& st, int lane, int warp) {
+  int c = 0;
+#pragma unroll
+  for (int i = 0; i < kLaneBits; ++i)
+    if ((lane >> i) & 1) c ^= pd.cls_w[st.lane[i]];
+  for (int i = 0; i < pd.D - kMinTileBits; ++i)
+    if ((warp >> i) & 1) c ^= pd.cls_w[st.warp[i]];
+  return c;
+}
+
+// class offset of register e from the class bits of the 4 register bits
+// (e is a compile-time constant after unrolling)
+__device__ __forceinline__ int reg_cls(int e, int w0, int w1, int w2, int w3) {
+  return ((e & 1) ? w0 : 0) ^ ((e & 2) ? w1 : 0) ^ ((e & 4) ? w2 : 0) ^ ((e & 8) ? w3 : 0);
+}
+
+// Class maxima of a tile held in the stage-0 mapping: slots[c] becomes the
+// largest exponent field (exp_of) of class c's elements.  The slots must be 0
+// on entry.  A stage's in-register levels put a level's column and row bit on
+// register bits (0,1) and (2,3), so e, e^3 (and e^12, e^15) share a class: one
+// atomic per class and thread.
+// Returns the largest exponent field of the thread's elements.
+template <class Raw, class ExpOf>
+__device__ __forceinline__ uint32_t class_max(const PassDesc& pd, const Raw (&raw)[kElems], int* slots, int lane,
+                                              int warp, ExpOf exp_of) {
+  const Stage& s0 = pd.st[0];
+  const int ct = cls_thread(pd, s0, lane, warp);
+  const int c0 = pd.cls_w[s0.reg[0]], c1 = pd.cls_w[s0.reg[1]], c2 = pd.cls_w[s0.reg[2]],
+            c3 = pd.cls_w[s0.reg[3]];
+  const int np = s0.npair;
+  uint32_t ex[kElems];
+  uint32_t hmax = 0;
+#pragma unroll
+  for (int e = 0; e < kElems; ++e) {
+    ex[e] = exp_of(raw[e]);
+    hmax = max(hmax, ex[e]);
+  }
+#pragma unroll
+  for (int e = 0; e < kElems; ++e) {
+    if (np >= 1 && (e & 2)) continue;
+    if (np >= 2 && (e & 8)) continue;
+    uint32_t m = ex[e];
+    if (np >= 1) m = max(m, ex[e ^ 3]);
+    if (np >= 2) m = max(m, max(ex[e ^ 12], ex[e ^ 15]));
+    if (m) atomicMax(slots + (ct ^ reg_cls(e, c0, c1, c2, c3)), (int)m);
+  }
+  return hmax;
+}
+
+__device__ __forceinline__ uint32_t exp_f64(const double2& x) {
+  return max((uint32_t)__double2hiint(x.x) & 0x7fffffffu, (uint32_t)__double2hiint(x.y) & 0x7fffffffu) >> 20;
+}
+__device__ __forceinline__ uint32_t exp_f32(const float2& x) {
+  return max(__float_as_uint(x.x) & 0x7fffffffu, __float_as_uint(x.y) & 0x7fffffffu) >> 23;
+}
+
+// Source-class index (previous pass's binary-point array) of a thread's
+// register 0 in stage st: XOR of its lane and warp bits' contributions.
+__device__ __forceinline__ uint32_t src_thread(const PassDesc& pd, const Stage& st, int lane, int warp) {
+  uint32_t c = 0;
+#pragma unroll
+  for (int i = 0; i < kLaneBits; ++i)
+    if ((lane >> i) & 1) c ^= pd.src_w[st.lane[i]];
+  for (int i = 0; i < pd.D - kMinTileBits; ++i)
+    if ((warp >> i) & 1) c ^= pd.src_w[st.warp[i]];
+  return c;
+}
+
+__device__ __forceinline__ uint32_t reg_src(int e, uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3) {
+  return ((e & 1) ? w0 : 0u) ^ ((e & 2) ? w1 : 0u) ^ ((e & 4) ? w2 : 0u) ^ ((e & 8) ? w3 : 0u);
+}
 
 __device__ __forceinline__ bool q_is_valid(int q) { return q > kQValidMin; }
 
-// v / 2^sh rounded toward zero (sh >= 0; 0 once sh >= 64)
+// v / 2^sh rounded toward zero (sh >= 0; 0 once sh >= 64): an odd function,
+// so conjugate sums stay exactly conjugate
 __device__ __forceinline__ long long shr_tz(long long v, unsigned sh) {
   const unsigned long long s = (unsigned long long)(v >> 63);
   unsigned long long a = ((unsigned long long)v ^ s) - s;
@@ -332,63 +413,25 @@ __device__ __forceinline__ long long shr_tz(long long v, unsigned sh) {
   return (long long)((a ^ s) - s);
 }
 
-// floor(v / 2^sh) (sh >= 0; 0 or -1 once sh >= 64)
-__device__ __forceinline__ long long shr_floor(long long v, unsigned sh) {
-  long long r;
-  asm("shr.s64 %0, %1, %2;" : "=l"(r) : "l"(v), "r"(sh));   // PTX clamps the amount at 64
-  return r;
-}
-
-// Alignment of the int64 sums of a previous pass to the tile's binary point.
-// Rounding toward minus infinity costs 2-3 instructions against ~11 for
-// toward zero; the error is below 2^-(62-K) of the tile's largest element.
-#ifdef TPD_ALIGN_TOWARD_ZERO
-#define TPD_ALIGN shr_tz
-#else
-#define TPD_ALIGN shr_floor
-#endif
-
-// Which unit converts each component between double and int64 (identical
-// results either way): integer instructions, or the fp64 conversion unit.
-#if defined(TPD_CVT_BOTH)
-#define TPD_TO_FIXED_RE FixedArith::to_fixed_cvt
-#define TPD_TO_FIXED_IM FixedArith::to_fixed_cvt
-#define TPD_TO_DOUBLE_RE FixedArith::to_double_cvt
-#define TPD_TO_DOUBLE_IM FixedArith::to_double_cvt
-#elif defined(TPD_CVT_RE)
-#define TPD_TO_FIXED_RE FixedArith::to_fixed_cvt
-#define TPD_TO_FIXED_IM FixedArith::to_fixed
-#define TPD_TO_DOUBLE_RE FixedArith::to_double_cvt
-#define TPD_TO_DOUBLE_IM FixedArith::to_double_int
-#else
-#define TPD_TO_FIXED_RE FixedArith::to_fixed
-#define TPD_TO_FIXED_IM FixedArith::to_fixed
-#define TPD_TO_DOUBLE_RE FixedArith::to_double_int
-#define TPD_TO_DOUBLE_IM FixedArith::to_double_int
-#endif
-
-// Tiles meeting an Inf or NaN run the IEEE fp64 butterfly instead.  Out of
-// line (never taken for finite data) so the hot path stays small in the
-// instruction cache.  Elements are re-read: doubles as such, int64 sums of a
-// previous pass converted with their tile's binary point.
+// Tiles meeting an Inf or NaN run the IEEE fp64 butterfly instead (rounded
+// every level, the paper's arithmetic), so non-finite inputs propagate as in
+// IEEE arithmetic.  Out of line: never taken for finite data.  Elements are
+// re-read: IEEE numbers as such, int64 sums of a previous pass converted with
+// their class's binary point; a pass that hands on int64 sums marks all its
+// classes of this tile as holding IEEE numbers.
 template <bool kDec, bool kCg = false, bool kCl = false>
-__device__ __noinline__ void ieee_tile(const PassDesc& pd, const PassArgs& args, void* matp, const int* q_in,
-                                       int* q_out, long long tile, long long base, long long pbase, int nbase,
+__device__ __noinline__ void ieee_tile(const PassDesc& pd, const PassArgs& args, void* matp, const int16_t* q_in,
+                                       int16_t* q_out, long long tile, long long base, uint32_t sbase, int nbase,
                                        unsigned char* smem, int lane, int warp) {
   double2 raw[kElems];
   load_tile<kCg>(pd, matp, base, lane, warp, raw);
   if (q_in != nullptr) {
     const Stage& s0 = pd.st[0];
-    long long pt = pbase;
-#pragma unroll
-    for (int i = 0; i < kLaneBits; ++i)
-      if ((lane >> i) & 1) pt += pd.prev_w[s0.lane[i]];
-    for (int i = 0; i < pd.D - kMinTileBits; ++i)
-      if ((warp >> i) & 1) pt += pd.prev_w[s0.warp[i]];
-    const int p0 = pd.prev_w[s0.reg[0]], p1 = pd.prev_w[s0.reg[1]], p2 = pd.prev_w[s0.reg[2]],
-              p3 = pd.prev_w[s0.reg[3]];
+    const uint32_t sb = sbase ^ src_thread(pd, s0, lane, warp);
+    const uint32_t w0 = pd.src_w[s0.reg[0]], w1 = pd.src_w[s0.reg[1]], w2 = pd.src_w[s0.reg[2]],
+                   w3 = pd.src_w[s0.reg[3]];
     for (int e = 0; e < kElems; ++e) {
-      const int q = ld_in<kCg>(q_in + pt + reg_off(e, p0, p1, p2, p3));
+      const int q = ld_in<kCg>(q_in + (sb ^ reg_src(e, w0, w1, w2, w3)));
       if (q == kQIeee) continue;
       if (!q_is_valid(q)) { raw[e] = make_double2(0.0, 0.0); continue; }
       raw[e].x = FixedArith::to_double_int(__double_as_longlong(raw[e].x), -q);
@@ -398,7 +441,10 @@ __device__ __noinline__ void ieee_tile(const PassDesc& pd, const PassArgs& args,
   const bool last = q_out == nullptr;
   const double mul = kDec ? pow2d(-pd.K) : (last ? pow2d(args.out_pow2) * args.out_mul : 1.0);
   finish_tile<F64Arith, kDec, kCl>(pd, args, matp, raw, mul, base, nbase, smem, lane, warp);
-  if (!last && threadIdx.x == 0 && (!kCl || cluster_rank() == 0)) q_out[tile] = kQIeee;
+  if (!last && (!kCl || cluster_rank() == 0)) {
+    const long long ncls = 1ll << (pd.D - pd.K);
+    for (long long c = threadIdx.x; c < ncls; c += blockDim.x) q_out[(tile << (pd.D - pd.K)) + c] = (int16_t)kQIeee;
+  }
 }
 
 // The tile's elements in the stage-0 mapping from a shared-memory copy.
@@ -413,316 +459,328 @@ __device__ __forceinline__ void load_tile_smem(const PassDesc& pd, const unsigne
   for (int e = 0; e < kElems; ++e) raw[e] = b[t + reg_off(e, w0, w1, w2, w3)];
 }
 
-// Role of a fixed-point pass (kRoleIntIn / kRoleIntOut of tpd_launch.h), a
-// compile-time choice so that each kernel carries only its own conversions
-// (smaller code, fewer registers).
+// Flags of the next pass's tiles that receive a nonzero (zero skipping).
+template <class NonZero>
+__device__ __forceinline__ void flag_next(const PassDesc& pd, const PassArgs& args, int nbase, int lane, int warp,
+                                          NonZero nz_of) {
+  const Stage& sl = pd.st[pd.nstage - 1];
+  const int nt = nbase + thread_next(pd, sl, lane, warp);
+  const int n0 = pd.next_w[sl.reg[0]], n1 = pd.next_w[sl.reg[1]], n2 = pd.next_w[sl.reg[2]],
+            n3 = pd.next_w[sl.reg[3]];
+  bool lanes_inside = true;
+#pragma unroll
+  for (int i = 0; i < kLaneBits; ++i) lanes_inside &= (pd.next_w[sl.lane[i]] == 0);
+#pragma unroll
+  for (int e = 0; e < kElems; ++e) {
+    const bool nz = nz_of(e);
+    const int id = nt + reg_off(e, n0, n1, n2, n3);
+    if (lanes_inside) {
+      if (__any_sync(kFull, nz) && lane == 0) args.flags_out[id] = 1;
+    } else if (nz) {
+      args.flags_out[id] = 1;
+    }
+  }
+}
 
-// xbuf: shared-memory exchange area (2^D x 16 bytes); red: 64 ints;
-// inbuf: the tile already copied to shared memory (stage-0 positions), or
-// nullptr to read it from global memory.
+// One complex128 tile of the block fixed point, in the role kRole (IEEE
+// numbers or int64 sums in, IEEE numbers or int64 sums out).
+// xbuf: exchange area (2^D x 16 bytes; a two-CTA cluster: half of it per
+// CTA); red: 64 ints; cls: 2^(D-K) class slots; inbuf: the tile already in
+// shared memory (stage-0 positions), or nullptr to read it from global memory.
+// sbase: the tile-id bits' part of the source-class index (kRoleIntIn).
 // kCl: one CTA of a two-CTA cluster (warp: the virtual warp, rank * 8 + the
-// CTA's own warp; red: this CTA's reduction slots).
+// CTA's own warp); each CTA keeps the class maxima of its own elements and
+// merges the peer's through distributed shared memory.
+//
+// Class slots: IEEE input, the class's largest exponent field E (binary point
+// q_in = max(E, 1) + K - 1084, where the largest lands below 2^(62-K));
+// int64 input, the largest source binary point + kQSlot (q_in = that point +
+// K: every element shifts right by at least K bits, toward zero, after which
+// the 2^K-term sums stay below 2^62), 0 for a class whose sources are all zero.
+constexpr int kQSlot = 4096;
+
 template <bool kDec, int kRole, bool kCg = false, bool kCl = false>
-__device__ __forceinline__ void fixed_tile(const PassDesc& pd, const PassArgs& args, void* matp, const int* q_in,
-                                           int* q_out, long long tile, long long base, long long pbase, int nbase,
-                                           const unsigned char* inbuf, unsigned char* xbuf, int* red, int lane,
-                                           int warp) {
+__device__ __forceinline__ void fixed_tile(const PassDesc& pd, const PassArgs& args, void* matp, const int16_t* q_in,
+                                           int16_t* q_out, long long tile, long long base, uint32_t sbase,
+                                           int nbase, const unsigned char* inbuf, unsigned char* xbuf, int* red,
+                                           int* cls, int lane, int warp) {
   using V = FixedArith::V;
-  const int nwarps = 1 << (pd.D - kMinTileBits - (kCl ? 1 : 0));   // this CTA's warps
-  const int lwarp = kCl ? (warp & 7) : warp;
-  unsigned char* smem = xbuf;
+  constexpr bool kIntIn = (kRole & kRoleIntIn) != 0;
+  constexpr bool kIntOut = (kRole & kRoleIntOut) != 0;
+  const int nthr = blockDim.x, nwarps = nthr >> 5, lwarp = threadIdx.x >> 5;
+  const int ncls = 1 << (pd.D - pd.K);
+  for (int i = threadIdx.x; i < ncls; i += nthr) cls[i] = 0;
+  const Stage& s0 = pd.st[0];
+  const int ct = cls_thread(pd, s0, lane, warp);
+  const int c0 = pd.cls_w[s0.reg[0]], c1 = pd.cls_w[s0.reg[1]], c2 = pd.cls_w[s0.reg[2]],
+            c3 = pd.cls_w[s0.reg[3]];
+  const int np = s0.npair;
   V v[kElems];
-  int qin;
-  if constexpr (!(kRole & kRoleIntIn)) {
-    // ---- first pass: IEEE doubles onto the tile's binary point
+  int tb;                                                // tile flags: 1 nonzero, 2 Inf / NaN
+  if constexpr (!kIntIn) {
+    // ---- IEEE doubles: class maxima of the exponent fields
     double2 raw[kElems];
     if (inbuf) load_tile_smem(pd, inbuf, lane, warp, raw);
     else load_tile<kCg>(pd, matp, base, lane, warp, raw);
     if constexpr (kCl) cluster_wait();                   // the peer CTA is running
-    uint32_t hmax = 0, nzw = 0;
-#pragma unroll
-    for (int e = 0; e < kElems; ++e) {
-      const uint32_t hx = (uint32_t)__double2hiint(raw[e].x) & 0x7fffffffu;
-      const uint32_t hy = (uint32_t)__double2hiint(raw[e].y) & 0x7fffffffu;
-      hmax = max(hmax, max(hx, hy));
-    }
+    __syncthreads();                                     // class slots cleared
+    const uint32_t hmax = class_max(pd, raw, cls, lane, warp, exp_f64);
+    uint32_t nzw = 0;
     if (args.skip_zero) {
 #pragma unroll
       for (int e = 0; e < kElems; ++e)
         nzw |= (uint32_t)__double2hiint(raw[e].x) << 1 | (uint32_t)__double2loint(raw[e].x) |
                (uint32_t)__double2hiint(raw[e].y) << 1 | (uint32_t)__double2loint(raw[e].y);
-      nzw = __reduce_or_sync(kFull, nzw);
     }
-    const uint32_t wmax = __reduce_max_sync(kFull, hmax >> 20);
-    int emax = 0, nz = 0;
+    tb = (__reduce_or_sync(kFull, nzw) != 0 ? 1 : 0) | (__any_sync(kFull, hmax == 2047) ? 2 : 0);
     if constexpr (kCl) {
-      // this CTA's warp maxima into its own slots 0..15 and the peer's 32..47
-      int* pred = peer_smem(red);
-      if (lane == 0) {
-        red[lwarp] = (int)wmax; red[16 + lwarp] = (int)nzw;
-        pred[32 + lwarp] = (int)wmax; pred[48 + lwarp] = (int)nzw;
-      }
-      cluster_sync();
-      for (int w = 0; w < nwarps; ++w) {
-        emax = max(emax, max(red[w], red[32 + w]));
-        nz |= red[16 + w] | red[48 + w];
-      }
+      if (lane == 0) { red[lwarp] = tb; peer_smem(red)[16 + lwarp] = tb; }
+      cluster_sync();                                    // both CTAs' atomics and flags are in
     } else {
-      if (lane == 0) { red[warp] = (int)wmax; red[16 + warp] = (int)nzw; }
+      if (lane == 0) red[lwarp] = tb;
       __syncthreads();
-      for (int w = 0; w < nwarps; ++w) { emax = max(emax, red[w]); nz |= red[16 + w]; }
     }
-    if (args.skip_zero && nz == 0) return;                // all +-0: outputs are zero already
-    if (emax == 2047) {                                   // Inf/NaN in the tile
-      ieee_tile<kDec, kCg, kCl>(pd, args, matp, nullptr, q_out, tile, base, pbase, nbase, smem, lane, warp);
-      return;
+    tb = 0;
+    for (int w = 0; w < nwarps; ++w) tb |= red[w] | (kCl ? red[16 + w] : 0);
+    if ((args.skip_zero && !(tb & 1)) || (tb & 2)) {
+      if (tb & 2) ieee_tile<kDec, kCg, kCl>(pd, args, matp, q_in, q_out, tile, base, sbase, nbase, xbuf, lane, warp);
+      return;                                            // (else all +-0: the outputs are zero already)
     }
-    // x * 2^S with S = 1084 - K - emax_eff puts the largest element below 2^(62-K)
-    const int emax_eff = max(emax, 1);
-    const int shift_base = 9 - pd.K - emax_eff;
+    if constexpr (kCl) {
+      const int* pcls = peer_smem(cls);
+      for (int i = threadIdx.x; i < ncls; i += nthr) cls[i] = max(cls[i], pcls[i]);
+      cluster_sync();                                    // both CTAs are done with the peer's slots
+    }
+    // onto the classes' binary points: x * 2^S_c, S_c = 1084 - K - max(E_c, 1)
 #pragma unroll
     for (int e = 0; e < kElems; ++e) {
-      v[e].re = TPD_TO_FIXED_RE(raw[e].x, shift_base);
-      v[e].im = TPD_TO_FIXED_IM(raw[e].y, shift_base);
+      const int sb = 9 - pd.K - max(cls[ct ^ reg_cls(e, c0, c1, c2, c3)], 1);
+      v[e].re = FixedArith::to_fixed(raw[e].x, sb);
+      v[e].im = FixedArith::to_fixed(raw[e].y, sb);
     }
-    qin = emax_eff + pd.K - 1084;                          // = -S
   } else {
-    // ---- later pass: int64 sums with their previous tile's binary point
+    // ---- int64 sums of a previous pass, each with its source class's binary point
     longlong2 raw[kElems];
+    int qs[kElems];
     if (inbuf) load_tile_smem(pd, inbuf, lane, warp, raw);
     else load_tile<kCg>(pd, matp, base, lane, warp, raw);
-    if constexpr (kCl) cluster_wait();                   // the peer CTA is running
-    // The tile's elements come from 2^prev_nb previous tiles (<= 2^kMaxPrevBits):
-    // their binary points are loaded once each into shared memory (qs), and
-    // each element finds its own there by its combination index.
-    const Stage& s0 = pd.st[0];
-    int* qs = red + 64;
-    int qmax = kQValidMin, ieee = 0;
     {
-      // (each CTA of a cluster gathers all of them: both see the same maximum)
-      const int nq = 1 << pd.prev_nb, nthr = 32 * nwarps;
-      for (int j = lane + 32 * lwarp; j < nq; j += nthr) {
-        long long idx = pbase;
-        for (int k = 0; k < pd.prev_nb; ++k)
-          if ((j >> k) & 1) idx += pd.prev_cw[k];
-        const int q = ld_in<kCg>(q_in + idx);
-        qs[j] = q;
-        qmax = max(qmax, q);
-        ieee |= (q == kQIeee);
-      }
-    }
-    int qj = 0;
+      const uint32_t sb = sbase ^ src_thread(pd, s0, lane, warp);
+      const uint32_t w0 = pd.src_w[s0.reg[0]], w1 = pd.src_w[s0.reg[1]], w2 = pd.src_w[s0.reg[2]],
+                     w3 = pd.src_w[s0.reg[3]];
 #pragma unroll
-    for (int i = 0; i < kLaneBits; ++i)
-      if ((lane >> i) & 1) qj += pd.prev_qw[s0.lane[i]];
-    for (int i = 0; i < pd.D - kMinTileBits; ++i)
-      if ((warp >> i) & 1) qj += pd.prev_qw[s0.warp[i]];
-    const int j0 = pd.prev_qw[s0.reg[0]], j1 = pd.prev_qw[s0.reg[1]], j2 = pd.prev_qw[s0.reg[2]],
-              j3 = pd.prev_qw[s0.reg[3]];
-    // kQIeee sits below kQValidMin, so it never wins the max
-    qmax = __reduce_max_sync(kFull, qmax);
-    ieee = __reduce_or_sync(kFull, ieee);
-    if (lane == 0) { red[lwarp] = qmax; red[16 + lwarp] = ieee; }
-    __syncthreads();
-    qmax = kQValidMin; ieee = 0;
-    for (int w = 0; w < nwarps; ++w) { qmax = max(qmax, red[w]); ieee |= red[16 + w]; }
-    if (ieee) {
-      ieee_tile<kDec, kCg, kCl>(pd, args, matp, q_in, q_out, tile, base, pbase, nbase, smem, lane, warp);
-      return;
+      for (int e = 0; e < kElems; ++e) qs[e] = ld_in<kCg>(q_in + (sb ^ reg_src(e, w0, w1, w2, w3)));
     }
-    if (qmax == kQValidMin) {                              // every source tile was zero
-      if (args.skip_zero) return;
-      qmax = 0;
-    }
-    qin = qmax + pd.K;
+    if constexpr (kCl) cluster_wait();                   // the peer CTA is running
+    __syncthreads();                                     // class slots cleared
+    int any_valid = 0, any_ieee = 0;
 #pragma unroll
     for (int e = 0; e < kElems; ++e) {
-      const int q = qs[qj + reg_off(e, j0, j1, j2, j3)];   // written before the barrier above
+      any_valid |= q_is_valid(qs[e]);
+      any_ieee |= qs[e] == kQIeee;
+    }
+#pragma unroll
+    for (int e = 0; e < kElems; ++e) {
+      if (np >= 1 && (e & 2)) continue;
+      if (np >= 2 && (e & 8)) continue;
+      auto slot = [&](int k) { return q_is_valid(qs[k]) ? qs[k] + kQSlot : 0; };
+      int m = slot(e);
+      if (np >= 1) m = max(m, slot(e ^ 3));
+      if (np >= 2) m = max(m, max(slot(e ^ 12), slot(e ^ 15)));
+      if (m) atomicMax(cls + (ct ^ reg_cls(e, c0, c1, c2, c3)), m);
+    }
+    tb = (__any_sync(kFull, any_valid) ? 1 : 0) | (__any_sync(kFull, any_ieee) ? 2 : 0);
+    if constexpr (kCl) {
+      if (lane == 0) { red[lwarp] = tb; peer_smem(red)[16 + lwarp] = tb; }
+      cluster_sync();
+    } else {
+      if (lane == 0) red[lwarp] = tb;
+      __syncthreads();
+    }
+    tb = 0;
+    for (int w = 0; w < nwarps; ++w) tb |= red[w] | (kCl ? red[16 + w] : 0);
+    if (tb & 2) {
+      ieee_tile<kDec, kCg, kCl>(pd, args, matp, q_in, q_out, tile, base, sbase, nbase, xbuf, lane, warp);
+      return;
+    }
+    if (args.skip_zero && !(tb & 1)) return;             // every source class was zero
+    if constexpr (kCl) {
+      const int* pcls = peer_smem(cls);
+      for (int i = threadIdx.x; i < ncls; i += nthr) cls[i] = max(cls[i], pcls[i]);
+      cluster_sync();
+    }
+    // realign onto q_in_c = (largest source point) + K, toward zero
+#pragma unroll
+    for (int e = 0; e < kElems; ++e) {
+      const int q = qs[e];
       if (q_is_valid(q)) {
-        const unsigned sh = (unsigned)(qin - q);
-        v[e].re = TPD_ALIGN(raw[e].x, sh);
-        v[e].im = TPD_ALIGN(raw[e].y, sh);
+        const unsigned sh = (unsigned)(cls[ct ^ reg_cls(e, c0, c1, c2, c3)] - kQSlot + pd.K - q);
+        v[e].re = shr_tz(raw[e].x, sh);
+        v[e].im = shr_tz(raw[e].y, sh);
       } else {
         v[e].re = 0; v[e].im = 0;
       }
     }
   }
+  // binary point of class c: q_in_c; the outputs hold q_in_c - K (decomposition:
+  // the 1/2 of Eq. 4 per level) or q_in_c (composition)
+  auto q_of_slot = [&](int slot) {
+    if constexpr (kIntIn) return slot - kQSlot + pd.K;
+    else return max(slot, 1) + pd.K - 1084;
+  };
+  if constexpr (kIntOut) {
+    if (!kCl || cluster_rank() == 0) {
+      int16_t* qo = q_out + (tile << (pd.D - pd.K));
+      for (int c = threadIdx.x; c < ncls; c += nthr) {
+        const int slot = cls[c];
+        qo[c] = (int16_t)((kIntIn && slot == 0) ? kQValidMin : q_of_slot(slot) - (kDec ? pd.K : 0));
+      }
+    }
+  }
 
-  // ---- the pass's levels
-  V* sm = reinterpret_cast<V*>(smem);
+  // ---- the pass's levels, exact
+  V* sm = reinterpret_cast<V*>(xbuf);
   for (int s = 0; s < pd.nstage; ++s) {
     if (s > 0) exchange<kCl>(v, pd, pd.st[s - 1], pd.st[s], sm, lane, warp, s > 1);
     stage_levels<FixedArith, kDec>(v, pd.st[s], lane);
   }
-  const int qout = qin - (kDec ? pd.K : 0);                // the 1/2 of Eq. 4 per level
 
-  // ---- store in place
+  // ---- store in place: int64 sums, or rounded once
   const Stage& sl = pd.st[pd.nstage - 1];
   const uint32_t g = (uint32_t)base + (uint32_t)thread_goff(pd, sl, lane, warp);
   const uint32_t w0 = 1u << pd.gbit[sl.reg[0]], w1 = 1u << pd.gbit[sl.reg[1]];
   const uint32_t w2 = 1u << pd.gbit[sl.reg[2]], w3 = 1u << pd.gbit[sl.reg[3]];
-  const bool flags = args.flags_out != nullptr;
-  int nt = 0, n0 = 0, n1 = 0, n2 = 0, n3 = 0;
-  bool lanes_inside = true;
-  if (flags) {
-    nt = nbase + thread_next(pd, sl, lane, warp);
-    n0 = pd.next_w[sl.reg[0]]; n1 = pd.next_w[sl.reg[1]];
-    n2 = pd.next_w[sl.reg[2]]; n3 = pd.next_w[sl.reg[3]];
-#pragma unroll
-    for (int i = 0; i < kLaneBits; ++i) lanes_inside &= (pd.next_w[sl.lane[i]] == 0);
-  }
-  if constexpr ((kRole & kRoleIntOut) != 0) {
+  if constexpr (kIntOut) {
     longlong2* mat = reinterpret_cast<longlong2*>(matp);
 #pragma unroll
     for (int e = 0; e < kElems; ++e) mat[g + reg_off(e, w0, w1, w2, w3)] = make_longlong2(v[e].re, v[e].im);
-    if (threadIdx.x == 0 && (!kCl || cluster_rank() == 0)) q_out[tile] = qout;
   } else {
+    // value = sum * 2^q_out_c * 2^out_pow2 (a composition's scale)
+    const int cl = cls_thread(pd, sl, lane, warp);
+    const int l0 = pd.cls_w[sl.reg[0]], l1 = pd.cls_w[sl.reg[1]], l2 = pd.cls_w[sl.reg[2]],
+              l3 = pd.cls_w[sl.reg[3]];
+    const bool resid = args.out_mul != 1.0;              // non-power-of-two composition scale (rare)
     double2* mat = reinterpret_cast<double2*>(matp);
-    const int T = -(qout + args.out_pow2);
-    const bool resid = args.out_mul != 1.0;                // non-power-of-two composition scale (rare)
-    if (FixedArith::fast_range(T) && !resid) {             // the whole tile rounds in the normal range
-      // real parts through the fp64 conversion unit, imaginary parts through
-      // integer instructions (identical roundings): the two pipes share the
-      // conversions (measured on GB300: n = 14 last pass 1.82 -> 1.67 ms;
-      // all of them on either pipe is slower)
-#pragma unroll
-      for (int e = 0; e < kElems; ++e)
-        mat[g + reg_off(e, w0, w1, w2, w3)] =
-            make_double2(FixedArith::to_double_cvt_fast(v[e].re, T), FixedArith::to_double_fast(v[e].im, T));
-    } else {
-#pragma unroll
-      for (int e = 0; e < kElems; ++e) {
-        double2 o;
-        o.x = TPD_TO_DOUBLE_RE(v[e].re, T);
-        o.y = TPD_TO_DOUBLE_IM(v[e].im, T);
-        if (resid) { o.x *= args.out_mul; o.y *= args.out_mul; }
-        mat[g + reg_off(e, w0, w1, w2, w3)] = o;
-      }
-    }
-  }
-  if (flags) {
 #pragma unroll
     for (int e = 0; e < kElems; ++e) {
-      const bool nz = (v[e].re | v[e].im) != 0;
-      const int id = nt + reg_off(e, n0, n1, n2, n3);
-      if (lanes_inside) {
-        if (__any_sync(kFull, nz) && lane == 0) args.flags_out[id] = 1;
-      } else if (nz) {
-        args.flags_out[id] = 1;
+      const int T = -(q_of_slot(cls[cl ^ reg_cls(e, l0, l1, l2, l3)]) - (kDec ? pd.K : 0) + args.out_pow2);
+      double2 o;
+      if (!resid && (FixedArith::fast_range(T) || (v[e].re | v[e].im) == 0)) {
+        // real parts through the fp64 conversion unit, imaginary parts through
+        // integer instructions (identical roundings): the two pipes share the
+        // conversions
+        o = make_double2(FixedArith::to_double_cvt_fast(v[e].re, T), FixedArith::to_double_fast(v[e].im, T));
+      } else {
+        o = FixedArith::to_double2_rare(v[e].re, v[e].im, T, args.out_mul);
       }
+      mat[g + reg_off(e, w0, w1, w2, w3)] = o;
     }
   }
+  if (args.flags_out != nullptr) flag_next(pd, args, nbase, lane, warp, [&](int e) { return (v[e].re | v[e].im) != 0; });
 }
 
-// ============================================================== fixed point, float storage
-//
-// Every pass of the complex64 fixed-point form reads floats, sums the tile's
-// K levels exactly in int64 on the tile's own binary point, and rounds the
-// results to float (RNE) as it stores: one rounding per pass, nothing handed
-// between passes but the floats.  Tiles meeting an Inf or NaN run the IEEE
+// One complex64 tile of the block fixed point: class c on the binary point
+// S_c = 188 - K - max(E_c, 1) (E_c its largest float exponent field): x * 2^S_c
+// is exact for components within 2^(38-K) of the class's largest, the
+// largest lands below 2^(62-K), the sums are exact in int64, and every output
+// is rounded to float once (RNE).  Tiles meeting an Inf or NaN run the IEEE
 // float butterfly instead.
 template <bool kDec, bool kCg>
 __device__ __forceinline__ void fixed32_tile(const PassDesc& pd, const PassArgs& args, void* matp, long long base,
-                                             int nbase, unsigned char* smem, int* red, int lane, int warp) {
+                                             int nbase, unsigned char* smem, int* red, int* cls, int lane, int warp) {
   using V = Fixed32Arith::V;
-  const int nwarps = 1 << (pd.D - kMinTileBits);
+  const int nthr = blockDim.x, nwarps = nthr >> 5;
+  const int ncls = 1 << (pd.D - pd.K);
+  for (int i = threadIdx.x; i < ncls; i += nthr) cls[i] = 0;
   float2 raw[kElems];
   load_tile<kCg>(pd, matp, base, lane, warp, raw);
-  uint32_t hmax = 0, nzw = 0;
+  __syncthreads();                                       // class slots cleared
+  const uint32_t hmax = class_max(pd, raw, cls, lane, warp, exp_f32);
+  uint32_t nzw = 0;
+  if (args.skip_zero) {
 #pragma unroll
-  for (int e = 0; e < kElems; ++e) {
-    const uint32_t hx = __float_as_uint(raw[e].x) & 0x7fffffffu, hy = __float_as_uint(raw[e].y) & 0x7fffffffu;
-    hmax = max(hmax, max(hx, hy));
-    nzw |= hx | hy;
+    for (int e = 0; e < kElems; ++e) nzw |= (__float_as_uint(raw[e].x) | __float_as_uint(raw[e].y)) << 1;
   }
-  const uint32_t wmax = __reduce_max_sync(kFull, hmax >> 23);
-  nzw = __reduce_or_sync(kFull, nzw);
-  if (lane == 0) { red[warp] = (int)wmax; red[16 + warp] = (int)nzw; }
+  const int tb = (__reduce_or_sync(kFull, nzw) != 0 ? 1 : 0) | (__any_sync(kFull, hmax == 255) ? 2 : 0);
+  if (lane == 0) red[warp] = tb;
   __syncthreads();
-  int emax = 0, nz = 0;
-  for (int w = 0; w < nwarps; ++w) { emax = max(emax, red[w]); nz |= red[16 + w]; }
-  if (args.skip_zero && nz == 0) return;                  // all +-0: outputs are zero already
-  if (emax == 255) {                                      // Inf/NaN in the tile
+  int t = 0;
+  for (int w = 0; w < nwarps; ++w) t |= red[w];
+  if (args.skip_zero && !(t & 1)) return;                // all +-0: the outputs are zero already
+  if (t & 2) {                                           // Inf/NaN in the tile
     finish_tile<F32Arith, kDec>(pd, args, matp, raw, kDec ? pow2d(-pd.K) : pow2d(args.out_pow2) * args.out_mul,
                                 base, nbase, smem, lane, warp);
     return;
   }
-  const int emax_eff = max(emax, 1);
-  const int rs_base = emax_eff + pd.K;
   V v[kElems];
+  {
+    const Stage& s0 = pd.st[0];
+    const int ct = cls_thread(pd, s0, lane, warp);
+    const int c0 = pd.cls_w[s0.reg[0]], c1 = pd.cls_w[s0.reg[1]], c2 = pd.cls_w[s0.reg[2]],
+              c3 = pd.cls_w[s0.reg[3]];
 #pragma unroll
-  for (int e = 0; e < kElems; ++e) {
-    v[e].re = Fixed32Arith::to_fixed(raw[e].x, rs_base);
-    v[e].im = Fixed32Arith::to_fixed(raw[e].y, rs_base);
+    for (int e = 0; e < kElems; ++e) {
+      const int rs_base = max(cls[ct ^ reg_cls(e, c0, c1, c2, c3)], 1) + pd.K;
+      v[e].re = Fixed32Arith::to_fixed(raw[e].x, rs_base);
+      v[e].im = Fixed32Arith::to_fixed(raw[e].y, rs_base);
+    }
   }
   V* sm = reinterpret_cast<V*>(smem);
   for (int s = 0; s < pd.nstage; ++s) {
     if (s > 0) exchange(v, pd, pd.st[s - 1], pd.st[s], sm, lane, warp, s > 1);
     stage_levels<Fixed32Arith, kDec>(v, pd.st[s], lane);
   }
-  // value = sum * 2^-S (S = 188 - K - emax_eff), times 2^-K for the 1/2 of
-  // Eq. 4 per level, times 2^out_pow2 for a composition's scale
-  const int T = 188 - pd.K - emax_eff + (kDec ? pd.K : 0) - args.out_pow2;
+  // value = sum * 2^-S_c, times 2^-K for the 1/2 of Eq. 4 per level, times
+  // 2^out_pow2 for a composition's scale
+  const int tbase = 188 - pd.K + (kDec ? pd.K : 0) - args.out_pow2;
   const bool resid = args.out_mul != 1.0;
-  const bool fast = Fixed32Arith::fast_range(T);
   const Stage& sl = pd.st[pd.nstage - 1];
   float2* mat = reinterpret_cast<float2*>(matp);
   const uint32_t g = (uint32_t)base + (uint32_t)thread_goff(pd, sl, lane, warp);
   const uint32_t w0 = 1u << pd.gbit[sl.reg[0]], w1 = 1u << pd.gbit[sl.reg[1]];
   const uint32_t w2 = 1u << pd.gbit[sl.reg[2]], w3 = 1u << pd.gbit[sl.reg[3]];
-  const bool flags = args.flags_out != nullptr;
-  int nt = 0, n0 = 0, n1 = 0, n2 = 0, n3 = 0;
-  bool lanes_inside = true;
-  if (flags) {
-    nt = nbase + thread_next(pd, sl, lane, warp);
-    n0 = pd.next_w[sl.reg[0]]; n1 = pd.next_w[sl.reg[1]];
-    n2 = pd.next_w[sl.reg[2]]; n3 = pd.next_w[sl.reg[3]];
-#pragma unroll
-    for (int i = 0; i < kLaneBits; ++i) lanes_inside &= (pd.next_w[sl.lane[i]] == 0);
-  }
+  const int cl = cls_thread(pd, sl, lane, warp);
+  const int l0 = pd.cls_w[sl.reg[0]], l1 = pd.cls_w[sl.reg[1]], l2 = pd.cls_w[sl.reg[2]], l3 = pd.cls_w[sl.reg[3]];
 #pragma unroll
   for (int e = 0; e < kElems; ++e) {
+    const int T = tbase - max(cls[cl ^ reg_cls(e, l0, l1, l2, l3)], 1);
     // real parts on the conversion unit, imaginary parts with integer
-    // instructions (identical roundings; n = 15: 31.3 -> 28.3 ms)
+    // instructions (identical roundings)
+    const bool fast = Fixed32Arith::fast_range(T) || v[e].re == 0;
     float2 o = make_float2(fast ? Fixed32Arith::to_float_cvt_fast(v[e].re, T) : Fixed32Arith::to_float(v[e].re, T),
                            Fixed32Arith::to_float(v[e].im, T));
     if (resid) { o.x = __fmul_rn(o.x, (float)args.out_mul); o.y = __fmul_rn(o.y, (float)args.out_mul); }
     mat[g + reg_off(e, w0, w1, w2, w3)] = o;
-    if (flags) {
-      const bool nzo = (v[e].re | v[e].im) != 0;
-      const int id = nt + reg_off(e, n0, n1, n2, n3);
-      if (lanes_inside) {
-        if (__any_sync(kFull, nzo) && lane == 0) args.flags_out[id] = 1;
-      } else if (nzo) {
-        args.flags_out[id] = 1;
-      }
-    }
   }
+  if (args.flags_out != nullptr) flag_next(pd, args, nbase, lane, warp, [&](int e) { return (v[e].re | v[e].im) != 0; });
 }
 
 // One tile of a pass: its position from the tile id, then the arithmetic's
 // load / levels / store.  smem: the exchange area (2^D x 16 bytes; half of it
-// per CTA of a two-CTA cluster) followed by 64 ints of reduction slots.
+// per CTA of a two-CTA cluster), 64 ints of reduction slots, then (block fixed
+// point) 2^(D-K) class slots.
 template <class A, bool kDec, int kRole, bool kCg, bool kCl = false>
-__device__ __forceinline__ void pass_tile(const PassDesc& pd, const PassArgs& args, void* matp, const int* q_in,
-                                          int* q_out, long long tile, unsigned char* smem, int lane, int warp) {
+__device__ __forceinline__ void pass_tile(const PassDesc& pd, const PassArgs& args, void* matp, const int16_t* q_in,
+                                          int16_t* q_out, long long tile, unsigned char* smem, int lane, int warp) {
   using Store = typename A::Store;
   static_assert(!(kCl && A::kFixed32), "two-CTA clusters serve complex128 tiles only");
   int* red = reinterpret_cast<int*>(smem + ((size_t)16 << (pd.D - (kCl ? 1 : 0))));
-  long long base = 0, pbase = 0;
+  int* cls = red + 64;
+  long long base = 0;
   int nbase = 0;
+  uint32_t sbase = 0;
   for (int j = 0; j < pd.nrest; ++j)
     if ((tile >> j) & 1) {
       base += 1ll << pd.rest_gbit[j];
       nbase += (int)pd.next_rest_w[j];
-      pbase += pd.prev_rest_w[j];
+      sbase ^= pd.src_rest_w[j];
     }
 
   if constexpr (A::kFixed) {
-    fixed_tile<kDec, kRole, kCg, kCl>(pd, args, matp, q_in, q_out, tile, base, pbase, nbase, nullptr, smem, red,
-                                      lane, warp);
+    fixed_tile<kDec, kRole, kCg, kCl>(pd, args, matp, q_in, q_out, tile, base, sbase, nbase, nullptr, smem, red,
+                                      cls, lane, warp);
   } else if constexpr (A::kFixed32) {
-    fixed32_tile<kDec, kCg>(pd, args, matp, base, nbase, smem, red, lane, warp);
+    fixed32_tile<kDec, kCg>(pd, args, matp, base, nbase, smem, red, cls, lane, warp);
   } else {
     Store raw[kElems];
     load_tile<kCg>(pd, matp, base, lane, warp, raw);
@@ -746,8 +804,7 @@ __device__ __forceinline__ void pass_tile(const PassDesc& pd, const PassArgs& ar
 // Tiles of up to 2^12 elements run 256-thread CTAs, several per SM; 2^13
 // element tiles run 512-thread CTAs.
 // kMinBlocks: CTAs of kThreads the compiler must fit on one SM (register
-// budget); the planner picks 3 for the conversion-heavy first and last
-// fixed-point passes and 2 elsewhere.  kRole: fixed point only (see above).
+// budget); the planner picks it per pass.
 template <class A, bool kDec, int kThreads, int kMinBlocks, int kRole = 0>
 __global__ void __launch_bounds__(kThreads, kMinBlocks)
     k_pass(const __grid_constant__ PassDesc pd, const __grid_constant__ PassArgs args) {
@@ -755,8 +812,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   long long tile = (long long)blockIdx.x + (long long)blockIdx.y * gridDim.x;
   void* matp = args.mat;
-  const int* q_in = args.q_in;
-  int* q_out = args.q_out;
+  const int16_t* q_in = args.q_in;
+  int16_t* q_out = args.q_out;
   if (args.chunked) {                      // one L2-sized chunk of the matrix: spread the CTA index
     unsigned long long t = args.chunk_or;
     for (int k = 0; k < args.nfree; ++k)
@@ -788,8 +845,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 2)
   const int warp = (int)(cluster_rank() << 3) | (tid >> 5);   // the 512-thread layout's warp
   long long tile = (long long)(blockIdx.x >> 1);
   void* matp = args.mat;
-  const int* q_in = args.q_in;
-  int* q_out = args.q_out;
+  const int16_t* q_in = args.q_in;
+  int16_t* q_out = args.q_out;
   if (args.chunked) {
     unsigned long long t = args.chunk_or;
     for (int k = 0; k < args.nfree; ++k)
@@ -861,6 +918,7 @@ __global__ void __launch_bounds__(256, 1)
   unsigned char* buf0 = smem;
   unsigned char* buf1 = smem + tb;
   int* red = reinterpret_cast<int*>(smem + 2 * tb);
+  int* cls = red + 64;
   long long tile = blockIdx.x;
   if (tile >= pd.ntiles) return;
   prefetch_tile(pd, args.mat, tile, buf0, lane, warp);
@@ -876,15 +934,16 @@ __global__ void __launch_bounds__(256, 1)
       cp_async_wait<0>();
     }
     __syncthreads();                      // ... and everyone's
-    long long base = 0, pbase = 0;
+    long long base = 0;
     int nbase = 0;
+    uint32_t sbase = 0;
     for (int j = 0; j < pd.nrest; ++j)
       if ((tile >> j) & 1) {
         base += 1ll << pd.rest_gbit[j];
         nbase += (int)pd.next_rest_w[j];
-        pbase += pd.prev_rest_w[j];
+        sbase ^= pd.src_rest_w[j];
       }
-    fixed_tile<kDec, kRole>(pd, args, args.mat, args.q_in, args.q_out, tile, base, pbase, nbase, cur, cur, red,
+    fixed_tile<kDec, kRole>(pd, args, args.mat, args.q_in, args.q_out, tile, base, sbase, nbase, cur, cur, red, cls,
                             lane, warp);
     __syncthreads();                      // the current buffer is refilled next iteration
   }
@@ -925,26 +984,23 @@ __device__ __forceinline__ void small_levels(typename A::V* sm, int n, int tid, 
   }
 }
 
+// All n levels of a whole matrix in shared memory.  Block fixed point: the
+// element (r, c) belongs to the class r xor c (its X-mask: every level keeps
+// it), and cls[x] holds that class's largest exponent field.
 template <class A, bool kDec>
-__device__ __forceinline__ void small_run(typename A::Store* mat, int n, int skip, int scale_mode,
-                                          unsigned char* smem, int tid, int nthr, int emax_in) {
+__device__ __forceinline__ void small_run(typename A::Store* mat, int n, int scale_mode, unsigned char* smem,
+                                          const int* cls, int tid, int nthr) {
   using V = typename A::V;
   V* sm = reinterpret_cast<V*>(smem);
-  const int count = 1 << (2 * n);
-  int shift_base = 0, outT = 0;
-  if constexpr (A::kFixed) {
-    const int emax_eff = max(emax_in, 1);
-    shift_base = 9 - n - emax_eff;
-    // fixed = x * 2^S with headroom for n levels; the output is sum * 2^-S,
-    // times 2^-n for the decomposition (the 1/2 of Eq. 4 per level) or for a
-    // composition scaled to the adjoint.
-    const int S = 1084 - n - emax_eff;
-    outT = (kDec || scale_mode) ? S + n : S;
-  }
+  const int count = 1 << (2 * n), cmask = (1 << n) - 1;
   for (int i = tid; i < count; i += nthr) {
     const typename A::Store x = mat[i];
     if constexpr (A::kFixed) {
-      V t; t.re = A::to_fixed(x.x, shift_base); t.im = A::to_fixed(x.y, shift_base);
+      // x * 2^S with S = 1084 - n - E: headroom for the 2^n-term sums of n levels
+      const int sb = 9 - n - max(cls[(i >> n) ^ (i & cmask)], 1);
+      V t;
+      t.re = A::to_fixed(x.x, sb);
+      t.im = A::to_fixed(x.y, sb);
       sm[i] = t;
     } else {
       sm[i] = A::load(x);
@@ -956,8 +1012,12 @@ __device__ __forceinline__ void small_run(typename A::Store* mat, int n, int ski
   for (int i = tid; i < count; i += nthr) {
     typename A::Store o;
     if constexpr (A::kFixed) {
-      o.x = A::to_double(sm[i].re, outT);
-      o.y = A::to_double(sm[i].im, outT);
+      // the output is sum * 2^-S, times 2^-n for the decomposition (the 1/2
+      // of Eq. 4 per level) or for a composition scaled to the adjoint
+      const int S = 1084 - n - max(cls[(i >> n) ^ (i & cmask)], 1);
+      const int T = (kDec || scale_mode) ? S + n : S;
+      o.x = A::to_double(sm[i].re, T);
+      o.y = A::to_double(sm[i].im, T);
     } else {
       o = A::store(sm[i], OutScale{0, 1.0}, mul);
     }
@@ -966,46 +1026,51 @@ __device__ __forceinline__ void small_run(typename A::Store* mat, int n, int ski
 }
 
 // A whole matrix of n <= 6 qubits by the CTA's nthr threads (all of them call
-// it): max exponent / nonzero test, then small_run (IEEE fallback for Inf/NaN).
+// it): nonzero test (and, block fixed point, the class maxima and the IEEE
+// fallback for Inf/NaN), then small_run.  smem: 4^n elements of A::V, then
+// (block fixed point) 2^n class slots.
 template <class A, bool kDec>
 __device__ __forceinline__ void small_matrix(typename A::Store* mat, int n, int skip_zero, int scale_mode,
                                              unsigned char* smem, int tid, int nthr) {
   using Store = typename A::Store;
   const int count = 1 << (2 * n);
-  // max exponent / nonzero over the whole matrix
-  uint32_t emax = 0, nzw = 0;
-  for (int i = tid; i < count; i += nthr) {
-    const Store x = mat[i];
-    uint32_t hx, hy, lx, ly;
-    if constexpr (sizeof(Store) == 16) {
-      hx = (uint32_t)__double2hiint(((const double2&)x).x) & 0x7fffffffu;
-      hy = (uint32_t)__double2hiint(((const double2&)x).y) & 0x7fffffffu;
-      lx = (uint32_t)__double2loint(((const double2&)x).x);
-      ly = (uint32_t)__double2loint(((const double2&)x).y);
-      emax = max(emax, max(hx >> 20, hy >> 20));
-    } else {
-      hx = __float_as_uint(((const float2&)x).x) & 0x7fffffffu;
-      hy = __float_as_uint(((const float2&)x).y) & 0x7fffffffu;
-      lx = ly = 0;
-    }
-    nzw |= hx | hy | lx | ly;
-  }
-  const int nz = __syncthreads_or((int)(nzw != 0));
-  if (skip_zero && !nz) return;
-  uint32_t* red = reinterpret_cast<uint32_t*>(smem);
-  emax = __reduce_max_sync(kFull, emax);
-  if ((tid & 31) == 0) red[tid >> 5] = emax;
-  __syncthreads();
-  uint32_t em = 0;
-  for (int w = 0; w < (nthr + 31) / 32; ++w) em = max(em, red[w]);
-  __syncthreads();
   if constexpr (A::kFixed) {
-    if (em == 2047) {
-      small_run<F64Arith, kDec>(mat, n, skip_zero, scale_mode, smem, tid, nthr, 0);
+    int* cls = reinterpret_cast<int*>(smem + ((size_t)16 << (2 * n)));
+    const int cmask = (1 << n) - 1;
+    for (int i = tid; i <= cmask; i += nthr) cls[i] = 0;
+    __syncthreads();
+    uint32_t hmax = 0, nzw = 0;
+    for (int i = tid; i < count; i += nthr) {
+      const double2 x = mat[i];
+      const uint32_t ex = exp_f64(x);
+      hmax = max(hmax, ex);
+      nzw |= (uint32_t)__double2hiint(x.x) << 1 | (uint32_t)__double2loint(x.x) |
+             (uint32_t)__double2hiint(x.y) << 1 | (uint32_t)__double2loint(x.y);
+      if (ex) atomicMax(cls + ((i >> n) ^ (i & cmask)), (int)ex);
+    }
+    const int nz = __syncthreads_or(nzw != 0);
+    const int inf = __syncthreads_or(hmax == 2047);
+    if (skip_zero && !nz) return;
+    if (inf) {
+      small_run<F64Arith, kDec>(mat, n, scale_mode, smem, nullptr, tid, nthr);
       return;
     }
+    small_run<A, kDec>(mat, n, scale_mode, smem, cls, tid, nthr);
+  } else {
+    uint32_t nzw = 0;
+    for (int i = tid; i < count; i += nthr) {
+      const Store x = mat[i];
+      if constexpr (sizeof(Store) == 16) {
+        nzw |= (uint32_t)__double2hiint(((const double2&)x).x) << 1 | (uint32_t)__double2loint(((const double2&)x).x) |
+               (uint32_t)__double2hiint(((const double2&)x).y) << 1 | (uint32_t)__double2loint(((const double2&)x).y);
+      } else {
+        nzw |= (__float_as_uint(((const float2&)x).x) | __float_as_uint(((const float2&)x).y)) << 1;
+      }
+    }
+    const int nz = __syncthreads_or(nzw != 0);
+    if (skip_zero && !nz) return;
+    small_run<A, kDec>(mat, n, scale_mode, smem, nullptr, tid, nthr);
   }
-  small_run<A, kDec>(mat, n, skip_zero, scale_mode, smem, tid, nthr, (int)em);
 }
 
 template <class A, bool kDec>

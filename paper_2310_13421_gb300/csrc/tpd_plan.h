@@ -66,26 +66,28 @@ struct PassDesc {
   int32_t has_next;
   int32_t next_w[kMaxTileBits];
   int64_t next_rest_w[2 * kMaxQubits];
-  // Fixed point between passes: an element's tile id in the PREVIOUS pass
-  // (whose per-tile binary point it was stored with), by the same linear rule.
   int32_t min_blocks;        // CTAs per SM the pass kernel is compiled for (2 or 3); D = 13: 1 = one
                              // CTA of 512 threads, 2 = a two-CTA cluster of 256 (complex128)
+  // Block fixed point: the *class* of a tile position.  A pass only ever adds
+  // elements that agree on every passenger bit and on x_j = r_j xor c_j of
+  // each of its levels j (Eq. 4 adds a00 to a11 and a01 to a10, and both
+  // outputs keep the quad's x), so each class -- 2^K elements -- is summed
+  // on its own binary point.  The class index is linear (XOR) in the tile
+  // bits: cls_w[i] is the class bit of tile bit i, a level's column and row
+  // bit sharing one; the column-type bits take class bits in ascending tile
+  // order, so the lowest tile bits (stage 0's lanes) get the lowest class
+  // bits.  2^(D-K) classes per tile.
+  int32_t cls_w[kMaxTileBits];
+  // Block fixed point between passes: a pass that does not end the plan
+  // stores its int64 sums in place and one binary point per class, at index
+  // (tile id << (D - K)) | class in its binary-point array.  The index, in the
+  // PREVIOUS pass's array, of the class an element of this pass came from is
+  // linear (XOR) in the element's global bits: src_w[i] per tile bit i and
+  // src_rest_w[j] per tile-id bit j (below 2^31: 2n - K bits).
   int32_t has_prev;
-  int32_t prev_w[kMaxTileBits];
-  int64_t prev_rest_w[2 * kMaxQubits];
-  // The tile's elements come from 2^prev_nb previous tiles: those that differ
-  // in the prev_nb tile bits i with prev_w[i] != 0.  prev_qw[i] numbers these
-  // combinations (1 << rank of bit i among them, 0 for the other bits) and
-  // prev_cw[k] is the previous-tile id step of the k-th of them.
-  int32_t prev_nb;
-  int32_t prev_qw[kMaxTileBits];
-  int32_t prev_cw[kMaxTileBits];
+  uint32_t src_w[kMaxTileBits];
+  uint32_t src_rest_w[2 * kMaxQubits];
 };
-
-// Binary points of previous tiles gathered into shared memory by a pass that
-// reads int64 sums (prev_nb <= kMaxPrevBits; more falls back to per-element
-// loads from global memory).
-constexpr int kMaxPrevBits = 10;
 
 // A whole-matrix plan: one pass per group of levels.
 struct Plan {

@@ -141,6 +141,19 @@ bool build_pass(int n, int b, int K, int D, int lf, double cs, PassDesc* pd, std
     L.r = (int)(std::find(t.begin(), t.end(), n + b + j) - t.begin());
     c.lev.push_back(L);
   }
+  // class bits (see PassDesc::cls_w): column-type tile bits in ascending
+  // order, each level's row bit on its column's class bit
+  {
+    std::vector<int> pos(D, -1);
+    int next = 0;
+    for (int i = 0; i < D; ++i) {
+      bool row = false;
+      for (const Level& L : c.lev) row |= L.r == i;
+      if (!row) pos[i] = next++;
+    }
+    for (const Level& L : c.lev) pos[L.r] = pos[L.c];
+    for (int i = 0; i < D; ++i) pd->cls_w[i] = 1 << pos[i];
+  }
   c.cx = 2.0; c.cs = cs;
   int nst = 0;
   const double cost = search(c, 0, (1u << K) - 1, &nst);
@@ -198,29 +211,23 @@ void set_next(PassDesc* cur, const PassDesc& nxt) {
   for (int j = 0; j < cur->nrest; ++j) cur->next_rest_w[j] = w(cur->rest_gbit[j]);
 }
 
-// Tile id in the previous pass of an element of `cur`, as linear weights.
-// false if the tile's elements came from more than 2^kMaxPrevBits tiles.
-bool set_prev(PassDesc* cur, const PassDesc& prv) {
-  std::vector<int> rest_prev(prv.rest_gbit, prv.rest_gbit + prv.nrest);
-  auto w = [&](int g) -> long long {
-    auto it = std::find(rest_prev.begin(), rest_prev.end(), g);
-    if (it == rest_prev.end()) return 0;
-    return 1ll << (int)(it - rest_prev.begin());
+// Index, in the previous pass's binary-point array, of an element's class
+// there, as XOR weights of the current pass's tile and tile-id bits: a global
+// bit that is a tile-id bit j of the previous pass contributes bit
+// (D' - K') + j (the tile id above the class bits), one that is a tile bit i
+// there its class bit cls_w[i].
+void set_src(PassDesc* cur, const PassDesc& prv) {
+  const int ncls_bits = prv.D - prv.K;
+  auto w = [&](int g) -> uint32_t {
+    for (int j = 0; j < prv.nrest; ++j)
+      if (prv.rest_gbit[j] == g) return 1u << (ncls_bits + j);
+    for (int i = 0; i < prv.D; ++i)
+      if (prv.gbit[i] == g) return (uint32_t)prv.cls_w[i];
+    return 0u;
   };
   cur->has_prev = 1;
-  for (int i = 0; i < cur->D; ++i) cur->prev_w[i] = (int32_t)w(cur->gbit[i]);
-  for (int j = 0; j < cur->nrest; ++j) cur->prev_rest_w[j] = w(cur->rest_gbit[j]);
-  cur->prev_nb = 0;
-  for (int i = 0; i < cur->D; ++i) {
-    cur->prev_qw[i] = 0;
-    if (cur->prev_w[i] != 0) {
-      cur->prev_qw[i] = 1 << cur->prev_nb;
-      cur->prev_cw[cur->prev_nb++] = cur->prev_w[i];
-    }
-  }
-  // every tile holds the three lowest column bits, so at most D - 3 <= 10
-  // tile bits select among previous tiles
-  return cur->prev_nb <= kMaxPrevBits;
+  for (int i = 0; i < cur->D; ++i) cur->src_w[i] = w(cur->gbit[i]);
+  for (int j = 0; j < cur->nrest; ++j) cur->src_rest_w[j] = w(cur->rest_gbit[j]);
 }
 
 }  // namespace
@@ -345,18 +352,11 @@ bool build_plan(int n, int dtype, int precision, int tile_bits_opt, int max_leve
     b += K;
   }
   for (int p = 0; p + 1 < plan->npass; ++p) set_next(&plan->pass[p], plan->pass[p + 1]);
-  for (int p = 1; p < plan->npass; ++p)
-    if (!set_prev(&plan->pass[p], plan->pass[p - 1])) {
-      if (err) *err = "a tile reads from too many previous tiles";
-      return false;
-    }
-  // Occupancy: the fixed point's first pass (double -> int64, long integer
-  // chains, few live values) gains from a third CTA per SM at a smaller
-  // register budget; the others keep two (measured on GB300: the last pass
-  // spills at three).
+  for (int p = 1; p < plan->npass; ++p) set_src(&plan->pass[p], plan->pass[p - 1]);
+  // Occupancy: complex128 fixed-point passes convert in both directions and
+  // keep two CTAs per SM (at three the 80-register budget spills).
   for (int p = 0; p < plan->npass; ++p) {
     PassDesc& pd = plan->pass[p];
-    const bool first_of_many = p == 0 && plan->npass > 1;
     // 2^13-element complex128 tiles: a two-CTA cluster of 256 threads
     // (min_blocks 2); other 2^13 tiles: one CTA of 512 threads (1)
     // Compensated and fixed-point complex64 (127-128 registers at two CTAs per
@@ -371,8 +371,7 @@ bool build_plan(int n, int dtype, int precision, int tile_bits_opt, int max_leve
     for (int s = 0; s < pd.nstage; ++s)
       if (pd.st[s].npair != 2 || pd.st[s].nshfl != 0) pairs_only = false;
     const bool two_c64 = pairs_only && (precision == 2 || pd.D < 12);
-    const bool three = (dtype == 0 && precision == 3 && first_of_many) ||
-                       (dtype == 1 && precision >= 2 && !two_c64);
+    const bool three = dtype == 1 && precision >= 2 && !two_c64;
     pd.min_blocks = pd.D > 12 ? (dtype == 0 ? 2 : 1) : (three ? 3 : 2);
   }
   return true;
@@ -393,6 +392,11 @@ std::string describe_plan(const Plan& plan) {
     s += buf;
     for (int i = 0; i < pd.D; ++i) {
       std::snprintf(buf, sizeof(buf), "%s%d", i ? "," : "", pd.gbit[i]);
+      s += buf;
+    }
+    s += " cls=";
+    for (int i = 0; i < pd.D; ++i) {
+      std::snprintf(buf, sizeof(buf), "%s%d", i ? "," : "", pd.cls_w[i]);
       s += buf;
     }
     for (int si = 0; si < pd.nstage; ++si) {

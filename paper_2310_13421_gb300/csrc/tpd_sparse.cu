@@ -14,10 +14,14 @@
 //     a01 -> X +v, Y +iv    a10 -> X +v, Y -iv
 // Entries with equal keys are summed in a hash table, zero sums dropped.
 //
-// Exactness: values are int64 on one binary point for the whole matrix
-// (x * 2^S, S = 1084 - n - max exponent, like a fixed-point pass with K = n),
-// so the sums are exact and independent of the order the atomics land in;
-// the weights are rounded to double once, at the end.  The output list is
+// Exactness: values are int64 on one binary point per X-mask x = r xor c
+// (x * 2^S_x, S_x = 1084 - n - the largest exponent among the entries of that
+// X-mask, like a fixed-point pass with K = n).  A level never changes an
+// entry's X-mask (Eq. 4: I, Z keep r_beta xor c_beta = 0, X, Y keep 1), so
+// every sum adds values on one binary point: the sums are exact and
+// independent of the order the atomics land in, and a weight's truncation
+// error is bounded by its own X-mask's entries.  The weights are rounded to
+// double once, at the end.  The output list is
 // sorted by string index (bitonic sort), so it does not depend on scheduling.
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -35,16 +39,19 @@ __device__ __forceinline__ uint32_t hash32(uint32_t k) {
   return k;
 }
 
-__global__ void k_sp_emax(const double2* __restrict__ vals, unsigned long long m, int* __restrict__ emax) {
-  int e = 0;
+// emax[x] = the largest exponent field among the entries of X-mask x = r xor c
+// (emax: 2^n ints, zero on entry; the index is masked to n bits, so that rows
+// or columns outside 0..2^n-1 cannot address outside the array)
+__global__ void k_sp_emax(const int* __restrict__ rows, const int* __restrict__ cols,
+                          const double2* __restrict__ vals, unsigned long long m, int n, int* __restrict__ emax) {
+  const int xmask = (1 << n) - 1;
   for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < m;
        i += (unsigned long long)gridDim.x * blockDim.x) {
     const int ex = (int)((unsigned long long)__double_as_longlong(vals[i].x) >> 52) & 0x7FF;
     const int ey = (int)((unsigned long long)__double_as_longlong(vals[i].y) >> 52) & 0x7FF;
-    e = max(e, max(ex, ey));
+    const int e = max(ex, ey);
+    if (e) atomicMax(emax + ((rows[i] ^ cols[i]) & xmask), e);
   }
-  for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
-  if ((threadIdx.x & 31) == 0) atomicMax(emax, e);
 }
 
 // x * 2^S truncated toward zero, S = 1084 - n - emax_eff (|result| < 2^(62-n)):
@@ -89,13 +96,13 @@ __device__ __forceinline__ double sp_to_double(long long v, int T) {
   return __longlong_as_double((long long)(bits | (s & 0x8000000000000000ull)));
 }
 
-// initial entries: key = r*N + c, value on the common binary point
+// initial entries: key = r*N + c, value on its X-mask's binary point
 __global__ void k_sp_init(const int* __restrict__ rows, const int* __restrict__ cols, const double2* __restrict__ vals,
                           unsigned long long m, int n, const int* __restrict__ emax, uint32_t* __restrict__ keys,
                           longlong2* __restrict__ v) {
   const unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
   if (i >= m) return;
-  const int emax_eff = max(*emax, 1);
+  const int emax_eff = max(emax[(rows[i] ^ cols[i]) & ((1 << n) - 1)], 1);
   keys[i] = ((uint32_t)rows[i] << n) | (uint32_t)cols[i];
   v[i] = make_longlong2(sp_to_fixed(vals[i].x, n, emax_eff), sp_to_fixed(vals[i].y, n, emax_eff));
 }
@@ -268,17 +275,20 @@ __global__ void __launch_bounds__(kSpLocalThreads) k_sp_local(unsigned long long
   for (unsigned t = threadIdx.x; t < cnt; t += blockDim.x) { skey[base + t] = sk[t]; sidx[base + t] = si[t]; }
 }
 
-__global__ void k_sp_emit(const longlong2* __restrict__ v, const unsigned long long* __restrict__ final_count,
+__global__ void k_sp_emit(const uint32_t* __restrict__ keys, const longlong2* __restrict__ v,
+                          const unsigned long long* __restrict__ final_count,
                           unsigned long long cap, const unsigned long long* __restrict__ skey,
                           const uint32_t* __restrict__ sidx, int n, const int* __restrict__ emax,
                           unsigned long long capacity, unsigned long long* __restrict__ strings,
                           double2* __restrict__ weights, unsigned long long* __restrict__ out_count) {
   const unsigned long long E = min(*final_count, cap);
-  const int emax_eff = max(*emax, 1);
-  const int T = 1084 - n - emax_eff + n;          // S of the input, and the 1/2 of Eq. 4 per level
+  const uint32_t xmask = (1u << n) - 1;
   for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < E && i < capacity;
        i += (unsigned long long)gridDim.x * blockDim.x) {
+    const uint32_t key = keys[sidx[i]];
     const longlong2 x = v[sidx[i]];
+    // S_x of the input, and the 1/2 of Eq. 4 per level (the labels keep x = r xor c)
+    const int T = 1084 - max(emax[((key >> n) ^ key) & xmask], 1);
     strings[i] = skey[i];
     weights[i] = make_double2(sp_to_double(x.x, T), sp_to_double(x.y, T));
   }
@@ -310,7 +320,7 @@ static SparseLayout sparse_layout(unsigned long long max_entries) {
   while (L.sortn < L.entries) L.sortn <<= 1;
   size_t off = 0;
   L.ctr = off; off += al(kSpCounters * sizeof(unsigned long long));
-  L.emax = off; off += al(sizeof(int));
+  L.emax = off; off += al(sizeof(int) << 15);     // one per X-mask, n <= 15
   L.keys = off; off += al(L.entries * 4);
   L.vals = off; off += al(L.entries * 16);
   L.tkeys = off; off += al(L.slots * 4);
@@ -339,13 +349,13 @@ cudaError_t launch_sparse(const int* rows, const int* cols, const void* vals, un
   uint32_t* sidx = reinterpret_cast<uint32_t*>(w + L.sidx);
   const unsigned long long cap = L.entries;
   cudaError_t e;
-  if ((e = cudaMemsetAsync(w, 0, L.keys, s)) != cudaSuccess) return e;        // counters, emax
+  if ((e = cudaMemsetAsync(w, 0, L.keys, s)) != cudaSuccess) return e;        // counters, X-mask maxima
   if ((e = cudaMemsetAsync(tkeys, 0xFF, L.slots * 4, s)) != cudaSuccess) return e;   // the table starts empty;
   if ((e = cudaMemsetAsync(tv, 0, L.slots * 16, s)) != cudaSuccess) return e;        // each level leaves it so
   const unsigned long long m0 = m < cap ? m : cap;
   k_sp_start<<<1, 1, 0, s>>>(ctr, m, cap);
   if (m0 > 0) {
-    k_sp_emax<<<grid_for(m0), 256, 0, s>>>(static_cast<const double2*>(vals), m0, emax);
+    k_sp_emax<<<grid_for(m0), 256, 0, s>>>(rows, cols, static_cast<const double2*>(vals), m0, n, emax);
     k_sp_init<<<(unsigned)((m0 + 255) / 256), 256, 0, s>>>(rows, cols, static_cast<const double2*>(vals), m0, n, emax,
                                                          keys, v);
   }
@@ -365,7 +375,7 @@ cudaError_t launch_sparse(const int* rows, const int* cols, const void* vals, un
       k_sp_bitonic<<<grid_for(L.sortn), 256, 0, s>>>(skey, sidx, fin, cap, j, k);
     k_sp_local<<<chunks, kSpLocalThreads, 0, s>>>(skey, sidx, fin, cap, k, k);
   }
-  k_sp_emit<<<grid_for(cap), 256, 0, s>>>(v, fin, cap, skey, sidx, n, emax, capacity, strings,
+  k_sp_emit<<<grid_for(cap), 256, 0, s>>>(keys, v, fin, cap, skey, sidx, n, emax, capacity, strings,
                                           static_cast<double2*>(weights), count);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (status) k_sp_status<<<1, 1, 0, s>>>(ctr, status);

@@ -27,11 +27,16 @@ def _threads():
 
 
 def hermitian(n, seed, dtype=np.complex128):
-    """A = (B + B^H)/2 with Re B, Im B i.i.d. N(0,1).  Exactly Hermitian in
-    floating point: entry (i,j) and (j,i) are conjugate sums of the same pair.
-    B is drawn in fixed row blocks, one stream per block, and symmetrised in
-    place tile by tile, so the bits do not depend on the thread count."""
-    N = 1 << n
+    """A = (B + B^H)/2 with Re B, Im B i.i.d. N(0,1), 2^n x 2^n.  Exactly
+    Hermitian in floating point: entry (i,j) and (j,i) are conjugate sums of
+    the same pair.  B is drawn in fixed row blocks, one stream per block, and
+    symmetrised in place tile by tile, so the bits do not depend on the thread
+    count."""
+    return hermitian_side(1 << n, seed, dtype)
+
+
+def hermitian_side(N, seed, dtype=np.complex128):
+    """hermitian() for any side N (e.g. d^n for n qudits of dimension d)."""
     rows_per = max(1, min(N, (1 << 22) // N))  # ~4M entries per stream
     A = np.empty((N, N), dtype=np.complex128)
 
@@ -57,6 +62,19 @@ def hermitian(n, seed, dtype=np.complex128):
     with concurrent.futures.ThreadPoolExecutor(_threads()) as ex:
         list(ex.map(draw, range(0, N, rows_per)))
         list(ex.map(sym, [(i, j) for i in range(0, N, T) for j in range(i, N, T)]))
+    if dtype == np.complex64:
+        return A.astype(np.complex64)
+    return A
+
+
+def diag_dominant(n, seed, scale, dtype=np.complex128):
+    """Hermitian matrix with a dominant diagonal: off-diagonal entries as in
+    hermitian() (N(0,1) parts, conjugate-symmetric), diagonal real
+    scale * N(0,1) -- strong local fields beside weak couplings, the case
+    where elements of very different size share a tile."""
+    A = hermitian(n, seed)
+    g = _rng(seed, 3)
+    A[np.diag_indices(1 << n)] = scale * g.standard_normal(1 << n)
     if dtype == np.complex64:
         return A.astype(np.complex64)
     return A

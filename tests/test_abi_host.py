@@ -64,11 +64,15 @@ def test_argument_errors_return_before_any_launch(L):
     assert L.tpd_workspace_size(10, L.TPD_C128, L.options(precision=1, skip_zero=True)) > 0
     assert L.tpd_workspace_size(10, L.TPD_C128, L.options(precision=1)) == 0
     assert L.tpd_decompose(4096, 10, L.TPD_C128, L.options(precision=1, skip_zero=True)) == L.TPD_ERR_WORKSPACE
-    # the fixed point keeps one binary point per tile between passes
+    # the block fixed point hands one int16 binary point per class (4^n / 2^K
+    # of them for a pass of K levels) to the next pass: n = 14, passes of 6, 4
+    # and 4 levels, 2 x 2^22 + 2 x 2^24 bytes; zero skipping adds one flag
+    # byte per tile of the passes after the first
     ws = L.tpd_workspace_size(14, L.TPD_C128, L.options())
-    assert ws >= 4 * (2 ** 16 + 2 ** 16)
-    assert L.tpd_workspace_size(14, L.TPD_C128, L.options(skip_zero=True)) > ws
-    assert L.tpd_workspace_size(6, L.TPD_C128, L.options()) == 0      # one pass: nothing between passes
+    assert ws == 2 * 2 ** 22 + 2 * 2 ** 24
+    assert L.tpd_workspace_size(14, L.TPD_C128, L.options(skip_zero=True)) == ws + 2 ** 16 + 2 ** 16
+    assert L.tpd_workspace_size(14, L.TPD_C128, L.options(precision=1)) == 0      # IEEE: nothing handed on
+    assert L.tpd_workspace_size(6, L.TPD_C128, L.options(skip_zero=True)) == 0    # one pass: nothing to hand on
     assert L.tpd_decompose(4096, 10, L.TPD_C128) == L.TPD_ERR_WORKSPACE
     assert L.tpd_decompose(4096, 10, L.TPD_C128, None, 4104, 1 << 20) == L.TPD_ERR_MISALIGNED
     # batched
@@ -99,6 +103,16 @@ def test_argument_errors_return_before_any_launch(L):
     assert L.tpd_nonzero_list(4096, 4, L.TPD_C128, 0.0, 0, 0, 0, 8192, 0, 0) == L.TPD_ERR_WORKSPACE
     assert L.tpd_nonzero_list(4096, 4, L.TPD_C128, -1.0, 0, 0, 0, 8192, 1 << 20, 4096) == L.TPD_ERR_INVALID_ARG
     assert L.tpd_nonzero_list(4096, 4, L.TPD_C128, 0.0, 0, 0, 5, 8192, 1 << 20, 4096) == L.TPD_ERR_INVALID_ARG
+    # Weyl basis: d in 2..5, d^n <= 65536
+    assert L.tpd_weyl_decompose(4096, 3, 1, L.TPD_C128) == L.TPD_ERR_INVALID_ARG      # d = 1
+    assert L.tpd_weyl_decompose(4096, 3, 6, L.TPD_C128) == L.TPD_ERR_INVALID_ARG      # d = 6
+    assert L.tpd_weyl_decompose(4096, 0, 3, L.TPD_C128) == L.TPD_ERR_INVALID_ARG      # n = 0
+    assert L.tpd_weyl_decompose(4096, 11, 3, L.TPD_C128) == L.TPD_ERR_INVALID_ARG     # 3^11 > 65536
+    assert L.tpd_weyl_decompose(0, 3, 3, L.TPD_C128) == L.TPD_ERR_INVALID_ARG         # null
+    assert L.tpd_weyl_decompose(4096, 3, 3, 5) == L.TPD_ERR_INVALID_ARG               # dtype
+    assert L.tpd_weyl_decompose(4104, 3, 3, L.TPD_C128) == L.TPD_ERR_MISALIGNED
+    assert L.tpd_weyl_compose(4096, 3, 3, L.TPD_C128, 0.0) == L.TPD_ERR_INVALID_ARG
+    assert L.tpd_weyl_compose(4100, 3, 3, L.TPD_C64, 1.0) == L.TPD_ERR_MISALIGNED
     # layout conversion and sums of squares
     assert L.tpd_convert_layout(4096, 1 << 20, 0, L.TPD_C128, 1) == L.TPD_ERR_INVALID_ARG      # n = 0
     assert L.tpd_convert_layout(4096, 4096 + 256, 4, L.TPD_C128, 1) == L.TPD_ERR_INVALID_ARG   # overlap
@@ -108,11 +122,11 @@ def test_argument_errors_return_before_any_launch(L):
     assert L.tpd_sum_squares(4096, 10, L.TPD_C128, 0, 1 << 20, 8192) == L.TPD_ERR_INVALID_ARG
     assert L.tpd_sum_squares(4104, 10, L.TPD_C128, 8192, 1 << 20, 8192) == L.TPD_ERR_MISALIGNED
     # workspace: control words (status, work counter, one completion counter per
-    # matrix and pass but the last) + bucket list + binary points
+    # matrix and pass but the last) + bucket list + bucketed pointers
     base = L.tpd_batched_workspace_size([3, 5], L.TPD_C128)
     assert base % 256 == 0 and base >= 256 + 256
     two_pass = L.tpd_batched_workspace_size([10] * 100, L.TPD_C128)
-    assert two_pass >= 4 * (4 + 100) + 4 * 100 + 4 * 100 * 256
+    assert two_pass >= 4 * (4 + 100) + 4 * 100 + 8 * 100 + 2 * 100 * 4 ** 10 // 2 ** 6
 
 
 # ------------------------------------------------------------------ plan emulation
@@ -253,15 +267,15 @@ def test_plan_choices_measured_on_gb300(L):
 
 
 def test_pass_occupancy_choices(L):
-    """CTAs per SM per pass: complex128 fixed point three in its first pass
-    only, a 2^13-element complex128 tile a two-CTA cluster (2), other 2^13
+    """CTAs per SM per pass: complex128 fixed point two (its passes convert
+    both ways), a 2^13-element complex128 tile a two-CTA cluster (2), other 2^13
     tiles one CTA of 512 threads (1); compensated and fixed-point complex64
     three, except in passes made only of two-level in-register stages: two
     for the compensated form, and for the fixed point on tiles below 2^12."""
     def ctas(n, dtype, prec):
         return [p["ctas"] for p in _parse(L.tpd_plan_describe(n, dtype, L.options(precision=prec))[1])]
-    assert ctas(14, 0, 0) == [3, 2, 2]
-    assert ctas(15, 0, 0) == [3, 2, 2]
+    assert ctas(14, 0, 0) == [2, 2, 2]
+    assert ctas(15, 0, 0) == [2, 2, 2]
     assert ctas(14, 0, 1) == [2, 2, 2]
     assert ctas(15, 1, 2) == [3, 2, 2, 3]
     assert ctas(15, 1, 3) == [3, 1, 2]

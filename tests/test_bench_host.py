@@ -6,11 +6,13 @@ import os
 import shutil
 import sys
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 sys.path.insert(0, ROOT)
 import bench  # noqa: E402
+from paper_2310_13421_gb300 import synth  # noqa: E402
 
 
 def test_code_only_drops_comments_and_blank_space():
@@ -42,3 +44,44 @@ def test_traffic_record_used_only_for_its_kernels_and_size():
     assert bench.measured_traffic(13) is None
     # DRAM traffic of a pass launch within 1 % of its algorithmic bytes (no re-reads)
     assert abs(rec["bytes_per_launch"] / rec["algorithmic_bytes_per_launch"] - 1) < 0.01
+
+
+def test_accuracy_rows_follow_the_rc_layout():
+    # the oracle's weights laid out in RC order (weight of string t at row
+    # bits = z, column bits = x xor z), read back by the bench's sampler, are
+    # the oracle's own X-rows; the accuracy leg then reports zero error, and a
+    # complex64 input gives the same rows through the gathered-diagonal path
+    import oracle
+    from _helpers import rc_positions
+    n = 6
+    A = synth.hermitian(n, seed=11)
+    W = np.empty(4 ** n, dtype=np.complex128)
+    W[rc_positions(n)] = oracle.coeffs_fwht(A)
+    xs = bench.accuracy_xs(n, count=8)
+    got = bench.rows_of(W.reshape(2 ** n, 2 ** n), n, xs)
+    assert np.array_equal(got, oracle.coeffs_xrows(A, xs))
+    acc = bench.oracle_accuracy(A, n, xs, {"exact": got})["exact"]
+    assert acc["normwise"] == 0 and acc["max_over_m_x"] == 0
+    A32 = A.astype(np.complex64)
+    assert np.array_equal(oracle.coeffs_xrows(A32, xs), oracle.coeffs_xrows(A32.astype(np.complex128), xs))
+
+
+def test_weyl_rows_follow_the_kernel_layout():
+    # the Weyl oracle's weights placed where the kernel puts them (row digits
+    # b, column digits a + b mod d), read back at the bench's positions, are
+    # the oracle's rows of the sampled shifts: zero error in the accuracy leg
+    from oracle import core
+    d, n = 3, 4
+    N = d ** n
+    A = synth.hermitian_side(N, seed=5)
+    c = core.weyl_coeffs_dft(A, d)
+    W = np.empty((N, N), dtype=np.complex128)
+    a = np.repeat(np.arange(N), N)
+    b = np.tile(np.arange(N), N)
+    W[b, bench._digit_add(a, b, d, n)] = c.reshape(-1)
+    a_s = np.array([0, 5, N - 1])
+    bb = np.arange(N)
+    got = np.stack([W[bb, bench._digit_add(bb, np.full(N, x), d, n)] for x in a_s])
+    assert np.array_equal(got, c[a_s])
+    acc = bench.weyl_accuracy(A, d, a_s, {"exact": got})["exact"]
+    assert acc["normwise"] == 0.0

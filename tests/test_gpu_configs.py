@@ -48,10 +48,8 @@ def test_config_n14_dense_c128(tpd):
         got, want = sample_rows(A, C, n, xs)
         assert_close(got, want, 1e-12, "n=14 " + prec)
         assert parseval(Ag, C, n) <= 1e-12
-        if prec == "plain":
-            assert torch.count_nonzero(C.imag).item() == 0    # Hermitian input: real weights, exactly
-        else:
-            assert torch.max(torch.abs(C.imag)).item() <= 1e-15 * torch.max(torch.abs(C)).item()
+        # Hermitian input: real weights, exactly (both arithmetics are odd-symmetric)
+        assert torch.count_nonzero(C.imag).item() == 0
         del C
     # zero skip on a dense input changes nothing
     C1 = tpd.decompose(Ag)
@@ -191,13 +189,15 @@ def test_config_n12_autograd(tpd):
     L0.backward()
     G = At.grad.detach()
     assert_close(G.cpu().numpy(), oracle.grad_weighted_sq(A, w), 1e-12, "oracle gradient")
-    # central differences on 64 entries: L is quadratic, so exact up to rounding
+    # central differences on 64 distinct random entries (real and imaginary
+    # direction each): L is quadratic, so exact up to rounding
     rng = np.random.default_rng(12)
+    flat = rng.choice(4 ** n, size=64, replace=False)
     hstep = 1e-2
     with torch.no_grad():
         base = torch.from_numpy(A).cuda()
-        for _ in range(32):
-            i, j = (int(v) for v in rng.integers(0, 2 ** n, size=2))
+        for f in flat:
+            i, j = divmod(int(f), 2 ** n)
             for unit in (1.0, 1j):
                 Ap = base.clone(); Ap[i, j] += hstep * unit
                 Am = base.clone(); Am[i, j] -= hstep * unit

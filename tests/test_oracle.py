@@ -237,50 +237,7 @@ def test_tfim_eq7_terms_recovered_exactly():
             assert w[synth.string_index(t)] == v
 
 
-# ---------------------------------------------------------------- the paper's Alg. 1 on the CPU
-
-@pytest.mark.parametrize("n", [1, 2, 3])
-def test_alg1_matches_kronecker(n):
-    A = synth.general(n, seed=300 + n)
-    assert np.allclose(oracle.tpd_alg1(A), kron.coeffs_kron(A), rtol=0, atol=1e-14)
-
-
-@pytest.mark.parametrize("n", [1, 4, 6, 8])
-def test_alg1_integer_inputs_exact(n):
-    A = synth.int_general(n, seed=310 + n)
-    assert np.array_equal(oracle.tpd_alg1(A), oracle.coeffs(A) if n <= 6 else oracle.coeffs_fwht(A))
-
-
-@pytest.mark.parametrize("n", [5, 8])
-def test_alg1_random_within_rounding_bound(n):
-    # every level rounds each output once (the 1/2 is exact) and is 2^-1/2 times
-    # unitary: normwise error <= n u / (1 - n u) against the exact weights
-    A = synth.general(n, seed=320 + n)
-    want = oracle.coeffs_fwht(A)
-    u = 2.0 ** -53
-    assert np.linalg.norm(oracle.tpd_alg1(A) - want) <= 2 * n * u * np.linalg.norm(want)
-
-
-def test_alg1_prunes_zero_cmws_exactly():
-    # planted Heisenberg chain (dyadic couplings): the recursion reaches only
-    # the planted strings' prefixes; every other weight is exactly 0
-    n = 8
-    J, h = synth.heisenberg_params(n, seed=330)
-    H = synth.heisenberg(n, J, h)
-    want = np.zeros(4 ** n, dtype=np.complex128)
-    for t, v in synth.heisenberg_terms(n, J, h).items():
-        want[synth.string_index(t)] = v
-    assert np.array_equal(oracle.tpd_alg1(H), want)
-    # a diagonal matrix has only I/Z strings (x-mask 0)
-    D = np.diag(synth.general(n, seed=331)[0]).astype(np.complex128)
-    w = oracle.tpd_alg1(D)
-    digits = np.arange(4 ** n)
-    only_iz = np.ones(4 ** n, dtype=bool)
-    for b in range(n):
-        only_iz &= np.isin((digits >> (2 * b)) & 3, (0, 3))
-    assert np.count_nonzero(w[~only_iz]) == 0
-    assert np.allclose(w, oracle.coeffs_fwht(D), rtol=0, atol=1e-15)
-
+# ---------------------------------------------------------------- the paper's Alg. 2 on the CPU
 
 @pytest.mark.parametrize("n", [1, 2, 3])
 def test_alg2_matches_kronecker(n):
@@ -288,10 +245,16 @@ def test_alg2_matches_kronecker(n):
     assert np.allclose(oracle.tpd_alg2(A), kron.coeffs_kron(A), rtol=0, atol=1e-14)
 
 
-@pytest.mark.parametrize("n", [4, 7, 9])
-def test_alg2_integer_exact_and_random_bound(n):
+@pytest.mark.parametrize("n", [1, 4, 6, 7, 9])
+def test_alg2_integer_inputs_exact(n):
     Ai = synth.int_general(n, seed=350 + n)
-    assert np.array_equal(oracle.tpd_alg2(Ai), oracle.coeffs_fwht(Ai))
+    assert np.array_equal(oracle.tpd_alg2(Ai), oracle.coeffs(Ai) if n <= 6 else oracle.coeffs_fwht(Ai))
+
+
+@pytest.mark.parametrize("n", [5, 8])
+def test_alg2_random_within_rounding_bound(n):
+    # every level rounds each output once (the 1/2 is exact) and is 2^-1/2 times
+    # unitary: normwise error <= n u / (1 - n u) against the exact weights
     A = synth.general(n, seed=360 + n)
     want = oracle.coeffs_fwht(A)
     assert np.linalg.norm(oracle.tpd_alg2(A) - want) <= 2 * n * 2.0 ** -53 * np.linalg.norm(want)
@@ -299,13 +262,29 @@ def test_alg2_integer_exact_and_random_bound(n):
     W = A.copy()
     oracle.tpd_alg2(W, overwrite=True)
     assert not np.array_equal(W, A)
+    # the thread count does not change the result (each quad is computed once)
+    assert np.array_equal(oracle.tpd_alg2(A, threads=1), oracle.tpd_alg2(A))
 
 
-def test_alg2_agrees_with_alg1_on_planted_chain():
-    n = 9
-    J, h = synth.heisenberg_params(n, seed=370)
+def test_alg2_prunes_zero_cmws_exactly():
+    # planted Heisenberg chain (dyadic couplings): exactly the planted strings
+    # are nonzero, with their exact values
+    n = 8
+    J, h = synth.heisenberg_params(n, seed=330)
     H = synth.heisenberg(n, J, h)
-    assert np.array_equal(oracle.tpd_alg2(H), oracle.tpd_alg1(H))
+    want = np.zeros(4 ** n, dtype=np.complex128)
+    for t, v in synth.heisenberg_terms(n, J, h).items():
+        want[synth.string_index(t)] = v
+    assert np.array_equal(oracle.tpd_alg2(H), want)
+    # a diagonal matrix has only I/Z strings (x-mask 0)
+    D = np.diag(synth.general(n, seed=331)[0]).astype(np.complex128)
+    w = oracle.tpd_alg2(D)
+    digits = np.arange(4 ** n)
+    only_iz = np.ones(4 ** n, dtype=bool)
+    for b in range(n):
+        only_iz &= np.isin((digits >> (2 * b)) & 3, (0, 3))
+    assert np.count_nonzero(w[~only_iz]) == 0
+    assert np.allclose(w, oracle.coeffs_fwht(D), rtol=0, atol=1e-15)
 
 
 # ---------------------------------------------------------------- gradient and adjoint

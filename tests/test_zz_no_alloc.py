@@ -13,8 +13,6 @@ from paper_2310_13421_gb300 import synth
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = 1e-12  # the complex128 tolerance of the other parity tests
-
 
 @pytest.fixture(scope="module")
 def L():
@@ -43,35 +41,32 @@ def _noalloc(L, A, n, opt):
     return out
 
 
-def _close(a, b):
-    d = torch.linalg.vector_norm(a - b).item()
-    ref = torch.linalg.vector_norm(b).item()
-    assert d <= TOL * ref, (d, ref)
-
-
 def test_noalloc_matches_decompose_on_consecutive_calls(L):
-    # n = 12 and 14 are multi-pass plans: their passes hand per-tile binary
-    # points (and, with zero skipping, flags) to one another in the scratch array
+    # multi-pass plans hand their per-class binary points (and, with zero
+    # skipping, per-tile flags) to one another in the scratch array
     cases = [
-        (12, synth.hermitian(12, seed=31), L.options()),
+        (12, synth.hermitian(12, seed=31), L.options(skip_zero=True)),
         (12, synth.heisenberg(12, *synth.heisenberg_params(12, seed=32)), L.options(skip_zero=True)),
-        (14, synth.hermitian(14, seed=33), L.options()),
+        (14, synth.hermitian(14, seed=33), L.options(skip_zero=True)),
         (12, synth.general(12, seed=34), L.options(skip_zero=True)),
+        (12, synth.general(12, seed=35), L.options()),
     ]
-    assert max(L.tpd_workspace_size(n, L.TPD_C128, opt) for n, _, opt in cases) <= L.TPD_NOALLOC_SCRATCH_BYTES
+    assert 0 < max(L.tpd_workspace_size(n, L.TPD_C128, opt) for n, _, opt in cases) <= L.TPD_NOALLOC_SCRATCH_BYTES
     for n, A, opt in cases:
         At = torch.from_numpy(A).cuda()
         want = _reference(L, At, n, opt)
         got1 = _noalloc(L, At, n, opt)
         got2 = _noalloc(L, At, n, opt)      # second call in a row reuses the array as left
         torch.cuda.synchronize()
-        _close(got1, want)
-        _close(got2, want)
+        # the same plan and arithmetic: identical bits (a stale flag would show)
+        assert torch.equal(got1, want)
+        assert torch.equal(got2, want)
 
 
 def test_noalloc_rejects_plans_larger_than_its_array(L):
-    # 2^9-element tiles at n = 16 need a 32 MiB workspace: refused before any launch
-    opt = L.options(tile_bits=9)
+    # 2^9-element tiles at n = 16 need gigabytes of binary points: refused
+    # before any launch
+    opt = L.options(tile_bits=9, skip_zero=True)
     assert L.tpd_workspace_size(16, L.TPD_C128, opt) > L.TPD_NOALLOC_SCRATCH_BYTES
     A = torch.zeros(16, dtype=torch.complex128, device="cuda")   # never touched
     st = L.tpd_decompose_noalloc(A.data_ptr(), 16, L.TPD_C128, opt, torch.cuda.current_stream().cuda_stream)
