@@ -9,6 +9,9 @@ candidates that reproduce the default plan's result exactly on an integer
 input, registers the fastest with ``tpd_tune_set`` (so single and batched
 calls use it) and caches the choice in a JSON file keyed by GPU name and SM
 count.  Small n is tuned on a batch of matrices through the batched call.
+``tune_batch`` tunes for a given mixed batch instead: every qubit count inside
+the batch it serves, timed as the whole batch, never slower than the
+planner's defaults on it.
 """
 import itertools
 import json
@@ -154,6 +157,83 @@ def tune(n, dtype="c128", precision="default", reps=5, batch_bytes=64 << 20, reg
     if cache is not None:
         save(cache, n, dtype, prec, res)
     return res
+
+
+def tune_batch(mats, precision="default", reps=3, margin=0.01, register=True):
+    """Tune for the batch the choices will serve: `mats`, CUDA matrices of
+    mixed sizes (all complex128 or all complex64), decomposed in place by the
+    batched call.  Starting from the planner's defaults, each qubit count in
+    the batch in turn tries its candidates (tile bits, levels per pass, CTAs
+    per SM) with the others fixed, timing the WHOLE batch; a candidate
+    replaces the incumbent only when the batch runs faster by more than
+    `margin`.  Finally the batch-wide form -- one launch per (qubit count,
+    pass) or one persistent launch -- is chosen the same way.  The defaults
+    are the first incumbents, so the result is never slower than them on this
+    batch (up to timing noise).  The matrices are restored after every run.
+    Returns {"per_n": {n: choice}, "variant": 0 or 2, "ms": t, "default_ms": t0}."""
+    if not mats:
+        raise ValueError("empty batch")
+    code, tdt = (L.TPD_C128, torch.complex128) if mats[0].dtype == torch.complex128 else (L.TPD_C64, torch.complex64)
+    prec = _PREC[precision] if isinstance(precision, str) else precision
+    ns = [m.shape[0].bit_length() - 1 for m in mats]
+    orig = [m.clone() for m in mats]
+    ptrs = torch.tensor([m.data_ptr() for m in mats], dtype=torch.int64, device="cuda")
+    ns_dev = torch.tensor(ns, dtype=torch.int32, device="cuda")
+    s = torch.cuda.current_stream()
+    for n in set(ns):
+        L.tpd_tune_set(n, code, prec, None)
+    choice = {n: dict(tile_bits=0, max_levels=0, variant=0) for n in set(ns)}
+
+    def run(batch_variant):
+        opt = L.options(precision=prec, variant=batch_variant)
+        wsb = L.tpd_batched_workspace_size(ns, code, opt)
+        ws = torch.empty(max(wsb, 16), dtype=torch.uint8, device="cuda")
+        times = []
+        for k in range(reps + 2):
+            for m, o in zip(mats, orig):
+                m.copy_(o)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            st = L.tpd_decompose_batched(ptrs.data_ptr(), ns_dev.data_ptr(), ns, code, opt, ws.data_ptr(), wsb,
+                                         s.cuda_stream)
+            e1.record(s)
+            if st != L.TPD_OK:
+                return None
+            torch.cuda.synchronize()
+            if k >= 2:
+                times.append(e0.elapsed_time(e1))
+        times.sort()
+        return times[len(times) // 2]
+
+    def apply(n, c):
+        if c["tile_bits"] == 0 and c["max_levels"] == 0 and c["variant"] == 0:
+            return L.tpd_tune_set(n, code, prec, None) == L.TPD_OK
+        return L.tpd_tune_set(n, code, prec, L.options(precision=prec, **c)) == L.TPD_OK
+
+    default_ms = best_ms = run(0)
+    for n in sorted(set(ns), key=lambda k: -ns.count(k) * 4 ** k):     # the largest share of the work first
+        for cand in candidates(n, "c128" if code == L.TPD_C128 else "c64", prec, batched=True):
+            c = {k: cand[k] for k in ("tile_bits", "max_levels", "variant")}
+            if c == choice[n] or c["variant"] == 2:       # the batch-wide form is chosen below
+                continue
+            if not _agrees_with_default(n, code, tdt, prec, cand) or not apply(n, c):
+                apply(n, choice[n])
+                continue
+            t = run(0)
+            if t is not None and t < best_ms * (1.0 - margin):
+                best_ms, choice[n] = t, c
+            else:
+                apply(n, choice[n])
+    batch_variant = 0
+    t2 = run(2)
+    if t2 is not None and t2 < best_ms * (1.0 - margin):
+        best_ms, batch_variant = t2, 2
+    for m, o in zip(mats, orig):
+        m.copy_(o)
+    if not register:
+        for n in set(ns):
+            L.tpd_tune_set(n, code, prec, None)
+    return {"per_n": choice, "variant": batch_variant, "ms": best_ms, "default_ms": default_ms}
 
 
 def save(path, n, dtype, precision, res):

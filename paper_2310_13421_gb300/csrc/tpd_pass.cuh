@@ -351,31 +351,68 @@ __device__ __forceinline__ int reg_cls(int e, int w0, int w1, int w2, int w3) {
 // on entry.  A stage's in-register levels put a level's column and row bit on
 // register bits (0,1) and (2,3), so e, e^3 (and e^12, e^15) share a class: one
 // atomic per class and thread.
-// Returns the largest exponent field of the thread's elements.
-template <class Raw, class ExpOf>
+// Slot values of elements: the exponent field of an IEEE element, or the
+// source binary point + kQSlot of an int64 one (0: a zero source).
+constexpr int kQSlot = 4096;
+struct ExpSlot64 {
+  __device__ __forceinline__ static int of(const double2& x) {
+    return (int)(max((uint32_t)__double2hiint(x.x) & 0x7fffffffu, (uint32_t)__double2hiint(x.y) & 0x7fffffffu) >> 20);
+  }
+};
+struct ExpSlot32 {
+  __device__ __forceinline__ static int of(const float2& x) {
+    return (int)(max(__float_as_uint(x.x) & 0x7fffffffu, __float_as_uint(x.y) & 0x7fffffffu) >> 23);
+  }
+};
+struct QSlot {
+  __device__ __forceinline__ static int of(int q) { return q > kQValidMin ? q + kQSlot : 0; }
+};
+
+// One atomic per in-thread class: with kNp in-register levels in the stage,
+// e, e^3 (and e^12, e^15) share a class.
+template <int kNp, class S, class T>
+__device__ __forceinline__ void class_atomics(const T (&x)[kElems], int* slots, int ct, int c0, int c1, int c2,
+                                              int c3) {
+#pragma unroll
+  for (int e = 0; e < kElems; ++e) {
+    if (kNp >= 1 && (e & 2)) continue;
+    if (kNp >= 2 && (e & 8)) continue;
+    int m = S::of(x[e]);
+    if (kNp >= 1) m = max(m, S::of(x[e ^ 3]));
+    if (kNp >= 2) m = max(m, max(S::of(x[e ^ 12]), S::of(x[e ^ 15])));
+    if (m) atomicMax(slots + (ct ^ reg_cls(e, c0, c1, c2, c3)), m);
+  }
+}
+
+// class_atomics for the stage's in-register level count, a uniform branch
+// to straight-line code for each count
+template <class S, class T>
+__device__ __forceinline__ void class_atomics_any(int np, const T (&x)[kElems], int* slots, int ct, int c0, int c1,
+                                                  int c2, int c3) {
+  if (np >= 2) class_atomics<2, S>(x, slots, ct, c0, c1, c2, c3);
+  else if (np == 1) class_atomics<1, S>(x, slots, ct, c0, c1, c2, c3);
+  else class_atomics<0, S>(x, slots, ct, c0, c1, c2, c3);
+}
+
+// Returns the largest exponent field of the thread's elements, and in lo
+// the smallest nonzero one (0x7fffffff if none).
+template <class S, class Raw, class ExpOf>
 __device__ __forceinline__ uint32_t class_max(const PassDesc& pd, const Raw (&raw)[kElems], int* slots, int lane,
-                                              int warp, ExpOf exp_of) {
+                                              int warp, ExpOf exp_of, int& lo) {
   const Stage& s0 = pd.st[0];
   const int ct = cls_thread(pd, s0, lane, warp);
   const int c0 = pd.cls_w[s0.reg[0]], c1 = pd.cls_w[s0.reg[1]], c2 = pd.cls_w[s0.reg[2]],
             c3 = pd.cls_w[s0.reg[3]];
-  const int np = s0.npair;
-  uint32_t ex[kElems];
-  uint32_t hmax = 0;
+  uint32_t hmax = 0, hmin = 0x7fffffffu;
 #pragma unroll
   for (int e = 0; e < kElems; ++e) {
-    ex[e] = exp_of(raw[e]);
-    hmax = max(hmax, ex[e]);
+    const uint32_t x = exp_of(raw[e]);
+    hmax = max(hmax, x);
+    hmin = min(hmin, x ? x : 0x7fffffffu);
   }
-#pragma unroll
-  for (int e = 0; e < kElems; ++e) {
-    if (np >= 1 && (e & 2)) continue;
-    if (np >= 2 && (e & 8)) continue;
-    uint32_t m = ex[e];
-    if (np >= 1) m = max(m, ex[e ^ 3]);
-    if (np >= 2) m = max(m, max(ex[e ^ 12], ex[e ^ 15]));
-    if (m) atomicMax(slots + (ct ^ reg_cls(e, c0, c1, c2, c3)), (int)m);
-  }
+  lo = (int)hmin;
+  // (the exponents are recomputed rather than kept: 16 registers fewer)
+  class_atomics_any<S>(s0.npair, raw, slots, ct, c0, c1, c2, c3);
   return hmax;
 }
 
@@ -403,6 +440,13 @@ __device__ __forceinline__ uint32_t reg_src(int e, uint32_t w0, uint32_t w1, uin
 }
 
 __device__ __forceinline__ bool q_is_valid(int q) { return q > kQValidMin; }
+
+// floor(v / 2^sh) (sh >= 0; 0 or -1 once sh >= 64)
+__device__ __forceinline__ long long shr_floor(long long v, unsigned sh) {
+  long long r;
+  asm("shr.s64 %0, %1, %2;" : "=l"(r) : "l"(v), "r"(sh));   // PTX clamps the amount at 64
+  return r;
+}
 
 // v / 2^sh rounded toward zero (sh >= 0; 0 once sh >= 64): an odd function,
 // so conjugate sums stay exactly conjugate
@@ -482,6 +526,32 @@ __device__ __forceinline__ void flag_next(const PassDesc& pd, const PassArgs& ar
   }
 }
 
+// Tile-wide reduction of the flags (OR) and of the range [lo, hi] of the
+// nonzero class slots, through red[0..16) / red[16..32) / red[32..48) (one
+// entry per warp; a two-CTA cluster writes its entries into both CTAs at the
+// 512-thread layout's warp index and meets at a cluster barrier).
+template <bool kCl>
+__device__ __forceinline__ void tile_reduce(int* red, int warp, int lane, int nwarps_total, int& tb, int& lo,
+                                            int& hi) {
+  tb = __reduce_or_sync(kFull, tb);
+  lo = (int)__reduce_min_sync(kFull, (unsigned)lo);
+  hi = (int)__reduce_max_sync(kFull, (unsigned)hi);
+  if (lane == 0) {
+    red[warp] = tb; red[16 + warp] = lo; red[32 + warp] = hi;
+    if constexpr (kCl) {
+      int* pr = peer_smem(red);
+      pr[warp] = tb; pr[16 + warp] = lo; pr[32 + warp] = hi;
+    }
+  }
+  if constexpr (kCl) cluster_sync();
+  else __syncthreads();
+  // lane w reads warp w's entries; one warp-wide reduction each
+  const bool in = lane < nwarps_total;
+  tb = (int)__reduce_or_sync(kFull, in ? (unsigned)red[lane] : 0u);
+  lo = (int)__reduce_min_sync(kFull, in ? (unsigned)red[16 + lane] : 0x7fffffffu);
+  hi = (int)__reduce_max_sync(kFull, in ? (unsigned)red[32 + lane] : 0u);
+}
+
 // One complex128 tile of the block fixed point, in the role kRole (IEEE
 // numbers or int64 sums in, IEEE numbers or int64 sums out).
 // xbuf: exchange area (2^D x 16 bytes; a two-CTA cluster: half of it per
@@ -497,7 +567,6 @@ __device__ __forceinline__ void flag_next(const PassDesc& pd, const PassArgs& ar
 // int64 input, the largest source binary point + kQSlot (q_in = that point +
 // K: every element shifts right by at least K bits, toward zero, after which
 // the 2^K-term sums stay below 2^62), 0 for a class whose sources are all zero.
-constexpr int kQSlot = 4096;
 
 template <bool kDec, int kRole, bool kCg = false, bool kCl = false>
 __device__ __forceinline__ void fixed_tile(const PassDesc& pd, const PassArgs& args, void* matp, const int16_t* q_in,
@@ -507,9 +576,11 @@ __device__ __forceinline__ void fixed_tile(const PassDesc& pd, const PassArgs& a
   using V = FixedArith::V;
   constexpr bool kIntIn = (kRole & kRoleIntIn) != 0;
   constexpr bool kIntOut = (kRole & kRoleIntOut) != 0;
-  const int nthr = blockDim.x, nwarps = nthr >> 5, lwarp = threadIdx.x >> 5;
+  const int nthr = blockDim.x;
+  const int nwarps_total = 1 << (pd.D - kMinTileBits);   // warps of the tile (both CTAs of a cluster)
   const int ncls = 1 << (pd.D - pd.K);
   for (int i = threadIdx.x; i < ncls; i += nthr) cls[i] = 0;
+  int slot_lo, slot_hi;                                  // range of the tile's nonzero class slots
   const Stage& s0 = pd.st[0];
   const int ct = cls_thread(pd, s0, lane, warp);
   const int c0 = pd.cls_w[s0.reg[0]], c1 = pd.cls_w[s0.reg[1]], c2 = pd.cls_w[s0.reg[2]],
@@ -524,7 +595,8 @@ __device__ __forceinline__ void fixed_tile(const PassDesc& pd, const PassArgs& a
     else load_tile<kCg>(pd, matp, base, lane, warp, raw);
     if constexpr (kCl) cluster_wait();                   // the peer CTA is running
     __syncthreads();                                     // class slots cleared
-    const uint32_t hmax = class_max(pd, raw, cls, lane, warp, exp_f64);
+    int lo;
+    const uint32_t hmax = class_max<ExpSlot64>(pd, raw, cls, lane, warp, exp_f64, lo);
     uint32_t nzw = 0;
     if (args.skip_zero) {
 #pragma unroll
@@ -532,16 +604,11 @@ __device__ __forceinline__ void fixed_tile(const PassDesc& pd, const PassArgs& a
         nzw |= (uint32_t)__double2hiint(raw[e].x) << 1 | (uint32_t)__double2loint(raw[e].x) |
                (uint32_t)__double2hiint(raw[e].y) << 1 | (uint32_t)__double2loint(raw[e].y);
     }
-    tb = (__reduce_or_sync(kFull, nzw) != 0 ? 1 : 0) | (__any_sync(kFull, hmax == 2047) ? 2 : 0);
-    if constexpr (kCl) {
-      if (lane == 0) { red[lwarp] = tb; peer_smem(red)[16 + lwarp] = tb; }
-      cluster_sync();                                    // both CTAs' atomics and flags are in
-    } else {
-      if (lane == 0) red[lwarp] = tb;
-      __syncthreads();
-    }
-    tb = 0;
-    for (int w = 0; w < nwarps; ++w) tb |= red[w] | (kCl ? red[16 + w] : 0);
+    tb = (nzw != 0 ? 1 : 0) | (hmax == 2047 ? 2 : 0);
+    int hi = (int)hmax;
+    tile_reduce<kCl>(red, warp, lane, nwarps_total, tb, lo, hi);   // both CTAs' atomics and flags are in
+    slot_lo = lo;
+    slot_hi = hi;
     if ((args.skip_zero && !(tb & 1)) || (tb & 2)) {
       if (tb & 2) ieee_tile<kDec, kCg, kCl>(pd, args, matp, q_in, q_out, tile, base, sbase, nbase, xbuf, lane, warp);
       return;                                            // (else all +-0: the outputs are zero already)
@@ -573,32 +640,20 @@ __device__ __forceinline__ void fixed_tile(const PassDesc& pd, const PassArgs& a
     }
     if constexpr (kCl) cluster_wait();                   // the peer CTA is running
     __syncthreads();                                     // class slots cleared
-    int any_valid = 0, any_ieee = 0;
+    int any_valid = 0, any_ieee = 0, lo = 0x7fffffff, hi = 0;
 #pragma unroll
     for (int e = 0; e < kElems; ++e) {
-      any_valid |= q_is_valid(qs[e]);
+      const bool ok = q_is_valid(qs[e]);
+      any_valid |= ok;
       any_ieee |= qs[e] == kQIeee;
+      lo = min(lo, ok ? qs[e] + kQSlot : 0x7fffffff);
+      hi = max(hi, ok ? qs[e] + kQSlot : 0);
     }
-#pragma unroll
-    for (int e = 0; e < kElems; ++e) {
-      if (np >= 1 && (e & 2)) continue;
-      if (np >= 2 && (e & 8)) continue;
-      auto slot = [&](int k) { return q_is_valid(qs[k]) ? qs[k] + kQSlot : 0; };
-      int m = slot(e);
-      if (np >= 1) m = max(m, slot(e ^ 3));
-      if (np >= 2) m = max(m, max(slot(e ^ 12), slot(e ^ 15)));
-      if (m) atomicMax(cls + (ct ^ reg_cls(e, c0, c1, c2, c3)), m);
-    }
-    tb = (__any_sync(kFull, any_valid) ? 1 : 0) | (__any_sync(kFull, any_ieee) ? 2 : 0);
-    if constexpr (kCl) {
-      if (lane == 0) { red[lwarp] = tb; peer_smem(red)[16 + lwarp] = tb; }
-      cluster_sync();
-    } else {
-      if (lane == 0) red[lwarp] = tb;
-      __syncthreads();
-    }
-    tb = 0;
-    for (int w = 0; w < nwarps; ++w) tb |= red[w] | (kCl ? red[16 + w] : 0);
+    class_atomics_any<QSlot>(np, qs, cls, ct, c0, c1, c2, c3);
+    tb = (any_valid ? 1 : 0) | (any_ieee ? 2 : 0);
+    tile_reduce<kCl>(red, warp, lane, nwarps_total, tb, lo, hi);
+    slot_lo = lo;
+    slot_hi = hi;
     if (tb & 2) {
       ieee_tile<kDec, kCg, kCl>(pd, args, matp, q_in, q_out, tile, base, sbase, nbase, xbuf, lane, warp);
       return;
@@ -609,13 +664,17 @@ __device__ __forceinline__ void fixed_tile(const PassDesc& pd, const PassArgs& a
       for (int i = threadIdx.x; i < ncls; i += nthr) cls[i] = max(cls[i], pcls[i]);
       cluster_sync();
     }
-    // realign onto q_in_c = (largest source point) + K, toward zero
+    // realign onto q_in_c = (largest source point) + K.  Conjugate partners
+    // (Hermitian inputs) have equal real parts and opposite imaginary parts:
+    // the real parts may round toward -inf (two instructions), the imaginary
+    // parts round toward zero (an odd function), and conjugate sums stay
+    // exactly conjugate
 #pragma unroll
     for (int e = 0; e < kElems; ++e) {
       const int q = qs[e];
       if (q_is_valid(q)) {
         const unsigned sh = (unsigned)(cls[ct ^ reg_cls(e, c0, c1, c2, c3)] - kQSlot + pd.K - q);
-        v[e].re = shr_tz(raw[e].x, sh);
+        v[e].re = shr_floor(raw[e].x, sh);
         v[e].im = shr_tz(raw[e].y, sh);
       } else {
         v[e].re = 0; v[e].im = 0;
@@ -661,19 +720,26 @@ __device__ __forceinline__ void fixed_tile(const PassDesc& pd, const PassArgs& a
               l3 = pd.cls_w[sl.reg[3]];
     const bool resid = args.out_mul != 1.0;              // non-power-of-two composition scale (rare)
     double2* mat = reinterpret_cast<double2*>(matp);
+    // T of a class, -(q_out + out_pow2), falls as its slot rises; zero
+    // classes (all of whose sums are 0) round to 0 at any T
+    const int tadj = -(kDec ? pd.K : 0) + args.out_pow2;
+    const bool fast = !resid && (slot_hi < slot_lo || (FixedArith::fast_range(-(q_of_slot(slot_hi) + tadj)) &&
+                                                       FixedArith::fast_range(-(q_of_slot(slot_lo) + tadj))));
+    if (fast) {
+      // real parts through the fp64 conversion unit, imaginary parts through
+      // integer instructions (identical roundings): the two pipes share the
+      // conversions
 #pragma unroll
-    for (int e = 0; e < kElems; ++e) {
-      const int T = -(q_of_slot(cls[cl ^ reg_cls(e, l0, l1, l2, l3)]) - (kDec ? pd.K : 0) + args.out_pow2);
-      double2 o;
-      if (!resid && (FixedArith::fast_range(T) || (v[e].re | v[e].im) == 0)) {
-        // real parts through the fp64 conversion unit, imaginary parts through
-        // integer instructions (identical roundings): the two pipes share the
-        // conversions
-        o = make_double2(FixedArith::to_double_cvt_fast(v[e].re, T), FixedArith::to_double_fast(v[e].im, T));
-      } else {
-        o = FixedArith::to_double2_rare(v[e].re, v[e].im, T, args.out_mul);
+      for (int e = 0; e < kElems; ++e) {
+        const int T = -(q_of_slot(cls[cl ^ reg_cls(e, l0, l1, l2, l3)]) + tadj);
+        mat[g + reg_off(e, w0, w1, w2, w3)] =
+            make_double2(FixedArith::to_double_cvt_fast(v[e].re, T), FixedArith::to_double_fast(v[e].im, T));
       }
-      mat[g + reg_off(e, w0, w1, w2, w3)] = o;
+    } else {
+      for (int e = 0; e < kElems; ++e) {
+        const int T = -(q_of_slot(cls[cl ^ reg_cls(e, l0, l1, l2, l3)]) + tadj);
+        mat[g + reg_off(e, w0, w1, w2, w3)] = FixedArith::to_double2_rare(v[e].re, v[e].im, T, args.out_mul);
+      }
     }
   }
   if (args.flags_out != nullptr) flag_next(pd, args, nbase, lane, warp, [&](int e) { return (v[e].re | v[e].im) != 0; });
@@ -695,7 +761,8 @@ __device__ __forceinline__ void fixed32_tile(const PassDesc& pd, const PassArgs&
   float2 raw[kElems];
   load_tile<kCg>(pd, matp, base, lane, warp, raw);
   __syncthreads();                                       // class slots cleared
-  const uint32_t hmax = class_max(pd, raw, cls, lane, warp, exp_f32);
+  int lo_unused;
+  const uint32_t hmax = class_max<ExpSlot32>(pd, raw, cls, lane, warp, exp_f32, lo_unused);
   uint32_t nzw = 0;
   if (args.skip_zero) {
 #pragma unroll

@@ -152,3 +152,37 @@ def test_inconsistent_device_sizes_touch_nothing(tpd, variant):
     for m, w in zip(mats, work):
         assert_exact(host(w), m)
     assert L.TPD_ERR_INVALID_ARG == STATUS_INVALID and L.TPD_ERR_TIMEOUT == STATUS_TIMEOUT
+
+
+def test_graph_replay_after_smaller_launches_of_the_same_kernels(tpd):
+    """Kernel nodes captured in a CUDA graph keep the dynamic shared-memory size
+    of their capture.  A kernel's shared-memory limit that later calls lower to
+    their own, smaller size (2^10-element tiles of the same pass kernels) would
+    make the replayed nodes -- or a profiler relaunching them one by one --
+    fail to launch; the library only ever raises the limit to each kernel's
+    largest launch.  The replay must run and give the captured calls' results."""
+    ns = [10, 10, 9, 8, 7]
+    mats = [gpu(synth.general(n, seed=9900 + i)) for i, n in enumerate(ns)]
+    want = [tpd.decompose(m) for m in mats]
+    work = [m.clone() for m in mats]
+    for prec_form in (0, 2):                          # per (n, pass) launches, one persistent launch
+        batch = tpd.Batch(work, variant=prec_form)
+        batch.decompose()                            # kernel attributes set outside the capture
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            batch.decompose()
+        # the same pass kernels launched with 2^10-element tiles (a quarter of the
+        # captured shared memory), and whole small matrices
+        for n in (8, 9, 10):
+            tpd.decompose(gpu(synth.general(n, seed=n)), tile_bits=10)
+        tpd.decompose(gpu(synth.general(3, seed=3)))
+        torch.cuda.synchronize()
+        for _ in range(2):
+            for w, m in zip(work, mats):
+                w.copy_(m)
+            g.replay()
+            torch.cuda.synchronize()
+            for w, r in zip(work, want):
+                assert torch.equal(w, r)
+        assert batch.status() == STATUS_OK
