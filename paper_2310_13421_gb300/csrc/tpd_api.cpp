@@ -250,7 +250,7 @@ tpd_status run_single(bool dec, int arith, void* mat, const Plan& plan, int skip
   };
   auto tuned_desc = [&](int p) {
     PassDesc tuned = plan.pass[p];            // occupancy override (variants 3 and 4)
-    if (tuned.D <= 12 && (variant == 3 || variant == 4)) tuned.min_blocks = variant == 3 ? 2 : 3;
+    if (tuned.D <= 12 && (variant == 3 || variant == 4)) tuned.min_blocks = variant == 3 ? kOccLow : kOccHigh;
     if (tuned.D > 12 && variant == 1) tuned.min_blocks = 1;   // one 512-thread CTA per tile
     return tuned;
   };

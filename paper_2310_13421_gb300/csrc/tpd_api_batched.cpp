@@ -245,7 +245,7 @@ tpd_status batched(bool dec, void* const* ptrs_dev, const int* ns_dev, const int
         const double scale = scale_mode ? std::ldexp(1.0, -n) : 1.0;
         pass_scaling(dec, arith, pd, last, scale_mode ? -n : 0, 1.0, scale, &a);
         PassDesc tuned = pd;                   // occupancy override (variants 3 and 4)
-        if (pd.D <= 12 && (variants[n] == 3 || variants[n] == 4)) tuned.min_blocks = variants[n] == 3 ? 2 : 3;
+        if (pd.D <= 12 && (variants[n] == 3 || variants[n] == 4)) tuned.min_blocks = variants[n] == 3 ? kOccLow : kOccHigh;
         if (pd.D > 12 && variants[n] == 1) tuned.min_blocks = 1;   // one 512-thread CTA per tile
         if (launch_pass(arith, dec, tuned, a, pd.ntiles * hist[n], s) != cudaSuccess) return TPD_ERR_CUDA;
       }

@@ -128,13 +128,13 @@ __device__ __forceinline__ void batch_pass_tile(const BatchSeg& sg, int p, const
   }
 }
 
-// 256 threads; dynamic shared memory: 2^12 x 16 bytes + 256 + 2^11 ints (a
+// kStdThreads threads; dynamic shared memory: 2^12 x 16 bytes + kRedBytes + 2^11 ints (a
 // D = 12 tile or a whole n <= 6 matrix, reduction slots, class slots of the
 // block fixed point).  Thread 0 keeps the claimed-ahead item in s_next (its own
 // slot: kept out of registers, which the tile needs) and hands it to the CTA
 // through s_work at the top of the loop.
 template <class A, bool kDec>
-__global__ void __launch_bounds__(256, 2) k_batch(const __grid_constant__ BatchParams bp) {
+__global__ void __launch_bounds__(kStdThreads, kOccLow) k_batch(const __grid_constant__ BatchParams bp) {
   using Store = typename A::Store;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned s_work, s_next;
@@ -221,18 +221,18 @@ __global__ void __launch_bounds__(256, 2) k_batch(const __grid_constant__ BatchP
 
 template <class A, bool kDec>
 cudaError_t launch_batch_t(const BatchParams& bp, int* grid_out, cudaStream_t s) {
-  const size_t smem = ((size_t)16 << 12) + 256 + (sizeof(int) << 11);
+  const size_t smem = ((size_t)16 << kStdTileBits) + kRedBytes + (sizeof(int) << (kStdTileBits - 1));
   auto kfn = k_batch<A, kDec>;
   cudaError_t e = ensure_smem_limit((const void*)kfn, smem);
   if (e != cudaSuccess) return e;
   int dev = 0, nsm = 0, per_sm = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, 256, smem)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, kStdThreads, smem)) != cudaSuccess) return e;
   long long grid = (long long)nsm * (per_sm > 0 ? per_sm : 1);
   if (grid > bp.total) grid = bp.total;
   if (grid_out) *grid_out = (int)grid;
-  kfn<<<(unsigned)grid, 256, smem, s>>>(bp);
+  kfn<<<(unsigned)grid, kStdThreads, smem, s>>>(bp);
   return cudaGetLastError();
 }
 

@@ -27,8 +27,9 @@ inline size_t class_slot_bytes(const PassDesc& pd) { return sizeof(int) << (pd.D
 // the instantiation for a pass's CTA size, occupancy and (block fixed point) role
 template <class A, bool kDec, int kRole>
 PassKernel pick_pass_kernel(const PassDesc& pd, int threads) {
-  if (threads > 256) return k_pass<A, kDec, 512, 1, kRole>;
-  return pd.min_blocks >= 3 ? k_pass<A, kDec, 256, 3, kRole> : k_pass<A, kDec, 256, 2, kRole>;
+  if (threads > kStdThreads) return k_pass<A, kDec, kBigThreads, 1, kRole>;
+  return pd.min_blocks >= kOccHigh ? k_pass<A, kDec, kStdThreads, kOccHigh, kRole>
+                                   : k_pass<A, kDec, kStdThreads, kOccLow, kRole>;
 }
 
 // the role of a complex128 block-fixed-point pass from its binary-point arrays
@@ -42,8 +43,9 @@ constexpr bool kClusterArith = std::is_same<A, FixedArith>::value || std::is_sam
 
 template <class A, bool kDec>
 cudaError_t launch_pass_cl_t(const PassDesc& pd, const PassArgs& args, long long ntiles_total, cudaStream_t s) {
-  const size_t smem = ((size_t)16 << (pd.D - 1)) + 256 + (kBlockFixed<A> ? class_slot_bytes(pd) : 0);
-  const size_t smem_max = ((size_t)16 << (kMaxTileBits - 1)) + 256 + (kBlockFixed<A> ? sizeof(int) << (kMaxTileBits - 1) : 0);
+  const size_t smem = ((size_t)16 << (pd.D - 1)) + kRedBytes + (kBlockFixed<A> ? class_slot_bytes(pd) : 0);
+  const size_t smem_max = ((size_t)16 << (kMaxTileBits - 1)) + kRedBytes +
+                          (kBlockFixed<A> ? sizeof(int) << (kMaxTileBits - 1) : 0);
   PassKernel kfn = k_pass_cl<A, kDec, 0>;
   if constexpr (A::kFixed) {
     switch (fixed_role(args)) {
@@ -57,7 +59,7 @@ cudaError_t launch_pass_cl_t(const PassDesc& pd, const PassArgs& args, long long
   if (e != cudaSuccess) return e;
   if (ntiles_total <= 0) return cudaSuccess;
   if (2 * ntiles_total > 0x7fffffffll) return cudaErrorInvalidValue;
-  kfn<<<(unsigned)(2 * ntiles_total), 256, smem, s>>>(pd, args);
+  kfn<<<(unsigned)(2 * ntiles_total), kClThreads, smem, s>>>(pd, args);
   return cudaGetLastError();
 }
 
@@ -69,9 +71,9 @@ cudaError_t launch_pass_t(const PassDesc& pd, const PassArgs& args, long long nt
   }
   const size_t vbytes = kBlockFixed<A> ? 16 : sizeof(typename A::V);
   // exchange area, reduction slots, class slots (block fixed point)
-  const size_t smem = ((size_t)1 << pd.D) * vbytes + 256 + (kBlockFixed<A> ? class_slot_bytes(pd) : 0);
-  const int dmax = threads > 256 ? kMaxTileBits : 12;
-  const size_t smem_max = ((size_t)1 << dmax) * vbytes + 256 + (kBlockFixed<A> ? sizeof(int) << (dmax - 1) : 0);
+  const size_t smem = ((size_t)1 << pd.D) * vbytes + kRedBytes + (kBlockFixed<A> ? class_slot_bytes(pd) : 0);
+  const int dmax = threads > kStdThreads ? kMaxTileBits : kStdTileBits;
+  const size_t smem_max = ((size_t)1 << dmax) * vbytes + kRedBytes + (kBlockFixed<A> ? sizeof(int) << (dmax - 1) : 0);
   PassKernel kfn = pick_pass_kernel<A, kDec, 0>(pd, threads);
   if constexpr (A::kFixed) {
     switch (fixed_role(args)) {
@@ -110,8 +112,8 @@ template <bool kDec>
 cudaError_t launch_pass_pipe_t(const PassDesc& pd, const PassArgs& args, int nsm, cudaStream_t s) {
   const int threads = 1 << (pd.D - kRegBits);
   // two tile buffers, reduction slots, class slots
-  const size_t smem = ((size_t)32 << pd.D) + 256 + class_slot_bytes(pd);
-  const size_t smem_max = ((size_t)32 << 12) + 256 + (sizeof(int) << 11);
+  const size_t smem = ((size_t)32 << pd.D) + kRedBytes + class_slot_bytes(pd);
+  const size_t smem_max = ((size_t)32 << kStdTileBits) + kRedBytes + (sizeof(int) << (kStdTileBits - 1));
   PassKernel kfn;
   switch (fixed_role(args)) {
     case kRoleIntIn: kfn = k_pass_pipe<kDec, kRoleIntIn>; break;

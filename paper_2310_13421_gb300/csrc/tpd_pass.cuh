@@ -183,7 +183,9 @@ __device__ __forceinline__ void shfl_level(typename A::V (&v)[kElems], int lbit,
 template <class A, bool kDec>
 __device__ __forceinline__ void stage_levels(typename A::V (&v)[kElems], const Stage& st, int lane) {
   if (st.npair >= 1) pair_level<A, kDec, 0, 1>(v);
-  if (st.npair >= 2) pair_level<A, kDec, 2, 3>(v);
+  if constexpr (kRegBits >= 4) {
+    if (st.npair >= 2) pair_level<A, kDec, 2, 3>(v);
+  }
   const int r0 = 2 * st.npair;
   for (int s = 0; s < st.nshfl; ++s) {
     const int lb = st.shfl_lane[s];
@@ -191,7 +193,9 @@ __device__ __forceinline__ void stage_levels(typename A::V (&v)[kElems], const S
       case 0: shfl_level<A, kDec, 0>(v, lb, lane); break;
       case 1: shfl_level<A, kDec, 1>(v, lb, lane); break;
       case 2: shfl_level<A, kDec, 2>(v, lb, lane); break;
-      default: shfl_level<A, kDec, 3>(v, lb, lane); break;
+      default:
+        if constexpr (kRegBits >= 4) shfl_level<A, kDec, 3>(v, lb, lane);
+        break;
     }
   }
 }
@@ -205,7 +209,7 @@ __device__ __forceinline__ void exchange(V (&v)[kElems], const PassDesc& pd, con
                                          const Stage& b, V* sm, int lane, int warp, bool sync_first) {
   if constexpr (kCl) {
     if (sync_first) cluster_sync();           // both CTAs have read the previous exchange
-    const int cb = b.warp[3];                 // >= 3: lanes hold tile bits 0..2
+    const int cb = b.warp[kClWarpBit];        // >= 3: lanes hold tile bits 0..2
     const int lowm = (1 << cb) - 1;
     auto squeeze = [&](int x) { return (x & lowm) | ((x >> 1) & ~lowm); };
     V* const mine = sm;
@@ -389,8 +393,13 @@ __device__ __forceinline__ void class_atomics(const T (&x)[kElems], int* slots, 
 template <class S, class T>
 __device__ __forceinline__ void class_atomics_any(int np, const T (&x)[kElems], int* slots, int ct, int c0, int c1,
                                                   int c2, int c3) {
-  if (np >= 2) class_atomics<2, S>(x, slots, ct, c0, c1, c2, c3);
-  else if (np == 1) class_atomics<1, S>(x, slots, ct, c0, c1, c2, c3);
+  if constexpr (kRegBits >= 4) {
+    if (np >= 2) {
+      class_atomics<2, S>(x, slots, ct, c0, c1, c2, c3);
+      return;
+    }
+  }
+  if (np >= 1) class_atomics<1, S>(x, slots, ct, c0, c1, c2, c3);
   else class_atomics<0, S>(x, slots, ct, c0, c1, c2, c3);
 }
 
@@ -527,9 +536,9 @@ __device__ __forceinline__ void flag_next(const PassDesc& pd, const PassArgs& ar
 }
 
 // Tile-wide reduction of the flags (OR) and of the range [lo, hi] of the
-// nonzero class slots, through red[0..16) / red[16..32) / red[32..48) (one
+// nonzero class slots, through red[0..32) / red[32..64) / red[64..96) (one
 // entry per warp; a two-CTA cluster writes its entries into both CTAs at the
-// 512-thread layout's warp index and meets at a cluster barrier).
+// one-CTA layout's warp index and meets at a cluster barrier).
 template <bool kCl>
 __device__ __forceinline__ void tile_reduce(int* red, int warp, int lane, int nwarps_total, int& tb, int& lo,
                                             int& hi) {
@@ -537,10 +546,10 @@ __device__ __forceinline__ void tile_reduce(int* red, int warp, int lane, int nw
   lo = (int)__reduce_min_sync(kFull, (unsigned)lo);
   hi = (int)__reduce_max_sync(kFull, (unsigned)hi);
   if (lane == 0) {
-    red[warp] = tb; red[16 + warp] = lo; red[32 + warp] = hi;
+    red[warp] = tb; red[32 + warp] = lo; red[64 + warp] = hi;
     if constexpr (kCl) {
       int* pr = peer_smem(red);
-      pr[warp] = tb; pr[16 + warp] = lo; pr[32 + warp] = hi;
+      pr[warp] = tb; pr[32 + warp] = lo; pr[64 + warp] = hi;
     }
   }
   if constexpr (kCl) cluster_sync();
@@ -548,8 +557,8 @@ __device__ __forceinline__ void tile_reduce(int* red, int warp, int lane, int nw
   // lane w reads warp w's entries; one warp-wide reduction each
   const bool in = lane < nwarps_total;
   tb = (int)__reduce_or_sync(kFull, in ? (unsigned)red[lane] : 0u);
-  lo = (int)__reduce_min_sync(kFull, in ? (unsigned)red[16 + lane] : 0x7fffffffu);
-  hi = (int)__reduce_max_sync(kFull, in ? (unsigned)red[32 + lane] : 0u);
+  lo = (int)__reduce_min_sync(kFull, in ? (unsigned)red[32 + lane] : 0x7fffffffu);
+  hi = (int)__reduce_max_sync(kFull, in ? (unsigned)red[64 + lane] : 0u);
 }
 
 // One complex128 tile of the block fixed point, in the role kRole (IEEE
@@ -768,11 +777,8 @@ __device__ __forceinline__ void fixed32_tile(const PassDesc& pd, const PassArgs&
 #pragma unroll
     for (int e = 0; e < kElems; ++e) nzw |= (__float_as_uint(raw[e].x) | __float_as_uint(raw[e].y)) << 1;
   }
-  const int tb = (__reduce_or_sync(kFull, nzw) != 0 ? 1 : 0) | (__any_sync(kFull, hmax == 255) ? 2 : 0);
-  if (lane == 0) red[warp] = tb;
-  __syncthreads();
-  int t = 0;
-  for (int w = 0; w < nwarps; ++w) t |= red[w];
+  int t = (nzw != 0 ? 1 : 0) | (hmax == 255 ? 2 : 0), hi_unused = 0;
+  tile_reduce<false>(red, warp, lane, nwarps, t, lo_unused, hi_unused);
   if (args.skip_zero && !(t & 1)) return;                // all +-0: the outputs are zero already
   if (t & 2) {                                           // Inf/NaN in the tile
     finish_tile<F32Arith, kDec>(pd, args, matp, raw, kDec ? pow2d(-pd.K) : pow2d(args.out_pow2) * args.out_mul,
@@ -832,7 +838,7 @@ __device__ __forceinline__ void pass_tile(const PassDesc& pd, const PassArgs& ar
   using Store = typename A::Store;
   static_assert(!(kCl && A::kFixed32), "two-CTA clusters serve complex128 tiles only");
   int* red = reinterpret_cast<int*>(smem + ((size_t)16 << (pd.D - (kCl ? 1 : 0))));
-  int* cls = red + 64;
+  int* cls = red + kRedInts;
   long long base = 0;
   int nbase = 0;
   uint32_t sbase = 0;
@@ -905,11 +911,11 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
 // Complex128 tiles of 2^13 elements as two-CTA clusters of 256 threads (see
 // the top of this file): grid = 2 x tiles, tile = cluster index.
 template <class A, bool kDec, int kRole = 0>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 2)
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kClThreads, 2)
     k_pass_cl(const __grid_constant__ PassDesc pd, const __grid_constant__ PassArgs args) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int tid = threadIdx.x, lane = tid & 31;
-  const int warp = (int)(cluster_rank() << 3) | (tid >> 5);   // the 512-thread layout's warp
+  const int warp = (int)(cluster_rank() << kClWarpBit) | (tid >> 5);   // the one-CTA layout's warp
   long long tile = (long long)(blockIdx.x >> 1);
   void* matp = args.mat;
   const int16_t* q_in = args.q_in;
@@ -977,7 +983,7 @@ __device__ __forceinline__ void prefetch_tile(const PassDesc& pd, const void* ma
 }
 
 template <bool kDec, int kRole>
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(kStdThreads, 1)
     k_pass_pipe(const __grid_constant__ PassDesc pd, const __grid_constant__ PassArgs args) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -985,7 +991,7 @@ __global__ void __launch_bounds__(256, 1)
   unsigned char* buf0 = smem;
   unsigned char* buf1 = smem + tb;
   int* red = reinterpret_cast<int*>(smem + 2 * tb);
-  int* cls = red + 64;
+  int* cls = red + kRedInts;
   long long tile = blockIdx.x;
   if (tile >= pd.ntiles) return;
   prefetch_tile(pd, args.mat, tile, buf0, lane, warp);

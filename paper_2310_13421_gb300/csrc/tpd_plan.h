@@ -28,19 +28,32 @@
 
 namespace tpd {
 
-constexpr int kRegBits = 4;                 // E = 16 elements per thread
+constexpr int kRegBits = 4;                 // E = 2^kRegBits elements per thread
 constexpr int kElems = 1 << kRegBits;
+constexpr int kRegSlots = 4;                // register-bit entries of a stage (those >= kRegBits unused, 0)
 constexpr int kLaneBits = 5;
 constexpr int kMinTileBits = kRegBits + kLaneBits;   // one warp
-constexpr int kMaxTileBits = 13;                      // 512 threads
+constexpr int kMaxTileBits = 13;
 constexpr int kMaxWarpBits = kMaxTileBits - kMinTileBits;
+constexpr int kStdTileBits = 12;                      // the default tile
+constexpr int kStdThreads = 1 << (kStdTileBits - kRegBits);   // threads of a default tile's CTA
+constexpr int kBigThreads = 1 << (kMaxTileBits - kRegBits);   // threads of a 2^13-element tile
+constexpr int kClThreads = kBigThreads / 2;                    // per CTA of a two-CTA cluster
+constexpr int kClWarpBit = kMaxWarpBits - 1;          // the warp bit that is the cluster rank
+// CTAs per SM the pass kernels are compiled for, a tile of up to 2^12
+// elements: kOccHigh (fewer registers per thread) or kOccLow
+constexpr int kOccHigh = kRegBits >= 4 ? 3 : 2;
+constexpr int kOccLow = kOccHigh - 1;
+// reduction slots of a CTA: 3 arrays of one int per warp (up to 32 warps)
+constexpr int kRedInts = 128;
+constexpr int kRedBytes = kRedInts * 4;
 constexpr int kMaxStages = 4;
 constexpr int kMaxQubits = 16;
 constexpr int kMaxRuns = 2 * kMaxQubits;
 constexpr int kMaxLevels = 6;
 
 struct Stage {
-  int8_t reg[kRegBits];      // tile bit of register-index bit i
+  int8_t reg[kRegSlots];     // tile bit of register-index bit i (i < kRegBits)
   int8_t lane[kLaneBits];    // tile bit of lane bit i
   int8_t warp[kMaxWarpBits]; // tile bit of warp bit i (D-9 of them)
   int8_t npair;              // in-register levels: reg bits (2p, 2p+1) = (column, row)

@@ -186,7 +186,7 @@ bool build_pass(int n, int b, int K, int D, int lf, double cs, PassDesc* pd, std
     for (int bit = 0; bit < D; ++bit)
       if (!used[bit]) warps.push_back(bit);
     std::sort(lanes.begin(), lanes.end());
-    for (int i = 0; i < kRegBits; ++i) st.reg[i] = (int8_t)regs[i];
+    for (int i = 0; i < kRegSlots; ++i) st.reg[i] = (int8_t)(i < kRegBits ? regs[i] : 0);
     for (int i = 0; i < kLaneBits; ++i) st.lane[i] = (int8_t)lanes[i];
     for (int i = 0; i < (int)warps.size(); ++i) st.warp[i] = (int8_t)warps[i];
     st.npair = (int8_t)ch.pairs.size();
@@ -372,7 +372,7 @@ bool build_plan(int n, int dtype, int precision, int tile_bits_opt, int max_leve
       if (pd.st[s].npair != 2 || pd.st[s].nshfl != 0) pairs_only = false;
     const bool two_c64 = pairs_only && (precision == 2 || pd.D < 12);
     const bool three = dtype == 1 && precision >= 2 && !two_c64;
-    pd.min_blocks = pd.D > 12 ? (dtype == 0 ? 2 : 1) : (three ? 3 : 2);
+    pd.min_blocks = pd.D > 12 ? (dtype == 0 ? 2 : 1) : (three ? kOccHigh : kOccLow);
   }
   return true;
 }
@@ -401,9 +401,14 @@ std::string describe_plan(const Plan& plan) {
     }
     for (int si = 0; si < pd.nstage; ++si) {
       const Stage& st = pd.st[si];
-      std::snprintf(buf, sizeof(buf), " | stage %d: pairs=%d shfl=%d reg=%d,%d,%d,%d lane=%d,%d,%d,%d,%d", si,
-                    st.npair, st.nshfl, st.reg[0], st.reg[1], st.reg[2], st.reg[3], st.lane[0], st.lane[1],
-                    st.lane[2], st.lane[3], st.lane[4]);
+      std::snprintf(buf, sizeof(buf), " | stage %d: pairs=%d shfl=%d reg=", si, st.npair, st.nshfl);
+      s += buf;
+      for (int i = 0; i < kRegBits; ++i) {
+        std::snprintf(buf, sizeof(buf), "%s%d", i ? "," : "", st.reg[i]);
+        s += buf;
+      }
+      std::snprintf(buf, sizeof(buf), " lane=%d,%d,%d,%d,%d", st.lane[0], st.lane[1], st.lane[2], st.lane[3],
+                    st.lane[4]);
       s += buf;
       s += " warp=";
       for (int i = 0; i < pd.D - kMinTileBits; ++i) {

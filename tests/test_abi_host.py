@@ -217,10 +217,18 @@ def _to_string_order(flat, n):
     return out
 
 
-@pytest.mark.parametrize("n,dtype,prec", [(5, 0, 0), (6, 0, 0), (7, 0, 0), (8, 0, 0), (7, 1, 0), (8, 1, 2),
-                                          (9, 0, 0), (9, 1, 3)])
+def _min_tile_bits(L):
+    # register bits of a thread (one stage's register list) plus five lane bits
+    return len(_parse(L.tpd_plan_describe(14, 0, L.options())[1])[0]["stages"][0]["reg"]) + 5
+
+
+@pytest.mark.parametrize("n,dtype,prec", [(4, 0, 0), (4, 1, 2), (5, 0, 0), (6, 0, 0), (7, 0, 0), (8, 0, 0),
+                                          (7, 1, 0), (8, 1, 2), (9, 0, 0), (9, 1, 3)])
 def test_plans_emulated_on_cpu_match_oracle(L, n, dtype, prec):
     npass, desc = L.tpd_plan_describe(n, dtype, L.options(precision=prec))
+    if 2 * n < _min_tile_bits(L):
+        assert npass == 0                     # the single-CTA small path
+        return
     passes = _parse(desc)
     assert len(passes) == npass
     assert sum(p["K"] for p in passes) == n
@@ -234,7 +242,7 @@ def test_plans_emulated_on_cpu_match_oracle(L, n, dtype, prec):
 def test_plans_exist_for_every_size(L, n):
     for dtype, prec in ((0, 0), (0, 1), (1, 0), (1, 2)):
         npass, desc = L.tpd_plan_describe(n, dtype, L.options(precision=prec))
-        if 2 * n < 9:
+        if 2 * n < _min_tile_bits(L):
             assert npass == 0
             continue
         passes = _parse(desc)
