@@ -203,17 +203,23 @@ def kernel_digest(csrc=None):
 
 
 def measured_traffic(n):
-    """Per-launch DRAM bytes of the pass kernel from the committed ncu summary,
-    if it was taken on the current kernel sources and the same matrix size."""
-    p = os.path.join(ROOT, "profiles", "traffic_n14_c128.json")
+    """Per-launch DRAM bytes of the complex128 fixed-point pass kernel at n
+    qubits, from the committed small-case ncu record (n = 13) scaled by the
+    elements a launch reads and writes (4^(n - 13)), if that record was taken
+    on the current kernel sources."""
+    p = os.path.join(ROOT, "profiles", "traffic_k_pass_fixed_n13.json")
     try:
         with open(p) as fh:
             d = json.load(fh)
     except (OSError, ValueError):
         return None
-    if d.get("kernel_digest") != kernel_digest() or d.get("qubits") != n:
+    m = d.get("captured_qubits")
+    if d.get("kernel_digest") != kernel_digest() or not isinstance(m, int) or n < m:
         return None
-    return d.get("bytes_per_launch")
+    per = d.get("bytes_per_launch_captured") or []
+    if not per:
+        return None
+    return float(np.mean(per)) * 4.0 ** (n - m)
 
 
 def time_decompose(tpd, L, torch, work, pristine, n, steps, warmup, precision, stream):

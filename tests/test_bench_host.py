@@ -37,13 +37,20 @@ def test_kernel_digest_ignores_comments_but_not_code(tmp_path):
 
 
 def test_traffic_record_used_only_for_its_kernels_and_size():
-    with open(os.path.join(ROOT, "profiles", "traffic_n14_c128.json")) as fh:
+    with open(os.path.join(ROOT, "profiles", "traffic_k_pass_fixed_n13.json")) as fh:
         rec = json.load(fh)
     current = rec["kernel_digest"] == bench.kernel_digest()
-    assert bench.measured_traffic(14) == (rec["bytes_per_launch"] if current else None)
-    assert bench.measured_traffic(13) is None
-    # DRAM traffic of a pass launch within 1 % of its algorithmic bytes (no re-reads)
-    assert abs(rec["bytes_per_launch"] / rec["algorithmic_bytes_per_launch"] - 1) < 0.01
+    mean = float(np.mean(rec["bytes_per_launch_captured"]))
+    assert bench.measured_traffic(14) == (4 * mean if current else None)
+    assert bench.measured_traffic(13) == (mean if current else None)
+    assert bench.measured_traffic(12) is None              # no scaling down from the captured size
+    # DRAM traffic of a pass launch near its algorithmic bytes (no re-reads):
+    # within 2 % on average, 5 % per launch (writes still in L2 when a launch
+    # ends are counted by the next one)
+    alg = rec["algorithmic_bytes_per_launch_captured"]
+    assert abs(mean / alg - 1) < 0.02
+    for b in rec["bytes_per_launch_captured"]:
+        assert abs(b / alg - 1) < 0.05
 
 
 def test_accuracy_rows_follow_the_rc_layout():
