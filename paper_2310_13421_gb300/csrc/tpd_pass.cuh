@@ -322,8 +322,8 @@ __device__ __forceinline__ void load_tile(const PassDesc& pd, const void* matp, 
 // components of its elements, so that its largest element lands below
 // 2^(62-K) and the 2^K-term sums of the pass are exact in int64; each output
 // is rounded once, to nearest even, when the pass stores it.  Components far
-// below their class's largest (more than 2^(9-K) binades for complex128,
-// 2^(38-K) for complex64) are truncated toward zero on loading, an error
+// below their class's largest (more than 9-K binades for complex128,
+// 38-K for complex64) are truncated toward zero on loading, an error
 // below 2^-(62-K) of that largest.  Elements of different X-masks never share
 // a binary point, so a weight's error is bounded by the magnitudes of its own
 // class, not by those of a large neighbour (a strong diagonal beside weak
@@ -536,7 +536,7 @@ __device__ __forceinline__ void flag_next(const PassDesc& pd, const PassArgs& ar
 }
 
 // Tile-wide reduction of the flags (OR) and of the range [lo, hi] of the
-// nonzero class slots, through red[0..32) / red[32..64) / red[64..96) (one
+// nonzero class slots, through red[0..S) / red[S..2S) / red[2S..3S), S = kRedStride (one
 // entry per warp; a two-CTA cluster writes its entries into both CTAs at the
 // one-CTA layout's warp index and meets at a cluster barrier).
 template <bool kCl>
@@ -546,10 +546,10 @@ __device__ __forceinline__ void tile_reduce(int* red, int warp, int lane, int nw
   lo = (int)__reduce_min_sync(kFull, (unsigned)lo);
   hi = (int)__reduce_max_sync(kFull, (unsigned)hi);
   if (lane == 0) {
-    red[warp] = tb; red[32 + warp] = lo; red[64 + warp] = hi;
+    red[warp] = tb; red[kRedStride + warp] = lo; red[2 * kRedStride + warp] = hi;
     if constexpr (kCl) {
       int* pr = peer_smem(red);
-      pr[warp] = tb; pr[32 + warp] = lo; pr[64 + warp] = hi;
+      pr[warp] = tb; pr[kRedStride + warp] = lo; pr[2 * kRedStride + warp] = hi;
     }
   }
   if constexpr (kCl) cluster_sync();
@@ -557,8 +557,8 @@ __device__ __forceinline__ void tile_reduce(int* red, int warp, int lane, int nw
   // lane w reads warp w's entries; one warp-wide reduction each
   const bool in = lane < nwarps_total;
   tb = (int)__reduce_or_sync(kFull, in ? (unsigned)red[lane] : 0u);
-  lo = (int)__reduce_min_sync(kFull, in ? (unsigned)red[32 + lane] : 0x7fffffffu);
-  hi = (int)__reduce_max_sync(kFull, in ? (unsigned)red[64 + lane] : 0u);
+  lo = (int)__reduce_min_sync(kFull, in ? (unsigned)red[kRedStride + lane] : 0x7fffffffu);
+  hi = (int)__reduce_max_sync(kFull, in ? (unsigned)red[2 * kRedStride + lane] : 0u);
 }
 
 // One complex128 tile of the block fixed point, in the role kRole (IEEE

@@ -44,8 +44,13 @@ constexpr int kClWarpBit = kMaxWarpBits - 1;          // the warp bit that is th
 // elements: kOccHigh (fewer registers per thread) or kOccLow
 constexpr int kOccHigh = kRegBits >= 4 ? 3 : 2;
 constexpr int kOccLow = kOccHigh - 1;
-// reduction slots of a CTA: 3 arrays of one int per warp (up to 32 warps)
-constexpr int kRedInts = 128;
+// Reduction slots of a CTA: one per warp of the largest tile for each of the
+// three tile-wide reductions, and as many spare.  Kept small: three
+// 2^12-element complex64 CTAs (64 KB each) must fit the 196 KB shared-memory
+// carve-out, which leaves the L1 room for their spilled registers (at 512
+// bytes they needed the 228 KB one: n = 15 compensated 20.55 -> 22.27 ms).
+constexpr int kRedStride = 1 << kMaxWarpBits;
+constexpr int kRedInts = 4 * kRedStride;
 constexpr int kRedBytes = kRedInts * 4;
 constexpr int kMaxStages = 4;
 constexpr int kMaxQubits = 16;
