@@ -177,8 +177,9 @@ def run_reference(args, world, rank):
 
 # ------------------------------------------------------------------ our arm
 
-KERNEL_SOURCES = ("tpd_pass.cuh", "tpd_arith.cuh", "tpd_plan.h", "tpd_launch.h", "tpd_planner.cpp",
-                  "tpd_kernels_impl.cuh", "tpd_kernels_fixed_dec.cu", "tpd_kernels_fixed_com.cu")
+KERNEL_SOURCES = ("tpd_pass.cuh", "tpd_arith.cuh", "tpd_plan.h", "tpd_shape.h", "tpd_launch.h", "tpd_planner.cpp",
+                  "tpd_kernels_impl.cuh", "tpd_kernels_fixed_dec.cu", "tpd_kernels_fixed_com.cu",
+                  "tpd_kernels_shapes_fixed.cu")
 
 
 def _code_only(text):

@@ -97,7 +97,12 @@ typedef struct {
                        2 = persistent CTAs that prefetch the next tile (complex128
                        block fixed point, single matrix, no zero skipping),
                        3 / 4 = one CTA per tile compiled for 2 / 3 CTAs per SM
-                       (tiles of up to 2^12 elements).
+                       (tiles of up to 2^12 elements),
+                       5 = the default form with every pass's tile layout read
+                       from its run-time descriptor (by default, passes whose
+                       layout is one of the library's compiled shapes run a
+                       kernel with that layout built in; both give identical
+                       results).
                        Batched calls: 0, 1, 3, 4 = one launch per (qubit count,
                        pass) over all matrices of that qubit count (the fastest
                        form measured on GB300); 2 = the whole batch in ONE

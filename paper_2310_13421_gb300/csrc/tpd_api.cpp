@@ -45,7 +45,7 @@ tpd_status check_options(int dtype, const tpd_options* opt, int* prec) {
   if (opt && opt->tile_bits != 0 && (opt->tile_bits < kMinTileBits || opt->tile_bits > kMaxTileBits))
     return TPD_ERR_INVALID_ARG;
   if (opt && (opt->max_levels < 0 || opt->max_levels > kMaxLevels)) return TPD_ERR_INVALID_ARG;
-  if (opt && (opt->variant < 0 || opt->variant > 4)) return TPD_ERR_INVALID_ARG;
+  if (opt && (opt->variant < 0 || opt->variant > 5)) return TPD_ERR_INVALID_ARG;
   *prec = p;
   return TPD_OK;
 }
@@ -252,6 +252,7 @@ tpd_status run_single(bool dec, int arith, void* mat, const Plan& plan, int skip
     PassDesc tuned = plan.pass[p];            // occupancy override (variants 3 and 4)
     if (tuned.D <= 12 && (variant == 3 || variant == 4)) tuned.min_blocks = variant == 3 ? kOccLow : kOccHigh;
     if (tuned.D > 12 && variant == 1) tuned.min_blocks = 1;   // one 512-thread CTA per tile
+    if (variant == 5) tuned.rt_layout = 1;    // layout read at run time
     return tuned;
   };
   // L2 chunking: the first F passes run chunk by chunk, each chunk (the

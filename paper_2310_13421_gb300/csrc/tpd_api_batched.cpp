@@ -247,6 +247,7 @@ tpd_status batched(bool dec, void* const* ptrs_dev, const int* ns_dev, const int
         PassDesc tuned = pd;                   // occupancy override (variants 3 and 4)
         if (pd.D <= 12 && (variants[n] == 3 || variants[n] == 4)) tuned.min_blocks = variants[n] == 3 ? kOccLow : kOccHigh;
         if (pd.D > 12 && variants[n] == 1) tuned.min_blocks = 1;   // one 512-thread CTA per tile
+        if (variants[n] == 5) tuned.rt_layout = 1;                 // layout read at run time
         if (launch_pass(arith, dec, tuned, a, pd.ntiles * hist[n], s) != cudaSuccess) return TPD_ERR_CUDA;
       }
       qbase += batched_q_bytes(plan, arith, hist[n]);

@@ -24,6 +24,21 @@ template <class A>
 constexpr bool kBlockFixed = A::kFixed || A::kFixed32;
 inline size_t class_slot_bytes(const PassDesc& pd) { return sizeof(int) << (pd.D - pd.K); }
 
+// The instantiation compiled for a pass's layout (tpd_shape.h), role and
+// occupancy, or nullptr: tpd_kernels_shapes_fixed.cu (complex128 block fixed
+// point), tpd_kernels_shapes_c64.cu (complex64).
+PassKernel shape_kernel_fixed(bool dec, int shape, int role, int min_blocks);
+PassKernel shape_kernel_c64(int arith, bool dec, int shape, int min_blocks);
+
+template <class A>
+constexpr int arith_code() {
+  if constexpr (std::is_same<A, FixedArith>::value) return kArithFixed;
+  else if constexpr (std::is_same<A, F64Arith>::value) return kArithF64;
+  else if constexpr (std::is_same<A, F32Arith>::value) return kArithF32;
+  else if constexpr (std::is_same<A, F32CArith>::value) return kArithF32C;
+  else return kArithF32Fixed;
+}
+
 // the instantiation for a pass's CTA size, occupancy and (block fixed point) role
 template <class A, bool kDec, int kRole>
 PassKernel pick_pass_kernel(const PassDesc& pd, int threads) {
@@ -74,13 +89,23 @@ cudaError_t launch_pass_t(const PassDesc& pd, const PassArgs& args, long long nt
   const size_t smem = ((size_t)1 << pd.D) * vbytes + kRedBytes + (kBlockFixed<A> ? class_slot_bytes(pd) : 0);
   const int dmax = threads > kStdThreads ? kMaxTileBits : kStdTileBits;
   const size_t smem_max = ((size_t)1 << dmax) * vbytes + kRedBytes + (kBlockFixed<A> ? sizeof(int) << (dmax - 1) : 0);
-  PassKernel kfn = pick_pass_kernel<A, kDec, 0>(pd, threads);
-  if constexpr (A::kFixed) {
-    switch (fixed_role(args)) {
-      case kRoleIntIn: kfn = pick_pass_kernel<A, kDec, kRoleIntIn>(pd, threads); break;
-      case kRoleIntOut: kfn = pick_pass_kernel<A, kDec, kRoleIntOut>(pd, threads); break;
-      case kRoleIntIn | kRoleIntOut: kfn = pick_pass_kernel<A, kDec, kRoleIntIn | kRoleIntOut>(pd, threads); break;
-      default: break;
+  PassKernel kfn = nullptr;
+  if (!pd.rt_layout && threads <= kStdThreads) {
+    const int shape = match_shape(pd);
+    if (shape >= 0) {
+      if constexpr (A::kFixed) kfn = shape_kernel_fixed(kDec, shape, fixed_role(args), pd.min_blocks);
+      else if constexpr (arith_code<A>() != kArithF64) kfn = shape_kernel_c64(arith_code<A>(), kDec, shape, pd.min_blocks);
+    }
+  }
+  if (kfn == nullptr) {
+    kfn = pick_pass_kernel<A, kDec, 0>(pd, threads);
+    if constexpr (A::kFixed) {
+      switch (fixed_role(args)) {
+        case kRoleIntIn: kfn = pick_pass_kernel<A, kDec, kRoleIntIn>(pd, threads); break;
+        case kRoleIntOut: kfn = pick_pass_kernel<A, kDec, kRoleIntOut>(pd, threads); break;
+        case kRoleIntIn | kRoleIntOut: kfn = pick_pass_kernel<A, kDec, kRoleIntIn | kRoleIntOut>(pd, threads); break;
+        default: break;
+      }
     }
   }
   cudaError_t e = ensure_smem_limit((const void*)kfn, smem_max);

@@ -25,6 +25,7 @@
 #include "tpd_arith.cuh"
 #include "tpd_launch.h"
 #include "tpd_plan.h"
+#include "tpd_shape.h"
 
 namespace tpd {
 
@@ -66,6 +67,76 @@ __device__ __forceinline__ T* peer_smem(T* p) {
   return cooperative_groups::this_cluster().map_shared_rank(p, cluster_rank() ^ 1u);
 }
 
+// -------------------------------------------------------------- pass geometry
+//
+// The device functions below read a pass's layout through a geometry object
+// `pd`: either the run-time PassDesc itself (any plan) or a GeoCT, which
+// gives the in-tile layout of a compiled shape (tpd_shape.h) as constants and
+// forwards the rest (global bit positions, tile-id and class-index weights)
+// to the run-time descriptor.  Both spell the same members (pd.D, pd.K,
+// pd.nstage, pd.st[s].reg[i], pd.cls_w[i], pd.gbit[i], ...), so one body of
+// code serves both; with a GeoCT, once the loops over stages and bits are
+// unrolled, every layout lookup is a constant.
+
+template <class Sh>
+struct StageCT {
+  struct Reg {
+    int s;
+    __device__ __forceinline__ int operator[](int i) const { return (int)((Sh::kReg >> (16 * s + 4 * i)) & 15); }
+  };
+  struct Lane {
+    int s;
+    __device__ __forceinline__ int operator[](int i) const { return (int)((Sh::kLane >> (20 * s + 4 * i)) & 15); }
+  };
+  struct Warp {
+    int s;
+    __device__ __forceinline__ int operator[](int i) const { return (int)((Sh::kWarp >> (16 * s + 4 * i)) & 15); }
+  };
+  struct ShflLane {
+    int s;
+    __device__ __forceinline__ int operator[](int j) const { return (int)((Sh::kShfl >> (12 * s + 3 * j)) & 7); }
+  };
+  Reg reg;
+  Lane lane;
+  Warp warp;
+  ShflLane shfl_lane;
+  int npair, nshfl;
+  __device__ __forceinline__ explicit StageCT(int s)
+      : reg{s}, lane{s}, warp{s}, shfl_lane{s}, npair((int)((Sh::kStg >> (8 * s)) & 3)),
+        nshfl((int)((Sh::kStg >> (8 * s + 2)) & 7)) {}
+};
+
+template <class Sh>
+struct GeoCT {
+  static constexpr int D = Sh::kD;
+  static constexpr int K = Sh::kK;
+  static constexpr int nstage = Sh::kNStage;
+  struct Cls {
+    __device__ __forceinline__ int operator[](int i) const { return 1 << (int)((Sh::kCls >> (4 * i)) & 15); }
+  };
+  struct Stages {
+    __device__ __forceinline__ StageCT<Sh> operator[](int s) const { return StageCT<Sh>(s); }
+  };
+  Cls cls_w;
+  Stages st;
+  const PassDesc& raw;
+  const int8_t (&gbit)[kMaxTileBits];
+  const int32_t (&next_w)[kMaxTileBits];
+  const uint32_t (&src_w)[kMaxTileBits];
+  const int32_t& nrest;
+  const int8_t (&rest_gbit)[2 * kMaxQubits];
+  const int64_t (&next_rest_w)[2 * kMaxQubits];
+  const uint32_t (&src_rest_w)[2 * kMaxQubits];
+  __device__ __forceinline__ explicit GeoCT(const PassDesc& p)
+      : raw(p), gbit(p.gbit), next_w(p.next_w), src_w(p.src_w), nrest(p.nrest), rest_gbit(p.rest_gbit),
+        next_rest_w(p.next_rest_w), src_rest_w(p.src_rest_w) {}
+};
+
+// the run-time descriptor behind a geometry
+__device__ __forceinline__ const PassDesc& raw_desc(const PassDesc& p) { return p; }
+template <class Sh>
+__device__ __forceinline__ const PassDesc& raw_desc(const GeoCT<Sh>& g) { return g.raw; }
+
 // Loads of data a pass reads.  kCg = false: the read-only path (ld.global.nc),
 // valid when nothing in the same launch writes the data; kCg = true: loads
 // cached in L2 only (ld.global.cg), for the persistent batched kernel whose
@@ -82,29 +153,35 @@ __device__ __forceinline__ double pow2d(int e) {
   return __longlong_as_double((long long)(1023 + e) << 52);
 }
 
-__device__ __forceinline__ long long thread_goff(const PassDesc& pd, const Stage& st, int lane, int warp) {
+template <class G, class S>
+__device__ __forceinline__ long long thread_goff(const G& pd, const S& st, int lane, int warp) {
   long long g = 0;
 #pragma unroll
   for (int i = 0; i < kLaneBits; ++i)
     if ((lane >> i) & 1) g += 1ll << pd.gbit[st.lane[i]];
+#pragma unroll
   for (int i = 0; i < pd.D - kMinTileBits; ++i)
     if ((warp >> i) & 1) g += 1ll << pd.gbit[st.warp[i]];
   return g;
 }
 
-__device__ __forceinline__ int thread_sidx(const PassDesc& pd, const Stage& st, int lane, int warp) {
+template <class G, class S>
+__device__ __forceinline__ int thread_sidx(const G& pd, const S& st, int lane, int warp) {
   int s = 0;
 #pragma unroll
   for (int i = 0; i < kLaneBits; ++i) s |= ((lane >> i) & 1) << st.lane[i];
+#pragma unroll
   for (int i = 0; i < pd.D - kMinTileBits; ++i) s |= ((warp >> i) & 1) << st.warp[i];
   return s;
 }
 
-__device__ __forceinline__ int thread_next(const PassDesc& pd, const Stage& st, int lane, int warp) {
+template <class G, class S>
+__device__ __forceinline__ int thread_next(const G& pd, const S& st, int lane, int warp) {
   int s = 0;
 #pragma unroll
   for (int i = 0; i < kLaneBits; ++i)
     if ((lane >> i) & 1) s += pd.next_w[st.lane[i]];
+#pragma unroll
   for (int i = 0; i < pd.D - kMinTileBits; ++i)
     if ((warp >> i) & 1) s += pd.next_w[st.warp[i]];
   return s;
@@ -180,13 +257,14 @@ __device__ __forceinline__ void shfl_level(typename A::V (&v)[kElems], int lbit,
   }
 }
 
-template <class A, bool kDec>
-__device__ __forceinline__ void stage_levels(typename A::V (&v)[kElems], const Stage& st, int lane) {
+template <class A, bool kDec, class S>
+__device__ __forceinline__ void stage_levels(typename A::V (&v)[kElems], const S& st, int lane) {
   if (st.npair >= 1) pair_level<A, kDec, 0, 1>(v);
   if constexpr (kRegBits >= 4) {
     if (st.npair >= 2) pair_level<A, kDec, 2, 3>(v);
   }
   const int r0 = 2 * st.npair;
+#pragma unroll
   for (int s = 0; s < st.nshfl; ++s) {
     const int lb = st.shfl_lane[s];
     switch (r0 + s) {
@@ -204,9 +282,9 @@ __device__ __forceinline__ void stage_levels(typename A::V (&v)[kElems], const S
 // tile is split over a two-CTA cluster (see above): an element goes to the
 // CTA whose rank equals its tile bit on b's highest warp bit, at its tile
 // index with that bit removed.
-template <bool kCl = false, class V>
-__device__ __forceinline__ void exchange(V (&v)[kElems], const PassDesc& pd, const Stage& a,
-                                         const Stage& b, V* sm, int lane, int warp, bool sync_first) {
+template <bool kCl = false, class V, class G, class S1, class S2>
+__device__ __forceinline__ void exchange(V (&v)[kElems], const G& pd, const S1& a, const S2& b, V* sm, int lane,
+                                         int warp, bool sync_first) {
   if constexpr (kCl) {
     if (sync_first) cluster_sync();           // both CTAs have read the previous exchange
     const int cb = b.warp[kClWarpBit];        // >= 3: lanes hold tile bits 0..2
@@ -254,8 +332,8 @@ __device__ __forceinline__ void exchange(V (&v)[kElems], const PassDesc& pd, con
 }
 
 // Stages, rounding and the in-place store, for arithmetic A on loaded data.
-template <class A, bool kDec, bool kCl = false, class Raw>
-__device__ __forceinline__ void finish_tile(const PassDesc& pd, const PassArgs& args, void* matp,
+template <class A, bool kDec, bool kCl = false, class G, class Raw>
+__device__ __forceinline__ void finish_tile(const G& pd, const PassArgs& args, void* matp,
                                             const Raw (&raw)[kElems], double mul, long long base,
                                             int nbase, unsigned char* smem, int lane, int warp) {
   using V = typename A::V;
@@ -264,11 +342,12 @@ __device__ __forceinline__ void finish_tile(const PassDesc& pd, const PassArgs& 
 #pragma unroll
   for (int e = 0; e < kElems; ++e) v[e] = A::load(raw[e]);
   V* sm = reinterpret_cast<V*>(smem);
+#pragma unroll
   for (int s = 0; s < pd.nstage; ++s) {
     if (s > 0) exchange<kCl>(v, pd, pd.st[s - 1], pd.st[s], sm, lane, warp, s > 1);
     stage_levels<A, kDec>(v, pd.st[s], lane);
   }
-  const Stage& sl = pd.st[pd.nstage - 1];
+  const auto& sl = pd.st[pd.nstage - 1];
   Store* mat = reinterpret_cast<Store*>(matp);
   const uint32_t g = (uint32_t)base + (uint32_t)thread_goff(pd, sl, lane, warp);
   const uint32_t w0 = 1u << pd.gbit[sl.reg[0]], w1 = 1u << pd.gbit[sl.reg[1]];
@@ -299,10 +378,10 @@ __device__ __forceinline__ void finish_tile(const PassDesc& pd, const PassArgs& 
   }
 }
 
-template <bool kCg = false, class Store>
-__device__ __forceinline__ void load_tile(const PassDesc& pd, const void* matp, long long base, int lane, int warp,
+template <bool kCg = false, class G, class Store>
+__device__ __forceinline__ void load_tile(const G& pd, const void* matp, long long base, int lane, int warp,
                                           Store (&raw)[kElems]) {
-  const Stage& s0 = pd.st[0];
+  const auto& s0 = pd.st[0];
   const Store* mat = reinterpret_cast<const Store*>(matp);
   // element indices in 32 bits: a matrix has at most 4^16 = 2^32 elements
   const uint32_t g = (uint32_t)base + (uint32_t)thread_goff(pd, s0, lane, warp);
@@ -334,11 +413,13 @@ __device__ __forceinline__ void load_tile(const PassDesc& pd, const void* matp, 
 // matrices give exactly real weights.
 
 // Class of a thread's register 0 in stage st: XOR of its lane and warp bits' class bits.
-__device__ __forceinline__ int cls_thread(const PassDesc& pd, const Stage& st, int lane, int warp) {
+template <class G, class S>
+__device__ __forceinline__ int cls_thread(const G& pd, const S& st, int lane, int warp) {
   int c = 0;
 #pragma unroll
   for (int i = 0; i < kLaneBits; ++i)
     if ((lane >> i) & 1) c ^= pd.cls_w[st.lane[i]];
+#pragma unroll
   for (int i = 0; i < pd.D - kMinTileBits; ++i)
     if ((warp >> i) & 1) c ^= pd.cls_w[st.warp[i]];
   return c;
@@ -405,10 +486,10 @@ __device__ __forceinline__ void class_atomics_any(int np, const T (&x)[kElems], 
 
 // Returns the largest exponent field of the thread's elements, and in lo
 // the smallest nonzero one (0x7fffffff if none).
-template <class S, class Raw, class ExpOf>
-__device__ __forceinline__ uint32_t class_max(const PassDesc& pd, const Raw (&raw)[kElems], int* slots, int lane,
+template <class S, class G, class Raw, class ExpOf>
+__device__ __forceinline__ uint32_t class_max(const G& pd, const Raw (&raw)[kElems], int* slots, int lane,
                                               int warp, ExpOf exp_of, int& lo) {
-  const Stage& s0 = pd.st[0];
+  const auto& s0 = pd.st[0];
   const int ct = cls_thread(pd, s0, lane, warp);
   const int c0 = pd.cls_w[s0.reg[0]], c1 = pd.cls_w[s0.reg[1]], c2 = pd.cls_w[s0.reg[2]],
             c3 = pd.cls_w[s0.reg[3]];
@@ -434,11 +515,13 @@ __device__ __forceinline__ uint32_t exp_f32(const float2& x) {
 
 // Source-class index (previous pass's binary-point array) of a thread's
 // register 0 in stage st: XOR of its lane and warp bits' contributions.
-__device__ __forceinline__ uint32_t src_thread(const PassDesc& pd, const Stage& st, int lane, int warp) {
+template <class G, class S>
+__device__ __forceinline__ uint32_t src_thread(const G& pd, const S& st, int lane, int warp) {
   uint32_t c = 0;
 #pragma unroll
   for (int i = 0; i < kLaneBits; ++i)
     if ((lane >> i) & 1) c ^= pd.src_w[st.lane[i]];
+#pragma unroll
   for (int i = 0; i < pd.D - kMinTileBits; ++i)
     if ((warp >> i) & 1) c ^= pd.src_w[st.warp[i]];
   return c;
@@ -501,10 +584,10 @@ __device__ __noinline__ void ieee_tile(const PassDesc& pd, const PassArgs& args,
 }
 
 // The tile's elements in the stage-0 mapping from a shared-memory copy.
-template <class Store>
-__device__ __forceinline__ void load_tile_smem(const PassDesc& pd, const unsigned char* buf, int lane, int warp,
+template <class G, class Store>
+__device__ __forceinline__ void load_tile_smem(const G& pd, const unsigned char* buf, int lane, int warp,
                                                Store (&raw)[kElems]) {
-  const Stage& s0 = pd.st[0];
+  const auto& s0 = pd.st[0];
   const Store* b = reinterpret_cast<const Store*>(buf);
   const int t = thread_sidx(pd, s0, lane, warp);
   const int w0 = 1 << s0.reg[0], w1 = 1 << s0.reg[1], w2 = 1 << s0.reg[2], w3 = 1 << s0.reg[3];
@@ -513,10 +596,10 @@ __device__ __forceinline__ void load_tile_smem(const PassDesc& pd, const unsigne
 }
 
 // Flags of the next pass's tiles that receive a nonzero (zero skipping).
-template <class NonZero>
-__device__ __forceinline__ void flag_next(const PassDesc& pd, const PassArgs& args, int nbase, int lane, int warp,
+template <class G, class NonZero>
+__device__ __forceinline__ void flag_next(const G& pd, const PassArgs& args, int nbase, int lane, int warp,
                                           NonZero nz_of) {
-  const Stage& sl = pd.st[pd.nstage - 1];
+  const auto& sl = pd.st[pd.nstage - 1];
   const int nt = nbase + thread_next(pd, sl, lane, warp);
   const int n0 = pd.next_w[sl.reg[0]], n1 = pd.next_w[sl.reg[1]], n2 = pd.next_w[sl.reg[2]],
             n3 = pd.next_w[sl.reg[3]];
@@ -577,8 +660,8 @@ __device__ __forceinline__ void tile_reduce(int* red, int warp, int lane, int nw
 // K: every element shifts right by at least K bits, toward zero, after which
 // the 2^K-term sums stay below 2^62), 0 for a class whose sources are all zero.
 
-template <bool kDec, int kRole, bool kCg = false, bool kCl = false>
-__device__ __forceinline__ void fixed_tile(const PassDesc& pd, const PassArgs& args, void* matp, const int16_t* q_in,
+template <bool kDec, int kRole, bool kCg = false, bool kCl = false, class G>
+__device__ __forceinline__ void fixed_tile(const G& pd, const PassArgs& args, void* matp, const int16_t* q_in,
                                            int16_t* q_out, long long tile, long long base, uint32_t sbase,
                                            int nbase, const unsigned char* inbuf, unsigned char* xbuf, int* red,
                                            int* cls, int lane, int warp) {
@@ -590,7 +673,7 @@ __device__ __forceinline__ void fixed_tile(const PassDesc& pd, const PassArgs& a
   const int ncls = 1 << (pd.D - pd.K);
   for (int i = threadIdx.x; i < ncls; i += nthr) cls[i] = 0;
   int slot_lo, slot_hi;                                  // range of the tile's nonzero class slots
-  const Stage& s0 = pd.st[0];
+  const auto& s0 = pd.st[0];
   const int ct = cls_thread(pd, s0, lane, warp);
   const int c0 = pd.cls_w[s0.reg[0]], c1 = pd.cls_w[s0.reg[1]], c2 = pd.cls_w[s0.reg[2]],
             c3 = pd.cls_w[s0.reg[3]];
@@ -619,7 +702,8 @@ __device__ __forceinline__ void fixed_tile(const PassDesc& pd, const PassArgs& a
     slot_lo = lo;
     slot_hi = hi;
     if ((args.skip_zero && !(tb & 1)) || (tb & 2)) {
-      if (tb & 2) ieee_tile<kDec, kCg, kCl>(pd, args, matp, q_in, q_out, tile, base, sbase, nbase, xbuf, lane, warp);
+      if (tb & 2)
+        ieee_tile<kDec, kCg, kCl>(raw_desc(pd), args, matp, q_in, q_out, tile, base, sbase, nbase, xbuf, lane, warp);
       return;                                            // (else all +-0: the outputs are zero already)
     }
     if constexpr (kCl) {
@@ -664,7 +748,7 @@ __device__ __forceinline__ void fixed_tile(const PassDesc& pd, const PassArgs& a
     slot_lo = lo;
     slot_hi = hi;
     if (tb & 2) {
-      ieee_tile<kDec, kCg, kCl>(pd, args, matp, q_in, q_out, tile, base, sbase, nbase, xbuf, lane, warp);
+      ieee_tile<kDec, kCg, kCl>(raw_desc(pd), args, matp, q_in, q_out, tile, base, sbase, nbase, xbuf, lane, warp);
       return;
     }
     if (args.skip_zero && !(tb & 1)) return;             // every source class was zero
@@ -708,13 +792,14 @@ __device__ __forceinline__ void fixed_tile(const PassDesc& pd, const PassArgs& a
 
   // ---- the pass's levels, exact
   V* sm = reinterpret_cast<V*>(xbuf);
+#pragma unroll
   for (int s = 0; s < pd.nstage; ++s) {
     if (s > 0) exchange<kCl>(v, pd, pd.st[s - 1], pd.st[s], sm, lane, warp, s > 1);
     stage_levels<FixedArith, kDec>(v, pd.st[s], lane);
   }
 
   // ---- store in place: int64 sums, or rounded once
-  const Stage& sl = pd.st[pd.nstage - 1];
+  const auto& sl = pd.st[pd.nstage - 1];
   const uint32_t g = (uint32_t)base + (uint32_t)thread_goff(pd, sl, lane, warp);
   const uint32_t w0 = 1u << pd.gbit[sl.reg[0]], w1 = 1u << pd.gbit[sl.reg[1]];
   const uint32_t w2 = 1u << pd.gbit[sl.reg[2]], w3 = 1u << pd.gbit[sl.reg[3]];
@@ -760,8 +845,8 @@ __device__ __forceinline__ void fixed_tile(const PassDesc& pd, const PassArgs& a
 // largest lands below 2^(62-K), the sums are exact in int64, and every output
 // is rounded to float once (RNE).  Tiles meeting an Inf or NaN run the IEEE
 // float butterfly instead.
-template <bool kDec, bool kCg>
-__device__ __forceinline__ void fixed32_tile(const PassDesc& pd, const PassArgs& args, void* matp, long long base,
+template <bool kDec, bool kCg, class G>
+__device__ __forceinline__ void fixed32_tile(const G& pd, const PassArgs& args, void* matp, long long base,
                                              int nbase, unsigned char* smem, int* red, int* cls, int lane, int warp) {
   using V = Fixed32Arith::V;
   const int nthr = blockDim.x, nwarps = nthr >> 5;
@@ -787,7 +872,7 @@ __device__ __forceinline__ void fixed32_tile(const PassDesc& pd, const PassArgs&
   }
   V v[kElems];
   {
-    const Stage& s0 = pd.st[0];
+    const auto& s0 = pd.st[0];
     const int ct = cls_thread(pd, s0, lane, warp);
     const int c0 = pd.cls_w[s0.reg[0]], c1 = pd.cls_w[s0.reg[1]], c2 = pd.cls_w[s0.reg[2]],
               c3 = pd.cls_w[s0.reg[3]];
@@ -799,6 +884,7 @@ __device__ __forceinline__ void fixed32_tile(const PassDesc& pd, const PassArgs&
     }
   }
   V* sm = reinterpret_cast<V*>(smem);
+#pragma unroll
   for (int s = 0; s < pd.nstage; ++s) {
     if (s > 0) exchange(v, pd, pd.st[s - 1], pd.st[s], sm, lane, warp, s > 1);
     stage_levels<Fixed32Arith, kDec>(v, pd.st[s], lane);
@@ -807,7 +893,7 @@ __device__ __forceinline__ void fixed32_tile(const PassDesc& pd, const PassArgs&
   // 2^out_pow2 for a composition's scale
   const int tbase = 188 - pd.K + (kDec ? pd.K : 0) - args.out_pow2;
   const bool resid = args.out_mul != 1.0;
-  const Stage& sl = pd.st[pd.nstage - 1];
+  const auto& sl = pd.st[pd.nstage - 1];
   float2* mat = reinterpret_cast<float2*>(matp);
   const uint32_t g = (uint32_t)base + (uint32_t)thread_goff(pd, sl, lane, warp);
   const uint32_t w0 = 1u << pd.gbit[sl.reg[0]], w1 = 1u << pd.gbit[sl.reg[1]];
@@ -832,8 +918,8 @@ __device__ __forceinline__ void fixed32_tile(const PassDesc& pd, const PassArgs&
 // load / levels / store.  smem: the exchange area (2^D x 16 bytes; half of it
 // per CTA of a two-CTA cluster), 64 ints of reduction slots, then (block fixed
 // point) 2^(D-K) class slots.
-template <class A, bool kDec, int kRole, bool kCg, bool kCl = false>
-__device__ __forceinline__ void pass_tile(const PassDesc& pd, const PassArgs& args, void* matp, const int16_t* q_in,
+template <class A, bool kDec, int kRole, bool kCg, bool kCl = false, class G>
+__device__ __forceinline__ void pass_tile(const G& pd, const PassArgs& args, void* matp, const int16_t* q_in,
                                           int16_t* q_out, long long tile, unsigned char* smem, int lane, int warp) {
   using Store = typename A::Store;
   static_assert(!(kCl && A::kFixed32), "two-CTA clusters serve complex128 tiles only");
@@ -878,7 +964,9 @@ __device__ __forceinline__ void pass_tile(const PassDesc& pd, const PassArgs& ar
 // element tiles run 512-thread CTAs.
 // kMinBlocks: CTAs of kThreads the compiler must fit on one SM (register
 // budget); the planner picks it per pass.
-template <class A, bool kDec, int kThreads, int kMinBlocks, int kRole = 0>
+// kShape: a compiled layout (tpd_shape.h) the launcher has matched to pd, or
+// -1 (the layout read from pd at run time).
+template <class A, bool kDec, int kThreads, int kMinBlocks, int kRole = 0, int kShape = -1>
 __global__ void __launch_bounds__(kThreads, kMinBlocks)
     k_pass(const __grid_constant__ PassDesc pd, const __grid_constant__ PassArgs args) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -905,7 +993,13 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
   if (tile >= pd.ntiles) return;
   if (args.flags_in != nullptr && args.flags_in[tile] == 0) return;
   if (args.need != nullptr && args.need[tile] == 0) return;
-  pass_tile<A, kDec, kRole, false>(pd, args, matp, q_in, q_out, tile, smem, lane, warp);
+  if constexpr (kShape < 0) {
+    pass_tile<A, kDec, kRole, false>(pd, args, matp, q_in, q_out, tile, smem, lane, warp);
+  } else {
+    static_assert(ShapeT<kShape>::kD <= kStdTileBits && (1 << (ShapeT<kShape>::kD - kRegBits)) <= kThreads,
+                  "compiled shapes are tiles of one CTA");
+    pass_tile<A, kDec, kRole, false>(GeoCT<ShapeT<kShape>>(pd), args, matp, q_in, q_out, tile, smem, lane, warp);
+  }
 }
 
 // Complex128 tiles of 2^13 elements as two-CTA clusters of 256 threads (see

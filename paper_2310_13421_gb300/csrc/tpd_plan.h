@@ -86,6 +86,8 @@ struct PassDesc {
   int64_t next_rest_w[2 * kMaxQubits];
   int32_t min_blocks;        // CTAs per SM the pass kernel is compiled for (2 or 3); D = 13: 1 = one
                              // CTA of 512 threads, 2 = a two-CTA cluster of 256 (complex128)
+  int32_t rt_layout;         // 1: run the kernel that reads the layout from this descriptor even
+                             // where a compiled shape (tpd_shape.h) matches it
   // Block fixed point: the *class* of a tile position.  A pass only ever adds
   // elements that agree on every passenger bit and on x_j = r_j xor c_j of
   // each of its levels j (Eq. 4 adds a00 to a11 and a01 to a10, and both

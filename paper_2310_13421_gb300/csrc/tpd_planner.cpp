@@ -1,6 +1,7 @@
 // Host planner: splits the n qubit levels into passes and lays out each pass's
 // tile and stages (see tpd_plan.h).
 #include "tpd_planner.h"
+#include "tpd_shape.h"
 
 #include <algorithm>
 #include <cstdio>
@@ -399,6 +400,9 @@ std::string describe_plan(const Plan& plan) {
       std::snprintf(buf, sizeof(buf), "%s%d", i ? "," : "", pd.cls_w[i]);
       s += buf;
     }
+    // the compiled tile layout (tpd_shape.h) this pass's layout equals, or -1
+    std::snprintf(buf, sizeof(buf), " shape=%d", match_shape(pd));
+    s += buf;
     for (int si = 0; si < pd.nstage; ++si) {
       const Stage& st = pd.st[si];
       std::snprintf(buf, sizeof(buf), " | stage %d: pairs=%d shfl=%d reg=", si, st.npair, st.nshfl);
