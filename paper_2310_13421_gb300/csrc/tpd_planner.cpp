@@ -361,17 +361,16 @@ bool build_plan(int n, int dtype, int precision, int tile_bits_opt, int max_leve
     // 2^13-element complex128 tiles: a two-CTA cluster of 256 threads
     // (min_blocks 2); other 2^13 tiles: one CTA of 512 threads (1)
     // Compensated and fixed-point complex64 (127-128 registers at two CTAs per
-    // SM) run faster at three despite a few spilled registers (n = 15:
-    // 22.34 -> 21.69 ms and 38.18 -> 37.34 ms), except in passes built only
-    // of stages with two in-register levels each: compensated ones keep two
-    // (n = 15 passes 2-3: 5.57 / 5.61 -> 5.43 / 5.50 ms; n = 14 passes 2-3:
-    // 1.41 / 1.41 -> 1.35 / 1.36 ms), fixed-point ones two on 2^11-element
-    // tiles only (n = 15 pass 3: 8.00 -> 7.68 ms; on 2^12 tiles, n = 14
-    // passes 2-3, three wins: 1.85 / 1.60 against 2.23 / 1.98 ms).
+    // SM) run faster at three: the compensated passes compiled for their tile
+    // layout (tpd_shape.h) fit 80 registers without spills (n = 15: 14.90 ->
+    // 13.17 ms, n = 14: 3.31 -> 2.88 ms against two CTAs in the passes made
+    // only of two-level in-register stages); the fixed-point ones keep two on
+    // 2^11-element tiles only (n = 15 pass 3: 8.00 -> 7.68 ms; on 2^12 tiles,
+    // n = 14 passes 2-3, three wins: 1.85 / 1.60 against 2.23 / 1.98 ms).
     bool pairs_only = pd.nstage > 1;
     for (int s = 0; s < pd.nstage; ++s)
       if (pd.st[s].npair != 2 || pd.st[s].nshfl != 0) pairs_only = false;
-    const bool two_c64 = pairs_only && (precision == 2 || pd.D < 12);
+    const bool two_c64 = pairs_only && precision == 3 && pd.D < 12;
     const bool three = dtype == 1 && precision >= 2 && !two_c64;
     pd.min_blocks = pd.D > 12 ? (dtype == 0 ? 2 : 1) : (three ? kOccHigh : kOccLow);
   }

@@ -278,22 +278,22 @@ def test_pass_occupancy_choices(L):
     """CTAs per SM per pass: complex128 fixed point two (its passes convert
     both ways), a 2^13-element complex128 tile a two-CTA cluster (2), other 2^13
     tiles one CTA of 512 threads (1); compensated and fixed-point complex64
-    three, except in passes made only of two-level in-register stages: two
-    for the compensated form, and for the fixed point on tiles below 2^12."""
+    three, except the fixed point's passes made only of two-level
+    in-register stages on tiles below 2^12: two."""
     def ctas(n, dtype, prec):
         return [p["ctas"] for p in _parse(L.tpd_plan_describe(n, dtype, L.options(precision=prec))[1])]
     assert ctas(14, 0, 0) == [2, 2, 2]
     assert ctas(15, 0, 0) == [2, 2, 2]
     assert ctas(14, 0, 1) == [2, 2, 2]
-    assert ctas(15, 1, 2) == [3, 2, 2, 3]
+    assert ctas(15, 1, 2) == [3, 3, 3, 3]
     assert ctas(15, 1, 3) == [3, 1, 2]
     assert ctas(14, 1, 3) == [3, 3, 3]
-    assert ctas(14, 1, 2) == [3, 2, 2]
+    assert ctas(14, 1, 2) == [3, 3, 3]
     assert ctas(14, 1, 1) == [2] * len(ctas(14, 1, 1))
     for n, dtype, prec in [(14, 1, 2), (15, 1, 2), (14, 1, 3), (15, 1, 3), (13, 1, 2)]:
         for p in _parse(L.tpd_plan_describe(n, dtype, L.options(precision=prec))[1]):
             pairs_only = len(p["stages"]) > 1 and all(s["npair"] == 2 and s["nshfl"] == 0 for s in p["stages"])
-            two = pairs_only and (prec == 2 or p["D"] < 12)
+            two = pairs_only and prec == 3 and p["D"] < 12
             assert p["ctas"] == (1 if p["D"] > 12 else 2 if two else 3)
 
 
