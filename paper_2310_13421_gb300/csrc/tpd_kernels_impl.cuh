@@ -27,6 +27,7 @@ inline size_t class_slot_bytes(const PassDesc& pd) { return sizeof(int) << (pd.D
 // The instantiation compiled for a pass's layout (tpd_shape.h), role and
 // occupancy, or nullptr: tpd_kernels_shapes_fixed.cu (complex128 block fixed
 // point), tpd_kernels_shapes_c64.cu (complex64).
+// min_blocks: the pass's CTAs per SM (1: one CTA of 512 threads on a 2^13-element tile).
 PassKernel shape_kernel_fixed(bool dec, int shape, int role, int min_blocks);
 PassKernel shape_kernel_c64(int arith, bool dec, int shape, int min_blocks);
 
@@ -90,7 +91,7 @@ cudaError_t launch_pass_t(const PassDesc& pd, const PassArgs& args, long long nt
   const int dmax = threads > kStdThreads ? kMaxTileBits : kStdTileBits;
   const size_t smem_max = ((size_t)1 << dmax) * vbytes + kRedBytes + (kBlockFixed<A> ? sizeof(int) << (dmax - 1) : 0);
   PassKernel kfn = nullptr;
-  if (!pd.rt_layout && threads <= kStdThreads) {
+  if (!pd.rt_layout) {
     const int shape = match_shape(pd);
     if (shape >= 0) {
       if constexpr (A::kFixed) kfn = shape_kernel_fixed(kDec, shape, fixed_role(args), pd.min_blocks);

@@ -26,12 +26,16 @@ PassKernel c64_table(int shape) {
 }  // namespace
 
 PassKernel shape_kernel_f32(int shape, int min_blocks);
+PassKernel shape_kernel_fx32(int shape, int min_blocks);
 
 PassKernel shape_kernel_c64(int arith, bool dec, int shape, int min_blocks) {
   if (!dec) return nullptr;
-  if (arith == kArithF32C)
+  if (arith == kArithF32C) {
+    if (shape == kShapeMid5D13) return nullptr;
     return min_blocks == kOccHigh ? c64_table<F32CArith, kOccHigh>(shape) : c64_table<F32CArith, kOccLow>(shape);
+  }
   if (arith == kArithF32) return shape_kernel_f32(shape, min_blocks);
+  if (arith == kArithF32Fixed) return shape_kernel_fx32(shape, min_blocks);
   return nullptr;
 }
 

@@ -20,6 +20,8 @@ PassKernel f32_table(int shape) {
 }  // namespace
 
 PassKernel shape_kernel_f32(int shape, int min_blocks) {
+  if (shape == kShapeMid5D13)
+    return min_blocks == 1 ? k_pass<F32Arith, true, kBigThreads, 1, 0, kShapeMid5D13> : nullptr;
   return min_blocks == kOccHigh ? f32_table<kOccHigh>(shape) : f32_table<kOccLow>(shape);
 }
 

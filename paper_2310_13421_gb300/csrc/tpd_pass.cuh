@@ -996,8 +996,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
   if constexpr (kShape < 0) {
     pass_tile<A, kDec, kRole, false>(pd, args, matp, q_in, q_out, tile, smem, lane, warp);
   } else {
-    static_assert(ShapeT<kShape>::kD <= kStdTileBits && (1 << (ShapeT<kShape>::kD - kRegBits)) <= kThreads,
-                  "compiled shapes are tiles of one CTA");
+    static_assert((1 << (ShapeT<kShape>::kD - kRegBits)) <= kThreads, "compiled shapes are tiles of one CTA");
     pass_tile<A, kDec, kRole, false>(GeoCT<ShapeT<kShape>>(pd), args, matp, q_in, q_out, tile, smem, lane, warp);
   }
 }

@@ -44,6 +44,7 @@ enum ShapeId {
   kShapeFirst4,       // 4 levels on 2^12, complex64 compensated first pass (128-byte runs)
   kShapeMid4D11,      // 4 levels + 3 passengers on 2^11 (n = 15 last pass)
   kShapeMid3,         // 3 levels + 6 passengers on 2^12 (compensated complex64 last passes)
+  kShapeMid5D13,      // 5 levels + 3 passengers on 2^13, one 512-thread CTA (complex64 n = 11, 15)
   kNumShapes
 };
 
@@ -102,6 +103,15 @@ constexpr ShapeDesc kShapes[kNumShapes] = {
      {0, 0, 0},
      {{0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}},
      {0, 1, 2, 3, 4, 5, 6, 7, 8, 6, 7, 8, 0}},
+    // kShapeMid5D13: 3 passengers, levels' column bits 3-7, row bits 8-12
+    {13, 5, 2,
+     {{5, 10, 8, 9}, {6, 11, 7, 12}, {0, 0, 0, 0}},
+     {{0, 1, 2, 3, 4}, {0, 1, 2, 3, 4}, {0, 0, 0, 0, 0}},
+     {{6, 7, 11, 12}, {5, 8, 9, 10}, {0, 0, 0, 0}},
+     {1, 2, 0},
+     {2, 0, 0},
+     {{3, 4, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}},
+     {0, 1, 2, 3, 4, 5, 6, 7, 3, 4, 5, 6, 7}},
 };
 
 // Packed forms (4 bits per tile-bit number, 3 per shuffle lane) from which

@@ -57,7 +57,8 @@ CASES = [
     # (storage, precision, n): every compiled layout, each role of the fixed point
     ("c128", "fixed", 9), ("c128", "fixed", 10), ("c128", "fixed", 12), ("c128", "fixed", 13),
     ("c128", "fixed", 14), ("c128", "fixed", 15),
-    ("c64", "plain", 12), ("c64", "plain", 13), ("c64", "plain", 14), ("c64", "plain", 15),
+    ("c64", "plain", 11), ("c64", "plain", 12), ("c64", "plain", 13), ("c64", "plain", 14), ("c64", "plain", 15),
+    ("c64", "fixed", 11), ("c64", "fixed", 12), ("c64", "fixed", 13), ("c64", "fixed", 15),
     ("c64", "compensated", 12), ("c64", "compensated", 13), ("c64", "compensated", 14),
     ("c64", "compensated", 15),
 ]
@@ -67,7 +68,7 @@ CASES = [
 def test_compiled_layouts_match_runtime_layouts(tpd, storage, precision, n):
     dtype = torch.complex128 if storage == "c128" else torch.complex64
     code = L.TPD_C128 if storage == "c128" else L.TPD_C64
-    prec = {"fixed": L.TPD_PREC_DEFAULT, "plain": L.TPD_PREC_PLAIN,
+    prec = {"fixed": L.TPD_PREC_FIXED, "plain": L.TPD_PREC_PLAIN,
             "compensated": L.TPD_PREC_COMPENSATED}[precision]
     assert any(s >= 0 for s in shapes_of(n, code, prec)), "no compiled layout in this plan"
     A = rand_matrix(n, dtype, 31000 + n)
@@ -78,7 +79,8 @@ def test_compiled_layouts_match_runtime_layouts(tpd, storage, precision, n):
     torch.cuda.empty_cache()
 
 
-@pytest.mark.parametrize("storage,precision", [("c128", "fixed"), ("c64", "plain"), ("c64", "compensated")])
+@pytest.mark.parametrize("storage,precision",
+                         [("c128", "fixed"), ("c64", "plain"), ("c64", "compensated"), ("c64", "fixed")])
 def test_zero_tiles_and_non_finite_tiles(tpd, storage, precision):
     dtype = torch.complex128 if storage == "c128" else torch.complex64
     n = 13
