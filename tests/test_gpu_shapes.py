@@ -55,7 +55,7 @@ def shapes_of(n, dtype, prec):
 
 CASES = [
     # (storage, precision, n): every compiled layout, each role of the fixed point
-    ("c128", "fixed", 9), ("c128", "fixed", 10), ("c128", "fixed", 12), ("c128", "fixed", 13),
+    ("c128", "fixed", 9), ("c128", "fixed", 10), ("c128", "fixed", 11), ("c128", "fixed", 12), ("c128", "fixed", 13),
     ("c128", "fixed", 14), ("c128", "fixed", 15),
     ("c64", "plain", 11), ("c64", "plain", 12), ("c64", "plain", 13), ("c64", "plain", 14), ("c64", "plain", 15),
     ("c64", "fixed", 11), ("c64", "fixed", 12), ("c64", "fixed", 13), ("c64", "fixed", 15),
