@@ -21,11 +21,11 @@
 // later item is skipped as soon as the status word is set, so the launch
 // always finishes and the context stays usable.
 //
-// Publication: the CTA finishes a tile's stores, barriers, and one thread (of
-// warp 1, so that warp 0 goes straight on to the next item) issues a
-// gpu-scope fence and increments the counter; the waiting thread polls with
-// ld.acquire.gpu and the CTA barriers before loading, and the loads of data
-// written in this launch go through L2 (ld.global.cg).
+// Publication: the CTA finishes an item's stores, barriers, and one thread
+// (of warp 1, so that warp 0 goes straight on to the next item) issues a
+// gpu-scope fence and adds the item's tile count to the counter; the waiting
+// thread polls with ld.acquire.gpu and the CTA barriers before loading, and
+// the loads of data written in this launch go through L2 (ld.global.cg).
 #pragma once
 
 #include <type_traits>
@@ -111,6 +111,25 @@ __device__ __forceinline__ void batch_pass_tile(const BatchSeg& sg, int p, const
   int16_t* q_out = args.q_out ? args.q_out + j * args.q_out_stride : nullptr;
   if constexpr (A::kFixed) {
     const int role = (p > 0 ? kRoleIntIn : 0) | (p + 1 < sg.npass ? kRoleIntOut : 0);
+    // the compiled layouts of the batch's largest matrices (n = 9, 10: a first
+    // pass of 5 or 6 levels, a last pass of 4); identical results to the
+    // run-time layout below
+    const int sh = sg.shape[p];
+    if (sh == kShapeFirst6 && role == kRoleIntOut) {
+      pass_tile<A, kDec, kRoleIntOut, true>(GeoCT<ShapeT<kShapeFirst6>>(pd), args, matp, q_in, q_out, tile, smem,
+                                            lane, warp);
+      return;
+    }
+    if (sh == kShapeFirst5 && role == kRoleIntOut) {
+      pass_tile<A, kDec, kRoleIntOut, true>(GeoCT<ShapeT<kShapeFirst5>>(pd), args, matp, q_in, q_out, tile, smem,
+                                            lane, warp);
+      return;
+    }
+    if (sh == kShapeMid4 && role == kRoleIntIn) {
+      pass_tile<A, kDec, kRoleIntIn, true>(GeoCT<ShapeT<kShapeMid4>>(pd), args, matp, q_in, q_out, tile, smem, lane,
+                                           warp);
+      return;
+    }
     switch (role) {
       case 0: pass_tile<A, kDec, 0, true>(pd, args, matp, q_in, q_out, tile, smem, lane, warp); break;
       case kRoleIntIn:
@@ -130,91 +149,130 @@ __device__ __forceinline__ void batch_pass_tile(const BatchSeg& sg, int p, const
 
 // kStdThreads threads; dynamic shared memory: 2^12 x 16 bytes + kRedBytes + 2^11 ints (a
 // D = 12 tile or a whole n <= 6 matrix, reduction slots, class slots of the
-// block fixed point).  Thread 0 keeps the claimed-ahead item in s_next (its own
-// slot: kept out of registers, which the tile needs) and hands it to the CTA
-// through s_work at the top of the loop.
+// block fixed point).  Thread 0 alone decodes each item (segment, pass,
+// matrix, tiles), claims the next one and does the lookups, and hands the
+// result to the CTA through shared memory behind one barrier; the claimed-ahead
+// item waits in s_next (its own slot: kept out of registers, which the tile
+// needs).
+constexpr int kItemEnd = 0, kItemBucket = 1, kItemSkip = 2, kItemRun = 3;
+
 template <class A, bool kDec>
 __global__ void __launch_bounds__(kStdThreads, kOccLow) k_batch(const __grid_constant__ BatchParams bp) {
   using Store = typename A::Store;
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ unsigned s_work, s_next;
-  __shared__ int s_ok;
+  __shared__ unsigned s_next;
+  __shared__ int s_kind, s_si, s_p;
+  __shared__ long long s_j, s_tile;
   __shared__ void* s_mat;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   unsigned* status = bp.ctrl + kCtrlStatus;
-  bool seen_bucket = false;
+  bool seen_bucket = false;                   // (thread 0's)
   if (tid == 0) s_next = atomicAdd(bp.ctrl + kCtrlWork, 1u);
   for (;;) {
-    if (tid == 0) s_work = s_next;
+    if (tid == 0) {
+      const long long w = s_next;
+      int kind = kItemRun, si = 0, p = 0;
+      long long j = 0, tile = 0;
+      if (w >= bp.total) {
+        kind = kItemEnd;
+      } else if (w == 0) {
+        kind = kItemBucket;
+        s_next = atomicAdd(bp.ctrl + kCtrlWork, 1u);
+      } else {
+        while (si + 1 < bp.nseg && w >= bp.seg[si + 1].first) ++si;
+        const BatchSeg& sg = bp.seg[si];
+        j = w - sg.first;                     // small matrices: one item each
+        if (sg.kind == kSegPipe) {
+          // item indices are below 2^31 (checked on the host): 32-bit division
+          const unsigned rel = (unsigned)(w - sg.first);
+          const unsigned ipp = (unsigned)(sg.tiles / sg.tpi);   // items per pass of a matrix
+          const unsigned per_round = (unsigned)sg.npass * ipp;
+          const unsigned round = rel / per_round;
+          const unsigned sub = rel - round * per_round;
+          p = (int)(sub / ipp);
+          tile = (long long)(sub - (unsigned)p * ipp) * sg.tpi;
+          j = (long long)round - (long long)p * sg.lag;
+          if (j < 0 || j >= sg.nmat) {        // empty slot of the pipeline's ramp
+            kind = kItemSkip;
+            s_next = atomicAdd(bp.ctrl + kCtrlWork, 1u);
+          }
+        }
+        if (kind == kItemRun) {
+          // The claim, the status word, the matrix pointer (once the bucketing
+          // is known to be done) and the first poll of the dependency are
+          // issued back to back, so their round trips overlap; only a
+          // dependency not yet met takes the polling loop.
+          const unsigned nxt = atomicAdd(bp.ctrl + kCtrlWork, 1u);   // claimed ahead
+          const unsigned st0 = ld_volatile(status);
+          unsigned long long mp = seen_bucket ? __ldcg(bp.bptrs + sg.item_start + j) : 0ull;
+          bool ok = st0 == 0;
+          if (ok && !seen_bucket) {
+            // the bucketing sets the status word (sizes disagreeing) before it
+            // releases its flag: read it again after acquiring the flag
+            ok = wait_count(bp.ctrl + kCtrlBucket, 1u, status) && ld_volatile(status) == 0;
+            if (ok) mp = __ldcg(bp.bptrs + sg.item_start + j);
+          }
+          if (ok && sg.kind == kSegPipe && p > 0) {
+            const unsigned* dep = bp.ctrl + kCtrlDone + sg.done + (long long)(p - 1) * sg.nmat + j;
+            const unsigned need = (unsigned)(sg.tiles + sg.wait_extra);
+            if (ld_acquire_gpu(dep) < need) ok = wait_count(dep, need, status);
+          }
+          seen_bucket = true;
+          s_mat = reinterpret_cast<void*>(mp);
+          s_next = nxt;
+          if (!ok) kind = kItemSkip;
+        }
+      }
+      s_kind = kind; s_si = si; s_p = p; s_j = j; s_tile = tile;
+    }
     __syncthreads();
-    const long long w = s_work;
-    if (w >= bp.total) break;
-    if (w == 0) {
-      if (tid == 0) s_next = atomicAdd(bp.ctrl + kCtrlWork, 1u);
-      bucket_item(bp, tid, blockDim.x);       // ends with barriers: s_work may be rewritten after it
-      seen_bucket = true;
+    const int kind = s_kind;
+    if (kind == kItemEnd) break;
+    if (kind == kItemBucket) {
+      bucket_item(bp, tid, blockDim.x);       // ends with barriers
+      if (tid == 0) seen_bucket = true;
       continue;
     }
-    int si = 0;
-    while (si + 1 < bp.nseg && w >= bp.seg[si + 1].first) ++si;
-    const BatchSeg& sg = bp.seg[si];
-    const long long rel = w - sg.first;
-    long long j = rel, tile = 0;              // small matrices: one item each
-    int p = 0;
-    if (sg.kind == kSegPipe) {
-      const long long per_round = (long long)sg.npass * sg.tiles;
-      const long long round = rel / per_round;
-      const long long sub = rel - round * per_round;
-      p = (int)(sub / sg.tiles);
-      tile = sub - p * sg.tiles;
-      j = round - (long long)p * sg.lag;
-      if (j < 0 || j >= sg.nmat) {            // empty slot of the pipeline's ramp
-        if (tid == 0) s_next = atomicAdd(bp.ctrl + kCtrlWork, 1u);
-        __syncthreads();                      // everyone has read s_work
-        continue;
-      }
-    }
-    unsigned* done = bp.ctrl + kCtrlDone + sg.done;
-    if (tid == 0) {
-      // The claim, the status word, the matrix pointer (once the bucketing is
-      // known to be done) and the first poll of the dependency are issued
-      // back to back, so their round trips overlap; only a dependency not yet
-      // met takes the polling loop.
-      const unsigned nxt = atomicAdd(bp.ctrl + kCtrlWork, 1u);   // claimed ahead
-      const unsigned st0 = ld_volatile(status);
-      unsigned long long mp = seen_bucket ? __ldcg(bp.bptrs + sg.item_start + j) : 0ull;
-      bool ok = st0 == 0;
-      if (ok && !seen_bucket) {
-        // the bucketing sets the status word (sizes disagreeing) before it
-        // releases its flag: read it again after acquiring the flag
-        ok = wait_count(bp.ctrl + kCtrlBucket, 1u, status) && ld_volatile(status) == 0;
-        if (ok) mp = __ldcg(bp.bptrs + sg.item_start + j);
-      }
-      if (ok && p > 0) {
-        const unsigned* dep = done + (long long)(p - 1) * sg.nmat + j;
-        const unsigned need = (unsigned)(sg.tiles + sg.wait_extra);
-        if (ld_acquire_gpu(dep) < need) ok = wait_count(dep, need, status);
-      }
-      s_mat = reinterpret_cast<void*>(mp);
-      s_ok = ok;
-      s_next = nxt;
-    }
-    __syncthreads();
-    seen_bucket = true;
-    if (s_ok) {
-      void* matp = s_mat;
+    // The item's state is re-read from shared memory where it is used (the
+    // s_* slots stay valid until the barrier that ends the item), so that
+    // nothing but the tile counter stays live across a tile's registers.
+    auto vol_int = [](const int& x) { return *reinterpret_cast<const volatile int*>(&x); };
+    auto vol_ll = [](const long long& x) { return *reinterpret_cast<const volatile long long*>(&x); };
+    if (kind == kItemRun) {
+      const BatchSeg& sg = bp.seg[s_si];
       if (sg.kind == kSegSmall) {
         // whole small matrices of the complex64 fixed-point form: the compensated kernel
         using SmallA = typename std::conditional<A::kFixed32, F32CArith, A>::type;
-        small_matrix<SmallA, kDec>(reinterpret_cast<Store*>(matp), sg.n, 0, bp.scale_mode, smem, tid, blockDim.x);
+        small_matrix<SmallA, kDec>(reinterpret_cast<Store*>(s_mat), sg.n, 0, bp.scale_mode, smem, tid, blockDim.x);
       } else {
-        batch_pass_tile<A, kDec>(sg, p, bp.desc[sg.desc + p], matp, j, tile, smem, lane, warp);
+        for (int k = 0;; ++k) {
+          const BatchSeg& sgk = bp.seg[vol_int(s_si)];
+          const int pk = vol_int(s_p);
+          void* const matp = *reinterpret_cast<void* const volatile*>(&s_mat);
+          batch_pass_tile<A, kDec>(sgk, pk, bp.desc[sgk.desc + pk], matp, vol_ll(s_j), vol_ll(s_tile) + k, smem,
+                                   lane, warp);
+          if (k + 1 >= bp.seg[vol_int(s_si)].tpi) break;
+          __syncthreads();                     // the tile is done with shared memory
+        }
       }
     }
-    __syncthreads();                          // the tile's stores are done (and smem is free)
-    if (tid == 32 && sg.kind == kSegPipe && p + 1 < sg.npass) {   // warp 0 goes on to the next item
+    // Completion of a pass item, published by one thread of warp 1 (warp 0
+    // goes on to the next item): its counter, read before the barrier that
+    // frees the s_* slots for thread 0.
+    unsigned* pub = nullptr;
+    unsigned pub_n = 0;
+    if (tid == 32 && kind == kItemRun) {
+      const BatchSeg& sg = bp.seg[vol_int(s_si)];
+      const int p = vol_int(s_p);
+      if (sg.kind == kSegPipe && p + 1 < sg.npass) {
+        pub = bp.ctrl + kCtrlDone + sg.done + (long long)p * sg.nmat + vol_ll(s_j);
+        pub_n = (unsigned)sg.tpi;
+      }
+    }
+    __syncthreads();                          // the item's stores are done (and smem is free)
+    if (pub != nullptr) {
       __threadfence();
-      atomicAdd(done + (long long)p * sg.nmat + j, 1u);
+      atomicAdd(pub, pub_n);
     }
   }
 }

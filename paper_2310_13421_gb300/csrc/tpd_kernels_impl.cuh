@@ -29,6 +29,7 @@ inline size_t class_slot_bytes(const PassDesc& pd) { return sizeof(int) << (pd.D
 // point), tpd_kernels_shapes_c64.cu (complex64).
 // min_blocks: the pass's CTAs per SM (1: one CTA of 512 threads on a 2^13-element tile).
 PassKernel shape_kernel_fixed(bool dec, int shape, int role, int min_blocks);
+PassKernel shape_kernel_fixed_cl(bool dec, int shape, int role);   // two-CTA clusters
 PassKernel shape_kernel_c64(int arith, bool dec, int shape, int min_blocks);
 
 template <class A>
@@ -69,6 +70,11 @@ cudaError_t launch_pass_cl_t(const PassDesc& pd, const PassArgs& args, long long
       case kRoleIntOut: kfn = k_pass_cl<A, kDec, kRoleIntOut>; break;
       case kRoleIntIn | kRoleIntOut: kfn = k_pass_cl<A, kDec, kRoleIntIn | kRoleIntOut>; break;
       default: break;
+    }
+    if (!pd.rt_layout) {
+      const int shape = match_shape(pd);
+      PassKernel sk = shape >= 0 ? shape_kernel_fixed_cl(kDec, shape, fixed_role(args)) : nullptr;
+      if (sk != nullptr) kfn = sk;
     }
   }
   cudaError_t e = ensure_smem_limit((const void*)kfn, smem_max);

@@ -31,4 +31,15 @@ PassKernel shape_kernel_fixed(bool dec, int shape, int role, int min_blocks) {
   return nullptr;
 }
 
+// 2^13-element tiles as two-CTA clusters (the 5-level passes of n = 11 and 15)
+PassKernel shape_kernel_fixed_cl(bool dec, int shape, int role) {
+  if (shape != kShapeMid5D13) return nullptr;
+  constexpr int kIn = kRoleIntIn, kInOut = kRoleIntIn | kRoleIntOut;
+  if (role == kInOut) return dec ? k_pass_cl<FixedArith, true, kInOut, kShapeMid5D13>
+                                 : k_pass_cl<FixedArith, false, kInOut, kShapeMid5D13>;
+  if (role == kIn) return dec ? k_pass_cl<FixedArith, true, kIn, kShapeMid5D13>
+                              : k_pass_cl<FixedArith, false, kIn, kShapeMid5D13>;
+  return nullptr;
+}
+
 }  // namespace tpd

@@ -73,18 +73,21 @@ struct SmallArgs {
 // then one *segment* per qubit count n.  For n >= 7 a segment holds every
 // pass of every matrix of that n, software-pipelined: round r = (pass 0 of
 // matrix r, pass 1 of matrix r - lag, pass 2 of matrix r - 2 lag, ...), each
-// pass as `tiles` items (tile-major), out-of-range (pass, matrix) slots empty.
+// pass as tiles / tpi items (tile-major), out-of-range (pass, matrix) slots empty.
 // A matrix's later passes thus run `lag` rounds after its earlier ones, while
 // its data (16 * 4^n bytes) is still in L2, so for matrices up to a few MB a
 // pass after the first reads, and the passes overwrite, lines that have not
 // gone back to HBM.  A tile of pass p > 0 waits (bounded) until all tiles of
 // pass p-1 of ITS matrix are done, counted per (pass, matrix) in `done`.  For
-// n <= 6 a segment holds one item per whole matrix.  A CTA claims its next
-// item as it starts the current one (two claims per CTA in flight).
+// n <= 6 a segment holds one item per whole matrix.  An item of a pipelined
+// segment is up to kBatchTilesPerItem consecutive tiles of one pass of one
+// matrix.  A CTA claims its next item as it starts the current one (two claims
+// per CTA in flight).
 constexpr int kBatchMaxDescs = 16;
 constexpr int kBatchMaxSegs = 12;
 constexpr int kBatchMaxN = 12;
 constexpr int kSegMaxPasses = 3;
+constexpr long long kBatchTilesPerItem = 16;
 constexpr int kSegSmall = 0;
 constexpr int kSegPipe = 1;
 
@@ -99,9 +102,10 @@ struct BatchSeg {
   int32_t lag;                // kSegPipe: rounds between consecutive passes of a matrix
   int32_t done;               // kSegPipe: counter of (pass p, matrix j) at ctrl[kCtrlDone + done + p * nmat + j]
   int32_t wait_extra;         // test hook: added to every wait's target
-  int32_t pad;
+  int8_t shape[4];            // kSegPipe, block fixed point: compiled layout of pass p (tpd_shape.h), or -1
   int64_t first;              // first work index of the segment
   int64_t tiles;              // tiles per pass (1 for kSegSmall)
+  int64_t tpi;                // kSegPipe: consecutive tiles of one pass per work item (divides tiles)
 };
 
 struct BatchParams {

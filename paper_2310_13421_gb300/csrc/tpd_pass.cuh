@@ -1003,7 +1003,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
 
 // Complex128 tiles of 2^13 elements as two-CTA clusters of 256 threads (see
 // the top of this file): grid = 2 x tiles, tile = cluster index.
-template <class A, bool kDec, int kRole = 0>
+template <class A, bool kDec, int kRole = 0, int kShape = -1>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kClThreads, 2)
     k_pass_cl(const __grid_constant__ PassDesc pd, const __grid_constant__ PassArgs args) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -1033,7 +1033,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kClThreads, 2)
   if (args.flags_in != nullptr && args.flags_in[tile] == 0) return;
   if (args.need != nullptr && args.need[tile] == 0) return;
   cluster_arrive_relaxed();
-  pass_tile<A, kDec, kRole, false, true>(pd, args, matp, q_in, q_out, tile, smem, lane, warp);
+  if constexpr (kShape < 0)
+    pass_tile<A, kDec, kRole, false, true>(pd, args, matp, q_in, q_out, tile, smem, lane, warp);
+  else
+    pass_tile<A, kDec, kRole, false, true>(GeoCT<ShapeT<kShape>>(pd), args, matp, q_in, q_out, tile, smem, lane,
+                                           warp);
 }
 
 // -------------------------------------------------------------- persistent, double buffered
