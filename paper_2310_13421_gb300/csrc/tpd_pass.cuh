@@ -231,7 +231,13 @@ __device__ __forceinline__ void pair_level(typename A::V (&v)[kElems]) {
 }
 
 // Cross-lane level: column bit on lane bit `lbit`, row bit on register bit RB.
-// Both lanes of a pair compute the same sums as pair_level, in the same order.
+// The two lanes of a pair swap their row-1 elements (one shuffle per pair):
+// the column-0 lane then holds (a00, a11), the column-1 lane (a01, a10), and
+// each computes the two outputs of its pair -- the same operations on the same
+// operands as pair_level.  The row-1 outputs stay in the lane that computed
+// them, so after the level register RB of a thread holds the element of its
+// partner lane's position ("twisted"): the exchange or store that follows
+// places it there (twist_add / twist_xor).
 template <class A, bool kDec, int RB>
 __device__ __forceinline__ void shfl_level(typename A::V (&v)[kElems], int lbit, int lane) {
   const int mask = 1 << lbit;
@@ -240,19 +246,54 @@ __device__ __forceinline__ void shfl_level(typename A::V (&v)[kElems], int lbit,
   for (int e = 0; e < kElems; ++e) {
     if ((e >> RB) & 1) continue;
     const int e1i = e | (1 << RB);
-    const typename A::V e0 = v[e], e1 = v[e1i];
-    const typename A::V p0 = A::shfl(e0, mask), p1 = A::shfl(e1, mask);
+    const typename A::V e0 = v[e];
+    const typename A::V r = A::shfl(v[e1i], mask);   // a11 / a10 (decomposition); Z / Y (composition)
     if (kDec) {
-      // column 0 holds a00 (row 0), a10 (row 1); column 1 holds a01, a11
-      v[e] = A::add(e0, p1);                    // I at (0,0) / X at (0,1)
-      const typename A::V d = A::sub(p0, e1);   // a01 - a10 / a00 - a11
-      v[e1i] = cb ? d : A::mul_i(d);            // Y at (1,0) / Z at (1,1)
+      v[e] = A::add(e0, r);                     // I = a00 + a11 at (0,0) / X = a01 + a10 at (0,1)
+      const typename A::V d = A::sub(e0, r);    // a00 - a11 / a01 - a10
+      v[e1i] = cb ? A::mul_i(d) : d;            // Z for (1,1) / Y for (1,0)
     } else {
       // column 0 holds I, Y; column 1 holds X, Z
-      const typename A::V t1 = cb ? A::mul_mi(p1) : p1;
-      const typename A::V t2 = cb ? A::neg(e1) : A::mul_i(e1);
-      v[e] = A::add(e0, t1);                    // I + Z / X - iY
-      v[e1i] = A::add(p0, t2);                  // X + iY / I - Z
+      v[e] = A::add(e0, cb ? A::mul_mi(r) : r);          // a00 = I + Z / a01 = X - iY
+      v[e1i] = A::add(e0, cb ? A::mul_i(r) : A::neg(r));  // a11 = I - Z / a10 = X + iY
+    }
+  }
+}
+
+// After a stage's shuffle levels, register bit 2 npair + s of every thread
+// also stands for its lane bit shfl_lane[s] flipped (see shfl_level): the
+// element in register e sits at the position of lane (lane ^ Tw(e)).  The
+// index weights of those register bits absorb it: an additive index (shared
+// memory, global element, next-pass tile) gains -+ the lane bit's weight for
+// a thread whose lane bit is 1 / 0 (twist_add); an XOR-linear one (the class)
+// gains the lane bit's class bit (twist_xor).
+template <class S, class T, class LaneW>
+__device__ __forceinline__ void twist_add(const S& st, int lane, T& w0, T& w1, T& w2, T& w3, LaneW lane_w) {
+#pragma unroll
+  for (int s = 0; s < kRegBits; ++s) {
+    if (s < st.nshfl) {
+      const int lb = st.shfl_lane[s];
+      const T d = lane_w(st.lane[lb]);
+      const T sd = ((lane >> lb) & 1) ? T(T(0) - d) : d;
+      const int rb = 2 * st.npair + s;
+      if (rb == 0) w0 += sd;
+      else if (rb == 1) w1 += sd;
+      else if (rb == 2) w2 += sd;
+      else w3 += sd;
+    }
+  }
+}
+template <class S, class T, class LaneW>
+__device__ __forceinline__ void twist_xor(const S& st, T& w0, T& w1, T& w2, T& w3, LaneW lane_w) {
+#pragma unroll
+  for (int s = 0; s < kRegBits; ++s) {
+    if (s < st.nshfl) {
+      const T d = lane_w(st.lane[st.shfl_lane[s]]);
+      const int rb = 2 * st.npair + s;
+      if (rb == 0) w0 ^= d;
+      else if (rb == 1) w1 ^= d;
+      else if (rb == 2) w2 ^= d;
+      else w3 ^= d;
     }
   }
 }
@@ -293,7 +334,7 @@ __device__ __forceinline__ void exchange(V (&v)[kElems], const G& pd, const S1& 
     V* const mine = sm;
     V* const peer = peer_smem(sm);
     const int rank = (int)cluster_rank();
-    {
+    if (a.nshfl == 0) {
       const int t = thread_sidx(pd, a, lane, warp);
       const int lt = squeeze(t), ot = (t >> cb) & 1;
       const int w0 = squeeze(1 << a.reg[0]), w1 = squeeze(1 << a.reg[1]);
@@ -303,6 +344,17 @@ __device__ __forceinline__ void exchange(V (&v)[kElems], const G& pd, const S1& 
       for (int e = 0; e < kElems; ++e) {
         const int own = ot ^ reg_off(e, o0, o1, o2, o3);
         (own == rank ? mine : peer)[lt + reg_off(e, w0, w1, w2, w3)] = v[e];
+      }
+    } else {
+      // twisted registers (shuffle levels): each element's full tile index,
+      // then its CTA and its index there
+      const int t = thread_sidx(pd, a, lane, warp);
+      int w0 = 1 << a.reg[0], w1 = 1 << a.reg[1], w2 = 1 << a.reg[2], w3 = 1 << a.reg[3];
+      twist_add(a, lane, w0, w1, w2, w3, [](int pos) { return 1 << pos; });
+#pragma unroll
+      for (int e = 0; e < kElems; ++e) {
+        const int te = t + reg_off(e, w0, w1, w2, w3);
+        (((te >> cb) & 1) == rank ? mine : peer)[squeeze(te)] = v[e];
       }
     }
     cluster_sync();
@@ -318,7 +370,8 @@ __device__ __forceinline__ void exchange(V (&v)[kElems], const G& pd, const S1& 
   if (sync_first) __syncthreads();
   {
     const int t = thread_sidx(pd, a, lane, warp);
-    const int w0 = 1 << a.reg[0], w1 = 1 << a.reg[1], w2 = 1 << a.reg[2], w3 = 1 << a.reg[3];
+    int w0 = 1 << a.reg[0], w1 = 1 << a.reg[1], w2 = 1 << a.reg[2], w3 = 1 << a.reg[3];
+    twist_add(a, lane, w0, w1, w2, w3, [](int pos) { return 1 << pos; });
 #pragma unroll
     for (int e = 0; e < kElems; ++e) sm[t + reg_off(e, w0, w1, w2, w3)] = v[e];
   }
@@ -350,8 +403,9 @@ __device__ __forceinline__ void finish_tile(const G& pd, const PassArgs& args, v
   const auto& sl = pd.st[pd.nstage - 1];
   Store* mat = reinterpret_cast<Store*>(matp);
   const uint32_t g = (uint32_t)base + (uint32_t)thread_goff(pd, sl, lane, warp);
-  const uint32_t w0 = 1u << pd.gbit[sl.reg[0]], w1 = 1u << pd.gbit[sl.reg[1]];
-  const uint32_t w2 = 1u << pd.gbit[sl.reg[2]], w3 = 1u << pd.gbit[sl.reg[3]];
+  uint32_t w0 = 1u << pd.gbit[sl.reg[0]], w1 = 1u << pd.gbit[sl.reg[1]];
+  uint32_t w2 = 1u << pd.gbit[sl.reg[2]], w3 = 1u << pd.gbit[sl.reg[3]];
+  twist_add(sl, lane, w0, w1, w2, w3, [&](int pos) { return 1u << pd.gbit[pos]; });
   const bool flags = args.flags_out != nullptr;
   int nt = 0, n0 = 0, n1 = 0, n2 = 0, n3 = 0;
   bool lanes_inside = true;
@@ -359,6 +413,7 @@ __device__ __forceinline__ void finish_tile(const G& pd, const PassArgs& args, v
     nt = nbase + thread_next(pd, sl, lane, warp);
     n0 = pd.next_w[sl.reg[0]]; n1 = pd.next_w[sl.reg[1]];
     n2 = pd.next_w[sl.reg[2]]; n3 = pd.next_w[sl.reg[3]];
+    twist_add(sl, lane, n0, n1, n2, n3, [&](int pos) { return (int)pd.next_w[pos]; });
 #pragma unroll
     for (int i = 0; i < kLaneBits; ++i) lanes_inside &= (pd.next_w[sl.lane[i]] == 0);
   }
@@ -601,8 +656,8 @@ __device__ __forceinline__ void flag_next(const G& pd, const PassArgs& args, int
                                           NonZero nz_of) {
   const auto& sl = pd.st[pd.nstage - 1];
   const int nt = nbase + thread_next(pd, sl, lane, warp);
-  const int n0 = pd.next_w[sl.reg[0]], n1 = pd.next_w[sl.reg[1]], n2 = pd.next_w[sl.reg[2]],
-            n3 = pd.next_w[sl.reg[3]];
+  int n0 = pd.next_w[sl.reg[0]], n1 = pd.next_w[sl.reg[1]], n2 = pd.next_w[sl.reg[2]], n3 = pd.next_w[sl.reg[3]];
+  twist_add(sl, lane, n0, n1, n2, n3, [&](int pos) { return (int)pd.next_w[pos]; });
   bool lanes_inside = true;
 #pragma unroll
   for (int i = 0; i < kLaneBits; ++i) lanes_inside &= (pd.next_w[sl.lane[i]] == 0);
@@ -801,8 +856,9 @@ __device__ __forceinline__ void fixed_tile(const G& pd, const PassArgs& args, vo
   // ---- store in place: int64 sums, or rounded once
   const auto& sl = pd.st[pd.nstage - 1];
   const uint32_t g = (uint32_t)base + (uint32_t)thread_goff(pd, sl, lane, warp);
-  const uint32_t w0 = 1u << pd.gbit[sl.reg[0]], w1 = 1u << pd.gbit[sl.reg[1]];
-  const uint32_t w2 = 1u << pd.gbit[sl.reg[2]], w3 = 1u << pd.gbit[sl.reg[3]];
+  uint32_t w0 = 1u << pd.gbit[sl.reg[0]], w1 = 1u << pd.gbit[sl.reg[1]];
+  uint32_t w2 = 1u << pd.gbit[sl.reg[2]], w3 = 1u << pd.gbit[sl.reg[3]];
+  twist_add(sl, lane, w0, w1, w2, w3, [&](int pos) { return 1u << pd.gbit[pos]; });
   if constexpr (kIntOut) {
     longlong2* mat = reinterpret_cast<longlong2*>(matp);
 #pragma unroll
@@ -810,8 +866,8 @@ __device__ __forceinline__ void fixed_tile(const G& pd, const PassArgs& args, vo
   } else {
     // value = sum * 2^q_out_c * 2^out_pow2 (a composition's scale)
     const int cl = cls_thread(pd, sl, lane, warp);
-    const int l0 = pd.cls_w[sl.reg[0]], l1 = pd.cls_w[sl.reg[1]], l2 = pd.cls_w[sl.reg[2]],
-              l3 = pd.cls_w[sl.reg[3]];
+    int l0 = pd.cls_w[sl.reg[0]], l1 = pd.cls_w[sl.reg[1]], l2 = pd.cls_w[sl.reg[2]], l3 = pd.cls_w[sl.reg[3]];
+    twist_xor(sl, l0, l1, l2, l3, [&](int pos) { return (int)pd.cls_w[pos]; });
     const bool resid = args.out_mul != 1.0;              // non-power-of-two composition scale (rare)
     double2* mat = reinterpret_cast<double2*>(matp);
     // T of a class, -(q_out + out_pow2), falls as its slot rises; zero
@@ -896,10 +952,12 @@ __device__ __forceinline__ void fixed32_tile(const G& pd, const PassArgs& args, 
   const auto& sl = pd.st[pd.nstage - 1];
   float2* mat = reinterpret_cast<float2*>(matp);
   const uint32_t g = (uint32_t)base + (uint32_t)thread_goff(pd, sl, lane, warp);
-  const uint32_t w0 = 1u << pd.gbit[sl.reg[0]], w1 = 1u << pd.gbit[sl.reg[1]];
-  const uint32_t w2 = 1u << pd.gbit[sl.reg[2]], w3 = 1u << pd.gbit[sl.reg[3]];
+  uint32_t w0 = 1u << pd.gbit[sl.reg[0]], w1 = 1u << pd.gbit[sl.reg[1]];
+  uint32_t w2 = 1u << pd.gbit[sl.reg[2]], w3 = 1u << pd.gbit[sl.reg[3]];
+  twist_add(sl, lane, w0, w1, w2, w3, [&](int pos) { return 1u << pd.gbit[pos]; });
   const int cl = cls_thread(pd, sl, lane, warp);
-  const int l0 = pd.cls_w[sl.reg[0]], l1 = pd.cls_w[sl.reg[1]], l2 = pd.cls_w[sl.reg[2]], l3 = pd.cls_w[sl.reg[3]];
+  int l0 = pd.cls_w[sl.reg[0]], l1 = pd.cls_w[sl.reg[1]], l2 = pd.cls_w[sl.reg[2]], l3 = pd.cls_w[sl.reg[3]];
+  twist_xor(sl, l0, l1, l2, l3, [&](int pos) { return (int)pd.cls_w[pos]; });
 #pragma unroll
   for (int e = 0; e < kElems; ++e) {
     const int T = tbase - max(cls[cl ^ reg_cls(e, l0, l1, l2, l3)], 1);
