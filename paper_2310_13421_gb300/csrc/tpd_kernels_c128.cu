@@ -22,6 +22,17 @@ cudaError_t ensure_smem_limit(const void* fn, size_t bytes) {
   return e;
 }
 
+int device_sm_count() {
+  static std::mutex mu;
+  static std::map<int, int> count;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  std::lock_guard<std::mutex> lk(mu);
+  int& c = count[dev];
+  if (c == 0 && cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) c = 0;
+  return c > 0 ? c : 1;
+}
+
 cudaError_t launch_pass_fixed_dec(const PassDesc& pd, const PassArgs& args, long long ntiles_total, cudaStream_t s);
 cudaError_t launch_pass_fixed_com(const PassDesc& pd, const PassArgs& args, long long ntiles_total, cudaStream_t s);
 cudaError_t launch_pass_pipe_fixed_dec(const PassDesc& pd, const PassArgs& args, int nsm, cudaStream_t s);

@@ -30,6 +30,8 @@ inline size_t class_slot_bytes(const PassDesc& pd) { return sizeof(int) << (pd.D
 // min_blocks: the pass's CTAs per SM (1: one CTA of 512 threads on a 2^13-element tile).
 PassKernel shape_kernel_fixed(bool dec, int shape, int role, int min_blocks);
 PassKernel shape_kernel_fixed_cl(bool dec, int shape, int role);   // two-CTA clusters
+PassKernel shape_kernel_fixed_pf(int shape, int role);              // persistent, prefetching
+int device_sm_count();                                              // of the current device (cached)
 PassKernel shape_kernel_c64(int arith, bool dec, int shape, int min_blocks);
 
 template <class A>
@@ -99,6 +101,28 @@ cudaError_t launch_pass_t(const PassDesc& pd, const PassArgs& args, long long nt
   PassKernel kfn = nullptr;
   if (!pd.rt_layout) {
     const int shape = match_shape(pd);
+    if constexpr (A::kFixed && kDec) {
+      // one matrix, every tile: the persistent form that prefetches each
+      // CTA's next tile while it finishes the current one
+      const bool plain = args.ptrs == nullptr && !args.skip_zero && args.flags_in == nullptr &&
+                         args.flags_out == nullptr && args.need == nullptr && !args.chunked;
+      PassKernel pk = (plain && shape >= 0 && pd.min_blocks == kOccLow && threads <= kStdThreads)
+                          ? shape_kernel_fixed_pf(shape, fixed_role(args)) : nullptr;
+      if (pk != nullptr) {
+        const size_t smem_pf = ((size_t)16 << pd.D) + kRedBytes + class_slot_bytes(pd);
+        const size_t smem_pf_max = ((size_t)16 << kStdTileBits) + kRedBytes + (sizeof(int) << (kStdTileBits - 1));
+        cudaError_t e = ensure_smem_limit((const void*)pk, smem_pf_max);
+        if (e != cudaSuccess) return e;
+        if (ntiles_total <= 0) return cudaSuccess;
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pk, threads, smem_pf);
+        if (e != cudaSuccess) return e;
+        long long grid = (long long)device_sm_count() * (per_sm > 0 ? per_sm : 1);
+        if (grid > ntiles_total) grid = ntiles_total;
+        pk<<<(unsigned)grid, threads, smem_pf, s>>>(pd, args);
+        return cudaGetLastError();
+      }
+    }
     if (shape >= 0) {
       if constexpr (A::kFixed) kfn = shape_kernel_fixed(kDec, shape, fixed_role(args), pd.min_blocks);
       else if constexpr (arith_code<A>() != kArithF64) kfn = shape_kernel_c64(arith_code<A>(), kDec, shape, pd.min_blocks);

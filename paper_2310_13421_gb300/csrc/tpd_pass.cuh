@@ -699,6 +699,41 @@ __device__ __forceinline__ void tile_reduce(int* red, int warp, int lane, int nw
   hi = (int)__reduce_max_sync(kFull, in ? (unsigned)red[2 * kRedStride + lane] : 0u);
 }
 
+// Asynchronous copies of a tile's elements into shared memory (the
+// prefetching pass forms): each thread copies its own stage-0 elements.
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+template <class G>
+__device__ __forceinline__ long long tile_base(const G& pd, long long tile) {
+  long long base = 0;
+  for (int j = 0; j < pd.nrest; ++j)
+    if ((tile >> j) & 1) base += 1ll << pd.rest_gbit[j];
+  return base;
+}
+
+// This thread's 16 elements of `tile` (stage-0 positions) into buf.
+template <class G>
+__device__ __forceinline__ void prefetch_tile(const G& pd, const void* matp, long long tile, unsigned char* buf,
+                                              int lane, int warp) {
+  const auto& s0 = pd.st[0];
+  const char* mat = reinterpret_cast<const char*>(matp);
+  const long long g = tile_base(pd, tile) + thread_goff(pd, s0, lane, warp);
+  const long long w0 = 1ll << pd.gbit[s0.reg[0]], w1 = 1ll << pd.gbit[s0.reg[1]];
+  const long long w2 = 1ll << pd.gbit[s0.reg[2]], w3 = 1ll << pd.gbit[s0.reg[3]];
+  const int t = thread_sidx(pd, s0, lane, warp);
+  const int v0 = 1 << s0.reg[0], v1 = 1 << s0.reg[1], v2 = 1 << s0.reg[2], v3 = 1 << s0.reg[3];
+#pragma unroll
+  for (int e = 0; e < kElems; ++e)
+    cp_async16(buf + 16 * (t + reg_off(e, v0, v1, v2, v3)), mat + 16 * (g + reg_off(e, w0, w1, w2, w3)));
+  cp_async_commit();
+}
+
 // One complex128 tile of the block fixed point, in the role kRole (IEEE
 // numbers or int64 sums in, IEEE numbers or int64 sums out).
 // xbuf: exchange area (2^D x 16 bytes; a two-CTA cluster: half of it per
@@ -719,8 +754,16 @@ template <bool kDec, int kRole, bool kCg = false, bool kCl = false, class G>
 __device__ __forceinline__ void fixed_tile(const G& pd, const PassArgs& args, void* matp, const int16_t* q_in,
                                            int16_t* q_out, long long tile, long long base, uint32_t sbase,
                                            int nbase, const unsigned char* inbuf, unsigned char* xbuf, int* red,
-                                           int* cls, int lane, int warp) {
+                                           int* cls, int lane, int warp, long long pf_tile = -1) {
   using V = FixedArith::V;
+  // pf_tile >= 0 (persistent form): once every thread is done with the
+  // exchange area, copy that tile's elements into it for the next round
+  auto prefetch_next = [&]() {
+    if (pf_tile >= 0) {
+      __syncthreads();
+      prefetch_tile(pd, matp, pf_tile, xbuf, lane, warp);
+    }
+  };
   constexpr bool kIntIn = (kRole & kRoleIntIn) != 0;
   constexpr bool kIntOut = (kRole & kRoleIntOut) != 0;
   const int nthr = blockDim.x;
@@ -759,6 +802,7 @@ __device__ __forceinline__ void fixed_tile(const G& pd, const PassArgs& args, vo
     if ((args.skip_zero && !(tb & 1)) || (tb & 2)) {
       if (tb & 2)
         ieee_tile<kDec, kCg, kCl>(raw_desc(pd), args, matp, q_in, q_out, tile, base, sbase, nbase, xbuf, lane, warp);
+      prefetch_next();
       return;                                            // (else all +-0: the outputs are zero already)
     }
     if constexpr (kCl) {
@@ -804,9 +848,13 @@ __device__ __forceinline__ void fixed_tile(const G& pd, const PassArgs& args, vo
     slot_hi = hi;
     if (tb & 2) {
       ieee_tile<kDec, kCg, kCl>(raw_desc(pd), args, matp, q_in, q_out, tile, base, sbase, nbase, xbuf, lane, warp);
+      prefetch_next();
       return;
     }
-    if (args.skip_zero && !(tb & 1)) return;             // every source class was zero
+    if (args.skip_zero && !(tb & 1)) {                   // every source class was zero
+      prefetch_next();
+      return;
+    }
     if constexpr (kCl) {
       const int* pcls = peer_smem(cls);
       for (int i = threadIdx.x; i < ncls; i += nthr) cls[i] = max(cls[i], pcls[i]);
@@ -850,6 +898,7 @@ __device__ __forceinline__ void fixed_tile(const G& pd, const PassArgs& args, vo
 #pragma unroll
   for (int s = 0; s < pd.nstage; ++s) {
     if (s > 0) exchange<kCl>(v, pd, pd.st[s - 1], pd.st[s], sm, lane, warp, s > 1);
+    if (s == pd.nstage - 1) prefetch_next();             // the last stage works in registers
     stage_levels<FixedArith, kDec>(v, pd.st[s], lane);
   }
 
@@ -1106,37 +1155,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kClThreads, 2)
 // on the current one, so HBM stays busy across the compute phase.  The waits
 // are the hardware's (cp.async.wait_group + barrier), with no spin loops.
 
-__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem_src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
-__device__ __forceinline__ long long tile_base(const PassDesc& pd, long long tile) {
-  long long base = 0;
-  for (int j = 0; j < pd.nrest; ++j)
-    if ((tile >> j) & 1) base += 1ll << pd.rest_gbit[j];
-  return base;
-}
-
-// This thread's 16 elements of `tile` (stage-0 positions) into buf.
-__device__ __forceinline__ void prefetch_tile(const PassDesc& pd, const void* matp, long long tile,
-                                              unsigned char* buf, int lane, int warp) {
-  const Stage& s0 = pd.st[0];
-  const char* mat = reinterpret_cast<const char*>(matp);
-  const long long g = tile_base(pd, tile) + thread_goff(pd, s0, lane, warp);
-  const long long w0 = 1ll << pd.gbit[s0.reg[0]], w1 = 1ll << pd.gbit[s0.reg[1]];
-  const long long w2 = 1ll << pd.gbit[s0.reg[2]], w3 = 1ll << pd.gbit[s0.reg[3]];
-  const int t = thread_sidx(pd, s0, lane, warp);
-  const int v0 = 1 << s0.reg[0], v1 = 1 << s0.reg[1], v2 = 1 << s0.reg[2], v3 = 1 << s0.reg[3];
-#pragma unroll
-  for (int e = 0; e < kElems; ++e)
-    cp_async16(buf + 16 * (t + reg_off(e, v0, v1, v2, v3)), mat + 16 * (g + reg_off(e, w0, w1, w2, w3)));
-  cp_async_commit();
-}
-
 template <bool kDec, int kRole>
 __global__ void __launch_bounds__(kStdThreads, 1)
     k_pass_pipe(const __grid_constant__ PassDesc pd, const __grid_constant__ PassArgs args) {
@@ -1174,6 +1192,43 @@ __global__ void __launch_bounds__(kStdThreads, 1)
     fixed_tile<kDec, kRole>(pd, args, args.mat, args.q_in, args.q_out, tile, base, sbase, nbase, cur, cur, red, cls,
                             lane, warp);
     __syncthreads();                      // the current buffer is refilled next iteration
+  }
+}
+
+// Persistent form of the block-fixed-point pass for a compiled layout (one
+// matrix, every tile: no zero skipping, partial masks or L2 chunks): a CTA
+// walks the tiles tile += gridDim.x, two CTAs per SM.  Each tile arrives in the
+// exchange area through cp.async, issued by the previous tile once its last
+// exchange has been read, so the copy runs while that tile's last stage, its
+// rounding and its stores execute; the waits are cp.async.wait_group and
+// barriers only.
+template <bool kDec, int kRole, int kShape>
+__global__ void __launch_bounds__(kStdThreads, kOccLow)
+    k_pass_pf(const __grid_constant__ PassDesc pd, const __grid_constant__ PassArgs args) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const GeoCT<ShapeT<kShape>> g(pd);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  unsigned char* buf = smem;
+  int* red = reinterpret_cast<int*>(smem + ((size_t)16 << ShapeT<kShape>::kD));
+  int* cls = red + kRedInts;
+  long long tile = blockIdx.x;
+  if (tile >= pd.ntiles) return;
+  prefetch_tile(g, args.mat, tile, buf, lane, warp);
+  for (; tile < pd.ntiles; tile += gridDim.x) {
+    cp_async_wait<0>();
+    __syncthreads();                      // the tile is in shared memory, everyone's copies included
+    long long base = 0;
+    int nbase = 0;
+    uint32_t sbase = 0;
+    for (int j = 0; j < pd.nrest; ++j)
+      if ((tile >> j) & 1) {
+        base += 1ll << pd.rest_gbit[j];
+        nbase += (int)pd.next_rest_w[j];
+        sbase ^= pd.src_rest_w[j];
+      }
+    const long long nxt = tile + gridDim.x;
+    fixed_tile<kDec, kRole>(g, args, args.mat, args.q_in, args.q_out, tile, base, sbase, nbase, buf, buf, red, cls,
+                            lane, warp, nxt < pd.ntiles ? nxt : -1);
   }
 }
 
