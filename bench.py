@@ -179,7 +179,7 @@ def run_reference(args, world, rank):
 
 KERNEL_SOURCES = ("tpd_pass.cuh", "tpd_arith.cuh", "tpd_plan.h", "tpd_shape.h", "tpd_launch.h", "tpd_planner.cpp",
                   "tpd_kernels_impl.cuh", "tpd_kernels_fixed_dec.cu", "tpd_kernels_fixed_com.cu",
-                  "tpd_kernels_shapes_fixed.cu")
+                  "tpd_kernels_shapes_fixed.cu", "tpd_kernels_c128.cu")
 
 
 def _code_only(text):
@@ -681,7 +681,10 @@ def run_ours(args, world, rank, local):
     peak = float(peaks.get("hbm_gbs", 6800.0))
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": None if (c64 or prec_eff != L.TPD_PREC_FIXED) else measured_traffic(n),
-                "kernel": "k_pass<%s,true> (one launch per pass, %d passes)" % (
+                "kernel": ("k_pass_pf (first pass: persistent, prefetching) / k_pass<FixedArith,dec> "
+                           "(later passes), compiled tile layouts; one launch per pass, %d passes" % npass)
+                if (not c64 and prec_eff == L.TPD_PREC_FIXED) else
+                "k_pass<%s,true> (one launch per pass, %d passes)" % (
                     {L.TPD_PREC_FIXED: "Fixed32Arith" if c64 else "FixedArith",
                      L.TPD_PREC_PLAIN: "F32Arith" if c64 else "F64Arith",
                      L.TPD_PREC_COMPENSATED: "F32CArith"}[prec_eff], npass),
