@@ -90,7 +90,12 @@ typedef struct {
                        tile (9..13), for tuning */
   int max_levels;   /* 0 = planner default; otherwise the most qubit levels fused
                        into one pass (1..6), for tuning */
-  int variant;      /* kernel form, for tuning: 0 = default, 1 = one CTA per tile
+  int variant;      /* kernel form, for tuning: 0 = default (a single complex128
+                       matrix without zero skipping or partial masks runs the
+                       block fixed point's first pass, and the 2^11-element
+                       last pass of n = 15, as persistent CTAs, two per SM,
+                       each copying its next tile into shared memory while it
+                       finishes the current one), 1 = one CTA per tile
                        (complex128 tiles of 2^13 elements otherwise run as a
                        cluster of two 256-thread CTAs sharing the tile through
                        distributed shared memory),
@@ -98,11 +103,11 @@ typedef struct {
                        block fixed point, single matrix, no zero skipping),
                        3 / 4 = one CTA per tile compiled for 2 / 3 CTAs per SM
                        (tiles of up to 2^12 elements),
-                       5 = the default form with every pass's tile layout read
+                       5 = one CTA per tile with every pass's tile layout read
                        from its run-time descriptor (by default, passes whose
                        layout is one of the library's compiled shapes run a
-                       kernel with that layout built in; both give identical
-                       results).
+                       kernel with that layout built in; all forms give
+                       identical results).
                        Batched calls: 0, 1, 3, 4 = one launch per (qubit count,
                        pass) over all matrices of that qubit count (the fastest
                        form measured on GB300); 2 = the whole batch in ONE
