@@ -371,7 +371,7 @@ def _digit_add(x, y, d, n):
 def time_weyl(tpd, L, torch, stream, d=3, n=9, seed=1006, shifts=8):
     """Decomposition in the Weyl (clock-and-shift) basis of n qudits of
     dimension d (the basis Sec. V names): a random d^n x d^n Hermitian matrix,
-    complex128 (fp64 arithmetic) and complex64 (fp32), one launch per qudit
+    complex128 (block fixed point, and fp64) and complex64 (fp32), one launch per qudit
     level, each reading and writing the whole matrix.  Returns the timings
     and, for the accuracy leg, the weights of a few shifts a (row digits b,
     column digits a + b) of each result."""
@@ -383,18 +383,23 @@ def time_weyl(tpd, L, torch, stream, d=3, n=9, seed=1006, shifts=8):
     b = np.arange(N, dtype=np.int64)
     pos = np.concatenate([b * N + _digit_add(b, np.full(N, a), d, n) for a in a_s])
     out, rows = {"d": d, "n": n, "side": N}, {}
-    for name, tt, code, elem in (("c128", torch.complex128, L.TPD_C128, 16), ("c64", torch.complex64, L.TPD_C64, 8)):
+    legs = (("c128", torch.complex128, L.TPD_C128, 16, L.TPD_PREC_DEFAULT,
+             "int64 block fixed point, one binary point per class of d summed elements"),
+            ("c128_fp64", torch.complex128, L.TPD_C128, 16, L.TPD_PREC_PLAIN, "fp64, rounded every level"),
+            ("c64", torch.complex64, L.TPD_C64, 8, L.TPD_PREC_DEFAULT, "fp32, rounded every level"))
+    for name, tt, code, elem, prec, arith in legs:
         src = torch.from_numpy(A).to("cuda", tt)
         work = torch.empty_like(src)
+        opt = L.options(precision=prec)
 
         def step():
-            st = L.tpd_weyl_decompose(work.data_ptr(), n, d, code, stream.cuda_stream)
+            st = L.tpd_weyl_decompose(work.data_ptr(), n, d, code, opt, stream.cuda_stream)
             assert st == 0, L.status_string(st)
 
         ms = _event_ms(torch, stream, step, setup=lambda: work.copy_(src))
         alg = 2 * n * N * N * elem
         out[name] = {"ms": ms, "coeffs_per_s": N * N / (ms * 1e-3), "hbm_gbs_algorithmic": alg / (ms * 1e-3) / 1e9,
-                     "launches": n, "arithmetic": "fp64" if elem == 16 else "fp32"}
+                     "launches": n, "arithmetic": arith}
         rows[name] = work.reshape(-1).index_select(0, torch.from_numpy(pos).cuda()).cpu().numpy() \
             .astype(np.complex128).reshape(len(a_s), N)
         del src, work

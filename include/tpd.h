@@ -329,17 +329,29 @@ tpd_status tpd_decompose_coo(const int* rows, const int* cols, const void* value
  *           (for d = 2 the Pauli RC layout, with c_{1,1} = i w_Y since
  *           XZ = -iY).
  *   n, d    1 <= n, 2 <= d <= 5, d^n <= 65536.
- *   dtype   TPD_C128 (IEEE fp64 arithmetic) or TPD_C64 (fp32), rounded every
- *           level.
+ *   dtype   TPD_C128 or TPD_C64.
+ *   opt     may be NULL (defaults); only opt->precision is read:
+ *           DEFAULT / FIXED: complex128 with d <= 4 in a block fixed point --
+ *             the d elements each DFT combines (one cyclic diagonal of a
+ *             block) on their own binary point in int64, the DFT exact for
+ *             d = 2, 4 and with sqrt(3) rounded once on that grid for d = 3,
+ *             one rounding to double per output and level (d = 2, 4 integer
+ *             inputs: exact); classes meeting Inf/NaN in IEEE fp64;
+ *           PLAIN (and DEFAULT for d = 5): IEEE fp64, rounded every level;
+ *           complex64: fp32, rounded every level (FIXED and COMPENSATED are
+ *           INVALID_ARG for complex64, FIXED for d = 5).
  * One kernel launch per qudit; no workspace; asynchronous on `stream`.
  * Errors: INVALID_ARG, MISALIGNED, CUDA. */
-tpd_status tpd_weyl_decompose(void* A, int n, int d, int dtype, void* stream);
+tpd_status tpd_weyl_decompose(void* A, int n, int d, int dtype, const tpd_options* opt, void* stream);
 
 /* Weyl-basis composition in place: C holds the weights c_{a,b} in the layout
  * tpd_weyl_decompose leaves; on return it holds scale * sum c_{a,b} W_{a,b}
- * (scale = d^-n: the adjoint of tpd_weyl_decompose, W_{a,b} being unitary).
- * scale finite and nonzero.  Arguments and errors as tpd_weyl_decompose. */
-tpd_status tpd_weyl_compose(void* C, int n, int d, int dtype, double scale, void* stream);
+ * (scale = d^-n: the adjoint of tpd_weyl_decompose, W_{a,b} being unitary;
+ * applied on the last level, exactly where it is a power of two).  scale
+ * finite and nonzero.  Arguments, arithmetic and errors as
+ * tpd_weyl_decompose. */
+tpd_status tpd_weyl_compose(void* C, int n, int d, int dtype, double scale, const tpd_options* opt,
+                            void* stream);
 
 /* Layout conversion, out of place.  RC is the layout every decomposition
  * leaves (see the conventions above); STRING puts the weight of

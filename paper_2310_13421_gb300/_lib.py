@@ -97,9 +97,9 @@ def load(path=None):
         lib.tpd_nonzero_workspace_size.restype = sz
         lib.tpd_nonzero_list.argtypes = [vp, i, i, ctypes.c_double, vp, vp, sz, vp, vp, sz, vp]
         lib.tpd_nonzero_list.restype = i
-        lib.tpd_weyl_decompose.argtypes = [vp, i, i, i, vp]
+        lib.tpd_weyl_decompose.argtypes = [vp, i, i, i, op, vp]
         lib.tpd_weyl_decompose.restype = i
-        lib.tpd_weyl_compose.argtypes = [vp, i, i, i, ctypes.c_double, vp]
+        lib.tpd_weyl_compose.argtypes = [vp, i, i, i, ctypes.c_double, op, vp]
         lib.tpd_weyl_compose.restype = i
         lib.tpd_convert_layout.argtypes = [vp, vp, i, i, i, vp]
         lib.tpd_convert_layout.restype = i
@@ -208,12 +208,12 @@ def tpd_nonzero_list(W, n, dtype, tol, strings, weights, capacity, count, worksp
                                        count or None, workspace or None, workspace_bytes, stream or None))
 
 
-def tpd_weyl_decompose(A, n, d, dtype, stream=0):
-    return int(load().tpd_weyl_decompose(A or None, n, d, dtype, stream or None))
+def tpd_weyl_decompose(A, n, d, dtype, opt=None, stream=0):
+    return int(load().tpd_weyl_decompose(A or None, n, d, dtype, _opt(opt), stream or None))
 
 
-def tpd_weyl_compose(C, n, d, dtype, scale, stream=0):
-    return int(load().tpd_weyl_compose(C or None, n, d, dtype, float(scale), stream or None))
+def tpd_weyl_compose(C, n, d, dtype, scale, opt=None, stream=0):
+    return int(load().tpd_weyl_compose(C or None, n, d, dtype, float(scale), _opt(opt), stream or None))
 
 
 def tpd_convert_layout(src, dst, n, dtype, to_string, stream=0):

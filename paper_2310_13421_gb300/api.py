@@ -338,27 +338,31 @@ def _qudits(t, d):
     return n
 
 
-def weyl_decompose(A, d, *, inplace=False, stream=None):
+def weyl_decompose(A, d, *, inplace=False, precision=None, stream=None):
     """Weights c_{a,b} = d^-n tr(W_{a,b}^* A) of a d^n x d^n CUDA matrix in the
     Weyl (clock-and-shift) basis W_{a,b} = X^a Z^b; the weight of (a, b)
-    sits at row digits b, column digits a + b mod d (see tpd_weyl_decompose)."""
+    sits at row digits b, column digits a + b mod d (see tpd_weyl_decompose).
+    precision: None / "fixed" (complex128, d <= 4: block fixed point) or
+    "plain" (IEEE, rounded every level)."""
     _check_device(A)
     n = _qudits(A, d)
+    opt = make_options(precision)
     with _enqueue(A.device, stream, A) as s:
         out = A if inplace else A.clone()
-        st = L.tpd_weyl_decompose(out.data_ptr(), n, int(d), _dtype_code(A), s)
+        st = L.tpd_weyl_decompose(out.data_ptr(), n, int(d), _dtype_code(A), opt, s)
     _raise(st, "tpd_weyl_decompose")
     return out
 
 
-def weyl_compose(C, d, *, scale=1.0, inplace=False, stream=None):
+def weyl_compose(C, d, *, scale=1.0, inplace=False, precision=None, stream=None):
     """scale * sum c_{a,b} W_{a,b} from weights in the layout of weyl_decompose
-    (scale d^-n: its adjoint)."""
+    (scale d^-n: its adjoint); precision as for weyl_decompose."""
     _check_device(C)
     n = _qudits(C, d)
+    opt = make_options(precision)
     with _enqueue(C.device, stream, C) as s:
         out = C if inplace else C.clone()
-        st = L.tpd_weyl_compose(out.data_ptr(), n, int(d), _dtype_code(C), float(scale), s)
+        st = L.tpd_weyl_compose(out.data_ptr(), n, int(d), _dtype_code(C), float(scale), opt, s)
     _raise(st, "tpd_weyl_compose")
     return out
 

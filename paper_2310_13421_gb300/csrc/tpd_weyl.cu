@@ -17,7 +17,19 @@
 // W_{1,1} = XZ = -iY).  The composition inverts each level:
 // A_{c+a, c} = sum_b omega^(b c) Omega_{a,b}.
 //
-// Arithmetic: complex128 in IEEE fp64, complex64 in fp32, rounded every level
+// Arithmetic.  complex64: IEEE fp32, rounded every level.  complex128: by
+// default (d = 2, 3, 4) a block fixed point, as for the Pauli basis: the d
+// elements one DFT combines (a cyclic diagonal of a block, a "class") go onto
+// their own binary point in int64, set by the largest exponent among their
+// components with headroom for the sums, the DFT runs in int64 -- exactly
+// for d = 2 and 4 (twiddles +-1, +-i); for d = 3 with the outputs computed
+// doubled, so that nothing is halved, and sqrt(3) multiplied once, rounded to
+// the nearest point of the class's grid -- and each output is rounded to
+// double once (RNE), the decomposition's 1/d folded in as an exponent (d = 2,
+// 4) or as the nearest integer of a third on the class grid (d = 3).  The
+// fp64 pipe of GB300 issues ~2 operations per clock per SM, far below what a
+// level at HBM speed needs; integer instructions are not.  Classes meeting
+// Inf or NaN, d = 5, and TPD_PREC_PLAIN run IEEE fp64 rounded every level
 // (the paper's arithmetic carried over).  d = 3 uses the 3-point DFT written
 // out (4 real additions-or-multiplications per element and level instead of
 // 12): with s = x1 + x2, u = x1 - x2, m = x0 - s/2 and h = sqrt(3)/2,
@@ -29,6 +41,7 @@
 #include <cmath>
 
 #include "tpd.h"
+#include "tpd_arith.cuh"
 
 namespace tpd {
 namespace {
@@ -62,6 +75,33 @@ struct Twiddles {
   T scale;            // factor applied to every output of this launch
 };
 
+// The d-point DFT of one class in the arithmetic T (y_b = sum_c omega^-bc x_c
+// for the decomposition, omega^+bc for the composition).
+template <class T, int D, bool kDec>
+__device__ __forceinline__ void dft_ieee(const Cx<T> (&x)[D], Cx<T> (&y)[D], const Twiddles<T>& tw) {
+  if constexpr (D == 3) {
+    const Cx<T> sm = cadd(x[1], x[2]), u = csub(x[1], x[2]);
+    const Cx<T> m = csub(x[0], Cx<T>{sm.re * T(0.5), sm.im * T(0.5)});
+    const Cx<T> hu = {u.re * tw.h, u.im * tw.h};
+    y[0] = cadd(x[0], sm);
+    // -i h u = (h u.im, -h u.re); the composition takes +i h u for y1
+    const Cx<T> mihu = {hu.im, -hu.re};
+    y[1] = kDec ? cadd(m, mihu) : csub(m, mihu);
+    y[2] = kDec ? csub(m, mihu) : cadd(m, mihu);
+  } else {
+#pragma unroll
+    for (int b = 0; b < D; ++b) {
+      Cx<T> acc = x[0];
+#pragma unroll
+      for (int c = 1; c < D; ++c) {
+        const int k = kDec ? (D - (b * c) % D) % D : (b * c) % D;
+        acc = cadd(acc, cmul(x[c], tw.re[k], tw.im[k]));
+      }
+      y[b] = acc;
+    }
+  }
+}
+
 // One qudit level on every d x d block: digit stride s (d^k for qudit n - k),
 // N = d^n, nblk = (N / D)^2 blocks.
 template <class T, int D, bool kDec>
@@ -90,27 +130,7 @@ __global__ void __launch_bounds__(256) k_weyl_level(typename C2<T>::t* __restric
       Cx<T> x[D], y[D];
 #pragma unroll
       for (int c = 0; c < D; ++c) x[c] = kDec ? in[(c + a) % D][c] : in[c][(a + c) % D];
-      if constexpr (D == 3) {
-        const Cx<T> sm = cadd(x[1], x[2]), u = csub(x[1], x[2]);
-        const Cx<T> m = csub(x[0], Cx<T>{sm.re * T(0.5), sm.im * T(0.5)});
-        const Cx<T> hu = {u.re * tw.h, u.im * tw.h};
-        y[0] = cadd(x[0], sm);
-        // -i h u = (h u.im, -h u.re); the composition takes +i h u for y1
-        const Cx<T> mihu = {hu.im, -hu.re};
-        y[1] = kDec ? cadd(m, mihu) : csub(m, mihu);
-        y[2] = kDec ? csub(m, mihu) : cadd(m, mihu);
-      } else {
-#pragma unroll
-        for (int b = 0; b < D; ++b) {
-          Cx<T> acc = x[0];
-#pragma unroll
-          for (int c = 1; c < D; ++c) {
-            const int k = kDec ? (D - (b * c) % D) % D : (b * c) % D;
-            acc = cadd(acc, cmul(x[c], tw.re[k], tw.im[k]));
-          }
-          y[b] = acc;
-        }
-      }
+      dft_ieee<T, D, kDec>(x, y, tw);
 #pragma unroll
       for (int b = 0; b < D; ++b) {
         if (kDec) out[b][(a + b) % D] = y[b];
@@ -126,6 +146,133 @@ __global__ void __launch_bounds__(256) k_weyl_level(typename C2<T>::t* __restric
         v.y = out[r][c].im * tw.scale;
         mat[base + r * rs + c * s] = v;
       }
+  }
+}
+
+// round(sqrt(3) * 2^62) and (2^64 + 2) / 3
+constexpr long long kSqrt3Q62 = 7987674492471257551ll;
+constexpr long long kThirdQ64 = 0x5555555555555556ll;
+
+// round(u * sqrt(3)) for |u| < 2^61 (the 128-bit product, rounded half up)
+__device__ __forceinline__ long long mul_sqrt3(long long u) {
+  const long long hi = __mul64hi(u, kSqrt3Q62);
+  const unsigned long long lo = (unsigned long long)u * (unsigned long long)kSqrt3Q62;
+  return (long long)(((unsigned long long)hi << 2) | (lo >> 62)) + (long long)((lo >> 61) & 1ull);
+}
+
+// the nearest integer to y / 3 for |y| < 2^62: q = floor(y / 3 + delta) with
+// |delta| < 1/6 is floor(y / 3) or, for y divisible by 3 and negative, one
+// less; the remainder y - 3 q in [0, 3] then says whether to round up
+__device__ __forceinline__ long long div3_rn(long long y) {
+  const long long q = __mul64hi(y, kThirdQ64);
+  const long long r = y - 3 * q;
+  return q + (r >= 2 ? 1 : 0);
+}
+
+__device__ __forceinline__ uint32_t exp_field(double2 v) {
+  return max((uint32_t)__double2hiint(v.x) & 0x7fffffffu, (uint32_t)__double2hiint(v.y) & 0x7fffffffu) >> 20;
+}
+
+// One qudit level in the complex128 block fixed point (d = 2, 3, 4; see the
+// top of this file).  out_pow2 / out_mul: the factor of this level's outputs
+// (the composition's scale, on its last level) beyond the 1/d of the
+// decomposition.
+template <int D, bool kDec>
+__global__ void __launch_bounds__(256) k_weyl_level_fx(double2* __restrict__ mat, long long N, long long s,
+                                                       long long nblk, const Twiddles<double> tw, int out_pow2,
+                                                       double out_mul) {
+  static_assert(D >= 2 && D <= 4, "fixed point for d = 2, 3, 4");
+  using I = long long;
+  constexpr int G = D == 2 ? 1 : (D == 4 ? 2 : 3);   // headroom: |outputs (d = 3: doubled)| < 2^G max
+  constexpr int kLogD = D == 2 ? 1 : (D == 4 ? 2 : 0);
+  const long long M = N / D;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nblk;
+       q += (long long)gridDim.x * blockDim.x) {
+    const long long qr = q / M, qc = q - qr * M;
+    const long long R = (qr / s) * s * D + qr % s;
+    const long long Cc = (qc / s) * s * D + qc % s;
+    const long long base = R * N + Cc, rs = s * N;
+    double2 in[D][D], out[D][D];
+#pragma unroll
+    for (int r = 0; r < D; ++r)
+#pragma unroll
+      for (int c = 0; c < D; ++c) in[r][c] = mat[base + r * rs + c * s];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      double2 x[D];
+      uint32_t E = 0;
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        x[c] = kDec ? in[(c + a) % D][c] : in[c][(a + c) % D];
+        E = max(E, exp_field(x[c]));
+      }
+      double2 y[D];
+      if (E == 2047u) {
+        // Inf or NaN in the class: IEEE fp64, as the plain path
+        Cx<double> xc[D], yc[D];
+#pragma unroll
+        for (int c = 0; c < D; ++c) xc[c] = {x[c].x, x[c].y};
+        dft_ieee<double, D, kDec>(xc, yc, tw);
+#pragma unroll
+        for (int b = 0; b < D; ++b) y[b] = make_double2(yc[b].re * tw.scale, yc[b].im * tw.scale);
+      } else {
+        // onto the class's binary point: x * 2^S, S = 1084 - G - max(E, 1)
+        const int sb = 9 - G - max((int)E, 1);
+        I xr[D], xi[D], yr[D], yi[D];
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          // real parts on the fp64 conversion unit, imaginary parts with
+          // integer instructions (the same values)
+          xr[c] = FixedArith::to_fixed_cvt_class(x[c].x, sb);
+          xi[c] = FixedArith::to_fixed(x[c].y, sb);
+        }
+        int T = sb + 1075;                    // value = sum * 2^-T
+        if constexpr (D == 2) {
+          yr[0] = xr[0] + xr[1]; yi[0] = xi[0] + xi[1];
+          yr[1] = xr[0] - xr[1]; yi[1] = xi[0] - xi[1];
+        } else if constexpr (D == 4) {
+          const I t0r = xr[0] + xr[2], t0i = xi[0] + xi[2], t1r = xr[0] - xr[2], t1i = xi[0] - xi[2];
+          const I t2r = xr[1] + xr[3], t2i = xi[1] + xi[3], t3r = xr[1] - xr[3], t3i = xi[1] - xi[3];
+          yr[0] = t0r + t2r; yi[0] = t0i + t2i;
+          yr[2] = t0r - t2r; yi[2] = t0i - t2i;
+          // decomposition: y1 = t1 - i t3, y3 = t1 + i t3; composition: conjugate twiddles
+          const I pr = t1r + t3i, pi = t1i - t3r, mr = t1r - t3i, mi = t1i + t3r;
+          yr[1] = kDec ? pr : mr; yi[1] = kDec ? pi : mi;
+          yr[3] = kDec ? mr : pr; yi[3] = kDec ? mi : pi;
+        } else {
+          // doubled: 2 y0 = 2 (x0 + s), 2 m = 2 x0 - s, 2 h u = sqrt(3) u
+          const I sr = xr[1] + xr[2], si = xi[1] + xi[2], ur = xr[1] - xr[2], ui = xi[1] - xi[2];
+          yr[0] = (xr[0] + sr) * 2; yi[0] = (xi[0] + si) * 2;
+          const I mr = 2 * xr[0] - sr, mi = 2 * xi[0] - si;
+          const I hr = mul_sqrt3(ur), hi = mul_sqrt3(ui);
+          // decomposition: 2 y1 = 2m - i (2hu), 2 y2 = 2m + i (2hu); composition: conjugate
+          const I ar = mr + hi, ai = mi - hr, br = mr - hi, bi = mi + hr;
+          yr[1] = kDec ? ar : br; yi[1] = kDec ? ai : bi;
+          yr[2] = kDec ? br : ar; yi[2] = kDec ? bi : ai;
+          T += 1;
+          if constexpr (kDec) {               // the 1/3 of the level, on the class grid
+#pragma unroll
+            for (int b = 0; b < D; ++b) { yr[b] = div3_rn(yr[b]); yi[b] = div3_rn(yi[b]); }
+          }
+        }
+        if constexpr (kDec) T += kLogD;       // the 1/d of the level (d = 2, 4)
+        T -= out_pow2;
+#pragma unroll
+        for (int b = 0; b < D; ++b) {
+          y[b] = make_double2(FixedArith::to_double_cvt(yr[b], T), FixedArith::to_double_int(yi[b], T));
+          if (out_mul != 1.0) { y[b].x *= out_mul; y[b].y *= out_mul; }
+        }
+      }
+#pragma unroll
+      for (int b = 0; b < D; ++b) {
+        if (kDec) out[b][(a + b) % D] = y[b];
+        else out[(b + a) % D][b] = y[b];
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < D; ++r)
+#pragma unroll
+      for (int c = 0; c < D; ++c) mat[base + r * rs + c * s] = out[r][c];
   }
 }
 
@@ -149,8 +296,20 @@ Twiddles<T> twiddles(int d, double scale) {
   return t;
 }
 
+// exponent of an exact power of two, else 0 with *resid = v
+int split_pow2(double v, double* resid) {
+  int e = 0;
+  const double m = std::frexp(v, &e);
+  if (m == 0.5 || m == -0.5) {
+    *resid = m < 0 ? -1.0 : 1.0;
+    return e - 1;
+  }
+  *resid = v;
+  return 0;
+}
+
 template <class T, bool kDec>
-cudaError_t launch_levels(void* mat, int n, int d, double last_scale, cudaStream_t st) {
+cudaError_t launch_levels(void* mat, int n, int d, double last_scale, bool fixed, cudaStream_t st) {
   long long N = 1;
   for (int k = 0; k < n; ++k) N *= d;
   const long long nblk = (N / d) * (N / d);
@@ -168,6 +327,21 @@ cudaError_t launch_levels(void* mat, int n, int d, double last_scale, cudaStream
     const double sc = kDec ? 1.0 / d : (k == n - 1 ? last_scale : 1.0);
     const Twiddles<T> tw = twiddles<T>(d, sc);
     S* m = static_cast<S*>(mat);
+    if constexpr (sizeof(T) == 8) {
+      if (fixed && d <= 4) {
+        double resid = 1.0;
+        const int p2 = kDec ? 0 : split_pow2(sc, &resid);
+        double2* md = reinterpret_cast<double2*>(mat);
+        const Twiddles<double>& twd = reinterpret_cast<const Twiddles<double>&>(tw);
+        switch (d) {
+          case 2: k_weyl_level_fx<2, kDec><<<(unsigned)grid, 256, 0, st>>>(md, N, s, nblk, twd, p2, resid); break;
+          case 3: k_weyl_level_fx<3, kDec><<<(unsigned)grid, 256, 0, st>>>(md, N, s, nblk, twd, p2, resid); break;
+          default: k_weyl_level_fx<4, kDec><<<(unsigned)grid, 256, 0, st>>>(md, N, s, nblk, twd, p2, resid); break;
+        }
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        continue;
+      }
+    }
     switch (d) {
       case 2: k_weyl_level<T, 2, kDec><<<(unsigned)grid, 256, 0, st>>>(m, N, s, nblk, tw); break;
       case 3: k_weyl_level<T, 3, kDec><<<(unsigned)grid, 256, 0, st>>>(m, N, s, nblk, tw); break;
@@ -179,8 +353,15 @@ cudaError_t launch_levels(void* mat, int n, int d, double last_scale, cudaStream
   return cudaSuccess;
 }
 
-tpd_status weyl_run(bool dec, void* A, int n, int d, int dtype, double scale, void* stream) {
+tpd_status weyl_run(bool dec, void* A, int n, int d, int dtype, double scale, const tpd_options* opt, void* stream) {
   if (A == nullptr || d < 2 || d > 5 || n < 1 || (dtype != TPD_C128 && dtype != TPD_C64)) return TPD_ERR_INVALID_ARG;
+  // arithmetic: complex128 block fixed point (d <= 4) unless PLAIN is asked
+  // for; complex64 fp32; FIXED for d = 5 or complex64 and COMPENSATED are
+  // not offered
+  const int prec = opt ? opt->precision : TPD_PREC_DEFAULT;
+  if (prec != TPD_PREC_DEFAULT && prec != TPD_PREC_PLAIN && prec != TPD_PREC_FIXED) return TPD_ERR_INVALID_ARG;
+  if (prec == TPD_PREC_FIXED && (dtype != TPD_C128 || d > 4)) return TPD_ERR_INVALID_ARG;
+  const bool fixed = dtype == TPD_C128 && d <= 4 && prec != TPD_PREC_PLAIN;
   long long N = 1;
   for (int k = 0; k < n; ++k) {
     N *= d;
@@ -192,9 +373,11 @@ tpd_status weyl_run(bool dec, void* A, int n, int d, int dtype, double scale, vo
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e;
   if (dtype == TPD_C128)
-    e = dec ? launch_levels<double, true>(A, n, d, 1.0, st) : launch_levels<double, false>(A, n, d, scale, st);
+    e = dec ? launch_levels<double, true>(A, n, d, 1.0, fixed, st)
+            : launch_levels<double, false>(A, n, d, scale, fixed, st);
   else
-    e = dec ? launch_levels<float, true>(A, n, d, 1.0, st) : launch_levels<float, false>(A, n, d, scale, st);
+    e = dec ? launch_levels<float, true>(A, n, d, 1.0, false, st)
+            : launch_levels<float, false>(A, n, d, scale, false, st);
   return e == cudaSuccess ? TPD_OK : TPD_ERR_CUDA;
 }
 
@@ -203,12 +386,13 @@ tpd_status weyl_run(bool dec, void* A, int n, int d, int dtype, double scale, vo
 
 extern "C" {
 
-tpd_status tpd_weyl_decompose(void* A, int n, int d, int dtype, void* stream) {
-  return tpd::weyl_run(true, A, n, d, dtype, 1.0, stream);
+tpd_status tpd_weyl_decompose(void* A, int n, int d, int dtype, const tpd_options* opt, void* stream) {
+  return tpd::weyl_run(true, A, n, d, dtype, 1.0, opt, stream);
 }
 
-tpd_status tpd_weyl_compose(void* C, int n, int d, int dtype, double scale, void* stream) {
-  return tpd::weyl_run(false, C, n, d, dtype, scale, stream);
+tpd_status tpd_weyl_compose(void* C, int n, int d, int dtype, double scale, const tpd_options* opt,
+                            void* stream) {
+  return tpd::weyl_run(false, C, n, d, dtype, scale, opt, stream);
 }
 
 }  // extern "C"

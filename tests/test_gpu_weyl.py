@@ -9,8 +9,13 @@ the final sum (five roundings, plus sqrt(3)/2 rounded once) and the 1/3 scale
 once more; for d = 2, 4, 5 the plain DFT adds at most d - 1 rounded products.
 So each level adds at most c_d u relative error in the 2-norm with c_d <= 16,
 and n levels give ||c^ - c|| <= 16 n u ||c|| (u = 2^-53 complex128, 2^-24
-complex64); the oracle's own fp64 error is far below it.  For d = 2 every
-operation is exact on integer inputs (twiddles +-1, scale 1/2): bit-exact.
+complex64); the oracle's own fp64 error is far below it.  The complex128 block
+fixed point (d = 2, 3, 4) rounds each output once per level (RNE) after sums
+that are exact on its class's grid, up to sqrt(3) and the third rounded on
+that grid (2^-59 of the class's largest element), so it meets the same bound
+-- per weight relative to its own shift's magnitude, since classes never mix
+shifts.  For d = 2 every operation is exact on integer inputs (twiddles +-1,
+scale 1/2): bit-exact in both arithmetics.
 """
 import numpy as np
 import pytest
@@ -66,19 +71,56 @@ def rand(N, seed, hermitian=False):
 
 
 @pytest.mark.parametrize("d,n", [(3, 1), (3, 2), (3, 3), (3, 4), (3, 5), (3, 6), (2, 5), (4, 3), (5, 2), (5, 3)])
-@pytest.mark.parametrize("dtype", ["c128", "c64"])
-def test_weyl_matches_oracle(tpd, d, n, dtype):
+@pytest.mark.parametrize("dtype,precision", [("c128", "fixed"), ("c128", "plain"), ("c64", None)])
+def test_weyl_matches_oracle(tpd, d, n, dtype, precision):
     N = d ** n
     A = rand(N, 1000 + 10 * d + n)
     tt, u = (torch.complex128, U64) if dtype == "c128" else (torch.complex64, U32)
     if dtype == "c64":
         A = A.astype(np.complex64)
+    if precision == "fixed" and d == 5:
+        precision = None                      # d = 5: IEEE fp64 (the default)
     want = core.weyl_coeffs_dft(A.astype(np.complex128), d)
-    got = to_ab(host(tpd.weyl_decompose(gpu(A, tt), d)).astype(np.complex128), d, n)
+    got = to_ab(host(tpd.weyl_decompose(gpu(A, tt), d, precision=precision)).astype(np.complex128), d, n)
     e = rel_err(got, want)
     assert e <= 16 * n * u, "d=%d n=%d %s: %.3e" % (d, n, dtype, e)
     m = np.max(np.abs(got - want)) / np.max(np.abs(want))
     assert m <= 16 * n * u
+
+
+@pytest.mark.parametrize("d", [2, 3, 4])
+def test_weyl_fixed_point_per_class_accuracy(tpd, d):
+    # block fixed point, complex128: each class (the d elements one DFT adds)
+    # has its own binary point, so a weak diagonal beside strong ones keeps
+    # fp64-class accuracy.  A strong diagonal (1e8) and weak off-diagonal
+    # entries (1e-4) in every block: the shifts a != 0 carry only weak
+    # entries, and their weights are checked per weight, relative to their
+    # own shift's magnitude, against the oracle.
+    n = {2: 6, 3: 4, 4: 3}[d]
+    N = d ** n
+    g = np.random.default_rng(1400 + d)
+    A = 1e-4 * (g.standard_normal((N, N)) + 1j * g.standard_normal((N, N)))
+    A[np.arange(N), np.arange(N)] = 1e8 * g.standard_normal(N)
+    want = core.weyl_coeffs_dft(A, d)
+    got = to_ab(host(tpd.weyl_decompose(gpu(A), d, precision="fixed")), d, n)
+    for a in range(1, N):
+        scale = np.max(np.abs(want[a]))
+        assert np.max(np.abs(got[a] - want[a])) <= 16 * n * U64 * scale, "shift %d" % a
+
+
+def test_weyl_fixed_point_non_finite_classes_follow_ieee(tpd):
+    # a class meeting Inf / NaN takes the IEEE DFT: the non-finite weights
+    # are where the fp64 form puts them, the finite ones agree to rounding
+    d, n = 3, 4
+    N = d ** n
+    A = rand(N, 1500)
+    A[7, 11] = np.inf
+    A[40, 2] = complex(0.0, np.nan)
+    fx = host(tpd.weyl_decompose(gpu(A), d, precision="fixed"))
+    fp = host(tpd.weyl_decompose(gpu(A), d, precision="plain"))
+    assert np.array_equal(np.isnan(fx), np.isnan(fp)) and np.array_equal(np.isinf(fx), np.isinf(fp))
+    fin = np.isfinite(fx) & np.isfinite(fp)
+    assert fin.sum() > 0 and rel_err(fx[fin], fp[fin]) <= 32 * n * U64
 
 
 @pytest.mark.parametrize("n", [1, 4, 7])
