@@ -50,10 +50,12 @@ def parse():
     p.add_argument("--qubits", type=int, default=N_QUBITS,
                    help="matrix size of the timed workload (14 = the metric's workload; smaller for profiling)")
     p.add_argument("--no-batch", action="store_true", help="skip the batch-of-4096 comparison run")
-    p.add_argument("--workload", choices=["dense", "batch"], default="dense",
+    p.add_argument("--workload", choices=["dense", "batch", "weyl"], default="dense",
                    help="dense: the metric's n=14 matrix (default); batch: only the batch comparison "
-                        "(--batch-count matrices, n ~ U{3..10}), e.g. for profiling")
+                        "(--batch-count matrices, n ~ U{3..10}); weyl: only the Weyl-basis row "
+                        "(--weyl-n qutrits); e.g. for profiling")
     p.add_argument("--batch-count", type=int, default=4096)
+    p.add_argument("--weyl-n", type=int, default=9, help="qutrits of the --workload weyl matrix")
     p.add_argument("--storage", choices=["c128", "c64"], default="c128",
                    help="dense workload storage (c128 = the metric's; c64 for profiling the fp32 forms)")
     p.add_argument("--precision", choices=["default", "fixed", "plain", "compensated"], default="default")
@@ -877,6 +879,18 @@ def run_batch_only(args):
     return 0
 
 
+def run_weyl_only(args):
+    import torch
+    import paper_2310_13421_gb300 as tpd
+    from paper_2310_13421_gb300 import _lib as L
+    tpd.build()
+    L.load()
+    res, rows = time_weyl(tpd, L, torch, torch.cuda.current_stream(), n=args.weyl_n)
+    res["error_vs_fp64_oracle"] = weyl_accuracy(*rows)
+    print(json.dumps({"workload": "Weyl basis, d = 3, n = %d" % args.weyl_n, "weyl": res}))
+    return 0
+
+
 def main():
     args = parse()
     world, rank, local = dist_env()
@@ -884,6 +898,8 @@ def main():
         return run_reference(args, world, rank)
     if args.workload == "batch":
         return run_batch_only(args)
+    if args.workload == "weyl":
+        return run_weyl_only(args)
     return run_ours(args, world, rank, local)
 
 

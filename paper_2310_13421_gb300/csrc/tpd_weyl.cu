@@ -68,6 +68,36 @@ __device__ __forceinline__ Cx<T> cmul(Cx<T> a, T wr, T wi) {
     return {__fsub_rn(__fmul_rn(a.re, wr), __fmul_rn(a.im, wi)), __fadd_rn(__fmul_rn(a.re, wi), __fmul_rn(a.im, wr))};
 }
 
+// Division of x < 2^32 by a divisor 0 < v < 2^32 fixed per launch: with
+// m = ceil(2^64 / v), floor(x m / 2^64) = floor(x / v) (the excess x (m -
+// 2^64 / v) / 2^64 < 2^-32 is below the gap 1 / v to the next integer).
+struct Div32 {
+  unsigned long long m;
+  uint32_t v;
+};
+inline Div32 make_div32(uint32_t v) {
+  Div32 d;
+  d.v = v;
+  d.m = v == 1 ? 0ull : (~0ull / v) + 1ull;    // ceil(2^64 / v) for every v > 1
+  return d;
+}
+__device__ __forceinline__ uint32_t div32(uint32_t x, const Div32& d) {
+  return d.v == 1 ? x : (uint32_t)__umul64hi((unsigned long long)x, d.m);
+}
+
+// The block of thread item q (q < nblk = (N/D)^2 < 2^30): its first element's
+// index and the stride between its rows (digit k of row and column 0).
+template <int D>
+__device__ __forceinline__ void weyl_block(uint32_t q, long long N, uint32_t s, const Div32& dM, const Div32& ds,
+                                           long long& base, long long& rs) {
+  const uint32_t qr = div32(q, dM), qc = q - qr * dM.v;
+  const uint32_t hr = div32(qr, ds), hc = div32(qc, ds);
+  const long long R = (long long)hr * s * D + (qr - hr * s);   // digit k of the row set to 0
+  const long long Cc = (long long)hc * s * D + (qc - hc * s);  // and of the column
+  base = R * N + Cc;
+  rs = (long long)s * N;
+}
+
 template <class T>
 struct Twiddles {
   T re[8], im[8];     // omega^k, k < d
@@ -178,20 +208,16 @@ __device__ __forceinline__ uint32_t exp_field(double2 v) {
 // (the composition's scale, on its last level) beyond the 1/d of the
 // decomposition.
 template <int D, bool kDec>
-__global__ void __launch_bounds__(256) k_weyl_level_fx(double2* __restrict__ mat, long long N, long long s,
-                                                       long long nblk, const Twiddles<double> tw, int out_pow2,
-                                                       double out_mul) {
+__global__ void __launch_bounds__(256) k_weyl_level_fx(double2* __restrict__ mat, long long N, uint32_t s,
+                                                       uint32_t nblk, const Div32 dM, const Div32 ds,
+                                                       const Twiddles<double> tw, int out_pow2, double out_mul) {
   static_assert(D >= 2 && D <= 4, "fixed point for d = 2, 3, 4");
   using I = long long;
   constexpr int G = D == 2 ? 1 : (D == 4 ? 2 : 3);   // headroom: |outputs (d = 3: doubled)| < 2^G max
   constexpr int kLogD = D == 2 ? 1 : (D == 4 ? 2 : 0);
-  const long long M = N / D;
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nblk;
-       q += (long long)gridDim.x * blockDim.x) {
-    const long long qr = q / M, qc = q - qr * M;
-    const long long R = (qr / s) * s * D + qr % s;
-    const long long Cc = (qc / s) * s * D + qc % s;
-    const long long base = R * N + Cc, rs = s * N;
+  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nblk; q += gridDim.x * blockDim.x) {
+    long long base, rs;
+    weyl_block<D>(q, N, s, dM, ds, base, rs);
     double2 in[D][D], out[D][D];
 #pragma unroll
     for (int r = 0; r < D; ++r)
@@ -221,9 +247,7 @@ __global__ void __launch_bounds__(256) k_weyl_level_fx(double2* __restrict__ mat
         I xr[D], xi[D], yr[D], yi[D];
 #pragma unroll
         for (int c = 0; c < D; ++c) {
-          // real parts on the fp64 conversion unit, imaginary parts with
-          // integer instructions (the same values)
-          xr[c] = FixedArith::to_fixed_cvt_class(x[c].x, sb);
+          xr[c] = FixedArith::to_fixed(x[c].x, sb);
           xi[c] = FixedArith::to_fixed(x[c].y, sb);
         }
         int T = sb + 1075;                    // value = sum * 2^-T
@@ -257,10 +281,22 @@ __global__ void __launch_bounds__(256) k_weyl_level_fx(double2* __restrict__ mat
         }
         if constexpr (kDec) T += kLogD;       // the 1/d of the level (d = 2, 4)
         T -= out_pow2;
+        // |sums| < 2^62: in the normal range after scaling (the usual case),
+        // real parts through the fp64 conversion unit and imaginary parts
+        // through integer instructions (identical roundings); else both the
+        // general way
+        if (FixedArith::fast_range(T)) {
 #pragma unroll
-        for (int b = 0; b < D; ++b) {
-          y[b] = make_double2(FixedArith::to_double_cvt(yr[b], T), FixedArith::to_double_int(yi[b], T));
-          if (out_mul != 1.0) { y[b].x *= out_mul; y[b].y *= out_mul; }
+          for (int b = 0; b < D; ++b)
+            y[b] = make_double2(FixedArith::to_double_cvt_fast(yr[b], T), FixedArith::to_double_fast(yi[b], T));
+        } else {
+#pragma unroll
+          for (int b = 0; b < D; ++b)
+            y[b] = make_double2(FixedArith::to_double_int(yr[b], T), FixedArith::to_double_int(yi[b], T));
+        }
+        if (out_mul != 1.0) {
+#pragma unroll
+          for (int b = 0; b < D; ++b) { y[b].x *= out_mul; y[b].y *= out_mul; }
         }
       }
 #pragma unroll
@@ -312,7 +348,8 @@ template <class T, bool kDec>
 cudaError_t launch_levels(void* mat, int n, int d, double last_scale, bool fixed, cudaStream_t st) {
   long long N = 1;
   for (int k = 0; k < n; ++k) N *= d;
-  const long long nblk = (N / d) * (N / d);
+  const long long nblk = (N / d) * (N / d);   // < 2^30: N <= 65536
+  const Div32 dM = make_div32((uint32_t)(N / d));
   int dev = 0, nsm = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
@@ -323,6 +360,7 @@ cudaError_t launch_levels(void* mat, int n, int d, double last_scale, bool fixed
   using S = typename C2<T>::t;
   long long s = 1;
   for (int k = 0; k < n; ++k, s *= d) {
+    const Div32 ds = make_div32((uint32_t)s);
     // the decomposition's 1/d per level; the composition's scale on its last level
     const double sc = kDec ? 1.0 / d : (k == n - 1 ? last_scale : 1.0);
     const Twiddles<T> tw = twiddles<T>(d, sc);
@@ -334,9 +372,18 @@ cudaError_t launch_levels(void* mat, int n, int d, double last_scale, bool fixed
         double2* md = reinterpret_cast<double2*>(mat);
         const Twiddles<double>& twd = reinterpret_cast<const Twiddles<double>&>(tw);
         switch (d) {
-          case 2: k_weyl_level_fx<2, kDec><<<(unsigned)grid, 256, 0, st>>>(md, N, s, nblk, twd, p2, resid); break;
-          case 3: k_weyl_level_fx<3, kDec><<<(unsigned)grid, 256, 0, st>>>(md, N, s, nblk, twd, p2, resid); break;
-          default: k_weyl_level_fx<4, kDec><<<(unsigned)grid, 256, 0, st>>>(md, N, s, nblk, twd, p2, resid); break;
+          case 2:
+            k_weyl_level_fx<2, kDec><<<(unsigned)grid, 256, 0, st>>>(md, N, (uint32_t)s, (uint32_t)nblk, dM, ds, twd,
+                                                                     p2, resid);
+            break;
+          case 3:
+            k_weyl_level_fx<3, kDec><<<(unsigned)grid, 256, 0, st>>>(md, N, (uint32_t)s, (uint32_t)nblk, dM, ds, twd,
+                                                                     p2, resid);
+            break;
+          default:
+            k_weyl_level_fx<4, kDec><<<(unsigned)grid, 256, 0, st>>>(md, N, (uint32_t)s, (uint32_t)nblk, dM, ds, twd,
+                                                                     p2, resid);
+            break;
         }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         continue;
