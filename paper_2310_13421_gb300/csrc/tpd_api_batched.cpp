@@ -124,9 +124,10 @@ tpd_status run_persistent(bool dec, int arith, void* const* ptrs_dev, const int*
     sg.kind = kSegPipe; sg.n = n; sg.npass = p.npass; sg.desc = ndesc;
     sg.item_start = item_start[n]; sg.nmat = hist[n];
     sg.tiles = p.pass[0].ntiles;
-    // a work item is up to 16 consecutive tiles of one pass of one matrix: the
+    // a work item is up to 32 consecutive tiles of one pass of one matrix: the
     // claim, lookups and completion count are paid once per item (GB300,
-    // 4096-matrix batch: 11.10 / 10.59 / 10.34 / 10.23 ms for 1 / 4 / 8 / 16)
+    // 4096-matrix batch: 11.10 / 10.59 / 10.34 / 10.23 ms for 1 / 4 / 8 / 16
+    // tiles; with the later kernels 9.56 / 9.50 / 9.64 ms for 16 / 32 / 64)
     sg.tpi = sg.tiles < kBatchTilesPerItem ? sg.tiles : kBatchTilesPerItem;
     const long long per_round = (long long)p.npass * (sg.tiles / sg.tpi);
     long long lag = (2 * inflight + per_round - 1) / per_round;

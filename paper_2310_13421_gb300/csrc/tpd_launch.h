@@ -87,7 +87,7 @@ constexpr int kBatchMaxDescs = 16;
 constexpr int kBatchMaxSegs = 12;
 constexpr int kBatchMaxN = 12;
 constexpr int kSegMaxPasses = 3;
-constexpr long long kBatchTilesPerItem = 16;
+constexpr long long kBatchTilesPerItem = 32;
 constexpr int kSegSmall = 0;
 constexpr int kSegPipe = 1;
 
