@@ -21,6 +21,7 @@ PassKernel fixed_table(int shape, int role) {
     case kShapeMid4 * 4 + kInOut: return fixed_k<kDec, kMin, kInOut, kShapeMid4>();
     case kShapeMid4 * 4 + kIn: return fixed_k<kDec, kMin, kIn, kShapeMid4>();
     case kShapeMid4D11 * 4 + kIn: return fixed_k<kDec, kMin, kIn, kShapeMid4D11>();
+    case kShapeMid4D11 * 4 + kInOut: return fixed_k<kDec, kMin, kInOut, kShapeMid4D11>();
     default: return nullptr;
   }
 }

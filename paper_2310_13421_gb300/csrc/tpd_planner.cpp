@@ -303,6 +303,18 @@ bool build_plan(int n, int dtype, int precision, int tile_bits_opt, int max_leve
       }
       g.insert(g.end(), rest.begin(), rest.end());
     }
+    // complex128: a middle pass (int64 in and out) on the smallest tile with
+    // 128-byte runs (2K + lf bits: 2^11 elements for 4 levels, four CTAs of
+    // 128 threads per SM instead of two of 256) -- measured on GB300 with the
+    // compiled layouts, n = 14 middle pass 1.550 -> 1.397 ms, n = 13 0.374 ->
+    // 0.340 ms, n = 16 25.9 / 26.9 -> 21.5 / 24.7 ms; the first and last
+    // passes keep 2^12 (the last one ran 3-4 % slower on 2^11), complex64
+    // keeps 2^12 (plain n = 14 passes 0.62 / 0.64 -> 0.68 / 0.74 ms)
+    if (dtype == 0 && !tile_bits_opt)
+      for (size_t i = 1; i + 1 < g.size(); ++i) {
+        const int Dsmall = std::max(kMinTileBits, 2 * g[i].first + lf);
+        if (Dsmall < g[i].second) g[i].second = Dsmall;
+      }
     return g;
   };
   // the first pass's level count: the least weighted pass count, then the

@@ -42,7 +42,7 @@ enum ShapeId {
   kShapeFirst5,       // 5 levels on 2^12 (n = 13 and others)
   kShapeMid4,         // 4 levels + 4 passengers on 2^12 (most later passes)
   kShapeFirst4,       // 4 levels on 2^12, complex64 compensated first pass (128-byte runs)
-  kShapeMid4D11,      // 4 levels + 3 passengers on 2^11 (n = 15 last pass)
+  kShapeMid4D11,      // 4 levels + 3 passengers on 2^11 (complex128 middle passes, n = 15 last pass)
   kShapeMid3,         // 3 levels + 6 passengers on 2^12 (compensated complex64 last passes)
   kShapeMid5D13,      // 5 levels + 3 passengers on 2^13, one 512-thread CTA (complex64 n = 11, 15)
   kNumShapes

@@ -67,10 +67,11 @@ def test_argument_errors_return_before_any_launch(L):
     # the block fixed point hands one int16 binary point per class (4^n / 2^K
     # of them for a pass of K levels) to the next pass: n = 14, passes of 6, 4
     # and 4 levels, 2 x 2^22 + 2 x 2^24 bytes; zero skipping adds one flag
-    # byte per tile of the passes after the first
+    # byte per tile of the passes after the first (the middle pass on
+    # 2^11-element tiles, 2^17 of them; the last on 2^12, 2^16)
     ws = L.tpd_workspace_size(14, L.TPD_C128, L.options())
     assert ws == 2 * 2 ** 22 + 2 * 2 ** 24
-    assert L.tpd_workspace_size(14, L.TPD_C128, L.options(skip_zero=True)) == ws + 2 ** 16 + 2 ** 16
+    assert L.tpd_workspace_size(14, L.TPD_C128, L.options(skip_zero=True)) == ws + 2 ** 17 + 2 ** 16
     assert L.tpd_workspace_size(14, L.TPD_C128, L.options(precision=1)) == 0      # IEEE: nothing handed on
     assert L.tpd_workspace_size(6, L.TPD_C128, L.options(skip_zero=True)) == 0    # one pass: nothing to hand on
     assert L.tpd_decompose(4096, 10, L.TPD_C128) == L.TPD_ERR_WORKSPACE
@@ -264,16 +265,18 @@ def test_plans_exist_for_every_size(L, n):
 
 def test_plan_choices_measured_on_gb300(L):
     """The planner's measured choices: complex128 n = 15 takes one 5-level pass
-    over 2^13-element tiles between 2^12 and 2^11 ones, n = 16 four passes over
-    2^12 rather than two 2^13 passes; the plain and fixed-point complex64
-    forms plan with 64-byte runs (n = 15 in three passes), the compensated
-    one with 128-byte runs (four)."""
+    over 2^13-element tiles between 2^12 and 2^11 ones, n = 16 four passes
+    rather than two 2^13 passes; complex128 middle passes (int64 in and out)
+    run on 2^11-element tiles, first and last passes on 2^12; the plain and
+    fixed-point complex64 forms plan with 64-byte runs (n = 15 in three
+    passes), the compensated one with 128-byte runs (four)."""
     def shape(n, dtype, prec):
         npass, desc = L.tpd_plan_describe(n, dtype, L.options(precision=prec))
         return [(p["K"], p["D"]) for p in _parse(desc)]
     assert shape(15, 0, 0) == [(6, 12), (5, 13), (4, 11)]
-    assert shape(16, 0, 0) == [(4, 12)] * 4
-    assert shape(14, 0, 0) == [(6, 12), (4, 12), (4, 12)]
+    assert shape(16, 0, 0) == [(4, 12), (4, 11), (4, 11), (4, 12)]
+    assert shape(14, 0, 0) == [(6, 12), (4, 11), (4, 12)]
+    assert shape(14, 1, 1) == [(6, 12), (4, 12), (4, 12)]       # complex64 keeps 2^12
     assert len(shape(15, 1, 3)) == 3 and len(shape(15, 1, 1)) == 3
     assert len(shape(15, 1, 2)) == 4
 
@@ -304,6 +307,8 @@ def test_pass_occupancy_choices(L):
 def test_tuned_defaults_apply_only_when_fields_are_zero(L):
     base = L.tpd_plan_describe(14, 0, L.options())
     small = L.tpd_plan_describe(14, 0, L.options(tile_bits=11))
+    base13 = L.tpd_plan_describe(13, 0, L.options())
+    base14_ieee = L.tpd_plan_describe(14, 0, L.options(precision=1))
     assert base != small
     try:
         assert L.tpd_tune_set(14, 0, 0, L.options(tile_bits=11)) == L.TPD_OK
@@ -314,9 +319,8 @@ def test_tuned_defaults_apply_only_when_fields_are_zero(L):
         assert L.tpd_plan_describe(14, 0, L.options(tile_bits=12)) == L.tpd_plan_describe(14, 0, L.options(
             tile_bits=12, max_levels=0))
         assert L.tpd_plan_describe(14, 0, L.options(max_levels=4))[1] != small[1]
-        assert L.tpd_plan_describe(13, 0, L.options()) == L.tpd_plan_describe(13, 0, L.options(tile_bits=12))
-        assert L.tpd_plan_describe(14, 0, L.options(precision=1)) == L.tpd_plan_describe(14, 0, L.options(
-            precision=1, tile_bits=12))
+        assert L.tpd_plan_describe(13, 0, L.options()) == base13
+        assert L.tpd_plan_describe(14, 0, L.options(precision=1)) == base14_ieee
         # removing the entry restores the planner
         assert L.tpd_tune_set(14, 0, 0, None) == L.TPD_OK
         assert L.tpd_plan_describe(14, 0, L.options()) == base
