@@ -39,6 +39,7 @@
 #include <stdint.h>
 
 #include <cmath>
+#include <type_traits>
 
 #include "tpd.h"
 #include "tpd_arith.cuh"
@@ -365,12 +366,12 @@ cudaError_t launch_levels(void* mat, int n, int d, double last_scale, bool fixed
     const double sc = kDec ? 1.0 / d : (k == n - 1 ? last_scale : 1.0);
     const Twiddles<T> tw = twiddles<T>(d, sc);
     S* m = static_cast<S*>(mat);
-    if constexpr (sizeof(T) == 8) {
+    if constexpr (std::is_same<T, double>::value) {
       if (fixed && d <= 4) {
         double resid = 1.0;
         const int p2 = kDec ? 0 : split_pow2(sc, &resid);
-        double2* md = reinterpret_cast<double2*>(mat);
-        const Twiddles<double>& twd = reinterpret_cast<const Twiddles<double>&>(tw);
+        double2* md = m;
+        const Twiddles<double>& twd = tw;
         switch (d) {
           case 2:
             k_weyl_level_fx<2, kDec><<<(unsigned)grid, 256, 0, st>>>(md, N, (uint32_t)s, (uint32_t)nblk, dM, ds, twd,
