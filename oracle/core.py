@@ -16,7 +16,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "tpd_oracle.c")
 _SRC_ALG2 = os.path.join(_HERE, "tpd_alg2.c")
 _SRC_WEYL = os.path.join(_HERE, "tpd_weyl.c")
-_SOURCES = (_SRC, _SRC_ALG2, _SRC_WEYL)
+_SRC_GM = os.path.join(_HERE, "tpd_gellmann.c")
+_SOURCES = (_SRC, _SRC_ALG2, _SRC_WEYL, _SRC_GM)
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
@@ -24,7 +25,7 @@ _lib = None
 
 
 def build_library(force=False):
-    """Compile tpd_oracle.c, tpd_alg2.c, tpd_weyl.c -> oracle/_build/liboracle.so (gcc, OpenMP)."""
+    """Compile tpd_oracle.c, tpd_alg2.c, tpd_weyl.c, tpd_gellmann.c -> oracle/_build/liboracle.so (gcc, OpenMP)."""
     os.makedirs(_BUILD, exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
             and os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(f) for f in _SOURCES)):
@@ -65,6 +66,12 @@ def _load():
             for f in (lib.oracle_weyl_coeffs, lib.oracle_weyl_coeffs_dft, lib.oracle_weyl_compose):
                 f.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp]
                 f.restype = ctypes.c_int
+            for f in (lib.oracle_gm_coeffs, lib.oracle_gm_compose):
+                f.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp]
+                f.restype = ctypes.c_int
+            i64p = ctypes.POINTER(ctypes.c_int64)
+            lib.oracle_gm_coeffs_at.argtypes = [dp, ctypes.c_int, ctypes.c_int, i64p, i64p, ctypes.c_int64, dp]
+            lib.oracle_gm_coeffs_at.restype = ctypes.c_int
             lib.oracle_num_threads.argtypes = []
             lib.oracle_num_threads.restype = ctypes.c_int
             _lib = lib
@@ -293,3 +300,60 @@ def weyl_compose(C, d):
     if _load().oracle_weyl_compose(_dptr(C), n, d, _dptr(A)):
         raise RuntimeError("oracle_weyl_compose failed")
     return A
+
+
+# ---------------------------------------------------------------- generalized Gell-Mann basis (qudits)
+
+def gellmann_coeffs(A, d):
+    """All d^2n coefficients g_(r,c) = tr(G_(r,c) A) / N_(r,c) in the
+    generalized Gell-Mann basis, as a (d^n, d^n) array indexed [r, c] (the
+    label of each basis element is a position of the d^n x d^n grid; see
+    tpd_gellmann.c).  The trace over the nonzeros of every tensor product."""
+    A, n = _square_d(A, d)
+    N = d ** n
+    out = np.empty((N, N), dtype=np.complex128)
+    if _load().oracle_gm_coeffs(_dptr(A), n, d, _dptr(out)):
+        raise RuntimeError("oracle_gm_coeffs failed")
+    return out
+
+
+def gellmann_coeffs_at(A, d, rows, cols):
+    """The coefficients of the labels (rows[i], cols[i]) (1-D array).  A matrix
+    in another storage type (complex64) is widened to complex128 exactly."""
+    A, n = _square_d(A, d)
+    N = d ** n
+    r = np.ascontiguousarray(rows, dtype=np.int64)
+    c = np.ascontiguousarray(cols, dtype=np.int64)
+    if r.shape != c.shape or r.ndim != 1:
+        raise ValueError("rows and cols must be 1-D arrays of one length")
+    if np.any(r < 0) or np.any(r >= N) or np.any(c < 0) or np.any(c >= N):
+        raise ValueError("label out of range")
+    out = np.empty(r.shape[0], dtype=np.complex128)
+    i64 = ctypes.POINTER(ctypes.c_int64)
+    if _load().oracle_gm_coeffs_at(_dptr(A), n, d, r.ctypes.data_as(i64), c.ctypes.data_as(i64), r.shape[0],
+                                   _dptr(out)):
+        raise RuntimeError("oracle_gm_coeffs_at failed")
+    return out
+
+
+def gellmann_compose(C, d):
+    """A = sum_(r,c) g_(r,c) G_(r,c) from the (d^n, d^n) coefficient array."""
+    C, n = _square_d(C, d)
+    N = d ** n
+    A = np.empty((N, N), dtype=np.complex128)
+    if _load().oracle_gm_compose(_dptr(C), n, d, _dptr(A)):
+        raise RuntimeError("oracle_gm_compose failed")
+    return A
+
+
+def gellmann_norms(d, n):
+    """N_(r,c) = tr(G_(r,c)^2) = prod over qudits of (d for the identity, 2
+    otherwise), as a (d^n, d^n) float array [r, c]."""
+    N = d ** n
+    r = np.repeat(np.arange(N), N).reshape(N, N)
+    c = np.tile(np.arange(N), N).reshape(N, N)
+    out = np.ones((N, N))
+    for _ in range(n):
+        out *= np.where((r % d == 0) & (c % d == 0), float(d), 2.0)
+        r, c = r // d, c // d
+    return out

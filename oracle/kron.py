@@ -86,3 +86,51 @@ def weyl_coeffs_kron(A, d):
             W = weyl_operator(d, _digits(a, d, n), _digits(b, d, n))
             out[a, b] = np.trace(W.conj().T @ A) / N
     return out
+
+
+# ---------------------------------------------------------------- generalized Gell-Mann basis (qudits)
+
+def gellmann_single(d, r, c):
+    """The single-qudit generalized Gell-Mann element of label (r, c), a dense
+    d x d matrix: the identity at (0, 0); the diagonal element
+    sqrt(2 / (l (l+1))) diag(1, ..., 1, -l, 0, ..., 0) (l ones) at (l, l);
+    E_rc + E_cr at (r, c) above the diagonal; -i E_cr + i E_rc at (r, c)
+    below it (the antisymmetric element of the pair c < r)."""
+    G = np.zeros((d, d), dtype=np.complex128)
+    if r == 0 and c == 0:
+        return np.eye(d, dtype=np.complex128)
+    if r == c:
+        diag = np.zeros(d)
+        diag[:r] = 1.0
+        diag[r] = -r
+        return np.diag(diag * np.sqrt(2.0 / (r * (r + 1)))).astype(np.complex128)
+    if r < c:
+        G[r, c] = G[c, r] = 1.0
+    else:
+        j, k = c, r
+        G[j, k] = -1j
+        G[k, j] = 1j
+    return G
+
+
+def gellmann_operator(d, r_digits, c_digits):
+    """The tensor product over qudits (qudit 1 outermost) of the single-qudit
+    elements labelled (r_j, c_j)."""
+    m = np.ones((1, 1), dtype=np.complex128)
+    for rj, cj in zip(r_digits, c_digits):
+        m = np.kron(m, gellmann_single(d, rj, cj))
+    return m
+
+
+def gellmann_coeffs_kron(A, d):
+    """g_(r,c) = tr(G_(r,c) A) / tr(G_(r,c)^2) for all labels by dense
+    products: (d^n, d^n) array [r, c]."""
+    A = np.asarray(A, dtype=np.complex128)
+    N = A.shape[0]
+    n = int(round(np.log(N) / np.log(d)))
+    out = np.empty((N, N), dtype=np.complex128)
+    for r in range(N):
+        for c in range(N):
+            G = gellmann_operator(d, _digits(r, d, n), _digits(c, d, n))
+            out[r, c] = np.trace(G @ A) / np.trace(G @ G).real
+    return out
