@@ -50,10 +50,10 @@ def parse():
     p.add_argument("--qubits", type=int, default=N_QUBITS,
                    help="matrix size of the timed workload (14 = the metric's workload; smaller for profiling)")
     p.add_argument("--no-batch", action="store_true", help="skip the batch-of-4096 comparison run")
-    p.add_argument("--workload", choices=["dense", "batch", "weyl"], default="dense",
+    p.add_argument("--workload", choices=["dense", "batch", "weyl", "gellmann"], default="dense",
                    help="dense: the metric's n=14 matrix (default); batch: only the batch comparison "
-                        "(--batch-count matrices, n ~ U{3..10}); weyl: only the Weyl-basis row "
-                        "(--weyl-n qutrits); e.g. for profiling")
+                        "(--batch-count matrices, n ~ U{3..10}); weyl / gellmann: only the Weyl- or "
+                        "Gell-Mann-basis row (--weyl-n qutrits); e.g. for profiling")
     p.add_argument("--batch-count", type=int, default=4096)
     p.add_argument("--weyl-n", type=int, default=9, help="qutrits of the --workload weyl matrix")
     p.add_argument("--storage", choices=["c128", "c64"], default="c128",
@@ -418,6 +418,60 @@ def weyl_accuracy(A, d, a_s, results):
             for name, got in results.items()}
 
 
+def time_gellmann(tpd, L, torch, stream, d=3, n=9, seed=1007, labels=256, A=None):
+    """Decomposition in the generalized Gell-Mann basis of n qudits of
+    dimension d (the other basis Sec. V names): a random d^n x d^n Hermitian
+    matrix (or the given one), complex128 (fp64) and complex64 (fp32), one
+    launch per qudit level, each reading and writing the whole matrix.
+    Returns the timings and, for the accuracy leg, the coefficients of a
+    sample of labels (r, c) of each result."""
+    from paper_2310_13421_gb300 import synth
+    N = d ** n
+    if A is None:
+        A = synth.hermitian_side(N, seed)
+    rng = np.random.default_rng(seed)
+    rows_, cols_ = rng.integers(0, N, labels), rng.integers(0, N, labels)
+    rows_[:3], cols_[:3] = (0, N - 1, 0), (0, N - 1, N - 1)
+    pos = torch.from_numpy(rows_ * N + cols_)
+    out, got = {"d": d, "n": n, "side": N}, {}
+    legs = (("c128", torch.complex128, L.TPD_C128, 16, "fp64, rounded every level"),
+            ("c64", torch.complex64, L.TPD_C64, 8, "fp32, rounded every level"))
+    for name, tt, code, elem, arith in legs:
+        src = torch.from_numpy(A).to("cuda", tt)
+        work = torch.empty_like(src)
+
+        def step():
+            st = L.tpd_gellmann_decompose(work.data_ptr(), n, d, code, None, stream.cuda_stream)
+            assert st == 0, L.status_string(st)
+
+        ms = _event_ms(torch, stream, step, setup=lambda: work.copy_(src))
+        alg = 2 * n * N * N * elem
+        imag_max = float(work.imag.abs().max().item())
+        out[name] = {"ms": ms, "coeffs_per_s": N * N / (ms * 1e-3), "hbm_gbs_algorithmic": alg / (ms * 1e-3) / 1e9,
+                     "launches": n, "arithmetic": arith, "hermitian_input_max_abs_imag": imag_max}
+        got[name] = work.reshape(-1).index_select(0, pos.cuda()).cpu().numpy().astype(np.complex128)
+        del src, work
+        torch.cuda.empty_cache()
+    return out, (A, d, rows_, cols_, got)
+
+
+def gellmann_accuracy(A, d, rows_, cols_, results):
+    """Accuracy leg for the Gell-Mann basis: the sampled labels' coefficients
+    against the Gell-Mann oracle (fp64) on the same matrix, in the weighted
+    norm sqrt(sum tr(G^2) |g|^2) over the sample."""
+    from oracle import core
+    want = core.gellmann_coeffs_at(A, d, rows_, cols_)
+    n = int(round(np.log(A.shape[0]) / np.log(d)))
+    w = np.ones(len(rows_))
+    r, c = np.array(rows_), np.array(cols_)
+    for _ in range(n):
+        w *= np.where((r % d == 0) & (c % d == 0), float(d), 2.0)
+        r, c = r // d, c // d
+    w = np.sqrt(w)
+    return {name: {"normwise_weighted": float(np.linalg.norm(w * (got - want)) / np.linalg.norm(w * want)),
+                   "coefficients": int(want.size)} for name, got in results.items()}
+
+
 def alg2_baseline(A, W_rc, n, samples=1 << 20):
     """The paper's algorithm on the host over the whole matrix -- the
     iterative form (Alg. 2, the CMWs of Eq. 4 level by level in place) on one
@@ -750,7 +804,7 @@ def run_ours(args, world, rank, local):
     extra = {}
     paper_arith = None
     acc_rows = {}            # results sampled for the accuracy leg: config -> (A, n, xs, {form: rows})
-    weyl_rows = None
+    weyl_rows = gm_rows = None
     if not args.no_extra and not c64 and prec_eff == L.TPD_PREC_FIXED:
         # fp64 butterfly (IEEE double, rounded per level) on the same matrix
         s64, p64, np64 = time_decompose(tpd, L, torch, work, pristine, n, 5, 2, L.TPD_PREC_PLAIN, stream)
@@ -820,6 +874,7 @@ def run_ours(args, world, rank, local):
         extra["rows_n14"] = time_rows(tpd, L, torch, stream)
         extra["helpers_n14"] = time_helpers(tpd, L, torch, stream)
         extra["weyl_d3_n9"], weyl_rows = time_weyl(tpd, L, torch, stream)
+        extra["gellmann_d3_n9"], gm_rows = time_gellmann(tpd, L, torch, stream, A=weyl_rows[0])
     if not args.no_extra and not args.no_batch and not c64:
         extra["batch_4096_n3_10"] = time_batch(tpd, L, torch, stream)
 
@@ -836,6 +891,9 @@ def run_ours(args, world, rank, local):
     if weyl_rows is not None and rank == 0 and world == 1:
         extra["weyl_d3_n9"]["error_vs_fp64_oracle"] = weyl_accuracy(*weyl_rows)
         weyl_rows = None
+    if gm_rows is not None and rank == 0 and world == 1:
+        extra["gellmann_d3_n9"]["error_vs_fp64_oracle"] = gellmann_accuracy(*gm_rows)
+        gm_rows = None
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -891,6 +949,18 @@ def run_weyl_only(args):
     return 0
 
 
+def run_gellmann_only(args):
+    import torch
+    import paper_2310_13421_gb300 as tpd
+    from paper_2310_13421_gb300 import _lib as L
+    tpd.build()
+    L.load()
+    res, rows = time_gellmann(tpd, L, torch, torch.cuda.current_stream(), n=args.weyl_n)
+    res["error_vs_fp64_oracle"] = gellmann_accuracy(*rows)
+    print(json.dumps({"workload": "generalized Gell-Mann basis, d = 3, n = %d" % args.weyl_n, "gellmann": res}))
+    return 0
+
+
 def main():
     args = parse()
     world, rank, local = dist_env()
@@ -900,6 +970,8 @@ def main():
         return run_batch_only(args)
     if args.workload == "weyl":
         return run_weyl_only(args)
+    if args.workload == "gellmann":
+        return run_gellmann_only(args)
     return run_ours(args, world, rank, local)
 
 

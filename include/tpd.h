@@ -353,6 +353,46 @@ tpd_status tpd_weyl_decompose(void* A, int n, int d, int dtype, const tpd_option
 tpd_status tpd_weyl_compose(void* C, int n, int d, int dtype, double scale, const tpd_options* opt,
                             void* stream);
 
+/* Decomposition in the generalized Gell-Mann basis of n qudits of dimension
+ * d -- the other tensorized basis Sec. V (Conclusion and Outlook) names as a
+ * natural candidate for the method.  One qudit's d^2 Hermitian elements are
+ * labelled by a position (r, c) of the d x d grid (E_jk the matrix unit):
+ *     (0, 0)           the identity                                   tr(G^2) = d
+ *     (l, l), l >= 1   D_l = sqrt(2 / (l (l+1))) (sum_{m<l} E_mm - l E_ll)     2
+ *     (j, k), j < k    S_jk = E_jk + E_kj                                       2
+ *     (k, j), j < k    A_jk = -i E_jk + i E_kj                                  2
+ * (d = 2: I, X, Y, Z at the positions Eq. 4 gives their weights; d = 3:
+ * Gell-Mann's lambda_1..lambda_8).  An n-qudit element is the tensor product
+ * over the digit pairs of its label (qudit 1 the most significant base-d
+ * digit of row and column), N_(r,c) the product of the traces, and in place
+ *
+ *     g_(r,c) = tr(G_(r,c) A) / N_(r,c),       A = sum_(r,c) g_(r,c) G_(r,c),
+ *
+ * by the recursion of Eqs. 3-5 with d x d blocks: each qudit level maps every
+ * block x to (x_jk + x_kj)/2 at (j, k), i (x_jk - x_kj)/2 at (k, j),
+ * c_l/2 (sum_{m<l} x_mm - l x_ll) at (l, l) and (1/d) sum_m x_mm at (0, 0)
+ * (c_l = sqrt(2 / (l (l+1)))); for d = 2 this is Eq. 4.
+ *   A       device, d^n x d^n complex of `dtype` (row-major, 16- / 8-byte
+ *           aligned); on return g_(r,c) sits at row r, column c.
+ *   n, d    1 <= n, 2 <= d <= 5, d^n <= 65536.
+ *   dtype   TPD_C128 (IEEE fp64) or TPD_C64 (fp32), rounded every level,
+ *           no fused multiply-adds: a Hermitian input gives exactly real
+ *           coefficients.
+ *   opt     may be NULL; opt->precision DEFAULT or PLAIN (the same
+ *           arithmetic); FIXED and COMPENSATED are INVALID_ARG.
+ * One kernel launch per qudit; no workspace; asynchronous on `stream`.
+ * Errors: INVALID_ARG, MISALIGNED, CUDA. */
+tpd_status tpd_gellmann_decompose(void* A, int n, int d, int dtype, const tpd_options* opt, void* stream);
+
+/* Generalized Gell-Mann composition in place: C holds g_(r,c) at row r,
+ * column c; on return it holds scale * sum g_(r,c) G_(r,c) (scale applied on
+ * the last level; scale = 1 inverts tpd_gellmann_decompose).  The adjoint of
+ * the decomposition is this composition applied to g_(r,c) / N_(r,c).  scale
+ * finite and nonzero.  Arguments, arithmetic and errors as
+ * tpd_gellmann_decompose. */
+tpd_status tpd_gellmann_compose(void* C, int n, int d, int dtype, double scale, const tpd_options* opt,
+                                void* stream);
+
 /* Layout conversion, out of place.  RC is the layout every decomposition
  * leaves (see the conventions above); STRING puts the weight of
  * t = (t_1, ..., t_n) at the base-4 index s = sum_j t_j 4^(n-j) (t_1 most

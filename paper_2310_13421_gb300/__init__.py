@@ -15,12 +15,15 @@ The CUDA library ``libtpd.so`` is loaded lazily on first use (the submodule
     decompose_coo(r, c, v, n)  sparse input: the list L from the nonzero entries (Alg. 2 on entries)
     weyl_decompose(A, d)       the same recursion in the Weyl (clock-and-shift) basis of qudits (Sec. V)
     weyl_compose(C, d)         its inverse / adjoint
+    gellmann_decompose(A, d)   the same recursion in the generalized Gell-Mann basis of qudits (Sec. V)
+    gellmann_compose(C, d)     its inverse
     string_order(n)            RC layout -> string order permutation (host index array)
     build()                    compile libtpd.so in-tree
 """
 __all__ = ["decompose", "compose", "decompose_batched", "compose_batched", "Batch", "Partial", "TPDFunction", "tpd",
            "string_order", "to_string_layout", "from_string_layout", "sum_squares", "nonzero_list", "decompose_coo",
-           "workspace_size", "weyl_decompose", "weyl_compose", "build"]
+           "workspace_size", "weyl_decompose", "weyl_compose", "gellmann_decompose", "gellmann_compose",
+           "build"]
 
 
 def build(force=False, verbose=False):
@@ -31,7 +34,8 @@ def build(force=False, verbose=False):
 def __getattr__(name):
     if name in ("decompose", "compose", "decompose_batched", "compose_batched", "Batch", "Partial", "string_order",
                 "to_string_layout", "from_string_layout", "sum_squares", "nonzero_list", "decompose_coo",
-                "workspace_size", "make_options", "weyl_decompose", "weyl_compose"):
+                "workspace_size", "make_options", "weyl_decompose", "weyl_compose", "gellmann_decompose",
+                "gellmann_compose"):
         from . import api
         return getattr(api, name)
     if name in ("TPDFunction", "tpd"):

@@ -31,7 +31,8 @@ SYMBOLS = (
     "tpd_tune_set", "tpd_tune_clear", "tpd_batch_status", "tpd_test_hold_batch_waits",
     "tpd_convert_layout", "tpd_sum_squares", "tpd_partial_workspace_size", "tpd_partial_prepare",
     "tpd_decompose_partial", "tpd_nonzero_workspace_size", "tpd_nonzero_list", "tpd_sparse_workspace_size",
-    "tpd_decompose_coo", "tpd_weyl_decompose", "tpd_weyl_compose",
+    "tpd_decompose_coo", "tpd_weyl_decompose", "tpd_weyl_compose", "tpd_gellmann_decompose",
+    "tpd_gellmann_compose",
 )
 
 # size of the library's own scratch array used by tpd_decompose_noalloc
@@ -101,6 +102,10 @@ def load(path=None):
         lib.tpd_weyl_decompose.restype = i
         lib.tpd_weyl_compose.argtypes = [vp, i, i, i, ctypes.c_double, op, vp]
         lib.tpd_weyl_compose.restype = i
+        lib.tpd_gellmann_decompose.argtypes = [vp, i, i, i, op, vp]
+        lib.tpd_gellmann_decompose.restype = i
+        lib.tpd_gellmann_compose.argtypes = [vp, i, i, i, ctypes.c_double, op, vp]
+        lib.tpd_gellmann_compose.restype = i
         lib.tpd_convert_layout.argtypes = [vp, vp, i, i, i, vp]
         lib.tpd_convert_layout.restype = i
         lib.tpd_sum_squares.argtypes = [vp, sz, i, vp, vp, sz, vp]
@@ -214,6 +219,14 @@ def tpd_weyl_decompose(A, n, d, dtype, opt=None, stream=0):
 
 def tpd_weyl_compose(C, n, d, dtype, scale, opt=None, stream=0):
     return int(load().tpd_weyl_compose(C or None, n, d, dtype, float(scale), _opt(opt), stream or None))
+
+
+def tpd_gellmann_decompose(A, n, d, dtype, opt=None, stream=0):
+    return int(load().tpd_gellmann_decompose(A or None, n, d, dtype, _opt(opt), stream or None))
+
+
+def tpd_gellmann_compose(C, n, d, dtype, scale, opt=None, stream=0):
+    return int(load().tpd_gellmann_compose(C or None, n, d, dtype, float(scale), _opt(opt), stream or None))
 
 
 def tpd_convert_layout(src, dst, n, dtype, to_string, stream=0):

@@ -367,6 +367,35 @@ def weyl_compose(C, d, *, scale=1.0, inplace=False, precision=None, stream=None)
     return out
 
 
+def gellmann_decompose(A, d, *, inplace=False, precision=None, stream=None):
+    """Coefficients g_(r,c) = tr(G_(r,c) A) / tr(G_(r,c)^2) of a d^n x d^n CUDA
+    matrix in the generalized Gell-Mann basis (identity, diagonal,
+    symmetric and antisymmetric elements; d = 2: the Pauli basis); g_(r,c)
+    sits at row r, column c (see tpd_gellmann_decompose).  IEEE arithmetic
+    of the storage type; precision None or "plain"."""
+    _check_device(A)
+    n = _qudits(A, d)
+    opt = make_options(precision)
+    with _enqueue(A.device, stream, A) as s:
+        out = A if inplace else A.clone()
+        st = L.tpd_gellmann_decompose(out.data_ptr(), n, int(d), _dtype_code(A), opt, s)
+    _raise(st, "tpd_gellmann_decompose")
+    return out
+
+
+def gellmann_compose(C, d, *, scale=1.0, inplace=False, precision=None, stream=None):
+    """scale * sum g_(r,c) G_(r,c) from coefficients in the layout of
+    gellmann_decompose (scale 1: its inverse)."""
+    _check_device(C)
+    n = _qudits(C, d)
+    opt = make_options(precision)
+    with _enqueue(C.device, stream, C) as s:
+        out = C if inplace else C.clone()
+        st = L.tpd_gellmann_compose(out.data_ptr(), n, int(d), _dtype_code(C), float(scale), opt, s)
+    _raise(st, "tpd_gellmann_compose")
+    return out
+
+
 def string_order(n):
     """Index array p with p[s] = flat RC position of string s (base-4 string
     index, t_1 most significant): rc_tensor.flatten()[p] is in string order."""

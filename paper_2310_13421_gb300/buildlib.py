@@ -22,7 +22,7 @@ CU_SOURCES = ["tpd_kernels_fixed_dec.cu", "tpd_kernels_fixed_com.cu", "tpd_kerne
               "tpd_kernels_shapes_fixed.cu", "tpd_kernels_shapes_c64.cu", "tpd_kernels_shapes_f32.cu",
               "tpd_kernels_shapes_fx32.cu",
               "tpd_kernels_batch_ieee.cu", "tpd_kernels_c128.cu", "tpd_kernels_c64.cu", "tpd_noalloc.cu", "tpd_layout.cu",
-              "tpd_sparse.cu", "tpd_weyl.cu"]
+              "tpd_sparse.cu", "tpd_weyl.cu", "tpd_gellmann.cu"]
 CPP_SOURCES = ["tpd_api.cpp", "tpd_api_batched.cpp", "tpd_api_extra.cpp", "tpd_planner.cpp"]
 
 

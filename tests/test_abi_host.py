@@ -118,6 +118,19 @@ def test_argument_errors_return_before_any_launch(L):
     assert L.tpd_weyl_decompose(4096, 3, 3, L.TPD_C64, fixed) == L.TPD_ERR_INVALID_ARG      # fixed: complex128
     assert L.tpd_weyl_decompose(4096, 3, 5, L.TPD_C128, fixed) == L.TPD_ERR_INVALID_ARG     # fixed: d <= 4
     assert L.tpd_weyl_decompose(4096, 3, 3, L.TPD_C128, comp) == L.TPD_ERR_INVALID_ARG      # no compensated form
+    # generalized Gell-Mann basis: d in 2..5, d^n <= 65536, IEEE arithmetic only
+    assert L.tpd_gellmann_decompose(4096, 3, 1, L.TPD_C128) == L.TPD_ERR_INVALID_ARG      # d = 1
+    assert L.tpd_gellmann_decompose(4096, 3, 6, L.TPD_C128) == L.TPD_ERR_INVALID_ARG      # d = 6
+    assert L.tpd_gellmann_decompose(4096, 0, 3, L.TPD_C128) == L.TPD_ERR_INVALID_ARG      # n = 0
+    assert L.tpd_gellmann_decompose(4096, 7, 5, L.TPD_C128) == L.TPD_ERR_INVALID_ARG      # 5^7 > 65536
+    assert L.tpd_gellmann_decompose(0, 3, 3, L.TPD_C128) == L.TPD_ERR_INVALID_ARG         # null
+    assert L.tpd_gellmann_decompose(4096, 3, 3, 5) == L.TPD_ERR_INVALID_ARG               # dtype
+    assert L.tpd_gellmann_decompose(4104, 3, 3, L.TPD_C128) == L.TPD_ERR_MISALIGNED
+    assert L.tpd_gellmann_decompose(4096, 3, 3, L.TPD_C128, fixed) == L.TPD_ERR_INVALID_ARG
+    assert L.tpd_gellmann_decompose(4096, 3, 3, L.TPD_C64, comp) == L.TPD_ERR_INVALID_ARG
+    assert L.tpd_gellmann_compose(4096, 3, 3, L.TPD_C128, 0.0) == L.TPD_ERR_INVALID_ARG
+    assert L.tpd_gellmann_compose(4096, 3, 3, L.TPD_C128, float("inf")) == L.TPD_ERR_INVALID_ARG
+    assert L.tpd_gellmann_compose(4100, 3, 3, L.TPD_C64, 1.0) == L.TPD_ERR_MISALIGNED
     # layout conversion and sums of squares
     assert L.tpd_convert_layout(4096, 1 << 20, 0, L.TPD_C128, 1) == L.TPD_ERR_INVALID_ARG      # n = 0
     assert L.tpd_convert_layout(4096, 4096 + 256, 4, L.TPD_C128, 1) == L.TPD_ERR_INVALID_ARG   # overlap

@@ -92,3 +92,20 @@ def test_weyl_rows_follow_the_kernel_layout():
     assert np.array_equal(got, c[a_s])
     acc = bench.weyl_accuracy(A, d, a_s, {"exact": got})["exact"]
     assert acc["normwise"] == 0.0
+
+
+def test_gellmann_accuracy_leg_reads_labels_at_their_positions():
+    # the Gell-Mann oracle's coefficients sit at row r, column c of their
+    # label (the kernel's layout): read back at the bench's sampled labels
+    # they give zero error, and a perturbed one a positive weighted error
+    from oracle import core
+    d, n = 3, 4
+    N = d ** n
+    A = synth.hermitian_side(N, seed=6)
+    g = core.gellmann_coeffs(A, d)
+    rows, cols = np.array([0, N - 1, 0, 7, 40]), np.array([0, N - 1, N - 1, 3, 40])
+    acc = bench.gellmann_accuracy(A, d, rows, cols, {"exact": g[rows, cols]})["exact"]
+    assert acc["normwise_weighted"] == 0.0 and acc["coefficients"] == 5
+    bad = g[rows, cols].copy()
+    bad[1] += 1e-6
+    assert bench.gellmann_accuracy(A, d, rows, cols, {"bad": bad})["bad"]["normwise_weighted"] > 0
