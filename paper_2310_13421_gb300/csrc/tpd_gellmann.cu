@@ -55,6 +55,30 @@ __device__ __forceinline__ float gadd(float a, float b) { return __fadd_rn(a, b)
 __device__ __forceinline__ float gsub(float a, float b) { return __fsub_rn(a, b); }
 __device__ __forceinline__ float gmul(float a, float b) { return __fmul_rn(a, b); }
 
+// x / 2 and 2 x.  For complex128 with integer instructions, bit for bit the
+// fp64 product for every input (normal: the exponent field moves by one;
+// zero and subnormal: the magnitude bits halved to nearest even, or doubled;
+// 2 x beyond the largest double: Inf; Inf and NaN pass unchanged), so the
+// fp64 pipe -- which bounds these kernels on GB300 -- only carries the adds,
+// subtractions and the irrational diagonal factors.  complex64: the fp32
+// multiply (not the bound there).
+__device__ __forceinline__ double ghalf(double x) {
+  const long long b = __double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7FF);
+  const long long sgn = b & (long long)0x8000000000000000ull, v = b & 0x7FFFFFFFFFFFFFFFll;
+  const long long sub = sgn | ((v >> 1) + ((v & (v >> 1)) & 1));         // e <= 1: v / 2, ties to even
+  return __longlong_as_double(e >= 2 && e < 0x7FF ? b - (1ll << 52) : (e < 2 ? sub : b));
+}
+__device__ __forceinline__ double gtwice(double x) {
+  const long long b = __double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7FF);
+  const long long sgn = b & (long long)0x8000000000000000ull, v = b & 0x7FFFFFFFFFFFFFFFll;
+  return __longlong_as_double(e == 0 ? (sgn | (v << 1))
+                                     : e < 0x7FE ? b + (1ll << 52) : (e == 0x7FE ? (sgn | 0x7FF0000000000000ll) : b));
+}
+__device__ __forceinline__ float ghalf(float x) { return __fmul_rn(x, 0.5f); }
+__device__ __forceinline__ float gtwice(float x) { return __fmul_rn(x, 2.0f); }
+
 template <class T>
 struct GmConst {
   T hc[kGmMaxD];   // c_l / 2: the decomposition's diagonal factors (l >= 1)
@@ -91,9 +115,8 @@ __global__ void __launch_bounds__(256) k_gellmann_level(typename GmVec<T>::t* __
       for (int i = j + 1; i < D; ++i) {
         const S a = x[j][i], b = x[i][j];
         if constexpr (kDec) {
-          const T h = T(0.5);
-          y[j][i] = {gmul(gadd(a.x, b.x), h), gmul(gadd(a.y, b.y), h)};
-          const T tr = gmul(gsub(a.x, b.x), h), ti = gmul(gsub(a.y, b.y), h);
+          y[j][i] = {ghalf(gadd(a.x, b.x)), ghalf(gadd(a.y, b.y))};
+          const T tr = ghalf(gsub(a.x, b.x)), ti = ghalf(gsub(a.y, b.y));
           y[i][j] = {-ti, tr};                                   // i (a - b) / 2
         } else {
           y[j][i] = {gadd(a.x, b.y), gsub(a.y, b.x)};            // a - i b
@@ -107,11 +130,14 @@ __global__ void __launch_bounds__(256) k_gellmann_level(typename GmVec<T>::t* __
 #pragma unroll
       for (int l = 1; l < D; ++l) {
         const S xl = x[l][l];
-        const S lx = l == 1 ? xl : S{gmul(k.l[l], xl.x), gmul(k.l[l], xl.y)};
+        S lx = xl;                                               // l x_ll
+        if (l == 2) lx = S{gtwice(xl.x), gtwice(xl.y)};
+        if (l >= 3) lx = S{gmul(k.l[l], xl.x), gmul(k.l[l], xl.y)};
         y[l][l] = {gmul(k.hc[l], gsub(P.x, lx.x)), gmul(k.hc[l], gsub(P.y, lx.y))};
         P = {gadd(P.x, xl.x), gadd(P.y, xl.y)};
       }
-      y[0][0] = {gmul(P.x, k.inv_d), gmul(P.y, k.inv_d)};
+      if constexpr (D == 2) y[0][0] = {ghalf(P.x), ghalf(P.y)};
+      else y[0][0] = {gmul(P.x, k.inv_d), gmul(P.y, k.inv_d)};
     } else {
       const S y0 = x[0][0];
       S Q = {T(0), T(0)};                                        // running sum_{l>m} c_l y_ll
