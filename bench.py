@@ -10,11 +10,17 @@ outside the timed events.
 Prints ONE JSON line (rank 0).  `value` = Pauli coeffs/s over all ranks with
 inputs resident in HBM; `e2e` = the same metric through the C ABI with host
 buffers (pinned), every step's host<->device copies inside the timed region
-(steps alternate over two streams, so copies in and out overlap); `roofline`
-= achieved HBM bandwidth of the pass kernel (algorithmic bytes: read + write
-of the matrix per pass launch) against the measured copy peak; `cpu_baseline`
-= the CPU oracle timed on a bounded sample; `extra` = the fp64 butterfly and
-the complex64 plain / compensated forms at n = 15.
+(steps alternate over three streams with their own buffers, so one step's
+copies overlap another's); `roofline` = achieved HBM bandwidth of the pass
+kernel (algorithmic bytes: read + write of the matrix per pass launch)
+against the measured copy peak; `paper_arithmetic` = the same metric with
+IEEE fp64 adds rounded per level; `cpu_baseline` = the CPU oracle timed on a
+bounded sample; `extra` = the complex64 plain / compensated / fixed-point
+forms at n = 15 beside the complex128 ones, the errors of every form against
+the fp64 oracle, the batch of 4096 matrices, the partial decomposition, zero
+skipping, sparse input, composition, autograd, the layout and norm helpers,
+the Weyl and generalized Gell-Mann bases (d = 3, n = 9) and the paper's
+Alg. 2 on the host.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
