@@ -133,7 +133,10 @@ __global__ void __launch_bounds__(256) k_gellmann_level(typename GmVec<T>::t* __
         S lx = xl;                                               // l x_ll
         if (l == 2) lx = S{gtwice(xl.x), gtwice(xl.y)};
         if (l >= 3) lx = S{gmul(k.l[l], xl.x), gmul(k.l[l], xl.y)};
-        y[l][l] = {gmul(k.hc[l], gsub(P.x, lx.x)), gmul(k.hc[l], gsub(P.y, lx.y))};
+        if (l == 1)                                              // c_1 / 2 = 1/2 exactly
+          y[l][l] = {ghalf(gsub(P.x, lx.x)), ghalf(gsub(P.y, lx.y))};
+        else
+          y[l][l] = {gmul(k.hc[l], gsub(P.x, lx.x)), gmul(k.hc[l], gsub(P.y, lx.y))};
         P = {gadd(P.x, xl.x), gadd(P.y, xl.y)};
       }
       if constexpr (D == 2) y[0][0] = {ghalf(P.x), ghalf(P.y)};
@@ -144,8 +147,11 @@ __global__ void __launch_bounds__(256) k_gellmann_level(typename GmVec<T>::t* __
 #pragma unroll
       for (int m = D - 1; m >= 1; --m) {
         const S ym = x[m][m];
-        y[m][m] = {gadd(y0.x, gsub(Q.x, gmul(k.lc[m], ym.x))), gadd(y0.y, gsub(Q.y, gmul(k.lc[m], ym.y)))};
-        Q = {gadd(Q.x, gmul(k.c[m], ym.x)), gadd(Q.y, gmul(k.c[m], ym.y))};
+        // c_1 = 1 and 1 c_1 = 1 exactly: no multiply for m = 1
+        const S cy = m == 1 ? ym : S{gmul(k.c[m], ym.x), gmul(k.c[m], ym.y)};
+        const S lcy = m == 1 ? ym : S{gmul(k.lc[m], ym.x), gmul(k.lc[m], ym.y)};
+        y[m][m] = {gadd(y0.x, gsub(Q.x, lcy.x)), gadd(y0.y, gsub(Q.y, lcy.y))};
+        Q = {gadd(Q.x, cy.x), gadd(Q.y, cy.y)};
       }
       y[0][0] = {gadd(y0.x, Q.x), gadd(y0.y, Q.y)};
     }
