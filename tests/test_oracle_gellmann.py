@@ -149,3 +149,33 @@ def test_gellmann_d2_is_the_pauli_decomposition(n):
     assert np.allclose(core.gellmann_coeffs(A, 2).reshape(-1), oracle.coeffs_fwht(A)[s], rtol=0, atol=1e-14)
     Ai = synth.int_general(n, seed=1910 + n)
     assert np.array_equal(core.gellmann_coeffs(Ai, 2).reshape(-1), oracle.coeffs_fwht(Ai)[s])
+
+
+def _level_map(x, d):
+    """One qudit level of the recursion on blocks x[..., r, c] (the d x d
+    analogue of Eq. 4 for this basis), written from the single-qudit
+    elements: y_(r,c) = tr(G_(r,c) x) / tr(G_(r,c)^2)."""
+    y = np.empty_like(x)
+    for r in range(d):
+        for c in range(d):
+            G = kron.gellmann_single(d, r, c)
+            y[..., r, c] = np.einsum("uv,...vu->...", G, x) / np.trace(G @ G).real
+    return y
+
+
+@pytest.mark.parametrize("d,n", [(3, 3), (2, 4), (4, 2), (5, 2)])
+def test_level_by_level_recursion_equals_the_trace_definition(d, n):
+    # the reading behind the GPU path: the trace factorises over the qudits,
+    # so applying the single-qudit map to every d x d block, one qudit at a
+    # time (in any order), gives the coefficients of the trace definition,
+    # each at the position of its label
+    A = rand(d ** n, 2500 + d + n)
+    want = core.gellmann_coeffs(A, d)
+    for order in (range(n), reversed(range(n))):
+        X = A.copy()
+        for k in order:                       # digit k of row and column (stride d^k)
+            s = d ** k
+            h = d ** n // (d * s)
+            B = X.reshape(h, d, s, h, d, s).transpose(0, 2, 3, 5, 1, 4)
+            X = _level_map(B, d).transpose(0, 4, 1, 2, 5, 3).reshape(d ** n, d ** n)
+        assert np.allclose(X, want, rtol=0, atol=1e-14)
