@@ -230,8 +230,30 @@ struct F64Arith {
     return o;
   }
   __device__ static __forceinline__ V load(Store s) { return s; }
+
+  // x * 2^-sh, 1 <= sh <= 11, with integer instructions and bit for bit the
+  // fp64 product: a normal result moves the exponent field; a subnormal or
+  // zero result is the magnitude in units of 2^-1074 shifted right with
+  // round to nearest even; Inf and NaN pass unchanged.  Keeps the pass's
+  // 2^-K off the fp64 pipe, which bounds this arithmetic on GB300.
+  __device__ static __forceinline__ double mul_pow2_neg(double x, int sh) {
+    const long long b = __double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7FF);
+    const unsigned long long sgn = (unsigned long long)b & 0x8000000000000000ull;
+    const unsigned long long m = (unsigned long long)b & 0x000FFFFFFFFFFFFFull;
+    const unsigned long long v = e == 0 ? m : (m | (1ull << 52)) << min(max(e - 1, 0), 10);
+    unsigned long long q = v >> sh;
+    const unsigned long long rem = v & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    q += (unsigned long long)((rem > half) | ((rem == half) & (q & 1ull)));
+    const long long sub = (long long)(sgn | q);
+    return __longlong_as_double(e > sh && e < 0x7FF ? b - ((long long)sh << 52) : (e == 0x7FF ? b : sub));
+  }
   __device__ static __forceinline__ Store store(V v, const OutScale& sc, double mul) {
     if (mul == 1.0) return v;
+    const long long mb = __double_as_longlong(mul);
+    const int sh = 1023 - (int)((mb >> 52) & 0x7FF);
+    if (mb > 0 && (mb & 0x000FFFFFFFFFFFFFll) == 0 && sh >= 1 && sh <= 11)   // mul = 2^-sh
+      return make_double2(mul_pow2_neg(v.x, sh), mul_pow2_neg(v.y, sh));
     return make_double2(__dmul_rn(v.x, mul), __dmul_rn(v.y, mul));
   }
   __device__ static __forceinline__ bool nonzero(Store o) {   // +-0 is zero, NaN is not
