@@ -29,6 +29,9 @@ CASES = [
      "const int k = (d - ddot(b, c, d, n)) % d;", "const int k = ddot(b, c, d, n);"),
     ("test_oracle_weyl.py", "tpd_weyl.c", "transposed operand A[c][c+a]",
      "const wcplx x = A[dadd(c, a, d, n) * N + c];", "const wcplx x = A[c * N + dadd(c, a, d, n)];"),
+    ("test_oracle_weyl.py", "tpd_weyl.c", "conjugated operand",
+     "const wcplx x = A[dadd(c, a, d, n) * N + c];",
+     "wcplx x = A[dadd(c, a, d, n) * N + c];\n        x.im = -x.im;"),
     ("test_oracle_weyl.py", "tpd_weyl.c", "scale d^-n left out",
      "const double scale = 1.0 / (double)N;", "const double scale = 1.0;"),
     ("test_oracle_gellmann.py", "tpd_gellmann.c", "antisymmetric element with the opposite sign",
