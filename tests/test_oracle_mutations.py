@@ -25,6 +25,12 @@ CASES = [
      "  w.im = ldexp(w.im, -n);", "  w.im = -ldexp(w.im, -n);"),
     ("test_oracle.py", "tpd_oracle.c", "scale 2^(1-n) instead of 2^-n",
      "  w.re = ldexp(w.re, -n);\n  w.im = ldexp(w.im, -n);", "  w.re = ldexp(w.re, 1 - n);\n  w.im = ldexp(w.im, 1 - n);"),
+    ("test_oracle.py", "tpd_alg2.c", "Alg. 2: Y as -i (a01 - a10) / 2",
+     "W[i10].re = -((a01.im - a10.im) * 0.5); W[i10].im = (a01.re - a10.re) * 0.5;",
+     "W[i10].re = (a01.im - a10.im) * 0.5; W[i10].im = -((a01.re - a10.re) * 0.5);"),
+    ("test_oracle.py", "tpd_alg2.c", "Alg. 2: I and Z swapped",
+     "W[i00].re = (a00.re + a11.re) * 0.5; W[i00].im = (a00.im + a11.im) * 0.5;",
+     "W[i00].re = (a00.re - a11.re) * 0.5; W[i00].im = (a00.im - a11.im) * 0.5;"),
     ("test_oracle_weyl.py", "tpd_weyl.c", "omega^(+b.c) instead of omega^(-b.c)",
      "const int k = (d - ddot(b, c, d, n)) % d;", "const int k = ddot(b, c, d, n);"),
     ("test_oracle_weyl.py", "tpd_weyl.c", "transposed operand A[c][c+a]",
