@@ -28,7 +28,7 @@ CASES = [
     ("test_oracle.py", "tpd_alg2.c", "Alg. 2: Y as -i (a01 - a10) / 2",
      "W[i10].re = -((a01.im - a10.im) * 0.5); W[i10].im = (a01.re - a10.re) * 0.5;",
      "W[i10].re = (a01.im - a10.im) * 0.5; W[i10].im = -((a01.re - a10.re) * 0.5);"),
-    ("test_oracle.py", "tpd_alg2.c", "Alg. 2: I and Z swapped",
+    ("test_oracle.py", "tpd_alg2.c", "Alg. 2: I computed as (a00 - a11) / 2",
      "W[i00].re = (a00.re + a11.re) * 0.5; W[i00].im = (a00.im + a11.im) * 0.5;",
      "W[i00].re = (a00.re - a11.re) * 0.5; W[i00].im = (a00.im - a11.im) * 0.5;"),
     ("test_oracle_weyl.py", "tpd_weyl.c", "omega^(+b.c) instead of omega^(-b.c)",
