@@ -118,3 +118,32 @@ def test_weyl_rows_of_chosen_shifts():
     assert np.array_equal(core.weyl_rows(A, d, shifts), full[shifts])
     A32 = A.astype(np.complex64)
     assert np.array_equal(core.weyl_rows(A32, d, shifts), core.weyl_coeffs_dft(A32.astype(np.complex128), d)[shifts])
+
+
+def test_d3_unit_matrices_match_hand_derived_weights():
+    # tests/golden/weyl_d3_unit_matrices.txt: the weights of the nine 3x3 unit
+    # matrices, derived by hand from X|j> = |j+1>, Z|j> = w^j |j>
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "weyl_d3_unit_matrices.txt")
+
+    def val(tok):
+        if tok.lstrip("-") == "s":
+            return (-1.0 if tok.startswith("-") else 1.0) * np.sqrt(3.0) / 6.0
+        return float(tok) / 6.0
+
+    seen = 0
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        head, a, *cols = line.split("|")
+        r, c = (int(v) for v in head.split())
+        E = np.zeros((3, 3), dtype=np.complex128)
+        E[r, c] = 1.0
+        want = np.zeros((3, 3), dtype=np.complex128)
+        for b, t in enumerate(cols):
+            re, im = t.split()
+            want[int(a), b] = val(re) + 1j * val(im)
+        assert np.allclose(core.weyl_coeffs(E, 3), want, rtol=0, atol=1e-15), (r, c)
+        assert np.allclose(kron.weyl_coeffs_kron(E, 3), want, rtol=0, atol=1e-15), (r, c)
+        seen += 1
+    assert seen == 9
